@@ -1,0 +1,156 @@
+/*
+ * libbesselk: the modified Bessel function of the second kind K_nu(x) and the
+ * Matern covariance matrices built on it, on one NVIDIA GB300 (sm_103a).
+ *
+ * Method (arXiv 2502.00356, Sec. IV-B): K_nu(x) is the integral of Eq.
+ * (integral), K_nu(x) = int_0^inf exp(-x cosh t) cosh(nu t) dt, evaluated in the
+ * log domain of Eq. (logintegrand), g(t) = log cosh(nu t) - x cosh t, by a
+ * trapezoid rule (Eq. (refined), weights multiplying the exponential) over
+ * the peak-centred window [t0, t1] = {t : g(t) >= log(eps) + g(t_max)}.
+ * The Matern entry is Sec. III-A's
+ *   M(r) = sigma^2 / (2^{nu-1} Gamma(nu)) (r/beta)^nu K_nu(r/beta),
+ * with M = sigma^2 where r == 0 (Algorithm 3).
+ *
+ * Conventions for every entry point:
+ *  - Array arguments are DEVICE pointers owned by the caller, unless a
+ *    parameter says "host".  Nothing is retained after the call returns.
+ *  - Work is enqueued on `stream` (NULL = the legacy default stream) and the
+ *    call returns without synchronising.  Kernel-side faults surface as
+ *    BK_ERR_CUDA from a later call or from bk_sync().
+ *  - Argument errors are detected on the host before any launch and return
+ *    BK_ERR_INVALID_ARG; nothing is enqueued in that case.
+ *  - bk_last_error() returns a thread-local message for the last failure.
+ *  - Locations use the structure-of-arrays layout [x_0..x_{n-1}, y_0..y_{n-1}]
+ *    (the paper passes the x and y vectors separately, Algorithm 3).
+ *  - Matrices are column-major: entry (i, j) at out[i + j * ld], ld >= rows.
+ *
+ * Element-wise domain (both forms): x == 0 gives +inf; x < 0 or NaN gives
+ * NaN; nu < 0 uses |nu| (K_{-nu} = K_nu, Eq. (integral) holds for real nu).
+ * Accuracy is stated for x in [1e-3, 140], |nu| <= 20 (the region of Sec.
+ * IV-C); other finite inputs are computed but not covered by that statement.
+ * A point whose bounded root search does not converge gives NaN and, when
+ * counters are supplied, increments BK_CTR_FAIL.
+ */
+#ifndef BESSELK_BK_H
+#define BESSELK_BK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;
+typedef struct CUstream_st* bk_stream_t; /* same type as cudaStream_t */
+
+typedef enum {
+  BK_OK = 0,
+  BK_ERR_INVALID_ARG = 1,   /* rejected on the host, nothing launched */
+  BK_ERR_CUDA = 2,          /* a CUDA runtime error (message in bk_last_error) */
+  BK_ERR_NOMEM = 3,         /* a workspace or plan is too small */
+  BK_ERR_UNSUPPORTED = 4,   /* option combination not available */
+  BK_ERR_NOT_CONVERGED = 5, /* reserved for host-side iterative helpers */
+  BK_ERR_NOT_LOADED = 6     /* the learned window has no weights */
+} bk_status;
+
+typedef enum { BK_F64 = 0, BK_F32 = 1 } bk_dtype;
+
+/* How the integration window [t0, t1] and the node count are found. */
+typedef enum {
+  BK_WIN_SEARCH = 0,  /* per-point peak and bound search (Sec. IV-B) */
+  BK_WIN_LEARNED = 1, /* predicted by the window network, checked, with fallback */
+  BK_WIN_FIXED = 2    /* the paper's fixed [0, t1] with b bins (Sec. IV-C) */
+} bk_window;
+
+/* Indices into the optional device counter array bk_opts.d_counters. */
+enum {
+  BK_CTR_FALLBACK = 0, /* learned windows rejected by the in-kernel check */
+  BK_CTR_FAIL = 1,     /* points returned as NaN because a search did not converge */
+  BK_CTR_NODES = 2,    /* integrand evaluations (quadrature nodes) */
+  BK_CTR_ITERS = 3,    /* root-finder iterations */
+  BK_CTR_EVALS = 4,    /* K_nu evaluations */
+  BK_NUM_COUNTERS = 8
+};
+
+typedef struct {
+  bk_window window;  /* default BK_WIN_SEARCH */
+  bk_dtype compute;  /* arithmetic of the integrand: BK_F64 (plain) or BK_F32 */
+  int fixed_bins;    /* BK_WIN_FIXED: number of bins b (paper: 40) */
+  double fixed_t1;   /* BK_WIN_FIXED: upper bound (paper: 9) */
+  /* Optional device array of BK_NUM_COUNTERS unsigned 64-bit counters that
+     kernels add to (never reset by the library).  NULL = no counting. */
+  unsigned long long* d_counters;
+} bk_opts;
+
+/* Fills *o with the defaults: BK_WIN_SEARCH, BK_F64, b = 40, t1 = 9, no counters. */
+void bk_opts_default(bk_opts* o);
+
+const char* bk_version(void);
+const char* bk_last_error(void);
+const char* bk_status_string(bk_status s);
+
+/* Waits for `stream` and reports any pending CUDA error as BK_ERR_CUDA. */
+bk_status bk_sync(bk_stream_t stream);
+
+/*
+ * bk_eval: out[i] = K_{nu[i]}(x[i]) for i < n, FP64 in and out, the plain
+ * FP64 form (per-point peak search, eps = 2^-52 window, self-checked
+ * trapezoid).  Cites Eq. (integral), Eq. (logintegrand), Eq. (refined) and
+ * the window of Sec. IV-B.  x, nu, out: device, n doubles each; out may alias
+ * neither input.  n == 0 is a no-op; n < 0 or a NULL pointer with n > 0 is
+ * BK_ERR_INVALID_ARG.
+ */
+bk_status bk_eval(const double* x, const double* nu, double* out, int64_t n, bk_stream_t stream);
+
+/*
+ * bk_eval_ex: as bk_eval with options.  out_dtype selects FP64 or FP32
+ * output; opts == NULL means bk_opts_default.  With opts->compute == BK_F32
+ * the integrand is evaluated in FP32 (the precision form).  When
+ * `log_out` is non-NULL it receives log K_nu(x) in the same dtype (useful
+ * where K_nu overflows, e.g. tiny x with large nu).
+ */
+bk_status bk_eval_ex(const double* x, const double* nu, void* out, void* log_out,
+                     bk_dtype out_dtype, int64_t n, const bk_opts* opts, bk_stream_t stream);
+
+/*
+ * bk_matern_tile: the full n x n Matern matrix of `n` locations (Sec. III-A,
+ * Algorithm 3), column-major with leading dimension ld >= n, written as
+ * FP64 (dtype BK_F64, plain FP64 form) or FP32 (BK_F32, precision form).
+ * Each unordered pair is evaluated once and written to (i, j) and (j, i);
+ * the diagonal and any pair at distance exactly 0 get sigma^2.
+ * locs: device, 2n doubles (SoA).  out: device, ld * n elements of dtype.
+ * Requires sigma2 >= 0, beta > 0, nu > 0, all finite.
+ */
+bk_status bk_matern_tile(const double* locs, int64_t n, double sigma2, double beta, double nu,
+                         void* out, int64_t ld, bk_dtype dtype, bk_stream_t stream);
+
+/* bk_matern_tile with options (window mode, counters). */
+bk_status bk_matern_tile_ex(const double* locs, int64_t n, double sigma2, double beta, double nu,
+                            void* out, int64_t ld, bk_dtype dtype, const bk_opts* opts,
+                            bk_stream_t stream);
+
+/*
+ * bk_matern_tile2: the m x n block between row locations locs1 (m points) and
+ * column locations locs2 (n points): out[i + j*ld] = M(|l2_j - l1_i|), the
+ * single-tile kernel of Algorithm 3 (GenerateMaternCovariance(l1, l2, ...)).
+ * ld >= m.  sigma^2 wherever the distance is exactly 0.
+ */
+bk_status bk_matern_tile2(const double* locs1, int64_t m, const double* locs2, int64_t n,
+                          double sigma2, double beta, double nu, void* out, int64_t ld,
+                          bk_dtype dtype, const bk_opts* opts, bk_stream_t stream);
+
+/*
+ * bk_morton_order (host only): perm[k] = index of the k-th location in
+ * Z-order (Sec. IV-D orders locations so that a tile holds nearby points).
+ * Coordinates are quantised to 16 bits over [0, 1] (clamped), x on the even
+ * bits and y on the odd bits, ties keep their input order.
+ * locs: HOST, 2n doubles (SoA).  perm: HOST, n int64.
+ */
+bk_status bk_morton_order(const double* locs, int64_t n, int64_t* perm);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BESSELK_BK_H */

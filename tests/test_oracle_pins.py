@@ -1,0 +1,210 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle itself.
+
+Each pin is chosen so that a plausible slip in the oracle (a dropped term, a
+wrong sign, a misplaced weight, a wrong bracket) fails at least one of them:
+
+* closed forms K_{1/2}, K_{3/2}, K_{5/2} over the whole x range;
+* the three-term recurrence Eq. (recurrence) (Sec. IV-A);
+* the Wronskian I_nu K_{nu+1} + I_{nu+1} K_nu = 1/x with scipy's I_nu;
+* the small-x expansion (1/2) Gamma(nu) (2/x)^nu [1 - x^2 / (4(nu - 1))];
+* Hankel's large-x expansion;
+* the Temme series of Sec. IV-A (a second, independent algorithm) for x < 0.1;
+* scipy.special.kv (AMOS) on a random grid, and mpmath where installed;
+* the epsilon-window of Sec. IV-B checked against its definition on a grid;
+* Matern entries (Sec. III-A) against the half-integer closed forms.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import special
+
+from paper_2502_00356_gb300 import inputs
+
+X_GRID = np.exp(np.linspace(np.log(1e-3), np.log(140.0), 41))
+
+
+def k_half_closed(x, order2):
+    """Closed forms of K_nu for nu = order2 / 2 in {1/2, 3/2, 5/2}."""
+    base = np.sqrt(np.pi / (2 * x)) * np.exp(-x)
+    if order2 == 1:
+        return base
+    if order2 == 3:
+        return base * (1 + 1 / x)
+    if order2 == 5:
+        return base * (1 + 3 / x + 3 / x ** 2)
+    raise ValueError(order2)
+
+
+@pytest.mark.parametrize("order2", [1, 3, 5])
+def test_closed_forms_half_integer(orc, order2):
+    nu = order2 / 2
+    got = orc.besselk(X_GRID, nu)
+    want = k_half_closed(X_GRID, order2)
+    np.testing.assert_allclose(got, want, rtol=2e-15, atol=0)
+
+
+def test_recurrence(orc):
+    # K_{nu+1} = K_{nu-1} + (2 nu / x) K_nu: all terms positive, no cancellation.
+    rng = np.random.default_rng(11)
+    x = np.exp(rng.uniform(np.log(1e-3), np.log(140), 40))
+    nu = rng.uniform(1.0, 12.0, 40)
+    km, k0, kp = orc.besselk(x, nu - 1), orc.besselk(x, nu), orc.besselk(x, nu + 1)
+    np.testing.assert_allclose(kp, km + (2 * nu / x) * k0, rtol=4e-15)
+
+
+def test_symmetry_in_order(orc):
+    x = np.array([1e-3, 0.3, 7.0, 140.0])
+    for nu in [0.2, 1.7, 9.5]:
+        assert np.array_equal(orc.besselk(x, nu), orc.besselk(x, -nu))
+
+
+def test_wronskian_with_library_besseli(orc):
+    rng = np.random.default_rng(12)
+    x = np.exp(rng.uniform(np.log(1e-2), np.log(100), 30))
+    nu = rng.uniform(0.05, 8.0, 30)
+    lhs = special.iv(nu, x) * orc.besselk(x, nu + 1) + special.iv(nu + 1, x) * orc.besselk(x, nu)
+    np.testing.assert_allclose(lhs * x, 1.0, rtol=1e-13)
+
+
+@pytest.mark.parametrize("nu", [2.5, 3.7, 6.2])
+def test_small_x_expansion(orc, nu):
+    x = 1e-3
+    lead = 0.5 * math.gamma(nu) * (2 / x) ** nu
+    ratio = float(orc.besselk(x, nu)) / lead
+    assert abs(ratio - (1 - x * x / (4 * (nu - 1)))) < 1e-12
+
+
+@pytest.mark.parametrize("x", [50.0, 90.0, 140.0])
+@pytest.mark.parametrize("nu", [0.3, 1.7, 3.2])
+def test_hankel_large_x(orc, x, nu):
+    mu = 4 * nu * nu
+    term, terms = 1.0, [1.0]
+    for k in range(1, 60):
+        term *= (mu - (2 * k - 1) ** 2) / (k * 8 * x)
+        if abs(term) < 1e-22 or abs(term) > abs(terms[-1]):
+            break
+        terms.append(term)
+    want = math.sqrt(math.pi / (2 * x)) * math.exp(-x) * math.fsum(terms)
+    assert abs(float(orc.besselk(x, nu)) / want - 1) < 2e-15
+
+
+def test_temme_series_agrees_with_integral(orc):
+    rng = np.random.default_rng(13)
+    x = np.exp(rng.uniform(np.log(1e-3), np.log(0.1), 30))
+    nu = rng.uniform(0.0, 20.0, 30)
+    # keep |mu| = |nu - round(nu)| away from 0 where the G1 quotient cancels
+    nu = np.where(np.abs(nu - np.floor(nu + 0.5)) < 1e-3, nu + 0.01, nu)
+    quad = orc.besselk(x, nu)
+    temme = np.array([orc.besselk_temme(a, b) for a, b in zip(x, nu)])
+    np.testing.assert_allclose(temme, quad, rtol=1e-14)
+    # integer order hits the mu == 0 limit branch
+    for xi, ni in [(0.05, 0.0), (0.01, 1.0), (0.002, 4.0)]:
+        assert abs(orc.besselk_temme(xi, ni) / float(orc.besselk(xi, ni)) - 1) < 1e-14
+
+
+def test_scipy_kv_random(orc):
+    x, nu = inputs.kv_pairs(300, seed=14, nu_hi=20.0)
+    got = orc.besselk(x, nu)
+    np.testing.assert_allclose(got, special.kv(nu, x), rtol=5e-14)
+
+
+def test_mpmath_points(orc):
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    for x, nu in [(1e-3, 0.05), (1e-3, 20.0), (0.01, 20.0), (0.1, 0.5), (2.0, 3.7), (140.0, 20.0),
+                  (37.0, 0.0), (0.5, 11.25)]:
+        ref = float(mp.besselk(nu, x))
+        assert abs(float(orc.besselk(x, nu)) / ref - 1) < 4e-16
+
+
+def test_domain_edges(orc):
+    assert np.isinf(orc.besselk(0.0, 1.0))
+    assert np.isnan(orc.besselk(-1.0, 1.0))
+    assert np.isnan(orc.besselk(np.nan, 1.0))
+
+
+def _g(t, x, nu):
+    # Eq. (logintegrand), evaluated independently in numpy for the window pins.
+    a = np.abs(nu * t)
+    return a + np.log1p(np.exp(-2 * a)) - np.log(2) - x * np.cosh(t)
+
+
+def test_window_definition(orc):
+    log_eps = -52 * np.log(2)
+    x, nu = inputs.kv_pairs(60, seed=15, nu_hi=20.0)
+    x = np.concatenate([x, [1.0, 0.25, 4.0]])       # nu^2 == x edge cases
+    nu = np.concatenate([nu, [1.0, 0.5, 2.0]])
+    w = orc.window(x, nu, log_eps)
+    for (ts, t0, t1, gs), xi, ni in zip(w, x, nu):
+        assert 0 <= t0 <= ts < t1
+        assert (ts == 0) == (ni * ni <= xi)
+        assert abs(gs - _g(ts, xi, ni)) <= 1e-12 * max(1.0, abs(gs))
+        grid = np.linspace(0, 1.5 * t1, 30001)
+        gg = _g(grid, xi, ni)
+        # t* is the maximiser
+        assert gg.max() <= gs + 1e-12 * max(1.0, abs(gs))
+        # every grid point outside [t0, t1] is below the eps threshold
+        outside = (grid < t0 - 1e-9) | (grid > t1 + 1e-9)
+        assert np.all(gg[outside] < gs + log_eps + 1e-9)
+        # the ends sit on the threshold (t0 only when it is interior)
+        assert abs(_g(t1, xi, ni) - gs - log_eps) < 1e-8 * max(1.0, abs(gs))
+        if t0 > 0:
+            assert abs(_g(t0, xi, ni) - gs - log_eps) < 1e-8 * max(1.0, abs(gs))
+
+
+def test_min_nodes_is_minimal(orc):
+    x = np.array([1e-3, 0.02, 0.7, 3.0, 60.0, 140.0])
+    nu = np.array([20.0, 0.1, 2.3, 0.5, 7.0, 1.0])
+    tol = 1e-8
+    N = orc.min_nodes(x, nu, tol)
+    w = orc.window(x, nu)
+    ref = special.kv(nu, x)
+    for Ni, (ts, t0, t1, gs), xi, ni, ri in zip(N, w, x, nu, ref):
+        assert Ni > 0
+
+        def trap(n):
+            t = np.linspace(t0, t1, n + 1)
+            f = np.exp(_g(t, xi, ni) - gs)
+            return np.exp(gs) * (t1 - t0) / n * (f.sum() - 0.5 * (f[0] + f[-1]))
+
+        assert abs(trap(Ni) / ri - 1) <= tol * 1.01
+        if Ni > 1:
+            assert abs(trap(Ni - 1) / ri - 1) > tol * 0.99
+
+
+def test_fixed_window_branch(orc):
+    # Eq. (refined) with the weights multiplying the exponential converges to
+    # log K on a wide enough window with many bins ...
+    for x, nu in [(0.5, 0.5), (2.0, 2.3), (0.1, 1.2)]:
+        want = math.log(float(special.kv(nu, x)))
+        assert abs(orc.fixed_window_log_k(x, nu, t1=14.0, bins=4000) - want) < 1e-12
+    # ... and the paper's t1 = 9, b = 40 is accurate for moderate x
+    assert abs(orc.fixed_window_log_k(1.0, 0.5) - math.log(special.kv(0.5, 1.0))) < 1e-12
+
+
+def test_matern_closed_forms(orc):
+    locs = inputs.jittered_grid(40, seed=16)
+    sigma2, beta = 1.7, 0.13
+    dx = locs[0][:, None] - locs[0][None, :]
+    dy = locs[1][:, None] - locs[1][None, :]
+    z = np.sqrt(dx * dx + dy * dy) / beta
+    forms = {0.5: np.exp(-z), 1.5: (1 + z) * np.exp(-z), 2.5: (1 + z + z * z / 3) * np.exp(-z)}
+    for nu, want in forms.items():
+        got = orc.matern_block(locs, locs, sigma2, beta, nu)
+        np.testing.assert_allclose(got, sigma2 * want, rtol=4e-15, atol=0)
+        assert np.array_equal(np.diag(got), np.full(40, sigma2))
+
+
+def test_matern_properties(orc):
+    locs = inputs.jittered_grid(60, seed=17)
+    locs[:, 5] = locs[:, 9]  # a duplicated location gets sigma^2 off the diagonal
+    sigma2, beta, nu = 1.3, 0.2, 2.3
+    M = orc.matern_block(locs, locs, sigma2, beta, nu)
+    assert np.array_equal(M, M.T)
+    assert M[5, 9] == sigma2 and M[9, 5] == sigma2
+    assert np.all(M > 0) and np.all(M <= sigma2)
+    keep = [i for i in range(60) if i != 9]
+    np.linalg.cholesky(M[np.ix_(keep, keep)])
+    I, J = inputs.entry_sample(60, 200, seed=18)
+    np.testing.assert_array_equal(orc.matern_entries(locs, I, J, sigma2, beta, nu), M[I, J])
