@@ -68,8 +68,9 @@ enum {
   BK_CTR_FALLBACK = 0, /* learned windows rejected by the in-kernel check */
   BK_CTR_FAIL = 1,     /* points returned as NaN because a search did not converge */
   BK_CTR_NODES = 2,    /* integrand evaluations (quadrature nodes) */
-  BK_CTR_ITERS = 3,    /* root-finder iterations */
+  BK_CTR_ITERS = 3,    /* window-end root-finder iterations */
   BK_CTR_EVALS = 4,    /* K_nu evaluations */
+  BK_CTR_PEAK_ITERS = 5, /* peak (t_max) root-finder iterations */
   BK_NUM_COUNTERS = 8
 };
 
@@ -148,6 +149,16 @@ bk_status bk_matern_tile2(const double* locs1, int64_t m, const double* locs2, i
  * locs: HOST, 2n doubles (SoA).  perm: HOST, n int64.
  */
 bk_status bk_morton_order(const double* locs, int64_t n, int64_t* perm);
+
+/*
+ * bk_probe_pipe: throughput probe for the roofline denominators (not part of
+ * the paper's method).  Launches grid x block threads; each runs `iters`
+ * trips of 8 independent operations on one pipe: kind 0 = FP64 FMA,
+ * 1 = FP32 FMA, 2 = ex2.approx.f32 on the MUFU unit.  Operations per launch =
+ * grid * block * iters * 8.  sink: device, grid * block doubles (written).
+ */
+bk_status bk_probe_pipe(int kind, int64_t iters, int grid, int block, double* sink,
+                        bk_stream_t stream);
 
 #ifdef __cplusplus
 }

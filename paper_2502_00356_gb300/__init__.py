@@ -1,0 +1,290 @@
+"""Python binding of libbesselk (include/bk.h): K_nu(x) and Matern covariance
+matrices on one GB300.
+
+The functions here have the C-ABI's names and only marshal arguments: they
+check tensor devices, dtypes and shapes, pass raw device pointers and the
+current torch CUDA stream, and raise ``BkError`` on a non-OK status.  Every
+step of the computation runs in the library's CUDA kernels; there is no CPU
+fallback, and calling any of them without the built library raises.
+
+PyTorch provides device memory and streams only.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+from . import inputs  # noqa: F401  (seeded generators; no method arithmetic)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libbesselk.so")
+
+BK_OK, BK_ERR_INVALID_ARG, BK_ERR_CUDA, BK_ERR_NOMEM = 0, 1, 2, 3
+BK_ERR_UNSUPPORTED, BK_ERR_NOT_CONVERGED, BK_ERR_NOT_LOADED = 4, 5, 6
+BK_F64, BK_F32 = 0, 1
+BK_WIN_SEARCH, BK_WIN_LEARNED, BK_WIN_FIXED = 0, 1, 2
+BK_CTR_FALLBACK, BK_CTR_FAIL, BK_CTR_NODES, BK_CTR_ITERS, BK_CTR_EVALS, BK_CTR_PEAK_ITERS = 0, 1, 2, 3, 4, 5
+BK_NUM_COUNTERS = 8
+
+#: every symbol include/bk.h declares (checked by the CPU tests)
+EXPORTS = (
+    "bk_opts_default", "bk_version", "bk_last_error", "bk_status_string", "bk_sync",
+    "bk_eval", "bk_eval_ex", "bk_matern_tile", "bk_matern_tile_ex", "bk_matern_tile2",
+    "bk_morton_order", "bk_probe_pipe",
+)
+
+
+class BkError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+_STATUS = {0: "BK_OK", 1: "BK_ERR_INVALID_ARG", 2: "BK_ERR_CUDA", 3: "BK_ERR_NOMEM",
+           4: "BK_ERR_UNSUPPORTED", 5: "BK_ERR_NOT_CONVERGED", 6: "BK_ERR_NOT_LOADED"}
+
+
+class bk_opts(ctypes.Structure):
+    _fields_ = [("window", ctypes.c_int), ("compute", ctypes.c_int), ("fixed_bins", ctypes.c_int),
+                ("fixed_t1", ctypes.c_double), ("d_counters", ctypes.c_void_p)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile the CUDA library (nvcc, sm_103a) into the package's _build/."""
+    from .buildlib import build as _build
+    return _build(force=force, verbose=verbose)
+
+
+def lib() -> ctypes.CDLL:
+    """Load libbesselk.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libbesselk is not built ({LIB_PATH} missing); "
+                               "run paper_2502_00356_gb300.build() first")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I64, D, I = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+        sig = {
+            "bk_opts_default": (None, [P]),
+            "bk_version": (ctypes.c_char_p, []),
+            "bk_last_error": (ctypes.c_char_p, []),
+            "bk_status_string": (ctypes.c_char_p, [I]),
+            "bk_sync": (I, [P]),
+            "bk_eval": (I, [P, P, P, I64, P]),
+            "bk_eval_ex": (I, [P, P, P, P, I, I64, P, P]),
+            "bk_matern_tile": (I, [P, I64, D, D, D, P, I64, I, P]),
+            "bk_matern_tile_ex": (I, [P, I64, D, D, D, P, I64, I, P, P]),
+            "bk_matern_tile2": (I, [P, I64, P, I64, D, D, D, P, I64, I, P, P]),
+            "bk_morton_order": (I, [P, I64, P]),
+            "bk_probe_pipe": (I, [I, I64, I, I, P, P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+        return L
+
+
+def _check(status: int) -> None:
+    if status != BK_OK:
+        msg = lib().bk_last_error().decode(errors="replace")
+        raise BkError(status, msg)
+
+
+def last_error() -> str:
+    return lib().bk_last_error().decode(errors="replace")
+
+
+def version() -> str:
+    return lib().bk_version().decode()
+
+
+# ---------------------------------------------------------------------------
+# torch marshalling helpers
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, int):
+        return stream or None
+    return stream.cuda_stream or None
+
+
+def _dev(t, name: str, dtype=None):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else (t.data_ptr() or None)
+
+
+def make_opts(window: int = BK_WIN_SEARCH, compute: int = BK_F64, fixed_bins: int = 40,
+              fixed_t1: float = 9.0, counters=None) -> bk_opts:
+    """A bk_opts struct; ``counters`` is an optional CUDA int64 tensor of
+    BK_NUM_COUNTERS entries that kernels add to."""
+    o = bk_opts()
+    lib().bk_opts_default(ctypes.byref(o))
+    o.window, o.compute, o.fixed_bins, o.fixed_t1 = int(window), int(compute), int(fixed_bins), float(fixed_t1)
+    if counters is not None:
+        torch = _torch()
+        _dev(counters, "counters", torch.int64)
+        if counters.numel() < BK_NUM_COUNTERS:
+            raise ValueError("counters needs BK_NUM_COUNTERS entries")
+        o.d_counters = counters.data_ptr()
+    return o
+
+
+def _dtype_code(torch_dtype) -> int:
+    torch = _torch()
+    if torch_dtype == torch.float64:
+        return BK_F64
+    if torch_dtype == torch.float32:
+        return BK_F32
+    raise TypeError("output dtype must be float64 or float32")
+
+
+def _torch_dtype(code: int):
+    torch = _torch()
+    return {BK_F64: torch.float64, BK_F32: torch.float32}[code]
+
+
+# ---------------------------------------------------------------------------
+# entry points (same names as the C-ABI)
+def bk_eval(x, nu, out=None, stream=None):
+    """out = K_nu(x), FP64 plain form.  x, nu: CUDA float64 tensors of equal size."""
+    torch = _torch()
+    _dev(x, "x", torch.float64)
+    _dev(nu, "nu", torch.float64)
+    if x.numel() != nu.numel():
+        raise ValueError("x and nu must have the same number of elements")
+    if out is None:
+        out = torch.empty_like(x)
+    _dev(out, "out", torch.float64)
+    if out.numel() != x.numel():
+        raise ValueError("out has the wrong size")
+    _check(lib().bk_eval(_ptr(x), _ptr(nu), _ptr(out), x.numel(), _stream_ptr(stream)))
+    return out
+
+
+def bk_eval_ex(x, nu, out=None, log_out=None, out_dtype=None, opts: Optional[bk_opts] = None,
+               stream=None, want_log: bool = False):
+    """K_nu(x) (and optionally log K_nu(x)) with options; returns (out, log_out)."""
+    torch = _torch()
+    _dev(x, "x", torch.float64)
+    _dev(nu, "nu", torch.float64)
+    n = x.numel()
+    if nu.numel() != n:
+        raise ValueError("x and nu must have the same number of elements")
+    if out_dtype is None:
+        out_dtype = out.dtype if out is not None else torch.float64
+    code = _dtype_code(out_dtype)
+    if out is None:
+        out = torch.empty(x.shape, dtype=out_dtype, device=x.device)
+    _dev(out, "out", out_dtype)
+    if want_log and log_out is None:
+        log_out = torch.empty(x.shape, dtype=out_dtype, device=x.device)
+    if log_out is not None:
+        _dev(log_out, "log_out", out_dtype)
+    optp = ctypes.byref(opts) if opts is not None else None
+    _check(lib().bk_eval_ex(_ptr(x), _ptr(nu), _ptr(out), _ptr(log_out), code, n, optp,
+                            _stream_ptr(stream)))
+    return out, log_out
+
+
+def _locs(locs, name="locs"):
+    torch = _torch()
+    _dev(locs, name, torch.float64)
+    if locs.dim() != 2 or locs.shape[0] != 2:
+        raise ValueError(f"{name} must have shape (2, n) (structure of arrays)")
+    return locs.shape[1]
+
+
+def bk_matern_tile(locs, sigma2: float, beta: float, nu: float, out=None, dtype=None,
+                   opts: Optional[bk_opts] = None, stream=None):
+    """Full n x n Matern matrix of SoA locations (2, n).  ``out`` is a CUDA
+    tensor viewed column-major: out[j, i] holds entry (i, j), i.e. pass a
+    (n, ld) row-major tensor; returns it."""
+    torch = _torch()
+    n = _locs(locs)
+    if out is None:
+        out = torch.empty((n, n), dtype=dtype or torch.float64, device=locs.device)
+    code = _dtype_code(out.dtype)
+    _dev(out, "out")
+    if out.dim() != 2 or out.shape[0] != n or out.shape[1] < n:
+        raise ValueError("out must be (n, ld) with ld >= n")
+    ld = out.shape[1]
+    optp = ctypes.byref(opts) if opts is not None else None
+    _check(lib().bk_matern_tile_ex(_ptr(locs), n, float(sigma2), float(beta), float(nu), _ptr(out),
+                                   ld, code, optp, _stream_ptr(stream)))
+    return out
+
+
+def bk_matern_tile2(locs1, locs2, sigma2: float, beta: float, nu: float, out=None, dtype=None,
+                    opts: Optional[bk_opts] = None, stream=None):
+    """m x n block between locs1 (2, m) and locs2 (2, n); ``out`` is (n, ld)
+    row-major = column-major m x n with leading dimension ld >= m."""
+    torch = _torch()
+    m = _locs(locs1, "locs1")
+    n = _locs(locs2, "locs2")
+    if out is None:
+        out = torch.empty((n, m), dtype=dtype or torch.float64, device=locs1.device)
+    code = _dtype_code(out.dtype)
+    _dev(out, "out")
+    if out.dim() != 2 or out.shape[0] != n or out.shape[1] < m:
+        raise ValueError("out must be (n, ld) with ld >= m")
+    optp = ctypes.byref(opts) if opts is not None else None
+    _check(lib().bk_matern_tile2(_ptr(locs1), m, _ptr(locs2), n, float(sigma2), float(beta),
+                                 float(nu), _ptr(out), out.shape[1], code, optp,
+                                 _stream_ptr(stream)))
+    return out
+
+
+def bk_morton_order(locs_host) -> "object":
+    """Host-side Z-order permutation of SoA locations (numpy array (2, n))."""
+    import numpy as np
+    a = np.ascontiguousarray(np.asarray(locs_host, dtype=np.float64))
+    if a.ndim != 2 or a.shape[0] != 2:
+        raise ValueError("locs must have shape (2, n)")
+    perm = np.empty(a.shape[1], dtype=np.int64)
+    _check(lib().bk_morton_order(a.ctypes.data_as(ctypes.c_void_p), a.shape[1],
+                                 perm.ctypes.data_as(ctypes.c_void_p)))
+    return perm
+
+
+def bk_sync(stream=None):
+    _check(lib().bk_sync(_stream_ptr(stream)))
+
+
+def bk_probe_pipe(kind: int, iters: int, grid: int, block: int, sink, stream=None):
+    """Launch a pipe-rate probe (0 FP64 FMA, 1 FP32 FMA, 2 MUFU ex2); the caller
+    times it.  Returns the number of operations the launch performs."""
+    torch = _torch()
+    _dev(sink, "sink", torch.float64)
+    if sink.numel() < grid * block:
+        raise ValueError("sink needs grid * block elements")
+    _check(lib().bk_probe_pipe(int(kind), int(iters), int(grid), int(block), _ptr(sink),
+                               _stream_ptr(stream)))
+    return grid * block * iters * 8

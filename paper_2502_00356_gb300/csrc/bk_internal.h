@@ -1,0 +1,37 @@
+// Internal declarations shared by the library's translation units (not part
+// of the public C-ABI in include/bk.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "bk.h"
+
+namespace bk {
+
+// Number of SMs of the current device (cached per device ordinal).
+int current_sm_count();
+
+// Records a message for bk_last_error() on this thread and returns `st`.
+bk_status set_error(bk_status st, const char* fmt, ...);
+
+// Converts a CUDA error into BK_ERR_CUDA with a message (BK_OK if none).
+bk_status check_cuda(cudaError_t e, const char* what);
+
+// ---- plain FP64 form (bk_plain.cu) ----
+cudaError_t launch_eval_f64(const double* x, const double* nu, void* out, void* log_out,
+                            bk_dtype out_t, int64_t n, unsigned long long* ctr, cudaStream_t s);
+
+// Full symmetric n x n matrix: lower-triangle tiles, each written twice.
+cudaError_t launch_matern_sym_f64(const double* locs, int64_t n, double sigma2, double beta,
+                                  double nu, void* out, int64_t ld, bk_dtype out_t,
+                                  unsigned long long* ctr, cudaStream_t s);
+
+// General m x n block between two location sets.
+cudaError_t launch_matern_block_f64(const double* locs1, int64_t m, const double* locs2,
+                                    int64_t n, double sigma2, double beta, double nu, void* out,
+                                    int64_t ld, bk_dtype out_t, unsigned long long* ctr,
+                                    cudaStream_t s);
+
+}  // namespace bk

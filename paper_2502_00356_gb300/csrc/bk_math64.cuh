@@ -1,0 +1,345 @@
+// FP64 device arithmetic for the plain form: exp and log written here (no
+// math-library internals), the peak/window search and the self-checked
+// trapezoid of Sec. IV-B.
+#pragma once
+
+#include <cstdint>
+
+namespace bk {
+
+// ---------------------------------------------------------------------------
+// Constants.  ln2 is split Cody-Waite style: kLn2Hi is ln 2 rounded to 32
+// significant bits (so k * kLn2Hi is exact for |k| < 2^21) and kLn2Lo is the
+// remainder; both were derived from a 50-digit value of ln 2.
+constexpr double kLog2e = 0x1.71547652b82fep+0;   // 1 / ln 2
+constexpr double kLn2 = 0x1.62e42fefa39efp-1;     // ln 2
+constexpr double kLn2Hi = 0x1.62e42fee00000p-1;
+constexpr double kLn2Lo = 0x1.a39ef35793c76p-33;
+constexpr double kRoundMagic = 6755399441055744.0;  // 1.5 * 2^52: adding it rounds to an integer
+constexpr double kSqrt2 = 1.4142135623730951;
+// -log(2^-52): the paper's machine epsilon (Sec. IV-C) in the window rule.
+constexpr double kLogInvEps64 = 36.04365338911715;
+
+__device__ __forceinline__ double pow2i(int k) {  // 2^k for k in [-1022, 1023]
+  return __hiloint2double((k + 1023) << 20, 0);
+}
+
+// e^r for |r| <= ln2/2 by its Taylor polynomial of degree 12 (truncation below
+// 0.3466^13 / 13! < 2e-16 relative), Horner form.
+__device__ __forceinline__ double exp_taylor12(double r) {
+  double p = 1.0 / 479001600.0;
+  p = fma(p, r, 1.0 / 39916800.0);
+  p = fma(p, r, 1.0 / 3628800.0);
+  p = fma(p, r, 1.0 / 362880.0);
+  p = fma(p, r, 1.0 / 40320.0);
+  p = fma(p, r, 1.0 / 5040.0);
+  p = fma(p, r, 1.0 / 720.0);
+  p = fma(p, r, 1.0 / 120.0);
+  p = fma(p, r, 1.0 / 24.0);
+  p = fma(p, r, 1.0 / 6.0);
+  p = fma(p, r, 0.5);
+  p = fma(p, r, 1.0);
+  p = fma(p, r, 1.0);
+  return p;
+}
+
+// Number of FP64 pipe operations in exp_bounded (for work accounting):
+// 1 fma + 1 add (rounding), 2 fma (reduction), 12 fma (polynomial), 1 mul.
+constexpr int kExpOps = 17;
+
+// e^a for a in [-708, 709] (callers clamp): Cody-Waite reduction
+// a = k ln2 + r, |r| <= ln2/2, then 2^k e^r.
+__device__ __forceinline__ double exp_bounded(double a) {
+  double kd = fma(a, kLog2e, kRoundMagic);
+  const int k = __double2loint(kd);
+  kd -= kRoundMagic;
+  double r = fma(-kd, kLn2Hi, a);
+  r = fma(-kd, kLn2Lo, r);
+  return exp_taylor12(r) * pow2i(k);
+}
+
+// e^a over the whole double range (NaN -> NaN, overflow -> inf, deep underflow -> 0).
+__device__ __forceinline__ double exp_full(double a) {
+  if (a != a) return a;
+  if (a > 709.782712893384) return __longlong_as_double(0x7ff0000000000000LL);
+  if (a < -745.2) return 0.0;
+  double kd = fma(a, kLog2e, kRoundMagic);
+  const int k = __double2loint(kd);
+  kd -= kRoundMagic;
+  double r = fma(-kd, kLn2Hi, a);
+  r = fma(-kd, kLn2Lo, r);
+  const int k1 = k >> 1;  // split 2^k so both halves are normal numbers
+  return (exp_taylor12(r) * pow2i(k1)) * pow2i(k - k1);
+}
+
+// log(a) for finite a > 0: a = 2^e m with m in [sqrt(1/2), sqrt(2)), then
+// log m = 2 atanh(s), s = (m - 1)/(m + 1), |s| <= 0.1716, from the series
+// atanh(s) = s sum_j s^{2j}/(2j+1) up to j = 9 (truncation < 3e-17 relative).
+constexpr int kLogOps = 24;  // approximate FP64 op count incl. the division
+__device__ __forceinline__ double log_pos(double a) {
+  int hi = __double2hiint(a);
+  int lo = __double2loint(a);
+  int e = 0;
+  if (hi < 0x00100000) {  // subnormal: scale into the normal range
+    a *= 0x1p54;
+    e = -54;
+    hi = __double2hiint(a);
+    lo = __double2loint(a);
+  }
+  e += (hi >> 20) - 1023;
+  double m = __hiloint2double((hi & 0x000fffff) | 0x3ff00000, lo);  // [1, 2)
+  if (m > kSqrt2) {
+    m *= 0.5;
+    e += 1;
+  }
+  const double s = (m - 1.0) / (m + 1.0);
+  const double s2 = s * s;
+  double q = 1.0 / 19.0;
+  q = fma(q, s2, 1.0 / 17.0);
+  q = fma(q, s2, 1.0 / 15.0);
+  q = fma(q, s2, 1.0 / 13.0);
+  q = fma(q, s2, 1.0 / 11.0);
+  q = fma(q, s2, 1.0 / 9.0);
+  q = fma(q, s2, 1.0 / 7.0);
+  q = fma(q, s2, 1.0 / 5.0);
+  q = fma(q, s2, 1.0 / 3.0);
+  q = fma(q, s2, 1.0);
+  const double lm = 2.0 * s * q;
+  const double ed = (double)e;
+  return fma(ed, kLn2Hi, fma(ed, kLn2Lo, lm));
+}
+
+// ---------------------------------------------------------------------------
+// Work tally of one evaluation (kept in registers; summed per warp when the
+// caller asked for counters).
+struct Tally {
+  unsigned nodes;       // integrand evaluations
+  unsigned iters;       // window-end Newton iterations
+  unsigned peak_iters;  // peak Newton iterations
+  unsigned fail;        // evaluations returned as NaN
+};
+
+// The window of Sec. IV-B.  ts = t_max, cs/ss = cosh/sinh(ts), [t0, t1] the
+// integration range.  The window ends are the roots of
+//   F(t) = nu (t - ts) - x (cosh t - cosh ts) + L  (+ ln 2 on the left),
+// L = -log eps.  F differs from g(t) - g(ts) + L only by
+// log((1 + e^{-2 nu t}) / (1 + e^{-2 nu ts})), which lies in (-ln 2, 0) right
+// of the peak and in [0, ln 2] left of it, so these roots enclose the
+// eps-window: the range is never narrower than the paper's.
+struct Window64 {
+  double ts, cs, t0, t1;
+};
+
+// a3: t_max = 0 when nu^2 <= x (g''(0) = nu^2 - x <= 0), else the root of
+// g'(t) = nu tanh(nu t) - x sinh t, which is concave on t > 0, positive just
+// right of 0 and negative at asinh(nu/x) (there nu tanh(nu t) < nu = x sinh t).
+// Safeguarded Newton inside that bracket.  Any point of the bracket is a
+// valid shift (g(t) <= g(t_max)), so hitting the iteration cap is not an
+// error; the tolerance is loose because only g(t_max) enters, to 2nd order.
+__device__ __forceinline__ void peak_f64(double x, double nu, double& ts, double& cs, Tally& tl) {
+  const double nu2 = nu * nu;
+  if (!(nu2 > x)) {
+    ts = 0.0;
+    cs = 1.0;
+    return;
+  }
+  const double q = nu / x;
+  double hi = log_pos(q + sqrt(fma(q, q, 1.0)));  // asinh(nu/x)
+  double lo = 0.0;
+  // small-t estimate from the cubic Taylor terms of g'
+  const double tc2 = (nu2 - x) / fma(nu2 * nu2, 1.0 / 3.0, x * (1.0 / 6.0));
+  double t = (tc2 < hi * hi) ? sqrt(tc2) : hi;
+  for (int it = 0; it < 40; ++it) {
+    ++tl.peak_iters;
+    const double e = exp_bounded(t);
+    const double er = 1.0 / e;
+    const double sh = 0.5 * (e - er), ch = 0.5 * (e + er);
+    const double w = exp_bounded(fmax(-2.0 * nu * t, -708.0));
+    const double r1 = 1.0 / (1.0 + w);
+    const double gp = fma(nu * (1.0 - w), r1, -x * sh);
+    const double gpp = fma(nu2 * 4.0 * w, r1 * r1, -x * ch);
+    if (gp > 0.0) lo = t; else hi = t;
+    // Past the inflection of g' (gpp < 0) a Newton step from the left lands
+    // right of the root; clamp it to the right bracket end, from where the
+    // iteration descends monotonically.  Before the inflection, bisect.
+    double tn;
+    if (gpp < 0.0) {
+      tn = t - gp / gpp;
+      if (tn > hi) tn = hi;
+      if (!(tn > lo)) tn = 0.5 * (lo + hi);
+    } else {
+      tn = 0.5 * (lo + hi);
+    }
+    const double dt = tn - t;
+    t = tn;
+    if (fabs(dt) <= 1e-8 * t) break;
+  }
+  ts = t;
+  const double e = exp_bounded(t);
+  cs = 0.5 * (e + 1.0 / e);
+}
+
+// a4: window ends.  Newton on the concave F approaches t1 from the right and
+// t0 from the left, so every iterate keeps the range at least as wide as the
+// eps-window.
+__device__ __forceinline__ Window64 window_f64(double x, double nu, double L, Tally& tl) {
+  Window64 w;
+  peak_f64(x, nu, w.ts, w.cs, tl);
+  const double ts = w.ts, cs = w.cs;
+  const double ss = sqrt(fmax(cs * cs - 1.0, 0.0));
+  // ---- t1: start right of the root.  cosh t - cs >= ss d + cs d^2/2 for
+  // d = t - ts >= 0, so the root d of  L + (nu - x ss) d - x cs d^2/2 = 0 is a
+  // right bound; in the exponential regime x e^t/2 >= L + x cs + nu t is one too.
+  {
+    const double a = x * cs, b = nu - x * ss;
+    double t = ts + (b + sqrt(fma(b, b, 2.0 * a * L))) / a;
+    const double tb = log_pos(2.0 * (L + a + nu * t) / x);
+    if (tb < t) t = tb;
+    for (int it = 0; it < 40; ++it) {
+      ++tl.iters;
+      const double e = exp_bounded(fmin(t, 709.0));
+      const double er = 1.0 / e;
+      const double F = fma(nu, t - ts, -x * (0.5 * (e + er) - cs)) + L;
+      const double Fp = fma(-0.5 * x, e - er, nu);
+      const double dt = F / Fp;
+      t -= dt;
+      if (fabs(dt) <= 1e-8 * t) break;
+    }
+    w.t1 = t;
+  }
+  // ---- t0: only when the peak is away from 0 and the integrand at 0 is
+  // below the threshold; Newton from the left on the increasing part.
+  w.t0 = 0.0;
+  if (ts > 0.0) {
+    const double Lp = L + kLn2;
+    const double G0 = fma(-nu, ts, x * (cs - 1.0)) + Lp;
+    if (G0 < 0.0) {
+      double t = fmax(0.0, ts - Lp / nu);
+      for (int it = 0; it < 40; ++it) {
+        ++tl.iters;
+        const double e = exp_bounded(t);
+        const double er = 1.0 / e;
+        const double G = fma(nu, t - ts, -x * (0.5 * (e + er) - cs)) + Lp;
+        const double Gp = fma(-0.5 * x, e - er, nu);
+        const double dt = G / Gp;
+        double tn = t - dt;
+        if (tn < 0.0) tn = 0.0;
+        const bool done = fabs(tn - t) <= 1e-8 * fmax(tn, 1e-3);
+        t = tn;
+        if (done) break;
+      }
+      w.t0 = t;
+    }
+  }
+  return w;
+}
+
+// Sum of the scaled integrand f(t)/f_s over `count` equispaced nodes
+// t_j = t_start + j H, where
+//   f(t) = e^{-x cosh t} cosh(nu t) = f_s exp(nu (t - ts) - x (cosh t - cs)) (1 + e^{-2 nu t}),
+//   f_s = e^{nu ts - x cs} / 2.
+// e^{t_j}, e^{-t_j} and e^{-2 nu t_j} follow geometric recurrences (one real
+// exp per node remains).  first/last receive the scaled end values.
+__device__ __forceinline__ double node_sum_f64(double t_start, double H, int count, double x,
+                                               double nu, double ts, double cs, double& first,
+                                               double& last) {
+  double E = exp_bounded(t_start);
+  double R = 1.0 / E;
+  const double P = exp_bounded(H);
+  const double Q = 1.0 / P;
+  double W = exp_bounded(fmax(-2.0 * nu * t_start, -708.0));
+  const double rho = exp_bounded(fmax(-2.0 * nu * H, -708.0));
+  const double A0 = fma(nu, t_start - ts, x * cs);
+  const double dA = nu * H;
+  const double xh = 0.5 * x;
+  double s = 0.0, jd = 0.0, f = 0.0;
+  for (int j = 0; j < count; ++j) {
+    const double arg = fma(-xh, E + R, fma(jd, dA, A0));
+    const double ev = exp_bounded(fmax(arg, -708.0));
+    f = fma(ev, W, ev);
+    if (j == 0) first = f;
+    s += f;
+    E *= P;
+    R *= Q;
+    W *= rho;
+    jd += 1.0;
+  }
+  last = f;
+  return s;
+}
+// FP64 ops per node in node_sum_f64 (work accounting): 2 fma + 1 add (arg),
+// 1 max, exp, 1 fma + 1 add (f, s), 3 mul + 1 add (recurrences).
+constexpr int kNodeOps64 = 9 + kExpOps;
+
+// ---------------------------------------------------------------------------
+// a5: node count.  For f analytic in the strip |Im t| < a with
+// int |f(t + i s)| dt <= M(a) I for |s| < a, the trapezoid rule with step h
+// on the whole line errs by at most 2 M(a) I / (e^{2 pi a / h} - 1)
+// (Trefethen & Weideman, SIAM Review 56 (2014), Thm 5.1).  Here
+// |f(t + i a)| <= e^{-x cos(a) cosh t} cosh(nu t), so M(a) <= K_nu(x cos a) /
+// K_nu(x), estimated by (cos a)^{-nu} e^{x (1 - cos a)} (the small- and
+// large-x behaviour of K_nu).  The step is the largest h over 16 strip
+// widths a_k = (k + 1/2) pi/32 with 2 pi a_k / h >= ln(2/tol) + nu lam_k + x mu_k,
+// lam_k = -ln cos a_k, mu_k = 1 - cos a_k, and N = ceil((t1 - t0)/h).
+// The arithmetic is FP32: N only needs a few correct digits.
+static __constant__ float kStripA[16] = {
+    4.908738521e-02f, 1.472621556e-01f, 2.454369261e-01f, 3.436116965e-01f,
+    4.417864669e-01f, 5.399612373e-01f, 6.381360078e-01f, 7.363107782e-01f,
+    8.344855486e-01f, 9.326603190e-01f, 1.030835089e+00f, 1.129009860e+00f,
+    1.227184630e+00f, 1.325359401e+00f, 1.423534171e+00f, 1.521708942e+00f};
+static __constant__ float kStripLam[16] = {
+    1.205269841e-03f, 1.088249011e-02f, 3.042698822e-02f, 6.023412881e-02f,
+    1.009377626e-01f, 1.534675349e-01f, 2.191421532e-01f, 2.998206135e-01f,
+    3.981534711e-01f, 5.180192619e-01f, 6.653321421e-01f, 8.496721254e-01f,
+    1.087999247e+00f, 1.414775403e+00f, 1.919157882e+00f, 3.014554825e+00f};
+static __constant__ float kStripMu[16] = {
+    1.204543795e-03f, 1.082349004e-02f, 2.996874681e-02f, 5.845593482e-02f,
+    9.601070688e-02f, 1.422713900e-01f, 1.967924685e-01f, 2.590488746e-01f,
+    3.284410452e-01f, 4.043006955e-01f, 4.858972558e-01f, 5.724449066e-01f,
+    6.631101466e-01f, 7.570198201e-01f, 8.532695255e-01f, 9.509323257e-01f};
+
+// Returns N in [2, n_max], or n_max + 1 when the bound asks for more nodes.
+__device__ __forceinline__ int strip_node_count(float x, float nu, float width, float log2_over_tol,
+                                                int n_max) {
+  float bn = 0.0f, bd = 1.0f;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const float d = fmaf(nu, kStripLam[k], fmaf(x, kStripMu[k], log2_over_tol));
+    if (kStripA[k] * bd > bn * d) {
+      bn = kStripA[k];
+      bd = d;
+    }
+  }
+  const float h = 6.28318531f * bn / bd;
+  const float nf = ceilf(width / h);
+  if (!(nf <= (float)n_max)) return n_max + 1;
+  return nf < 2.0f ? 2 : (int)nf;
+}
+
+// a6/a7: trapezoid on [t0, t1] with N intervals from the strip bound, in the
+// log domain: log K = nu ts - x cs - ln 2 + log(h S), S the weighted sum of
+// the scaled integrand (node_sum_f64).  Sets tl.fail (and returns NaN) when
+// N would exceed n_max.
+__device__ __forceinline__ double log_kv_f64(double x, double nu, float log2_over_tol, int n_max,
+                                             Tally& tl) {
+  const Window64 w = window_f64(x, nu, kLogInvEps64, tl);
+  const double width = w.t1 - w.t0;
+  const int N = strip_node_count((float)x, (float)nu, (float)width, log2_over_tol, n_max);
+  if (N > n_max) {
+    ++tl.fail;
+    return __longlong_as_double(0x7ff8000000000000LL);
+  }
+  const double h = width / N;
+  double f0, fN;
+  double S = node_sum_f64(w.t0, h, N + 1, x, nu, w.ts, w.cs, f0, fN);
+  tl.nodes += N + 1;
+  S -= 0.5 * (f0 + fN);
+  return fma(nu, w.ts, -x * w.cs) - kLn2 + log_pos(h * S);
+}
+
+// ln(2 / tol) for the plain form: tol = 1e-13 keeps the quadrature error
+// about three orders below the 1e-10 relative accuracy the form promises.
+constexpr float kPlainLog2OverTol = 30.6267f;
+constexpr int kPlainMaxNodes = 1024;
+
+}  // namespace bk

@@ -1,0 +1,80 @@
+// Pipe-rate probes for the roofline denominators of this ALU-bound library:
+// FP64 FMA, FP32 FMA and the MUFU ex2 unit.  Each thread runs `iters` trips
+// of 8 independent dependency chains (enough instruction-level parallelism
+// to keep a pipe busy) and writes one value to `sink` so nothing is removed.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "bk_internal.h"
+
+namespace bk {
+namespace {
+
+__global__ void probe_dfma(int64_t iters, double* sink) {
+  double a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = 1.0 + 1e-3 * (threadIdx.x + k);
+  const double m = 0.9999999, c = 1e-7;
+  for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = fma(a[k], m, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += a[k];
+  sink[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+__global__ void probe_ffma(int64_t iters, double* sink) {
+  float a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = 1.0f + 1e-3f * (threadIdx.x + k);
+  const float m = 0.9999f, c = 1e-4f;
+  for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = fmaf(a[k], m, c);
+  }
+  float s = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += a[k];
+  sink[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+__device__ __forceinline__ float ex2_neg(float v) {  // 2^-v on the MUFU unit
+  float r;
+  asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(-v));
+  return r;
+}
+
+__global__ void probe_ex2(int64_t iters, double* sink) {
+  float a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = 0.5f + 1e-3f * (threadIdx.x + k);
+  for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = ex2_neg(a[k]);  // stays in [0.5, 1)
+  }
+  float s = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += a[k];
+  sink[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+}  // namespace
+}  // namespace bk
+
+extern "C" bk_status bk_probe_pipe(int kind, int64_t iters, int grid, int block, double* sink,
+                                   bk_stream_t stream) {
+  using namespace bk;
+  if (iters < 0 || grid < 1 || block < 1 || block > 1024 || sink == nullptr)
+    return set_error(BK_ERR_INVALID_ARG, "bk_probe_pipe: bad launch arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  switch (kind) {
+    case 0: probe_dfma<<<grid, block, 0, s>>>(iters, sink); break;
+    case 1: probe_ffma<<<grid, block, 0, s>>>(iters, sink); break;
+    case 2: probe_ex2<<<grid, block, 0, s>>>(iters, sink); break;
+    default: return set_error(BK_ERR_INVALID_ARG, "bk_probe_pipe: unknown kind %d", kind);
+  }
+  return check_cuda(cudaGetLastError(), "bk_probe_pipe launch");
+}

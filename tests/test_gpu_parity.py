@@ -1,0 +1,208 @@
+"""GPU parity of the plain FP64 form against the CPU oracle, through the C-ABI.
+
+Tolerances: K_nu within 1e-10 relative; Matern entries within 1e-10 absolute
+(entries lie in (0, sigma^2] with sigma^2 = O(1)).  Sizes span several tiles
+with ragged tails; the full-size workloads are checked on sampled entries the
+oracle computes one by one, and exhaustively through closed forms.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2502_00356_gb300 as bk
+from paper_2502_00356_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+K_RTOL = 1e-10
+M_ATOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    bk.build()
+    return torch.device("cuda:0")
+
+
+def to_dev(a, dev):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+
+
+def gpu_eval(x, nu, dev, **kw):
+    out = bk.bk_eval(to_dev(x, dev), to_dev(nu, dev), **kw)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def assert_rel(got, want, rtol):
+    rel = np.abs(got / want - 1.0)
+    i = int(np.argmax(rel))
+    assert rel.max() <= rtol, f"max rel {rel.max():.3e} at {i}: got {got[i]!r} want {want[i]!r}"
+
+
+@pytest.mark.parametrize("n", [1, 31, 129, 1000, 4097])
+def test_eval_parity_ragged(dev, n):
+    x, nu = inputs.kv_pairs(n, seed=100 + n)
+    got = gpu_eval(x, nu, dev)
+    assert_rel(got, oracle.besselk(x, nu), K_RTOL)
+
+
+def test_eval_parity_region_grid(dev):
+    # the region of Sec. IV-C: x in [1e-3, 140], nu in (0, 20], plus nu = 0
+    xs = np.exp(np.linspace(np.log(1e-3), np.log(140.0), 45))
+    ns = np.linspace(0.0, 20.0, 41)
+    X, V = (a.ravel() for a in np.meshgrid(xs, ns))
+    got = gpu_eval(X, V, dev)
+    assert_rel(got, oracle.besselk(X, V), K_RTOL)
+
+
+def test_eval_full_size_sampled(dev):
+    # 100,000 seeded pairs, x log-uniform in [1e-3, 140], nu in [0.05, 10]
+    x, nu = inputs.kv_pairs(100_000, seed=1)
+    got = gpu_eval(x, nu, dev)
+    assert np.all(np.isfinite(got)) and np.all(got > 0)
+    idx = np.random.default_rng(5).choice(x.size, 3000, replace=False)
+    assert_rel(got[idx], oracle.besselk(x[idx], nu[idx]), K_RTOL)
+
+
+def test_eval_domain_edges(dev):
+    x = np.array([0.0, -1.0, np.nan, np.inf, 2.0, 2.0, 1e-3, 0.5])
+    nu = np.array([1.0, 1.0, 1.0, 1.0, -3.3, np.nan, 20.0, 0.0])
+    got = gpu_eval(x, nu, dev)
+    assert np.isposinf(got[0]) and np.isnan(got[1]) and np.isnan(got[2]) and got[3] == 0.0
+    assert abs(got[4] / oracle.besselk(2.0, 3.3) - 1) < K_RTOL
+    assert np.isnan(got[5])
+    assert abs(got[6] / oracle.besselk(1e-3, 20.0) - 1) < K_RTOL
+    assert abs(got[7] / oracle.besselk(0.5, 0.0) - 1) < K_RTOL
+
+
+def test_eval_empty_and_log_output(dev):
+    e = torch.empty(0, dtype=torch.float64, device=dev)
+    assert bk.bk_eval(e, e).numel() == 0
+    x, nu = inputs.kv_pairs(500, seed=7, nu_hi=20.0)
+    out, lout = bk.bk_eval_ex(to_dev(x, dev), to_dev(nu, dev), want_log=True)
+    torch.cuda.synchronize()
+    _, lref = oracle.besselk(x, nu, return_log=True)
+    err = np.abs(np.expm1(lout.cpu().numpy() - lref))
+    assert err.max() < K_RTOL
+    out32, _ = bk.bk_eval_ex(to_dev(x, dev), to_dev(nu, dev), out_dtype=torch.float32)
+    torch.cuda.synchronize()
+    ref = oracle.besselk(x, nu)
+    ok = (ref < 3e38) & (ref > 1.2e-38)  # the FP32 normal range
+    assert_rel(out32.cpu().numpy().astype(np.float64)[ok], ref[ok], 1.2e-7)
+
+
+def test_eval_counters(dev):
+    x, nu = inputs.kv_pairs(2000, seed=8)
+    ctr = torch.zeros(bk.BK_NUM_COUNTERS, dtype=torch.int64, device=dev)
+    opts = bk.make_opts(counters=ctr)
+    bk.bk_eval_ex(to_dev(x, dev), to_dev(nu, dev), opts=opts)
+    torch.cuda.synchronize()
+    c = ctr.cpu().numpy()
+    assert c[bk.BK_CTR_EVALS] == 2000 and c[bk.BK_CTR_FAIL] == 0
+    assert 2000 * 5 < c[bk.BK_CTR_NODES] < 2000 * 80
+    assert c[bk.BK_CTR_ITERS] > 0 and c[bk.BK_CTR_PEAK_ITERS] > 0
+
+
+# ---------------------------------------------------------------------------
+# Matern matrices
+
+def gpu_matern(locs, sigma2, beta, nu, dev, dtype=torch.float64, ld=None):
+    n = locs.shape[1]
+    out = torch.full((n, ld or n), float("nan"), dtype=dtype, device=dev)
+    bk.bk_matern_tile(to_dev(locs, dev), sigma2, beta, nu, out=out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("n", [1, 2, 33, 70, 130])
+@pytest.mark.parametrize("nu", [0.5, 1.37, 2.3])
+def test_matern_full_parity(dev, n, nu):
+    locs = inputs.morton_sorted(inputs.jittered_grid(n, seed=200 + n))
+    sigma2, beta = 1.3, 0.1
+    got = gpu_matern(locs, sigma2, beta, nu, dev)  # got[j, i] = M(i, j)
+    want = oracle.matern_block(locs, locs, sigma2, beta, nu)
+    assert np.abs(got.T - want).max() <= M_ATOL
+    assert np.array_equal(got, got.T)
+    assert np.all(np.diag(got) == sigma2)
+
+
+def test_matern_ld_padding_and_duplicates(dev):
+    locs = inputs.jittered_grid(40, seed=31)
+    locs[:, 7] = locs[:, 3]
+    got = gpu_matern(locs, 1.0, 0.2, 1.1, dev, ld=45)
+    assert np.all(np.isnan(got[:, 40:]))  # padding rows of each column untouched
+    M = got[:, :40]
+    assert M[3, 7] == 1.0 and M[7, 3] == 1.0
+    want = oracle.matern_block(locs, locs, 1.0, 0.2, 1.1)
+    assert np.abs(M.T - want).max() <= M_ATOL
+
+
+def test_matern_tile2_block(dev):
+    l1 = inputs.jittered_grid(45, seed=41)
+    l2 = inputs.jittered_grid(77, seed=42) * 0.8 + 0.1
+    out = bk.bk_matern_tile2(to_dev(l1, dev), to_dev(l2, dev), 0.7, 0.15, 1.9)
+    torch.cuda.synchronize()
+    want = oracle.matern_block(l1, l2, 0.7, 0.15, 1.9)
+    assert np.abs(out.cpu().numpy().T - want).max() <= M_ATOL
+
+
+def test_matern_fp32_output_of_plain_form(dev):
+    locs = inputs.morton_sorted(inputs.jittered_grid(100, seed=51))
+    got32 = gpu_matern(locs, 1.0, 0.1, 1.5, dev, dtype=torch.float32)
+    got64 = gpu_matern(locs, 1.0, 0.1, 1.5, dev)
+    np.testing.assert_array_equal(got32, got64.astype(np.float32).astype(np.float64))
+
+
+def closed_form(z, nu):
+    if nu == 0.5:
+        return torch.exp(-z)
+    if nu == 1.5:
+        return (1 + z) * torch.exp(-z)
+    raise ValueError(nu)
+
+
+@pytest.mark.parametrize("nu", [0.5, 1.5, 2.3])
+def test_matern_full_size_20000(dev, nu):
+    """The n = 20,000 jittered-grid workload (beta = 0.1, sigma^2 = 1): every
+    entry against the closed form for nu = 1/2 and 3/2, and a 4,000-entry
+    oracle sample (with near-diagonal pairs) for each nu."""
+    n, beta = 20_000, 0.1
+    locs = inputs.morton_sorted(inputs.jittered_grid(n, seed=2))
+    L = to_dev(locs, dev)
+    out = torch.empty((n, n), dtype=torch.float64, device=dev)
+    bk.bk_matern_tile(L, 1.0, beta, nu, out=out)
+    torch.cuda.synchronize()
+    assert bool(torch.isfinite(out).all())
+    if nu in (0.5, 1.5):
+        worst = 0.0
+        for c0 in range(0, n, 2000):  # column slabs keep the temporary small
+            cols = L[:, c0:c0 + 2000]
+            d = torch.sqrt((L[0][:, None] - cols[0][None, :]) ** 2 + (L[1][:, None] - cols[1][None, :]) ** 2)
+            ref = closed_form(d / beta, nu)
+            worst = max(worst, float((out[c0:c0 + 2000, :].T - ref).abs().max()))
+        assert worst <= M_ATOL
+    I, J = inputs.entry_sample(n, 4000, seed=6)
+    got = out[torch.as_tensor(J, device=dev), torch.as_tensor(I, device=dev)].cpu().numpy()
+    want = oracle.matern_entries(locs, I, J, 1.0, beta, nu)
+    assert np.abs(got - want).max() <= M_ATOL
+    # symmetry on a sample of transposed pairs
+    assert torch.equal(out[torch.as_tensor(J, device=dev), torch.as_tensor(I, device=dev)],
+                       out[torch.as_tensor(I, device=dev), torch.as_tensor(J, device=dev)])
+    del out
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("nu", [0.5, 1.5, 2.3])
+def test_matern_cholesky_4000(dev, nu):
+    locs = inputs.morton_sorted(inputs.jittered_grid(4000, seed=3))
+    out = torch.empty((4000, 4000), dtype=torch.float64, device=dev)
+    bk.bk_matern_tile(to_dev(locs, dev), 1.0, 0.1, nu, out=out)
+    torch.cuda.synchronize()
+    _, info = torch.linalg.cholesky_ex(out)
+    assert int(info) == 0
