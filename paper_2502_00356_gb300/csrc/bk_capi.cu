@@ -59,8 +59,8 @@ bk_status check_opts(const bk_opts* o) {
     return set_error(BK_ERR_INVALID_ARG, "opts.compute: unknown dtype %d", (int)o->compute);
   if (o->window == BK_WIN_FIXED && (o->fixed_bins < 1 || !(o->fixed_t1 > 0.0) || !finite(o->fixed_t1)))
     return set_error(BK_ERR_INVALID_ARG, "opts: fixed window needs fixed_bins >= 1 and fixed_t1 > 0");
-  if (o->window != BK_WIN_SEARCH || o->compute != BK_F64)
-    return set_error(BK_ERR_UNSUPPORTED, "this build supports window=SEARCH with compute=F64 only");
+  if (o->window != BK_WIN_SEARCH)
+    return set_error(BK_ERR_UNSUPPORTED, "this build supports window=SEARCH only");
   return BK_OK;
 }
 
@@ -140,9 +140,11 @@ bk_status bk_eval_ex(const double* x, const double* nu, void* out, void* log_out
   if (n == 0) return BK_OK;
   if (x == nullptr || nu == nullptr || out == nullptr)
     return set_error(BK_ERR_INVALID_ARG, "x, nu and out must be non-NULL when n > 0");
-  return check_cuda(launch_eval_f64(x, nu, out, log_out, out_dtype, n, o.d_counters,
-                                    (cudaStream_t)stream),
-                    "bk_eval launch");
+  const cudaError_t e =
+      (o.compute == BK_F64)
+          ? launch_eval_f64(x, nu, out, log_out, out_dtype, n, o.d_counters, (cudaStream_t)stream)
+          : launch_eval_f32(x, nu, out, log_out, out_dtype, n, o.d_counters, (cudaStream_t)stream);
+  return check_cuda(e, "bk_eval launch");
 }
 
 bk_status bk_eval(const double* x, const double* nu, double* out, int64_t n, bk_stream_t stream) {
@@ -159,13 +161,17 @@ bk_status bk_matern_tile_ex(const double* locs, int64_t n, double sigma2, double
   if ((st = check_dtype(dtype)) != BK_OK) return st;
   if ((st = check_theta(sigma2, beta, nu)) != BK_OK) return st;
   if ((st = check_matrix(out, n, n, ld)) != BK_OK) return st;
-  if (opts == nullptr) o.compute = BK_F64;
+  if (opts == nullptr) o.compute = dtype;  // the output dtype picks the form by default
   if ((st = check_opts(&o)) != BK_OK) return st;
   if (n == 0) return BK_OK;
   if (locs == nullptr) return set_error(BK_ERR_INVALID_ARG, "locs is NULL");
-  return check_cuda(launch_matern_sym_f64(locs, n, sigma2, beta, nu, out, ld, dtype,
-                                          o.d_counters, (cudaStream_t)stream),
-                    "bk_matern_tile launch");
+  const cudaError_t e =
+      (o.compute == BK_F64)
+          ? launch_matern_sym_f64(locs, n, sigma2, beta, nu, out, ld, dtype, o.d_counters,
+                                  (cudaStream_t)stream)
+          : launch_matern_sym_f32(locs, n, sigma2, beta, nu, out, ld, dtype, o.d_counters,
+                                  (cudaStream_t)stream);
+  return check_cuda(e, "bk_matern_tile launch");
 }
 
 bk_status bk_matern_tile(const double* locs, int64_t n, double sigma2, double beta, double nu,
@@ -178,18 +184,22 @@ bk_status bk_matern_tile2(const double* locs1, int64_t m, const double* locs2, i
                           bk_dtype dtype, const bk_opts* opts, bk_stream_t stream) {
   bk_opts o;
   bk_opts_default(&o);
-  if (opts != nullptr) o = *opts;
   bk_status st;
   if ((st = check_dtype(dtype)) != BK_OK) return st;
+  if (opts != nullptr) o = *opts; else o.compute = dtype;
   if ((st = check_theta(sigma2, beta, nu)) != BK_OK) return st;
   if ((st = check_matrix(out, m, n, ld)) != BK_OK) return st;
   if ((st = check_opts(&o)) != BK_OK) return st;
   if (m == 0 || n == 0) return BK_OK;
   if (locs1 == nullptr || locs2 == nullptr)
     return set_error(BK_ERR_INVALID_ARG, "locs1 and locs2 must be non-NULL");
-  return check_cuda(launch_matern_block_f64(locs1, m, locs2, n, sigma2, beta, nu, out, ld, dtype,
-                                            o.d_counters, (cudaStream_t)stream),
-                    "bk_matern_tile2 launch");
+  const cudaError_t e =
+      (o.compute == BK_F64)
+          ? launch_matern_block_f64(locs1, m, locs2, n, sigma2, beta, nu, out, ld, dtype,
+                                    o.d_counters, (cudaStream_t)stream)
+          : launch_matern_block_f32(locs1, m, locs2, n, sigma2, beta, nu, out, ld, dtype,
+                                    o.d_counters, (cudaStream_t)stream);
+  return check_cuda(e, "bk_matern_tile2 launch");
 }
 
 bk_status bk_morton_order(const double* locs, int64_t n, int64_t* perm) {

@@ -34,4 +34,15 @@ cudaError_t launch_matern_block_f64(const double* locs1, int64_t m, const double
                                     int64_t ld, bk_dtype out_t, unsigned long long* ctr,
                                     cudaStream_t s);
 
+// ---- FP32 precision form (bk_fp32.cu) ----
+cudaError_t launch_eval_f32(const double* x, const double* nu, void* out, void* log_out,
+                            bk_dtype out_t, int64_t n, unsigned long long* ctr, cudaStream_t s);
+cudaError_t launch_matern_sym_f32(const double* locs, int64_t n, double sigma2, double beta,
+                                  double nu, void* out, int64_t ld, bk_dtype out_t,
+                                  unsigned long long* ctr, cudaStream_t s);
+cudaError_t launch_matern_block_f32(const double* locs1, int64_t m, const double* locs2,
+                                    int64_t n, double sigma2, double beta, double nu, void* out,
+                                    int64_t ld, bk_dtype out_t, unsigned long long* ctr,
+                                    cudaStream_t s);
+
 }  // namespace bk

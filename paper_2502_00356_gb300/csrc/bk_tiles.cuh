@@ -1,0 +1,238 @@
+// Kernels shared by the FP64 and FP32 forms: the bk_eval kernel, the fused
+// symmetric Matern tile writer and the m x n block writer, templated on a
+// Form policy that supplies one K_nu evaluation and one Matern entry:
+//   static double eval(double x, double nu, Tally&, unsigned& evals, double& log_k);
+//   static double matern(double xi, double yi, double xj, double yj, double sigma2,
+//                        double beta, double nu, double log_pref, Tally&, unsigned& evals);
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "bk.h"
+#include "bk_math64.cuh"
+
+namespace bk {
+
+constexpr double kInf = __builtin_huge_val();
+
+template <typename T>
+__device__ __forceinline__ T to_out(double v);
+template <>
+__device__ __forceinline__ double to_out<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ float to_out<float>(double v) { return (float)v; }
+
+// Adds this warp's tallies to the caller's counters (one atomic per warp and
+// counter).  Every lane of the warp must call it.
+__device__ __forceinline__ void flush_tally(unsigned long long* ctr, const Tally& tl,
+                                            unsigned evals) {
+  if (ctr == nullptr) return;
+  unsigned long long v[5] = {tl.fail, tl.nodes, tl.iters, evals, tl.peak_iters};
+  const int idx[5] = {BK_CTR_FAIL, BK_CTR_NODES, BK_CTR_ITERS, BK_CTR_EVALS, BK_CTR_PEAK_ITERS};
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    unsigned long long a = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    if ((threadIdx.x & 31) == 0 && a) atomicAdd(ctr + idx[k], a);
+  }
+}
+
+
+// The element-wise domain rules of the C-ABI around a form's evaluation.
+template <class Form>
+__device__ __forceinline__ double eval_domain(double x, double nu, Tally& tl, unsigned& evals,
+                                              double& log_k) {
+  nu = fabs(nu);
+  if (x > 0.0 && x < kInf && nu < kInf) return Form::eval(x, nu, tl, evals, log_k);
+  if (x == 0.0 && nu == nu) {
+    log_k = kInf;
+    return kInf;
+  }
+  if (x == kInf && nu < kInf) {
+    log_k = -kInf;
+    return 0.0;
+  }
+  log_k = __longlong_as_double(0x7ff8000000000000LL);
+  return log_k;
+}
+
+template <class Form, typename OutT>
+__global__ void __launch_bounds__(128) eval_kernel(const double* __restrict__ x,
+                                                   const double* __restrict__ nu,
+                                                   OutT* __restrict__ out,
+                                                   OutT* __restrict__ log_out, int64_t n,
+                                                   unsigned long long* __restrict__ ctr) {
+  Tally tl{0u, 0u, 0u, 0u};
+  unsigned evals = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    double lk;
+    const double k = eval_domain<Form>(x[i], nu[i], tl, evals, lk);
+    out[i] = to_out<OutT>(k);
+    if (log_out != nullptr) log_out[i] = to_out<OutT>(lk);
+  }
+  flush_tally(ctr, tl, evals);
+}
+
+// a1: log of the Matern prefactor sigma^2 / (2^{nu-1} Gamma(nu)) (Sec. III-A).
+__device__ __forceinline__ double matern_log_prefactor(double sigma2, double nu) {
+  const double ls = (sigma2 > 0.0) ? log_pos(sigma2) : -kInf;
+  return ls - (nu - 1.0) * kLn2 - lgamma(nu);
+}
+
+constexpr int kTile = 32;     // tile edge (rows and columns)
+constexpr int kWarps = 8;     // 256 threads: warp w computes columns w, w+8, w+16, w+24
+constexpr int kThreads = kWarps * 32;
+
+// Full symmetric matrix.  Tiles of the lower triangle (I >= J) are numbered
+// tix = I (I + 1)/2 + J and visited grid-stride.  Lane i of warp w computes
+// M(r0 + i, c0 + c) for c = w + 8k: a warp covers one column against 32
+// consecutive (Morton-near) rows, so its lanes see similar distances.  The
+// tile is staged in shared memory and stored twice with coalesced 32-element
+// column segments: as block (I, J) and, transposed, as block (J, I).
+template <class Form, typename OutT>
+__global__ void __launch_bounds__(kThreads) matern_sym_kernel(
+    const double* __restrict__ locs, int64_t n, double sigma2, double beta, double nu,
+    OutT* __restrict__ out, int64_t ld, int64_t ntiles, unsigned long long* __restrict__ ctr) {
+  __shared__ double s_rx[kTile], s_ry[kTile], s_cx[kTile], s_cy[kTile];
+  __shared__ OutT s_tile[kTile][kTile + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const double log_pref = matern_log_prefactor(sigma2, nu);
+  Tally tl{0u, 0u, 0u, 0u};
+  unsigned evals = 0;
+  for (int64_t tix = blockIdx.x; tix < ntiles; tix += gridDim.x) {
+    int64_t I = (int64_t)((sqrt(8.0 * (double)tix + 1.0) - 1.0) * 0.5);
+    while (I * (I + 1) / 2 > tix) --I;
+    while ((I + 1) * (I + 2) / 2 <= tix) ++I;
+    const int64_t J = tix - I * (I + 1) / 2;
+    const int64_t r0 = I * kTile, c0 = J * kTile;
+    __syncthreads();  // the previous tile's shared data is no longer read
+    if (warp == 0) {
+      const int64_t i = r0 + lane;
+      s_rx[lane] = (i < n) ? locs[i] : 0.0;
+      s_ry[lane] = (i < n) ? locs[n + i] : 0.0;
+    } else if (warp == 1) {
+      const int64_t j = c0 + lane;
+      s_cx[lane] = (j < n) ? locs[j] : 0.0;
+      s_cy[lane] = (j < n) ? locs[n + j] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int k = 0; k < kTile / kWarps; ++k) {
+      const int c = warp + kWarps * k;
+      double v = 0.0;
+      if (r0 + lane < n && c0 + c < n)
+        v = Form::matern(s_rx[lane], s_ry[lane], s_cx[c], s_cy[c], sigma2, beta, nu,
+                             log_pref, tl, evals);
+      s_tile[lane][c] = to_out<OutT>(v);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kTile / kWarps; ++k) {
+      const int c = warp + kWarps * k;
+      const int64_t i = r0 + lane, j = c0 + c;
+      if (i < n && j < n) out[i + j * ld] = s_tile[lane][c];
+    }
+    if (I != J) {
+#pragma unroll
+      for (int k = 0; k < kTile / kWarps; ++k) {
+        const int c = warp + kWarps * k;
+        const int64_t i = c0 + lane, j = r0 + c;  // entry (c0+lane, r0+c) = M(r0+c, c0+lane)
+        if (i < n && j < n) out[i + j * ld] = s_tile[c][lane];
+      }
+    }
+  }
+  flush_tally(ctr, tl, evals);
+}
+
+// General m x n block (Algorithm 3's single tile between two location sets).
+template <class Form, typename OutT>
+__global__ void __launch_bounds__(kThreads) matern_block_kernel(
+    const double* __restrict__ locs1, int64_t m, const double* __restrict__ locs2, int64_t n,
+    double sigma2, double beta, double nu, OutT* __restrict__ out, int64_t ld, int64_t tiles_m,
+    int64_t ntiles, unsigned long long* __restrict__ ctr) {
+  __shared__ double s_rx[kTile], s_ry[kTile], s_cx[kTile], s_cy[kTile];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const double log_pref = matern_log_prefactor(sigma2, nu);
+  Tally tl{0u, 0u, 0u, 0u};
+  unsigned evals = 0;
+  for (int64_t tix = blockIdx.x; tix < ntiles; tix += gridDim.x) {
+    const int64_t r0 = (tix % tiles_m) * kTile, c0 = (tix / tiles_m) * kTile;
+    __syncthreads();
+    if (warp == 0) {
+      const int64_t i = r0 + lane;
+      s_rx[lane] = (i < m) ? locs1[i] : 0.0;
+      s_ry[lane] = (i < m) ? locs1[m + i] : 0.0;
+    } else if (warp == 1) {
+      const int64_t j = c0 + lane;
+      s_cx[lane] = (j < n) ? locs2[j] : 0.0;
+      s_cy[lane] = (j < n) ? locs2[n + j] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int k = 0; k < kTile / kWarps; ++k) {
+      const int c = warp + kWarps * k;
+      const int64_t i = r0 + lane, j = c0 + c;
+      if (i < m && j < n)
+        out[i + j * ld] = to_out<OutT>(Form::matern(s_rx[lane], s_ry[lane], s_cx[c], s_cy[c],
+                                                        sigma2, beta, nu, log_pref, tl, evals));
+    }
+  }
+  flush_tally(ctr, tl, evals);
+}
+
+
+// Blocks for a grid-stride launch: min(work, SMs x per_sm).
+int grid_for(int64_t work_items, int per_sm);
+
+template <class Form>
+cudaError_t launch_eval_form(const double* x, const double* nu, void* out, void* log_out,
+                             bk_dtype out_t, int64_t n, unsigned long long* ctr, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int grid = grid_for((n + 127) / 128, 16);
+  if (out_t == BK_F64)
+    eval_kernel<Form, double><<<grid, 128, 0, s>>>(x, nu, (double*)out, (double*)log_out, n, ctr);
+  else
+    eval_kernel<Form, float><<<grid, 128, 0, s>>>(x, nu, (float*)out, (float*)log_out, n, ctr);
+  return cudaGetLastError();
+}
+
+template <class Form>
+cudaError_t launch_matern_sym_form(const double* locs, int64_t n, double sigma2, double beta,
+                                   double nu, void* out, int64_t ld, bk_dtype out_t,
+                                   unsigned long long* ctr, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int64_t nb = (n + kTile - 1) / kTile;
+  const int64_t ntiles = nb * (nb + 1) / 2;
+  const int grid = grid_for(ntiles, 4);
+  if (out_t == BK_F64)
+    matern_sym_kernel<Form, double><<<grid, kThreads, 0, s>>>(locs, n, sigma2, beta, nu,
+                                                              (double*)out, ld, ntiles, ctr);
+  else
+    matern_sym_kernel<Form, float><<<grid, kThreads, 0, s>>>(locs, n, sigma2, beta, nu,
+                                                             (float*)out, ld, ntiles, ctr);
+  return cudaGetLastError();
+}
+
+template <class Form>
+cudaError_t launch_matern_block_form(const double* locs1, int64_t m, const double* locs2,
+                                     int64_t n, double sigma2, double beta, double nu, void* out,
+                                     int64_t ld, bk_dtype out_t, unsigned long long* ctr,
+                                     cudaStream_t s) {
+  if (m == 0 || n == 0) return cudaSuccess;
+  const int64_t tm = (m + kTile - 1) / kTile, tn = (n + kTile - 1) / kTile;
+  const int64_t ntiles = tm * tn;
+  const int grid = grid_for(ntiles, 4);
+  if (out_t == BK_F64)
+    matern_block_kernel<Form, double><<<grid, kThreads, 0, s>>>(
+        locs1, m, locs2, n, sigma2, beta, nu, (double*)out, ld, tm, ntiles, ctr);
+  else
+    matern_block_kernel<Form, float><<<grid, kThreads, 0, s>>>(
+        locs1, m, locs2, n, sigma2, beta, nu, (float*)out, ld, tm, ntiles, ctr);
+  return cudaGetLastError();
+}
+
+}  // namespace bk

@@ -112,10 +112,10 @@ def test_eval_counters(dev):
 # ---------------------------------------------------------------------------
 # Matern matrices
 
-def gpu_matern(locs, sigma2, beta, nu, dev, dtype=torch.float64, ld=None):
+def gpu_matern(locs, sigma2, beta, nu, dev, dtype=torch.float64, ld=None, opts=None):
     n = locs.shape[1]
     out = torch.full((n, ld or n), float("nan"), dtype=dtype, device=dev)
-    bk.bk_matern_tile(to_dev(locs, dev), sigma2, beta, nu, out=out)
+    bk.bk_matern_tile(to_dev(locs, dev), sigma2, beta, nu, out=out, opts=opts)
     torch.cuda.synchronize()
     return out.cpu().numpy().astype(np.float64)
 
@@ -154,7 +154,8 @@ def test_matern_tile2_block(dev):
 
 def test_matern_fp32_output_of_plain_form(dev):
     locs = inputs.morton_sorted(inputs.jittered_grid(100, seed=51))
-    got32 = gpu_matern(locs, 1.0, 0.1, 1.5, dev, dtype=torch.float32)
+    got32 = gpu_matern(locs, 1.0, 0.1, 1.5, dev, dtype=torch.float32,
+                       opts=bk.make_opts(compute=bk.BK_F64))
     got64 = gpu_matern(locs, 1.0, 0.1, 1.5, dev)
     np.testing.assert_array_equal(got32, got64.astype(np.float32).astype(np.float64))
 
