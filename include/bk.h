@@ -151,6 +151,51 @@ bk_status bk_matern_tile2(const double* locs1, int64_t m, const double* locs2, i
 bk_status bk_morton_order(const double* locs, int64_t n, int64_t* perm);
 
 /*
+ * Batched persistent form.  A maximum-likelihood sweep regenerates many
+ * covariance matrices of uneven n with per-instance (sigma^2, beta, nu)
+ * every likelihood evaluation (Sec. III-A; the paper accelerates exactly this
+ * step of the MLE loop).  bk_matern_batched builds all of them in ONE
+ * persistent launch: CTAs take lower-triangle tiles of any instance from a
+ * device counter.  The plan (created once per list of sizes) owns the work
+ * list and that counter; the call itself allocates nothing and does not
+ * synchronise, so it can be captured in a CUDA graph.  Calls that use the
+ * same plan must not overlap on the GPU (they share the counter).
+ */
+typedef struct {
+  const double* locs; /* device, 2n doubles (SoA) */
+  int64_t n;          /* must equal the plan's size for this instance */
+  double sigma2, beta, nu;
+  void* out;          /* device, ld * n elements of the batch dtype, column-major */
+  int64_t ld;         /* >= n */
+} bk_matern_desc;
+
+typedef struct bk_plan bk_plan;
+
+/* sizes: HOST array of `count` instance sizes.  dtype: output dtype of every
+   instance; opts (may be NULL) selects the form (default: compute = dtype).
+   Allocates the plan's device work list; picks a launch shape from the
+   autotune cache when one exists for this GPU, dtype, form and size bucket. */
+bk_status bk_batched_plan_create(bk_plan** plan, const int64_t* sizes, int32_t count,
+                                 bk_dtype dtype, const bk_opts* opts);
+bk_status bk_batched_plan_destroy(bk_plan* plan);
+/* Reports the work list size and the launch shape (any output may be NULL). */
+bk_status bk_batched_plan_info(const bk_plan* plan, int64_t* total_tiles, int* warps,
+                               int* ctas_per_sm, int* chunk, int* tuned);
+/* Times launch shapes (warps per CTA, CTAs per SM, tiles per grab) on the
+   first `sample_tiles` tiles (<= 0: all) of the caller's batch, keeps the
+   fastest in the plan and appends it to the cache file ($BK_AUTOTUNE_CACHE,
+   else $XDG_CACHE_HOME or ~/.cache /libbesselk/autotune.txt).  Writes into the
+   instances' outputs and synchronises `stream`. */
+bk_status bk_batched_autotune(bk_plan* plan, const bk_matern_desc* d_descs, int64_t sample_tiles,
+                              bk_stream_t stream);
+/* d_descs: DEVICE array of `count` descriptors (caller-owned).  A descriptor
+   that does not match the plan (n, ld < n, NULL pointers, beta or nu <= 0,
+   sigma2 < 0) is skipped in-kernel and counted in BK_CTR_FAIL when the
+   plan's opts supplied counters. */
+bk_status bk_matern_batched(const bk_matern_desc* d_descs, int32_t count, bk_dtype dtype,
+                            const bk_plan* plan, bk_stream_t stream);
+
+/*
  * bk_probe_pipe: throughput probe for the roofline denominators (not part of
  * the paper's method).  Launches grid x block threads; each runs `iters`
  * trips of 8 independent operations on one pipe: kind 0 = FP64 FMA,

@@ -32,7 +32,8 @@ BK_NUM_COUNTERS = 8
 EXPORTS = (
     "bk_opts_default", "bk_version", "bk_last_error", "bk_status_string", "bk_sync",
     "bk_eval", "bk_eval_ex", "bk_matern_tile", "bk_matern_tile_ex", "bk_matern_tile2",
-    "bk_morton_order", "bk_probe_pipe",
+    "bk_morton_order", "bk_probe_pipe", "bk_batched_plan_create", "bk_batched_plan_destroy",
+    "bk_batched_plan_info", "bk_batched_autotune", "bk_matern_batched",
 )
 
 
@@ -85,6 +86,11 @@ def lib() -> ctypes.CDLL:
             "bk_matern_tile2": (I, [P, I64, P, I64, D, D, D, P, I64, I, P, P]),
             "bk_morton_order": (I, [P, I64, P]),
             "bk_probe_pipe": (I, [I, I64, I, I, P, P]),
+            "bk_batched_plan_create": (I, [P, P, ctypes.c_int32, I, P]),
+            "bk_batched_plan_destroy": (I, [P]),
+            "bk_batched_plan_info": (I, [P, P, P, P, P, P]),
+            "bk_batched_autotune": (I, [P, P, I64, P]),
+            "bk_matern_batched": (I, [P, ctypes.c_int32, I, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -288,3 +294,86 @@ def bk_probe_pipe(kind: int, iters: int, grid: int, block: int, sink, stream=Non
     _check(lib().bk_probe_pipe(int(kind), int(iters), int(grid), int(block), _ptr(sink),
                                _stream_ptr(stream)))
     return grid * block * iters * 8
+
+
+# ---------------------------------------------------------------------------
+# batched persistent form
+
+#: numpy layout of bk_matern_desc (56 bytes, natural alignment)
+DESC_DTYPE = None
+
+
+def _desc_dtype():
+    global DESC_DTYPE
+    if DESC_DTYPE is None:
+        import numpy as np
+        DESC_DTYPE = np.dtype([("locs", "<u8"), ("n", "<i8"), ("sigma2", "<f8"), ("beta", "<f8"),
+                               ("nu", "<f8"), ("out", "<u8"), ("ld", "<i8")])
+    return DESC_DTYPE
+
+
+def make_descs(instances, device=None):
+    """Pack [(locs (2, n) CUDA f64, sigma2, beta, nu, out (n, ld) CUDA tensor), ...]
+    into a device array of bk_matern_desc (a uint8 tensor)."""
+    import numpy as np
+    torch = _torch()
+    arr = np.zeros(len(instances), dtype=_desc_dtype())
+    for k, (locs, s2, be, nu, out) in enumerate(instances):
+        n = _locs(locs)
+        _dev(out, "out")
+        if out.dim() != 2 or out.shape[0] != n or out.shape[1] < n:
+            raise ValueError(f"instance {k}: out must be (n, ld) with ld >= n")
+        arr[k] = (locs.data_ptr(), n, float(s2), float(be), float(nu), out.data_ptr(), out.shape[1])
+    dev = device or (instances[0][0].device if instances else torch.device("cuda"))
+    return torch.from_numpy(arr.view(np.uint8).copy()).to(dev)
+
+
+class BatchedPlan:
+    """Work list and launch shape for a fixed list of instance sizes."""
+
+    def __init__(self, sizes, dtype=None, opts: Optional[bk_opts] = None):
+        import numpy as np
+        torch = _torch()
+        self.sizes = np.ascontiguousarray(np.asarray(sizes, dtype=np.int64))
+        self.dtype_code = _dtype_code(dtype or torch.float64)
+        self.count = int(self.sizes.size)
+        self._opts = opts  # keeps the counters pointer alive with the plan
+        h = ctypes.c_void_p()
+        optp = ctypes.byref(opts) if opts is not None else None
+        _check(lib().bk_batched_plan_create(ctypes.byref(h), self.sizes.ctypes.data_as(ctypes.c_void_p),
+                                            self.count, self.dtype_code, optp))
+        self.handle = h
+
+    def info(self) -> dict:
+        t, w, c, ch, tu = (ctypes.c_int64(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int(),
+                           ctypes.c_int())
+        _check(lib().bk_batched_plan_info(self.handle, ctypes.byref(t), ctypes.byref(w),
+                                          ctypes.byref(c), ctypes.byref(ch), ctypes.byref(tu)))
+        return {"total_tiles": t.value, "warps": w.value, "ctas_per_sm": c.value,
+                "chunk": ch.value, "tuned": bool(tu.value)}
+
+    def autotune(self, d_descs, sample_tiles: int = 0, stream=None):
+        _check(lib().bk_batched_autotune(self.handle, _ptr(d_descs), int(sample_tiles),
+                                         _stream_ptr(stream)))
+        return self.info()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().bk_batched_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def bk_matern_batched(d_descs, plan: BatchedPlan, stream=None):
+    """All instances of `plan` in one persistent launch (graph-capturable)."""
+    torch = _torch()
+    _dev(d_descs, "d_descs", torch.uint8)
+    if d_descs.numel() != plan.count * _desc_dtype().itemsize:
+        raise ValueError("d_descs does not hold plan.count descriptors")
+    _check(lib().bk_matern_batched(_ptr(d_descs), plan.count, plan.dtype_code, plan.handle,
+                                   _stream_ptr(stream)))

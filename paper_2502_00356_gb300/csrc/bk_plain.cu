@@ -7,34 +7,10 @@
 #include <cstdint>
 
 #include "bk_internal.h"
-#include "bk_math64.cuh"
+#include "bk_forms.cuh"
 #include "bk_tiles.cuh"
 
 namespace bk {
-
-struct FormF64 {
-  static __device__ __forceinline__ double eval(double x, double nu, Tally& tl, unsigned& evals,
-                                                double& log_k) {
-    ++evals;
-    log_k = log_kv_f64(x, nu, kPlainLog2OverTol, kPlainMaxNodes, tl);
-    return exp_full(log_k);
-  }
-
-  // a2 + a3..a7 for one entry: distance, x = r / beta, log K_nu(x),
-  // M = exp(log prefactor + nu log x + log K).  sigma^2 where r == 0
-  // (Algorithm 3 tests the computed distance for exact zero).
-  static __device__ __forceinline__ double matern(double xi, double yi, double xj, double yj,
-                                                  double sigma2, double beta, double nu,
-                                                  double log_pref, Tally& tl, unsigned& evals) {
-    const double dx = xj - xi, dy = yj - yi;
-    const double r = sqrt(fma(dx, dx, dy * dy));
-    if (r == 0.0) return sigma2;
-    const double z = r / beta;
-    ++evals;
-    const double lk = log_kv_f64(z, nu, kPlainLog2OverTol, kPlainMaxNodes, tl);
-    return exp_full(fma(nu, log_pos(z), log_pref) + lk);
-  }
-};
 
 int grid_for(int64_t work_items, int per_sm) {
   const int64_t cap = (int64_t)current_sm_count() * per_sm;

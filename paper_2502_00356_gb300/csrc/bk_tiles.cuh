@@ -87,63 +87,83 @@ constexpr int kTile = 32;     // tile edge (rows and columns)
 constexpr int kWarps = 8;     // 256 threads: warp w computes columns w, w+8, w+16, w+24
 constexpr int kThreads = kWarps * 32;
 
-// Full symmetric matrix.  Tiles of the lower triangle (I >= J) are numbered
-// tix = I (I + 1)/2 + J and visited grid-stride.  Lane i of warp w computes
-// M(r0 + i, c0 + c) for c = w + 8k: a warp covers one column against 32
-// consecutive (Morton-near) rows, so its lanes see similar distances.  The
-// tile is staged in shared memory and stored twice with coalesced 32-element
-// column segments: as block (I, J) and, transposed, as block (J, I).
+// One 32 x 32 tile (I, J), I >= J, of a symmetric matrix: lane i of warp w
+// computes M(r0 + i, c0 + c) for c = w, w + WARPS, ...: a warp covers one
+// column against 32 consecutive (Morton-near) rows, so its lanes see similar
+// distances.  The tile is staged in shared memory and stored twice with
+// coalesced 32-element column segments: as block (I, J) and, transposed, as
+// block (J, I).  Diagonal tiles are computed whole (both halves).  Callers
+// synchronise the block before the shared arrays are reused.
+template <typename OutT>
+struct SymTileSmem {
+  double rx[kTile], ry[kTile], cx[kTile], cy[kTile];
+  OutT tile[kTile][kTile + 1];
+};
+
+template <class Form, typename OutT, int WARPS>
+__device__ __forceinline__ void sym_tile(SymTileSmem<OutT>& sm, const double* __restrict__ locs,
+                                         int64_t n, int64_t I, int64_t J, double sigma2,
+                                         double beta, double nu, double log_pref,
+                                         OutT* __restrict__ out, int64_t ld, Tally& tl,
+                                         unsigned& evals) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t r0 = I * kTile, c0 = J * kTile;
+  if (warp == 0) {
+    const int64_t i = r0 + lane;
+    sm.rx[lane] = (i < n) ? locs[i] : 0.0;
+    sm.ry[lane] = (i < n) ? locs[n + i] : 0.0;
+  } else if (warp == 1) {
+    const int64_t j = c0 + lane;
+    sm.cx[lane] = (j < n) ? locs[j] : 0.0;
+    sm.cy[lane] = (j < n) ? locs[n + j] : 0.0;
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int c = warp; c < kTile; c += WARPS) {
+    double v = 0.0;
+    if (r0 + lane < n && c0 + c < n)
+      v = Form::matern(sm.rx[lane], sm.ry[lane], sm.cx[c], sm.cy[c], sigma2, beta, nu, log_pref,
+                       tl, evals);
+    sm.tile[lane][c] = to_out<OutT>(v);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int c = warp; c < kTile; c += WARPS) {
+    const int64_t i = r0 + lane, j = c0 + c;
+    if (i < n && j < n) out[i + j * ld] = sm.tile[lane][c];
+  }
+  if (I != J) {
+#pragma unroll
+    for (int c = warp; c < kTile; c += WARPS) {
+      const int64_t i = c0 + lane, j = r0 + c;  // entry (c0+lane, r0+c) = M(r0+c, c0+lane)
+      if (i < n && j < n) out[i + j * ld] = sm.tile[c][lane];
+    }
+  }
+}
+
+// Lower-triangle tile number t = I (I + 1)/2 + J  ->  (I, J).
+__device__ __forceinline__ void tri_tile(int64_t t, int64_t& I, int64_t& J) {
+  I = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+  while (I * (I + 1) / 2 > t) --I;
+  while ((I + 1) * (I + 2) / 2 <= t) ++I;
+  J = t - I * (I + 1) / 2;
+}
+
+// Full symmetric matrix: its lower-triangle tiles visited grid-stride.
 template <class Form, typename OutT>
 __global__ void __launch_bounds__(kThreads) matern_sym_kernel(
     const double* __restrict__ locs, int64_t n, double sigma2, double beta, double nu,
     OutT* __restrict__ out, int64_t ld, int64_t ntiles, unsigned long long* __restrict__ ctr) {
-  __shared__ double s_rx[kTile], s_ry[kTile], s_cx[kTile], s_cy[kTile];
-  __shared__ OutT s_tile[kTile][kTile + 1];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ SymTileSmem<OutT> sm;
   const double log_pref = matern_log_prefactor(sigma2, nu);
   Tally tl{0u, 0u, 0u, 0u};
   unsigned evals = 0;
   for (int64_t tix = blockIdx.x; tix < ntiles; tix += gridDim.x) {
-    int64_t I = (int64_t)((sqrt(8.0 * (double)tix + 1.0) - 1.0) * 0.5);
-    while (I * (I + 1) / 2 > tix) --I;
-    while ((I + 1) * (I + 2) / 2 <= tix) ++I;
-    const int64_t J = tix - I * (I + 1) / 2;
-    const int64_t r0 = I * kTile, c0 = J * kTile;
+    int64_t I, J;
+    tri_tile(tix, I, J);
     __syncthreads();  // the previous tile's shared data is no longer read
-    if (warp == 0) {
-      const int64_t i = r0 + lane;
-      s_rx[lane] = (i < n) ? locs[i] : 0.0;
-      s_ry[lane] = (i < n) ? locs[n + i] : 0.0;
-    } else if (warp == 1) {
-      const int64_t j = c0 + lane;
-      s_cx[lane] = (j < n) ? locs[j] : 0.0;
-      s_cy[lane] = (j < n) ? locs[n + j] : 0.0;
-    }
-    __syncthreads();
-#pragma unroll 1
-    for (int k = 0; k < kTile / kWarps; ++k) {
-      const int c = warp + kWarps * k;
-      double v = 0.0;
-      if (r0 + lane < n && c0 + c < n)
-        v = Form::matern(s_rx[lane], s_ry[lane], s_cx[c], s_cy[c], sigma2, beta, nu,
-                             log_pref, tl, evals);
-      s_tile[lane][c] = to_out<OutT>(v);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < kTile / kWarps; ++k) {
-      const int c = warp + kWarps * k;
-      const int64_t i = r0 + lane, j = c0 + c;
-      if (i < n && j < n) out[i + j * ld] = s_tile[lane][c];
-    }
-    if (I != J) {
-#pragma unroll
-      for (int k = 0; k < kTile / kWarps; ++k) {
-        const int c = warp + kWarps * k;
-        const int64_t i = c0 + lane, j = r0 + c;  // entry (c0+lane, r0+c) = M(r0+c, c0+lane)
-        if (i < n && j < n) out[i + j * ld] = s_tile[c][lane];
-      }
-    }
+    sym_tile<Form, OutT, kWarps>(sm, locs, n, I, J, sigma2, beta, nu, log_pref, out, ld, tl,
+                                 evals);
   }
   flush_tally(ctr, tl, evals);
 }

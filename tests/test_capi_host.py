@@ -109,3 +109,19 @@ def test_generators_are_seeded_and_shaped():
     inst = inputs.batched_instances(256)
     ns = np.array([i.n for i in inst])
     assert len(inst) == 256 and ns.min() >= 500 and ns.max() <= 8000
+
+
+def test_batched_host_checks(L):
+    fake = ctypes.c_void_p(0x1000)
+    h = ctypes.c_void_p()
+    sizes = np.array([10, 20], dtype=np.int64)
+    sp = sizes.ctypes.data_as(ctypes.c_void_p)
+    assert L.bk_batched_plan_create(ctypes.byref(h), sp, 0, 0, None) == bk.BK_ERR_INVALID_ARG
+    assert L.bk_batched_plan_create(ctypes.byref(h), None, 2, 0, None) == bk.BK_ERR_INVALID_ARG
+    assert L.bk_batched_plan_create(ctypes.byref(h), sp, 2, 5, None) == bk.BK_ERR_INVALID_ARG
+    neg = np.array([10, -1], dtype=np.int64)
+    assert L.bk_batched_plan_create(ctypes.byref(h), neg.ctypes.data_as(ctypes.c_void_p), 2, 0,
+                                    None) == bk.BK_ERR_INVALID_ARG
+    assert L.bk_matern_batched(fake, 2, 0, None, None) == bk.BK_ERR_INVALID_ARG
+    assert L.bk_batched_plan_destroy(None) == bk.BK_OK
+    assert bk._desc_dtype().itemsize == 56
