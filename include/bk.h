@@ -196,6 +196,29 @@ bk_status bk_matern_batched(const bk_matern_desc* d_descs, int32_t count, bk_dty
                             const bk_plan* plan, bk_stream_t stream);
 
 /*
+ * bk_matern_batched_static: the work of bk_matern_batched without a plan and
+ * without allocating anything.  The paper has no counterpart; this entry
+ * point exists for callers that cannot call cudaMalloc where they build their
+ * matrices: code inside a framework that owns all device memory through its
+ * own pool allocator (an extra cudaMalloc may fail or stall other streams),
+ * and real-time or embedded services that forbid allocation after start-up.
+ * Its scratch (work list and tile counter) is a fixed array compiled into the
+ * library, held by every GPU that loads the library until the process exits;
+ * it fits at most 4096 instances (count > 4096 is BK_ERR_INVALID_ARG).
+ * The first call on a device resolves that array's device address (this also
+ * loads the library's device code there), so make the first call on each
+ * device before any stream capture.  All calls share the one array and each
+ * call rewrites it (work list, counter zeroed) before use: calls that can
+ * overlap on the GPU (other streams, other host threads) race with each
+ * other and must be ordered by the caller.  Descriptors as for
+ * bk_matern_batched; dtype picks the output type and the form (compute =
+ * dtype); an invalid descriptor is skipped.  Launch shape fixed (8 warps,
+ * 2 CTAs per SM).  Enqueues two kernels on `stream` and does not synchronise.
+ */
+bk_status bk_matern_batched_static(const bk_matern_desc* d_descs, int32_t count, bk_dtype dtype,
+                                   bk_stream_t stream);
+
+/*
  * bk_probe_pipe: throughput probe for the roofline denominators (not part of
  * the paper's method).  Launches grid x block threads; each runs `iters`
  * trips of 8 independent operations on one pipe: kind 0 = FP64 FMA,

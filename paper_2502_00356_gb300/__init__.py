@@ -34,6 +34,7 @@ EXPORTS = (
     "bk_eval", "bk_eval_ex", "bk_matern_tile", "bk_matern_tile_ex", "bk_matern_tile2",
     "bk_morton_order", "bk_probe_pipe", "bk_batched_plan_create", "bk_batched_plan_destroy",
     "bk_batched_plan_info", "bk_batched_autotune", "bk_matern_batched",
+    "bk_matern_batched_static",
 )
 
 
@@ -91,6 +92,7 @@ def lib() -> ctypes.CDLL:
             "bk_batched_plan_info": (I, [P, P, P, P, P, P]),
             "bk_batched_autotune": (I, [P, P, I64, P]),
             "bk_matern_batched": (I, [P, ctypes.c_int32, I, P, P]),
+            "bk_matern_batched_static": (I, [P, ctypes.c_int32, I, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -377,3 +379,20 @@ def bk_matern_batched(d_descs, plan: BatchedPlan, stream=None):
         raise ValueError("d_descs does not hold plan.count descriptors")
     _check(lib().bk_matern_batched(_ptr(d_descs), plan.count, plan.dtype_code, plan.handle,
                                    _stream_ptr(stream)))
+
+
+#: most instances bk_matern_batched_static accepts (its scratch is a fixed array)
+STATIC_MAX_INSTANCES = 4096
+
+
+def bk_matern_batched_static(d_descs, count: int, dtype=None, stream=None):
+    """bk_matern_batched without a plan and without any allocation, for
+    callers that cannot allocate device memory at this point (see bk.h).
+    At most STATIC_MAX_INSTANCES instances; calls that overlap on the GPU
+    race on the shared scratch, so order them."""
+    torch = _torch()
+    _dev(d_descs, "d_descs", torch.uint8)
+    if d_descs.numel() != int(count) * _desc_dtype().itemsize:
+        raise ValueError("d_descs does not hold `count` descriptors")
+    code = _dtype_code(dtype or torch.float64)
+    _check(lib().bk_matern_batched_static(_ptr(d_descs), int(count), code, _stream_ptr(stream)))

@@ -401,3 +401,166 @@ bk_status bk_batched_autotune(bk_plan* plan, const bk_matern_desc* d_descs, int6
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free batched entry point (bk_matern_batched_static).
+//
+// bk_batched_plan_create calls cudaMalloc for the work list and the tile
+// counter.  Some callers cannot allocate device memory where they build
+// their matrices: code running inside a framework that owns all device
+// memory through its own pool (a cudaMalloc there can fail, or stall other
+// streams while the driver maps memory), and real-time or embedded services
+// that forbid allocation after start-up.  For them the same batched work runs
+// with its scratch in the fixed array below, which is part of the loaded
+// library image: every GPU that loads the library holds it until the process
+// exits.  It fits kStaticMaxInstances instances.
+
+namespace bk {
+namespace {
+
+constexpr int kStaticMaxInstances = 4096;
+// Word layout of the scratch (8-byte words; each part starts on 256 bytes):
+// [0] tile counter, [kStaticPrefixOff ...] count + 1 tile offsets,
+// [kStaticSizesOff ...] count instance sizes.
+constexpr int kStaticPrefixOff = 32;
+constexpr int kStaticSizesOff = ((kStaticPrefixOff + kStaticMaxInstances + 1 + 31) / 32) * 32;
+constexpr int kStaticWords = kStaticSizesOff + kStaticMaxInstances;
+
+static __device__ __align__(256) unsigned long long g_static_scratch[kStaticWords];
+
+// One block: reads each descriptor's n, writes the sizes and the tile prefix
+// sums, and zeroes the tile counter (the scratch keeps the previous call's
+// contents, so everything is rewritten here every call).
+__global__ void __launch_bounds__(1024) static_batch_prep_kernel(
+    const bk_matern_desc* __restrict__ descs, int count, unsigned long long* __restrict__ scratch) {
+  int64_t* prefix = (int64_t*)(scratch + kStaticPrefixOff);
+  int64_t* sizes = (int64_t*)(scratch + kStaticSizesOff);
+  __shared__ int64_t part[1024];
+  const int per = (count + (int)blockDim.x - 1) / (int)blockDim.x;
+  const int k0 = (int)threadIdx.x * per, k1 = min(count, k0 + per);
+  int64_t local = 0;
+  for (int k = k0; k < k1; ++k) {
+    const int64_t n = descs[k].n;
+    sizes[k] = n;
+    const int64_t nb = (n > 0) ? (n + kTile - 1) / kTile : 0;
+    local += nb * (nb + 1) / 2;
+  }
+  part[threadIdx.x] = local;
+  __syncthreads();
+  for (int off = 1; off < (int)blockDim.x; off <<= 1) {  // inclusive scan of the partial sums
+    const int64_t v = ((int)threadIdx.x >= off) ? part[threadIdx.x - off] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int64_t run = (threadIdx.x == 0) ? 0 : part[threadIdx.x - 1];
+  for (int k = k0; k < k1; ++k) {
+    prefix[k] = run;
+    const int64_t n = sizes[k];
+    const int64_t nb = (n > 0) ? (n + kTile - 1) / kTile : 0;
+    run += nb * (nb + 1) / 2;
+  }
+  if (threadIdx.x == blockDim.x - 1) prefix[count] = part[blockDim.x - 1];
+  if (threadIdx.x == 0) scratch[0] = 0ull;
+}
+
+// The persistent kernel of bk_matern_batched, with its work list, tile total
+// and counter taken from the static scratch (filled by the preparation
+// kernel earlier on the same stream).
+template <class Form, typename OutT, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) matern_batched_static_kernel(
+    const bk_matern_desc* __restrict__ descs, int count, unsigned long long* __restrict__ scratch) {
+  const int64_t* prefix = (const int64_t*)(scratch + kStaticPrefixOff);
+  const int64_t* sizes = (const int64_t*)(scratch + kStaticSizesOff);
+  const int64_t limit = prefix[count];
+  __shared__ BatchSmem<OutT> sm;
+  Tally tl{0u, 0u, 0u, 0u};
+  unsigned evals = 0;
+  int cur = -1;
+  while (true) {
+    __syncthreads();
+    if (threadIdx.x == 0) sm.item = (int64_t)atomicAdd(scratch, 1ull);
+    __syncthreads();
+    const int64_t w = sm.item;
+    if (w >= limit) break;
+    const int k = find_instance(prefix, count, w);
+    if (k != cur) {
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        bk_matern_desc d = descs[k];
+        const bool ok = d.n == sizes[k] && d.ld >= d.n && d.locs != nullptr &&
+                        d.out != nullptr && d.beta > 0.0 && d.nu > 0.0 && d.sigma2 >= 0.0;
+        if (!ok) d.n = 0;  // an invalid descriptor is skipped
+        sm.locs = d.locs;
+        sm.out = (OutT*)d.out;
+        sm.n = d.n;
+        sm.ld = d.ld;
+        sm.sigma2 = d.sigma2;
+        sm.beta = d.beta;
+        sm.nu = d.nu;
+        sm.log_pref = matern_log_prefactor(d.sigma2, d.nu);
+      }
+      __syncthreads();
+      cur = k;
+    }
+    int64_t I, J;
+    tri_tile(w - prefix[k], I, J);
+    __syncthreads();
+    sym_tile<Form, OutT, WARPS>(sm.tile, sm.locs, sm.n, I, J, sm.sigma2, sm.beta, sm.nu,
+                                sm.log_pref, sm.out, sm.ld, tl, evals);
+  }
+}
+
+std::mutex g_static_mutex;
+unsigned long long* g_static_addr[64] = {nullptr};
+
+// Device address of the scratch on the current device.  The array's name in
+// host code is only a host-side handle, so it is resolved once per device
+// with cudaGetSymbolAddress (this first call also loads the library's device
+// code on that device).
+bk_status static_scratch_address(unsigned long long** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return check_cuda(e, "bk_matern_batched_static: cudaGetDevice");
+  if (dev < 0 || dev >= 64)
+    return set_error(BK_ERR_UNSUPPORTED, "bk_matern_batched_static: device %d out of range", dev);
+  std::lock_guard<std::mutex> lk(g_static_mutex);
+  if (g_static_addr[dev] == nullptr) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess)
+      return check_cuda(e, "bk_matern_batched_static: cudaGetSymbolAddress");
+    g_static_addr[dev] = (unsigned long long*)p;
+  }
+  *out = g_static_addr[dev];
+  return BK_OK;
+}
+
+}  // namespace
+}  // namespace bk
+
+extern "C" bk_status bk_matern_batched_static(const bk_matern_desc* d_descs, int32_t count,
+                                              bk_dtype dtype, bk_stream_t stream) {
+  using namespace bk;
+  if (count < 1 || count > kStaticMaxInstances)
+    return set_error(BK_ERR_INVALID_ARG,
+                     "bk_matern_batched_static: count must be in [1, %d] (got %d); use a plan "
+                     "(bk_batched_plan_create) for larger batches",
+                     kStaticMaxInstances, (int)count);
+  if (d_descs == nullptr) return set_error(BK_ERR_INVALID_ARG, "d_descs is NULL");
+  if (dtype != BK_F64 && dtype != BK_F32)
+    return set_error(BK_ERR_INVALID_ARG, "dtype: unknown value %d", (int)dtype);
+  unsigned long long* scratch = nullptr;
+  bk_status st = static_scratch_address(&scratch);
+  if (st != BK_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  static_batch_prep_kernel<<<1, 1024, 0, s>>>(d_descs, count, scratch);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return check_cuda(e, "bk_matern_batched_static: preparation launch");
+  const int grid = current_sm_count() * 2;
+  if (dtype == BK_F64)
+    matern_batched_static_kernel<FormF64, double, 8><<<grid, 256, 0, s>>>(d_descs, count, scratch);
+  else
+    matern_batched_static_kernel<FormF32, float, 8><<<grid, 256, 0, s>>>(d_descs, count, scratch);
+  return check_cuda(cudaGetLastError(), "bk_matern_batched_static launch");
+}
