@@ -82,9 +82,13 @@ typedef struct {
   /* Optional device array of BK_NUM_COUNTERS unsigned 64-bit counters that
      kernels add to (never reset by the library).  NULL = no counting. */
   unsigned long long* d_counters;
+  /* BK_WIN_LEARNED: the window network (trained or loaded); must outlive
+     every call and plan that uses it. */
+  const struct bk_learned* learned;
 } bk_opts;
 
-/* Fills *o with the defaults: BK_WIN_SEARCH, BK_F64, b = 40, t1 = 9, no counters. */
+/* Fills *o with the defaults: BK_WIN_SEARCH, BK_F64, b = 40, t1 = 9, no
+   counters, no network. */
 void bk_opts_default(bk_opts* o);
 
 const char* bk_version(void);
@@ -194,6 +198,56 @@ bk_status bk_batched_autotune(bk_plan* plan, const bk_matern_desc* d_descs, int6
    plan's opts supplied counters. */
 bk_status bk_matern_batched(const bk_matern_desc* d_descs, int32_t count, bk_dtype dtype,
                             const bk_plan* plan, bk_stream_t stream);
+
+/*
+ * Learned window (not in the paper; the window search of Sec. IV-B is the
+ * part it replaces).  A 2 -> 64 -> 64 -> 64 -> 4 tanh network maps
+ * (ln x, nu) to (t*, t* - t0, t1 - t*, ln N) of the eps = 2^-23 window.  It is
+ * trained on the GPU by this library's kernels (bk_learned_train) on labels
+ * from a bounds search, and used through bk_opts.window = BK_WIN_LEARNED with
+ * compute = BK_F32: the network is tabulated on a 512 x 256 grid over
+ * ln x in [ln 1e-3, ln 140] and nu in [0.05, 20] after every training or
+ * load, kernels interpolate the table, widen the window by a relative and an
+ * absolute margin and check it (the integrand at both ends must be below
+ * eps times its value at the predicted peak, checked with an upper bound of
+ * g); points outside the grid or failing the check use the window search and
+ * are counted in BK_CTR_FALLBACK.
+ */
+typedef struct bk_learned bk_learned;
+
+/* Allocates a network with Glorot-uniform weights drawn from `seed`
+   (synchronises the device). */
+bk_status bk_learned_create(bk_learned** model, uint64_t seed);
+bk_status bk_learned_destroy(bk_learned* model);
+/* Adam steps (learning rate decayed by a cosine from lr to lr/20 over the
+   call) on mini-batches of `batch` samples (a multiple of 128) drawn with
+   replacement by a counter-based hash of (seed, step).  Data (device,
+   caller-owned): x[n], nu[n] and labels[n][6] = (t*, t0, t1, g(t*), N, any),
+   as written by the oracle's label script.  The target mean and standard
+   deviation are taken from this data on the first call.  d_loss (device,
+   optional): receives the mean squared error of each step.  Rebuilds the
+   table at the end.  Enqueued on `stream`. */
+bk_status bk_learned_train(bk_learned* model, const double* d_x, const double* d_nu,
+                           const double* d_labels, int64_t n, int32_t steps, int32_t batch,
+                           float lr, uint64_t seed, float* d_loss, bk_stream_t stream);
+/* Full-batch gradient of the training loss over samples 0 .. n-1 (n a
+   multiple of 128) into d_grad[8772] (device), and the loss into *d_loss. */
+bk_status bk_learned_grad(bk_learned* model, const double* d_x, const double* d_nu,
+                          const double* d_labels, int64_t n, float* d_grad, float* d_loss,
+                          bk_stream_t stream);
+/* Per-point network outputs: d_out[4 i ..] = (t*, t0, t1, N) for (x[i], nu[i]). */
+bk_status bk_learned_infer(const bk_learned* model, const double* d_x, const double* d_nu,
+                           float* d_out, int64_t n, bk_stream_t stream);
+/* Host copies of the 8772 parameters (get and/or set; set rebuilds the table)
+   and of the 8 target statistics (mean[4], std[4]); synchronising. */
+bk_status bk_learned_params(bk_learned* model, float* h_get, const float* h_set);
+bk_status bk_learned_stats(bk_learned* model, float* h_get8, const float* h_set8);
+/* Relative and absolute window margins (defaults 0.05 and 0.02). */
+bk_status bk_learned_set_margins(bk_learned* model, float rel, float abs_margin);
+/* Checkpoint with parameters, Adam state, step count and target statistics,
+   guarded by a checksum; load resumes training where save left it. */
+bk_status bk_learned_save(const bk_learned* model, const char* path);
+bk_status bk_learned_load(bk_learned* model, const char* path);
 
 /*
  * bk_matern_batched_static: the work of bk_matern_batched without a plan and

@@ -72,6 +72,7 @@ def _load():
             "oracle_window_trapezoid_log_k": (D, [D, D, D, D, I64]),
             "oracle_min_nodes": (I64, [D, D, D, D, I64]),
             "oracle_min_nodes_batch": (None, [P, P, D, D, I64, P, I64, I]),
+            "oracle_window_labels_batch": (None, [P, P, D, D, I64, P, I64, I]),
             "oracle_fixed_window_log_k": (D, [D, D, D, I64]),
             "oracle_matern_entries": (None, [P, I64, P, P, I64, D, D, D, P, I]),
             "oracle_matern_block": (None, [P, I64, P, I64, D, D, D, P, I64, I]),
@@ -152,6 +153,16 @@ def min_nodes(x, nu, rel_tol: float, log_eps: float = LOG_EPS64, nmax: int = 512
     out = np.empty(xa.size, dtype=np.int64)
     _load().oracle_min_nodes_batch(_ptr(xa), _ptr(na), float(log_eps), float(rel_tol), int(nmax),
                                    _ptr(out), xa.size, int(threads))
+    return out
+
+
+def window_labels(x, nu, log_eps: float, rel_tol: float, nmax: int = 256,
+                  threads: int = 0) -> np.ndarray:
+    """Rows (t*, t0, t1, g(t*), N, log T_ref) of the eps-window labels."""
+    _, xa, na = _bcast(x, nu)
+    out = np.empty((xa.size, 6), dtype=np.float64)
+    _load().oracle_window_labels_batch(_ptr(xa), _ptr(na), float(log_eps), float(rel_tol),
+                                       int(nmax), _ptr(out), xa.size, int(threads))
     return out
 
 

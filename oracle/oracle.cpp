@@ -367,6 +367,37 @@ int64_t oracle_min_nodes(double x, double nu, double log_eps, double rel_tol, in
   return 0;
 }
 
+// Labels of the learned window: out[6*i ..] = (t*, t0, t1, g(t*), N, T_ref)
+// where [t0, t1] is the eps-window (bisection, as oracle_window), N the
+// smallest interval count whose trapezoid on that window is within rel_tol of
+// the 512-interval trapezoid on the same window (T_ref; the window's own
+// truncation is not part of N's job), or 0 if none up to nmax.
+void oracle_window_labels_batch(const double* x, const double* nu, double log_eps, double rel_tol,
+                                int64_t nmax, double* out, int64_t n, int nthreads) {
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+  for (int64_t i = 0; i < n; ++i) {
+    ld ts, a, b, gs;
+    const ld X = (ld)x[i], V = fabsl((ld)nu[i]);
+    window_ld(X, V, (ld)log_eps, &ts, &a, &b, &gs);
+    const ld ref = trapezoid_log_k(X, V, a, b, 512, gs);
+    long found = 0;
+    for (long N = 1; N <= (long)nmax; ++N) {
+      const ld v = trapezoid_log_k(X, V, a, b, N, gs);
+      if (fabsl(expm1l(v - ref)) <= (ld)rel_tol) { found = N; break; }
+    }
+    double* o = out + 6 * i;
+    o[0] = (double)ts;
+    o[1] = (double)a;
+    o[2] = (double)b;
+    o[3] = (double)gs;
+    o[4] = (double)found;
+    o[5] = (double)ref;
+  }
+}
+
 void oracle_min_nodes_batch(const double* x, const double* nu, double log_eps, double rel_tol,
                             int64_t nmax, int64_t* out, int64_t n, int nthreads) {
 #ifdef _OPENMP

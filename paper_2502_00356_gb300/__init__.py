@@ -34,7 +34,9 @@ EXPORTS = (
     "bk_eval", "bk_eval_ex", "bk_matern_tile", "bk_matern_tile_ex", "bk_matern_tile2",
     "bk_morton_order", "bk_probe_pipe", "bk_batched_plan_create", "bk_batched_plan_destroy",
     "bk_batched_plan_info", "bk_batched_autotune", "bk_matern_batched",
-    "bk_matern_batched_static",
+    "bk_matern_batched_static", "bk_learned_create", "bk_learned_destroy", "bk_learned_train",
+    "bk_learned_grad", "bk_learned_infer", "bk_learned_params", "bk_learned_stats",
+    "bk_learned_set_margins", "bk_learned_save", "bk_learned_load",
 )
 
 
@@ -50,7 +52,8 @@ _STATUS = {0: "BK_OK", 1: "BK_ERR_INVALID_ARG", 2: "BK_ERR_CUDA", 3: "BK_ERR_NOM
 
 class bk_opts(ctypes.Structure):
     _fields_ = [("window", ctypes.c_int), ("compute", ctypes.c_int), ("fixed_bins", ctypes.c_int),
-                ("fixed_t1", ctypes.c_double), ("d_counters", ctypes.c_void_p)]
+                ("fixed_t1", ctypes.c_double), ("d_counters", ctypes.c_void_p),
+                ("learned", ctypes.c_void_p)]
 
 
 _lock = threading.Lock()
@@ -93,6 +96,17 @@ def lib() -> ctypes.CDLL:
             "bk_batched_autotune": (I, [P, P, I64, P]),
             "bk_matern_batched": (I, [P, ctypes.c_int32, I, P, P]),
             "bk_matern_batched_static": (I, [P, ctypes.c_int32, I, P]),
+            "bk_learned_create": (I, [P, ctypes.c_uint64]),
+            "bk_learned_destroy": (I, [P]),
+            "bk_learned_train": (I, [P, P, P, P, I64, ctypes.c_int32, ctypes.c_int32,
+                                     ctypes.c_float, ctypes.c_uint64, P, P]),
+            "bk_learned_grad": (I, [P, P, P, P, I64, P, P, P]),
+            "bk_learned_infer": (I, [P, P, P, P, I64, P]),
+            "bk_learned_params": (I, [P, P, P]),
+            "bk_learned_stats": (I, [P, P, P]),
+            "bk_learned_set_margins": (I, [P, ctypes.c_float, ctypes.c_float]),
+            "bk_learned_save": (I, [P, ctypes.c_char_p]),
+            "bk_learned_load": (I, [P, ctypes.c_char_p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -150,11 +164,18 @@ def _ptr(t) -> Optional[int]:
 
 
 def make_opts(window: int = BK_WIN_SEARCH, compute: int = BK_F64, fixed_bins: int = 40,
-              fixed_t1: float = 9.0, counters=None) -> bk_opts:
+              fixed_t1: float = 9.0, counters=None, learned=None) -> bk_opts:
     """A bk_opts struct; ``counters`` is an optional CUDA int64 tensor of
-    BK_NUM_COUNTERS entries that kernels add to."""
+    BK_NUM_COUNTERS entries that kernels add to; ``learned`` a LearnedWindow
+    (implies window = BK_WIN_LEARNED and compute = BK_F32 unless given)."""
     o = bk_opts()
     lib().bk_opts_default(ctypes.byref(o))
+    if learned is not None:
+        if window == BK_WIN_SEARCH:
+            window = BK_WIN_LEARNED
+        if compute == BK_F64:
+            compute = BK_F32
+        o.learned = learned.handle.value
     o.window, o.compute, o.fixed_bins, o.fixed_t1 = int(window), int(compute), int(fixed_bins), float(fixed_t1)
     if counters is not None:
         torch = _torch()
@@ -396,3 +417,93 @@ def bk_matern_batched_static(d_descs, count: int, dtype=None, stream=None):
         raise ValueError("d_descs does not hold `count` descriptors")
     code = _dtype_code(dtype or torch.float64)
     _check(lib().bk_matern_batched_static(_ptr(d_descs), int(count), code, _stream_ptr(stream)))
+
+
+# ---------------------------------------------------------------------------
+# learned window
+
+N_MLP_PARAMS = 8772
+
+
+class LearnedWindow:
+    """The window network (bk_learned): training, inference, checkpoints."""
+
+    def __init__(self, seed: int = 0, path: Optional[str] = None):
+        h = ctypes.c_void_p()
+        _check(lib().bk_learned_create(ctypes.byref(h), ctypes.c_uint64(seed)))
+        self.handle = h
+        if path is not None:
+            self.load(path)
+
+    def train(self, x, nu, labels, steps: int, batch: int = 8192, lr: float = 2e-3,
+              seed: int = 1, loss=None, stream=None):
+        torch = _torch()
+        for t, name in ((x, "x"), (nu, "nu"), (labels, "labels")):
+            _dev(t, name, torch.float64)
+        n = x.numel()
+        if labels.numel() != 6 * n or nu.numel() != n:
+            raise ValueError("labels must be (n, 6) and nu (n,)")
+        if loss is not None:
+            _dev(loss, "loss", torch.float32)
+            if loss.numel() < steps:
+                raise ValueError("loss needs `steps` entries")
+        _check(lib().bk_learned_train(self.handle, _ptr(x), _ptr(nu), _ptr(labels), n, int(steps),
+                                      int(batch), float(lr), ctypes.c_uint64(seed), _ptr(loss),
+                                      _stream_ptr(stream)))
+
+    def grad(self, x, nu, labels, stream=None):
+        """(gradient[8772], loss) of the full-batch loss over the given samples."""
+        torch = _torch()
+        n = x.numel()
+        g = torch.empty(N_MLP_PARAMS, dtype=torch.float32, device=x.device)
+        loss = torch.zeros(1, dtype=torch.float32, device=x.device)
+        _check(lib().bk_learned_grad(self.handle, _ptr(x), _ptr(nu), _ptr(labels), n, _ptr(g),
+                                     _ptr(loss), _stream_ptr(stream)))
+        return g, loss
+
+    def infer(self, x, nu, stream=None):
+        torch = _torch()
+        out = torch.empty((x.numel(), 4), dtype=torch.float32, device=x.device)
+        _check(lib().bk_learned_infer(self.handle, _ptr(x), _ptr(nu), _ptr(out), x.numel(),
+                                      _stream_ptr(stream)))
+        return out
+
+    def params(self, new=None):
+        import numpy as np
+        cur = np.empty(N_MLP_PARAMS, dtype=np.float32)
+        setp = None
+        if new is not None:
+            new = np.ascontiguousarray(np.asarray(new, dtype=np.float32))
+            setp = new.ctypes.data_as(ctypes.c_void_p)
+        _check(lib().bk_learned_params(self.handle, cur.ctypes.data_as(ctypes.c_void_p), setp))
+        return cur
+
+    def stats(self, new=None):
+        import numpy as np
+        cur = np.empty(8, dtype=np.float32)
+        setp = None
+        if new is not None:
+            new = np.ascontiguousarray(np.asarray(new, dtype=np.float32))
+            setp = new.ctypes.data_as(ctypes.c_void_p)
+        _check(lib().bk_learned_stats(self.handle, cur.ctypes.data_as(ctypes.c_void_p), setp))
+        return cur
+
+    def set_margins(self, rel: float, abs_margin: float):
+        _check(lib().bk_learned_set_margins(self.handle, float(rel), float(abs_margin)))
+
+    def save(self, path: str):
+        _check(lib().bk_learned_save(self.handle, path.encode()))
+
+    def load(self, path: str):
+        _check(lib().bk_learned_load(self.handle, path.encode()))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().bk_learned_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

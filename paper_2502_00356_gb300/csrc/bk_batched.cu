@@ -49,11 +49,11 @@ struct BatchSmem {
 // *next (scratch, zeroed before the launch) until `limit` tiles are taken.
 template <class Form, typename OutT, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) matern_batched_kernel(
-    const bk_matern_desc* __restrict__ descs, int count, const int64_t* __restrict__ prefix,
+    const Form form, const bk_matern_desc* __restrict__ descs, int count, const int64_t* __restrict__ prefix,
     const int64_t* __restrict__ sizes, int64_t limit, unsigned long long* __restrict__ next,
     int chunk, unsigned long long* __restrict__ ctr) {
   __shared__ BatchSmem<OutT> sm;
-  Tally tl{0u, 0u, 0u, 0u};
+  Tally tl{0u, 0u, 0u, 0u, 0u};
   unsigned evals = 0;
   int cur = -1;
   while (true) {
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(WARPS * 32) matern_batched_kernel(
       int64_t I, J;
       tri_tile(w - __ldg(prefix + k), I, J);
       __syncthreads();
-      sym_tile<Form, OutT, WARPS>(sm.tile, sm.locs, sm.n, I, J, sm.sigma2, sm.beta, sm.nu,
+      sym_tile<Form, OutT, WARPS>(form, sm.tile, sm.locs, sm.n, I, J, sm.sigma2, sm.beta, sm.nu,
                                   sm.log_pref, sm.out, sm.ld, tl, evals);
     }
   }
@@ -121,12 +121,19 @@ struct bk_plan {
 namespace bk {
 namespace {
 
+template <class Form>
+Form make_form(const bk_plan*) { return Form{}; }
+template <>
+FormF32Learned make_form<FormF32Learned>(const bk_plan* p) {
+  return FormF32Learned{learned_view(p->opts.learned)};
+}
+
 template <class Form, typename OutT, int WARPS>
 cudaError_t launch_batched_t(const bk_plan* p, const bk_matern_desc* d, int64_t limit,
                              int ctas_per_sm, int chunk, cudaStream_t s) {
   const int grid = current_sm_count() * ctas_per_sm;
   matern_batched_kernel<Form, OutT, WARPS><<<grid, WARPS * 32, 0, s>>>(
-      d, p->count, p->d_prefix, p->d_sizes, limit, p->d_next, chunk, p->opts.d_counters);
+      make_form<Form>(p), d, p->count, p->d_prefix, p->d_sizes, limit, p->d_next, chunk, p->opts.d_counters);
   return cudaGetLastError();
 }
 
@@ -142,9 +149,15 @@ cudaError_t launch_batched(const bk_plan* p, const bk_matern_desc* d, int64_t li
   cudaError_t e = cudaMemsetAsync(p->d_next, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   const bool f64 = (p->opts.compute == BK_F64);
-  if (p->dtype == BK_F64)
+  const bool learned = (p->opts.window == BK_WIN_LEARNED);
+  if (p->dtype == BK_F64) {
+    if (learned)
+      return launch_batched_w<FormF32Learned, double>(p, d, limit, warps, ctas_per_sm, chunk, s);
     return f64 ? launch_batched_w<FormF64, double>(p, d, limit, warps, ctas_per_sm, chunk, s)
                : launch_batched_w<FormF32, double>(p, d, limit, warps, ctas_per_sm, chunk, s);
+  }
+  if (learned)
+    return launch_batched_w<FormF32Learned, float>(p, d, limit, warps, ctas_per_sm, chunk, s);
   return f64 ? launch_batched_w<FormF64, float>(p, d, limit, warps, ctas_per_sm, chunk, s)
              : launch_batched_w<FormF32, float>(p, d, limit, warps, ctas_per_sm, chunk, s);
 }
@@ -153,7 +166,14 @@ int max_ctas_per_sm(const bk_plan* p, int warps) {
   int blocks = 0;
   const void* fn = nullptr;
   const bool f64 = (p->opts.compute == BK_F64);
-  if (p->dtype == BK_F64) {
+  if (p->opts.window == BK_WIN_LEARNED) {
+    if (p->dtype == BK_F64)
+      fn = (warps == 4) ? (const void*)matern_batched_kernel<FormF32Learned, double, 4>
+                        : (const void*)matern_batched_kernel<FormF32Learned, double, 8>;
+    else
+      fn = (warps == 4) ? (const void*)matern_batched_kernel<FormF32Learned, float, 4>
+                        : (const void*)matern_batched_kernel<FormF32Learned, float, 8>;
+  } else if (p->dtype == BK_F64) {
     if (warps == 4) fn = f64 ? (const void*)matern_batched_kernel<FormF64, double, 4>
                              : (const void*)matern_batched_kernel<FormF32, double, 4>;
     else fn = f64 ? (const void*)matern_batched_kernel<FormF64, double, 8>
@@ -232,8 +252,8 @@ std::string make_key(const bk_plan* p) {
   int bucket = 0;
   while ((1LL << bucket) < p->total_tiles) ++bucket;
   char buf[256];
-  std::snprintf(buf, sizeof(buf), "%s|out%d|compute%d|tiles2^%d", name.c_str(), (int)p->dtype,
-                (int)p->opts.compute, bucket);
+  std::snprintf(buf, sizeof(buf), "%s|out%d|compute%d|win%d|tiles2^%d", name.c_str(),
+                (int)p->dtype, (int)p->opts.compute, (int)p->opts.window, bucket);
   return std::string(buf);
 }
 
@@ -257,8 +277,11 @@ bk_status bk_batched_plan_create(bk_plan** plan, const int64_t* sizes, int32_t c
   if (opts != nullptr) o = *opts; else o.compute = dtype;
   if (o.compute != BK_F64 && o.compute != BK_F32)
     return set_error(BK_ERR_INVALID_ARG, "opts.compute: unknown dtype %d", (int)o.compute);
-  if (o.window != BK_WIN_SEARCH)
-    return set_error(BK_ERR_UNSUPPORTED, "batched: this build supports window=SEARCH only");
+  if (o.window == BK_WIN_FIXED)
+    return set_error(BK_ERR_UNSUPPORTED, "batched: the fixed window is not built in this version");
+  if (o.window == BK_WIN_LEARNED && (o.compute != BK_F32 || !learned_ready(o.learned)))
+    return set_error(o.compute != BK_F32 ? BK_ERR_UNSUPPORTED : BK_ERR_NOT_LOADED,
+                     "batched: the learned window needs compute = BK_F32 and a network with weights");
   std::vector<int64_t> prefix((size_t)count + 1, 0);
   for (int32_t k = 0; k < count; ++k) {
     if (sizes[k] < 0) return set_error(BK_ERR_INVALID_ARG, "sizes[%d] < 0", (int)k);
@@ -474,7 +497,7 @@ __global__ void __launch_bounds__(WARPS * 32) matern_batched_static_kernel(
   const int64_t* sizes = (const int64_t*)(scratch + kStaticSizesOff);
   const int64_t limit = prefix[count];
   __shared__ BatchSmem<OutT> sm;
-  Tally tl{0u, 0u, 0u, 0u};
+  Tally tl{0u, 0u, 0u, 0u, 0u};
   unsigned evals = 0;
   int cur = -1;
   while (true) {
@@ -506,7 +529,7 @@ __global__ void __launch_bounds__(WARPS * 32) matern_batched_static_kernel(
     int64_t I, J;
     tri_tile(w - prefix[k], I, J);
     __syncthreads();
-    sym_tile<Form, OutT, WARPS>(sm.tile, sm.locs, sm.n, I, J, sm.sigma2, sm.beta, sm.nu,
+    sym_tile<Form, OutT, WARPS>(Form{}, sm.tile, sm.locs, sm.n, I, J, sm.sigma2, sm.beta, sm.nu,
                                 sm.log_pref, sm.out, sm.ld, tl, evals);
   }
 }

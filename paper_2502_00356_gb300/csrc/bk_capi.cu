@@ -59,8 +59,15 @@ bk_status check_opts(const bk_opts* o) {
     return set_error(BK_ERR_INVALID_ARG, "opts.compute: unknown dtype %d", (int)o->compute);
   if (o->window == BK_WIN_FIXED && (o->fixed_bins < 1 || !(o->fixed_t1 > 0.0) || !finite(o->fixed_t1)))
     return set_error(BK_ERR_INVALID_ARG, "opts: fixed window needs fixed_bins >= 1 and fixed_t1 > 0");
-  if (o->window != BK_WIN_SEARCH)
-    return set_error(BK_ERR_UNSUPPORTED, "this build supports window=SEARCH only");
+  if (o->window == BK_WIN_FIXED)
+    return set_error(BK_ERR_UNSUPPORTED, "the fixed window is not built in this version");
+  if (o->window == BK_WIN_LEARNED) {
+    if (o->compute != BK_F32)
+      return set_error(BK_ERR_UNSUPPORTED, "the learned window needs compute = BK_F32 "
+                                           "(the network is trained on eps = 2^-23 windows)");
+    if (!learned_ready(o->learned))
+      return set_error(BK_ERR_NOT_LOADED, "opts.learned has no trained or loaded weights");
+  }
   return BK_OK;
 }
 
@@ -105,6 +112,7 @@ void bk_opts_default(bk_opts* o) {
   o->fixed_bins = 40;
   o->fixed_t1 = 9.0;
   o->d_counters = nullptr;
+  o->learned = nullptr;
 }
 
 const char* bk_version(void) { return "libbesselk 0.1.0 (sm_103a)"; }
@@ -140,10 +148,13 @@ bk_status bk_eval_ex(const double* x, const double* nu, void* out, void* log_out
   if (n == 0) return BK_OK;
   if (x == nullptr || nu == nullptr || out == nullptr)
     return set_error(BK_ERR_INVALID_ARG, "x, nu and out must be non-NULL when n > 0");
+  cudaStream_t s = (cudaStream_t)stream;
   const cudaError_t e =
-      (o.compute == BK_F64)
-          ? launch_eval_f64(x, nu, out, log_out, out_dtype, n, o.d_counters, (cudaStream_t)stream)
-          : launch_eval_f32(x, nu, out, log_out, out_dtype, n, o.d_counters, (cudaStream_t)stream);
+      (o.window == BK_WIN_LEARNED)
+          ? launch_eval_learned(o.learned, x, nu, out, log_out, out_dtype, n, o.d_counters, s)
+      : (o.compute == BK_F64)
+          ? launch_eval_f64(x, nu, out, log_out, out_dtype, n, o.d_counters, s)
+          : launch_eval_f32(x, nu, out, log_out, out_dtype, n, o.d_counters, s);
   return check_cuda(e, "bk_eval launch");
 }
 
@@ -165,12 +176,14 @@ bk_status bk_matern_tile_ex(const double* locs, int64_t n, double sigma2, double
   if ((st = check_opts(&o)) != BK_OK) return st;
   if (n == 0) return BK_OK;
   if (locs == nullptr) return set_error(BK_ERR_INVALID_ARG, "locs is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
   const cudaError_t e =
-      (o.compute == BK_F64)
-          ? launch_matern_sym_f64(locs, n, sigma2, beta, nu, out, ld, dtype, o.d_counters,
-                                  (cudaStream_t)stream)
-          : launch_matern_sym_f32(locs, n, sigma2, beta, nu, out, ld, dtype, o.d_counters,
-                                  (cudaStream_t)stream);
+      (o.window == BK_WIN_LEARNED)
+          ? launch_matern_sym_learned(o.learned, locs, n, sigma2, beta, nu, out, ld, dtype,
+                                      o.d_counters, s)
+      : (o.compute == BK_F64)
+          ? launch_matern_sym_f64(locs, n, sigma2, beta, nu, out, ld, dtype, o.d_counters, s)
+          : launch_matern_sym_f32(locs, n, sigma2, beta, nu, out, ld, dtype, o.d_counters, s);
   return check_cuda(e, "bk_matern_tile launch");
 }
 
@@ -193,12 +206,16 @@ bk_status bk_matern_tile2(const double* locs1, int64_t m, const double* locs2, i
   if (m == 0 || n == 0) return BK_OK;
   if (locs1 == nullptr || locs2 == nullptr)
     return set_error(BK_ERR_INVALID_ARG, "locs1 and locs2 must be non-NULL");
+  cudaStream_t s = (cudaStream_t)stream;
   const cudaError_t e =
-      (o.compute == BK_F64)
+      (o.window == BK_WIN_LEARNED)
+          ? launch_matern_block_learned(o.learned, locs1, m, locs2, n, sigma2, beta, nu, out, ld,
+                                        dtype, o.d_counters, s)
+      : (o.compute == BK_F64)
           ? launch_matern_block_f64(locs1, m, locs2, n, sigma2, beta, nu, out, ld, dtype,
-                                    o.d_counters, (cudaStream_t)stream)
+                                    o.d_counters, s)
           : launch_matern_block_f32(locs1, m, locs2, n, sigma2, beta, nu, out, ld, dtype,
-                                    o.d_counters, (cudaStream_t)stream);
+                                    o.d_counters, s);
   return check_cuda(e, "bk_matern_tile2 launch");
 }
 

@@ -45,4 +45,17 @@ cudaError_t launch_matern_block_f32(const double* locs1, int64_t m, const double
                                     int64_t ld, bk_dtype out_t, unsigned long long* ctr,
                                     cudaStream_t s);
 
+// ---- learned window (bk_learned.cu); `m` must have weights (learned_ready)
+bool learned_ready(const bk_learned* m);
+cudaError_t launch_eval_learned(const bk_learned* m, const double* x, const double* nu, void* out,
+                                void* log_out, bk_dtype out_t, int64_t n, unsigned long long* ctr,
+                                cudaStream_t s);
+cudaError_t launch_matern_sym_learned(const bk_learned* m, const double* locs, int64_t n,
+                                      double sigma2, double beta, double nu, void* out, int64_t ld,
+                                      bk_dtype out_t, unsigned long long* ctr, cudaStream_t s);
+cudaError_t launch_matern_block_learned(const bk_learned* m, const double* locs1, int64_t m_,
+                                        const double* locs2, int64_t n, double sigma2,
+                                        double beta, double nu, void* out, int64_t ld,
+                                        bk_dtype out_t, unsigned long long* ctr, cudaStream_t s);
+
 }  // namespace bk

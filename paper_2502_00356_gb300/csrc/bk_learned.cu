@@ -1,0 +1,671 @@
+// The learned window (a10, a11): a 2 -> 64 -> 64 -> 64 -> 4 tanh network
+// mapping (ln x, nu) to (t*, t* - t0, t1 - t*, ln N) of the eps = 2^-23
+// window, trained on the GPU by the kernels below (fused forward/backward per
+// 128-sample chunk, Adam), then tabulated on a (ln x, nu) grid by the
+// inference kernel for the FP32 form's kernels to interpolate and check.
+//
+// Parameters: one flat float array, W1 (64x2), b1, W2 (64x64), b2, W3 (64x64),
+// b3, W4 (4x64), b4, each W row-major as W[out][in] (8772 floats).
+// Inputs: u_x = (ln x - c_x)/s_x, u_nu = (nu - c_nu)/s_nu mapping
+// [ln 1e-3, ln 140] x [0.05, 20] onto [-1, 1]^2.  Targets are standardised
+// with their mean and standard deviation over the training set.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "bk_forms.cuh"
+#include "bk_internal.h"
+#include "bk_tiles.cuh"
+
+namespace bk {
+
+constexpr int kH = 64;
+constexpr int kOffW1 = 0, kOffB1 = 128, kOffW2 = 192, kOffB2 = 4288, kOffW3 = 4352,
+              kOffB3 = 8448, kOffW4 = 8512, kOffB4 = 8768, kNParams = 8772;
+constexpr float kUxC = 0.5f * (kTabLx0 + kTabLx1), kUxS = 0.5f * (kTabLx1 - kTabLx0);
+constexpr float kUnC = 0.5f * (kTabNu0 + kTabNu1), kUnS = 0.5f * (kTabNu1 - kTabNu0);
+constexpr int kChunk = 128;     // samples per CTA in training
+constexpr int kTrainThreads = 256;
+constexpr int kWStride = kH + 1;  // padded rows of the transposed weights in shared memory
+
+// Counter-based hash (SplitMix64 finaliser): the k-th draw of stream `seed`.
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// ---- initialisation: Glorot-uniform weights, zero biases
+__global__ void mlp_init_kernel(float* __restrict__ p, uint64_t seed) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kNParams) return;
+  float fan_in, fan_out;
+  if (i < kOffB1) { fan_in = 2; fan_out = kH; }
+  else if (i < kOffW2) { p[i] = 0.0f; return; }
+  else if (i < kOffB2) { fan_in = kH; fan_out = kH; }
+  else if (i < kOffW3) { p[i] = 0.0f; return; }
+  else if (i < kOffB3) { fan_in = kH; fan_out = kH; }
+  else if (i < kOffW4) { p[i] = 0.0f; return; }
+  else if (i < kOffB4) { fan_in = kH; fan_out = 4; }
+  else { p[i] = 0.0f; return; }
+  const float a = sqrtf(6.0f / (fan_in + fan_out));
+  const double u = (double)(mix64(seed * 0x100000001B3ull + (uint64_t)i) >> 11) * 0x1.0p-53;
+  p[i] = (float)((2.0 * u - 1.0) * a);
+}
+
+// ---- targets from oracle labels (rows t*, t0, t1, g(t*), N, ...; 6 doubles)
+__device__ __forceinline__ void label_targets(const double* __restrict__ lab, float t[4]) {
+  t[0] = (float)lab[0];
+  t[1] = (float)(lab[0] - lab[1]);
+  t[2] = (float)(lab[2] - lab[0]);
+  t[3] = logf((float)fmax(lab[4], 1.0));
+}
+
+// Sums and sums of squares of the four targets (double atomics into acc[8]).
+__global__ void target_stats_kernel(const double* __restrict__ labels, int64_t n,
+                                    double* __restrict__ acc) {
+  double s[4] = {0, 0, 0, 0}, q[4] = {0, 0, 0, 0};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float t[4];
+    label_targets(labels + 6 * i, t);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      s[k] += t[k];
+      q[k] += (double)t[k] * t[k];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    double a = s[k], b = q[k];
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, o);
+      b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(acc + k, a);
+      atomicAdd(acc + 4 + k, b);
+    }
+  }
+}
+
+__global__ void target_stats_finish_kernel(const double* __restrict__ acc, int64_t n,
+                                           float* __restrict__ stats) {
+  const int k = threadIdx.x;
+  if (k >= 4) return;
+  const double m = acc[k] / (double)n;
+  const double v = fmax(acc[4 + k] / (double)n - m * m, 1e-12);
+  stats[k] = (float)m;
+  stats[4 + k] = (float)sqrt(v);
+}
+
+// ---- training step: forward, MSE gradient and backward for 128 samples per
+// CTA, parameters' gradients added atomically to grad; partial loss to *loss.
+struct TrainSmem {
+  float Wt1[2 * kH], b1[kH];
+  float Wt2[kH * kWStride], b2[kH];   // transposed: Wt[k][j] = W[j][k], row stride 65
+  float Wt3[kH * kWStride], b3[kH];
+  float W4[4 * kH], b4[4];
+  float U[kChunk][2], T[kChunk][4], DY[kChunk][4];
+  float H1[kChunk][kH], H2[kChunk][kH], H3[kChunk][kH];
+};
+
+__device__ __forceinline__ void load_params(TrainSmem& s, const float* __restrict__ p) {
+  for (int i = threadIdx.x; i < kNParams; i += blockDim.x) {
+    const float v = p[i];
+    if (i < kOffB1) { const int j = i / 2, k = i % 2; s.Wt1[k * kH + j] = v; }
+    else if (i < kOffW2) s.b1[i - kOffB1] = v;
+    else if (i < kOffB2) { const int r = i - kOffW2, j = r / kH, k = r % kH; s.Wt2[k * kWStride + j] = v; }
+    else if (i < kOffW3) s.b2[i - kOffB2] = v;
+    else if (i < kOffB3) { const int r = i - kOffW3, j = r / kH, k = r % kH; s.Wt3[k * kWStride + j] = v; }
+    else if (i < kOffW4) s.b3[i - kOffB3] = v;
+    else if (i < kOffB4) s.W4[i - kOffW4] = v;
+    else s.b4[i - kOffB4] = v;
+  }
+}
+
+// out[s][j] = tanh(b[j] + sum_k Wt[k][j] in[s][k]) for the 128 samples.
+__device__ __forceinline__ void dense_tanh(const float* __restrict__ Wt, int wstride,
+                                           const float* __restrict__ b,
+                                           const float (*in)[kH], float (*out)[kH]) {
+  const int j = threadIdx.x & (kH - 1), sg = threadIdx.x >> 6;
+  float acc[kChunk / 4];
+#pragma unroll
+  for (int i = 0; i < kChunk / 4; ++i) acc[i] = b[j];
+  for (int k = 0; k < kH; ++k) {
+    const float w = Wt[k * wstride + j];
+#pragma unroll
+    for (int i = 0; i < kChunk / 4; ++i) acc[i] = fmaf(w, in[sg + 4 * i][k], acc[i]);
+  }
+#pragma unroll
+  for (int i = 0; i < kChunk / 4; ++i) out[sg + 4 * i][j] = tanhf(acc[i]);
+}
+
+// gradW[j][k] += sum_s D[s][j] X[s][k] (X has 64 columns).
+__device__ __forceinline__ void grad_w(float* __restrict__ g, const float (*D)[kH],
+                                       const float (*X)[kH]) {
+  const int k = threadIdx.x & (kH - 1), jg = threadIdx.x >> 6;
+  float acc[kH / 4];
+#pragma unroll
+  for (int i = 0; i < kH / 4; ++i) acc[i] = 0.0f;
+  for (int s = 0; s < kChunk; ++s) {
+    const float xv = X[s][k];
+#pragma unroll
+    for (int i = 0; i < kH / 4; ++i) acc[i] = fmaf(D[s][jg + 4 * i], xv, acc[i]);
+  }
+#pragma unroll
+  for (int i = 0; i < kH / 4; ++i) atomicAdd(g + (jg + 4 * i) * kH + k, acc[i]);
+}
+
+// db[j] += sum_s D[s][j]
+__device__ __forceinline__ void grad_b(float* __restrict__ g, const float (*D)[kH]) {
+  if (threadIdx.x < kH) {
+    float a = 0.0f;
+    for (int s = 0; s < kChunk; ++s) a += D[s][threadIdx.x];
+    atomicAdd(g + threadIdx.x, a);
+  }
+}
+
+// D_in[s][k] = (sum_j W[j][k] D_out[s][j]) (1 - H[s][k]^2), in place over H.
+__device__ __forceinline__ void back_tanh(const float* __restrict__ Wt, const float (*Dout)[kH],
+                                          float (*H)[kH]) {
+  const int k = threadIdx.x & (kH - 1), sg = threadIdx.x >> 6;
+  float acc[kChunk / 4];
+#pragma unroll
+  for (int i = 0; i < kChunk / 4; ++i) acc[i] = 0.0f;
+  for (int j = 0; j < kH; ++j) {
+    const float w = Wt[k * kWStride + j];  // W[j][k]
+#pragma unroll
+    for (int i = 0; i < kChunk / 4; ++i) acc[i] = fmaf(w, Dout[sg + 4 * i][j], acc[i]);
+  }
+  __syncthreads();  // every thread has read Dout before H (which may alias it) is overwritten
+#pragma unroll
+  for (int i = 0; i < kChunk / 4; ++i) {
+    const float h = H[sg + 4 * i][k];
+    H[sg + 4 * i][k] = acc[i] * (1.0f - h * h);
+  }
+}
+
+__global__ void __launch_bounds__(kTrainThreads) mlp_train_kernel(
+    const float* __restrict__ params, float* __restrict__ grad, const double* __restrict__ x,
+    const double* __restrict__ nu, const double* __restrict__ labels, int64_t n,
+    const float* __restrict__ stats, int batch, uint64_t seed, uint64_t step,
+    float* __restrict__ loss) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TrainSmem& s = *reinterpret_cast<TrainSmem*>(smem_raw);
+  load_params(s, params);
+  // samples drawn with replacement: index = hash(seed, step, position) mod n
+  if (threadIdx.x < kChunk) {
+    const int pos = blockIdx.x * kChunk + threadIdx.x;
+    // step == ~0 selects the samples 0 .. batch-1 in order (full-batch gradient)
+    const uint64_t h = mix64(seed ^ mix64(step * 0x9E3779B97F4A7C15ull + (uint64_t)pos));
+    const int64_t i = (step == ~0ull) ? (int64_t)pos : (int64_t)(h % (uint64_t)n);
+    s.U[threadIdx.x][0] = ((float)log(x[i]) - kUxC) / kUxS;
+    s.U[threadIdx.x][1] = ((float)nu[i] - kUnC) / kUnS;
+    float t[4];
+    label_targets(labels + 6 * i, t);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) s.T[threadIdx.x][k] = (t[k] - stats[k]) / stats[4 + k];
+  }
+  __syncthreads();
+  // layer 1 (2 inputs)
+  {
+    const int j = threadIdx.x & (kH - 1), sg = threadIdx.x >> 6;
+    for (int i = 0; i < kChunk / 4; ++i) {
+      const int sm = sg + 4 * i;
+      s.H1[sm][j] = tanhf(fmaf(s.Wt1[j], s.U[sm][0], fmaf(s.Wt1[kH + j], s.U[sm][1], s.b1[j])));
+    }
+  }
+  __syncthreads();
+  dense_tanh(s.Wt2, kWStride, s.b2, s.H1, s.H2);
+  __syncthreads();
+  dense_tanh(s.Wt3, kWStride, s.b3, s.H2, s.H3);
+  __syncthreads();
+  // output layer and dL/dy for L = mean over batch and 4 outputs of (y - t)^2
+  float lsum = 0.0f;
+  for (int e = threadIdx.x; e < kChunk * 4; e += blockDim.x) {
+    const int sm = e >> 2, o = e & 3;
+    float y = s.b4[o];
+    for (int k = 0; k < kH; ++k) y = fmaf(s.W4[o * kH + k], s.H3[sm][k], y);
+    const float r = y - s.T[sm][o];
+    s.DY[sm][o] = 2.0f * r / (float)(batch * 4);
+    lsum += r * r;
+  }
+  for (int o = 16; o > 0; o >>= 1) lsum += __shfl_down_sync(0xffffffffu, lsum, o);
+  if ((threadIdx.x & 31) == 0 && loss != nullptr) atomicAdd(loss, lsum / (float)(batch * 4));
+  __syncthreads();
+  // W4, b4 gradients
+  for (int e = threadIdx.x; e < 4 * kH; e += blockDim.x) {
+    const int o = e / kH, k = e % kH;
+    float a = 0.0f;
+    for (int sm = 0; sm < kChunk; ++sm) a = fmaf(s.DY[sm][o], s.H3[sm][k], a);
+    atomicAdd(grad + kOffW4 + e, a);
+  }
+  if (threadIdx.x < 4) {
+    float a = 0.0f;
+    for (int sm = 0; sm < kChunk; ++sm) a += s.DY[sm][threadIdx.x];
+    atomicAdd(grad + kOffB4 + threadIdx.x, a);
+  }
+  __syncthreads();
+  // D3 = (W4^T dy) (1 - h3^2), in place over H3
+  {
+    const int k = threadIdx.x & (kH - 1), sg = threadIdx.x >> 6;
+    for (int i = 0; i < kChunk / 4; ++i) {
+      const int sm = sg + 4 * i;
+      float a = 0.0f;
+#pragma unroll
+      for (int o = 0; o < 4; ++o) a = fmaf(s.W4[o * kH + k], s.DY[sm][o], a);
+      const float h = s.H3[sm][k];
+      s.H3[sm][k] = a * (1.0f - h * h);
+    }
+  }
+  __syncthreads();
+  grad_w(grad + kOffW3, s.H3, s.H2);
+  grad_b(grad + kOffB3, s.H3);
+  __syncthreads();
+  back_tanh(s.Wt3, s.H3, s.H2);  // D2 over H2
+  __syncthreads();
+  grad_w(grad + kOffW2, s.H2, s.H1);
+  grad_b(grad + kOffB2, s.H2);
+  __syncthreads();
+  back_tanh(s.Wt2, s.H2, s.H1);  // D1 over H1
+  __syncthreads();
+  // W1 (64 x 2), b1
+  for (int e = threadIdx.x; e < 2 * kH; e += blockDim.x) {
+    const int j = e / 2, k = e % 2;
+    float a = 0.0f;
+    for (int sm = 0; sm < kChunk; ++sm) a = fmaf(s.H1[sm][j], s.U[sm][k], a);
+    atomicAdd(grad + kOffW1 + e, a);
+  }
+  grad_b(grad + kOffB1, s.H1);
+}
+
+// Adam (Kingma & Ba 2015) with bias correction; zeroes the gradient.
+__global__ void adam_kernel(float* __restrict__ p, float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, float lr, float b1, float b2, float eps,
+                            float c1, float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kNParams) return;
+  const float gi = g[i];
+  const float mi = fmaf(b1, m[i], (1.0f - b1) * gi);
+  const float vi = fmaf(b2, v[i], (1.0f - b2) * gi * gi);
+  m[i] = mi;
+  v[i] = vi;
+  p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  g[i] = 0.0f;
+}
+
+// Per-point forward (SIMT): standardised network outputs for inputs u.
+__device__ __forceinline__ void mlp_point(const float* __restrict__ p, float u0, float u1,
+                                          float y[4]) {
+  float h1[kH], h2[kH];
+#pragma unroll 4
+  for (int j = 0; j < kH; ++j)
+    h1[j] = tanhf(fmaf(__ldg(p + kOffW1 + 2 * j), u0,
+                       fmaf(__ldg(p + kOffW1 + 2 * j + 1), u1, __ldg(p + kOffB1 + j))));
+  for (int j = 0; j < kH; ++j) {
+    float a = __ldg(p + kOffB2 + j);
+#pragma unroll 8
+    for (int k = 0; k < kH; ++k) a = fmaf(__ldg(p + kOffW2 + j * kH + k), h1[k], a);
+    h2[j] = tanhf(a);
+  }
+  for (int j = 0; j < kH; ++j) {
+    float a = __ldg(p + kOffB3 + j);
+#pragma unroll 8
+    for (int k = 0; k < kH; ++k) a = fmaf(__ldg(p + kOffW3 + j * kH + k), h2[k], a);
+    h1[j] = tanhf(a);  // h3
+  }
+#pragma unroll
+  for (int o = 0; o < 4; ++o) {
+    float a = __ldg(p + kOffB4 + o);
+#pragma unroll 8
+    for (int k = 0; k < kH; ++k) a = fmaf(__ldg(p + kOffW4 + o * kH + k), h1[k], a);
+    y[o] = a;
+  }
+}
+
+// Network outputs, de-standardised, on the (ln x, nu) grid of the table.
+__global__ void mlp_table_kernel(const float* __restrict__ p, const float* __restrict__ stats,
+                                 float4* __restrict__ table) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kTabX * kTabNu) return;
+  const int ix = i % kTabX, in = i / kTabX;
+  const float lx = kTabLx0 + (kTabLx1 - kTabLx0) * (float)ix / (float)(kTabX - 1);
+  const float nv = kTabNu0 + (kTabNu1 - kTabNu0) * (float)in / (float)(kTabNu - 1);
+  float y[4];
+  mlp_point(p, (lx - kUxC) / kUxS, (nv - kUnC) / kUnS, y);
+  table[i] = make_float4(fmaf(y[0], stats[4], stats[0]), fmaf(y[1], stats[5], stats[1]),
+                         fmaf(y[2], stats[6], stats[2]), fmaf(y[3], stats[7], stats[3]));
+}
+
+// Per-point inference for arbitrary (x, nu): out[4 i ..] = (t*, t0, t1, N).
+__global__ void mlp_infer_kernel(const float* __restrict__ p, const float* __restrict__ stats,
+                                 const double* __restrict__ x, const double* __restrict__ nu,
+                                 float* __restrict__ out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float y[4];
+  mlp_point(p, ((float)log(x[i]) - kUxC) / kUxS, ((float)nu[i] - kUnC) / kUnS, y);
+  const float ts = fmaf(y[0], stats[4], stats[0]);
+  out[4 * i + 0] = ts;
+  out[4 * i + 1] = ts - fmaf(y[1], stats[5], stats[1]);
+  out[4 * i + 2] = ts + fmaf(y[2], stats[6], stats[2]);
+  out[4 * i + 3] = expf(fmaf(y[3], stats[7], stats[3]));
+}
+
+// The training kernel needs more than 48 KB of dynamic shared memory: opt in
+// once per device.
+cudaError_t set_train_smem() {
+  static bool done[64] = {false};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+  e = cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(TrainSmem));
+  if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
+  return e;
+}
+
+}  // namespace bk
+
+// ---------------------------------------------------------------------------
+struct bk_learned {
+  int device;
+  float* d_params;
+  float* d_grad;
+  float* d_m;
+  float* d_v;
+  float* d_stats;   // mean[4], std[4]
+  double* d_acc;    // 8 accumulators for the statistics
+  float4* d_table;  // kTabNu x kTabX
+  int64_t step;
+  uint64_t seed;
+  int has_stats;
+  float margin_rel, margin_abs;
+};
+
+namespace bk {
+namespace {
+
+constexpr char kMagic[8] = {'B', 'K', 'W', 'I', 'N', 'D', '0', '1'};
+
+uint64_t fnv1a(const unsigned char* d, size_t n, uint64_t h = 1469598103934665603ull) {
+  for (size_t i = 0; i < n; ++i) {
+    h ^= d[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+cudaError_t build_table(bk_learned* m, cudaStream_t s) {
+  const int n = kTabX * kTabNu;
+  mlp_table_kernel<<<(n + 127) / 128, 128, 0, s>>>(m->d_params, m->d_stats, m->d_table);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+LearnedView learned_view(const bk_learned* m) {
+  LearnedView v;
+  v.table = m->d_table;
+  v.margin_rel = m->margin_rel;
+  v.margin_abs = m->margin_abs;
+  return v;
+}
+
+bool learned_ready(const bk_learned* m) { return m != nullptr && m->has_stats; }
+
+cudaError_t launch_eval_learned(const bk_learned* m, const double* x, const double* nu, void* out,
+                                void* log_out, bk_dtype out_t, int64_t n, unsigned long long* ctr,
+                                cudaStream_t s) {
+  return launch_eval_form(FormF32Learned{learned_view(m)}, x, nu, out, log_out, out_t, n, ctr, s);
+}
+
+cudaError_t launch_matern_sym_learned(const bk_learned* m, const double* locs, int64_t n,
+                                      double sigma2, double beta, double nu, void* out, int64_t ld,
+                                      bk_dtype out_t, unsigned long long* ctr, cudaStream_t s) {
+  return launch_matern_sym_form(FormF32Learned{learned_view(m)}, locs, n, sigma2, beta, nu, out,
+                                ld, out_t, ctr, s);
+}
+
+cudaError_t launch_matern_block_learned(const bk_learned* m, const double* locs1, int64_t m_,
+                                        const double* locs2, int64_t n, double sigma2,
+                                        double beta, double nu, void* out, int64_t ld,
+                                        bk_dtype out_t, unsigned long long* ctr, cudaStream_t s) {
+  return launch_matern_block_form(FormF32Learned{learned_view(m)}, locs1, m_, locs2, n, sigma2,
+                                  beta, nu, out, ld, out_t, ctr, s);
+}
+
+}  // namespace bk
+
+using namespace bk;
+
+extern "C" {
+
+bk_status bk_learned_create(bk_learned** model, uint64_t seed) {
+  if (model == nullptr) return set_error(BK_ERR_INVALID_ARG, "model is NULL");
+  *model = nullptr;
+  bk_learned* m = new bk_learned();
+  std::memset(m, 0, sizeof(*m));
+  m->seed = seed;
+  m->margin_rel = 0.05f;
+  m->margin_abs = 0.02f;
+  cudaError_t e = cudaGetDevice(&m->device);
+  const size_t pb = kNParams * sizeof(float);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&m->d_params, pb);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&m->d_grad, pb);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&m->d_m, pb);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&m->d_v, pb);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&m->d_stats, 8 * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&m->d_acc, 8 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&m->d_table, (size_t)kTabX * kTabNu * sizeof(float4));
+  if (e == cudaSuccess) e = cudaMemset(m->d_grad, 0, pb);
+  if (e == cudaSuccess) e = cudaMemset(m->d_m, 0, pb);
+  if (e == cudaSuccess) e = cudaMemset(m->d_v, 0, pb);
+  if (e == cudaSuccess) {
+    mlp_init_kernel<<<(kNParams + 255) / 256, 256>>>(m->d_params, seed);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    bk_learned_destroy(m);
+    return check_cuda(e, "bk_learned_create");
+  }
+  *model = m;
+  return BK_OK;
+}
+
+bk_status bk_learned_destroy(bk_learned* m) {
+  if (m == nullptr) return BK_OK;
+  cudaFree(m->d_params);
+  cudaFree(m->d_grad);
+  cudaFree(m->d_m);
+  cudaFree(m->d_v);
+  cudaFree(m->d_stats);
+  cudaFree(m->d_acc);
+  cudaFree(m->d_table);
+  delete m;
+  return BK_OK;
+}
+
+bk_status bk_learned_train(bk_learned* m, const double* d_x, const double* d_nu,
+                           const double* d_labels, int64_t n, int32_t steps, int32_t batch,
+                           float lr, uint64_t seed, float* d_loss, bk_stream_t stream) {
+  if (m == nullptr) return set_error(BK_ERR_INVALID_ARG, "model is NULL");
+  if (n < 1 || steps < 0 || batch < kChunk || batch % kChunk != 0 || !(lr > 0.0f))
+    return set_error(BK_ERR_INVALID_ARG,
+                     "bk_learned_train: need n >= 1, steps >= 0, batch a positive multiple of %d, "
+                     "lr > 0", kChunk);
+  if (d_x == nullptr || d_nu == nullptr || d_labels == nullptr)
+    return set_error(BK_ERR_INVALID_ARG, "bk_learned_train: NULL data");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = set_train_smem();
+  if (e != cudaSuccess) return check_cuda(e, "bk_learned_train: shared memory opt-in");
+  if (!m->has_stats) {
+    cudaMemsetAsync(m->d_acc, 0, 8 * sizeof(double), s);
+    const int grid = std::min<int64_t>((n + 255) / 256, (int64_t)current_sm_count() * 8);
+    target_stats_kernel<<<grid, 256, 0, s>>>(d_labels, n, m->d_acc);
+    target_stats_finish_kernel<<<1, 32, 0, s>>>(m->d_acc, n, m->d_stats);
+    m->has_stats = 1;
+  }
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  for (int32_t k = 0; k < steps; ++k) {
+    // cosine decay from lr to 0.05 lr over this call's steps
+    const float lrk = lr * (0.05f + 0.95f * 0.5f * (1.0f + cosf(3.14159265f * k / fmaxf(1.0f, (float)steps))));
+    mlp_train_kernel<<<batch / kChunk, kTrainThreads, sizeof(TrainSmem), s>>>(
+        m->d_params, m->d_grad, d_x, d_nu, d_labels, n, m->d_stats, batch, seed, (uint64_t)m->step,
+        d_loss != nullptr ? d_loss + k : nullptr);
+    m->step += 1;
+    const float c1 = 1.0f - powf(b1, (float)m->step), c2 = 1.0f - powf(b2, (float)m->step);
+    adam_kernel<<<(kNParams + 255) / 256, 256, 0, s>>>(m->d_params, m->d_grad, m->d_m, m->d_v, lrk,
+                                                       b1, b2, eps, c1, c2);
+  }
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = build_table(m, s);
+  return check_cuda(e, "bk_learned_train");
+}
+
+bk_status bk_learned_grad(bk_learned* m, const double* d_x, const double* d_nu,
+                          const double* d_labels, int64_t n, float* d_grad_out, float* d_loss,
+                          bk_stream_t stream) {
+  // The full-batch gradient of the training loss over the first n samples
+  // (n a multiple of 128), for checking the backward pass.
+  if (m == nullptr || d_grad_out == nullptr || n < kChunk || n % kChunk != 0)
+    return set_error(BK_ERR_INVALID_ARG, "bk_learned_grad: need a model, an output and n = 128 k");
+  if (!m->has_stats) return set_error(BK_ERR_NOT_LOADED, "bk_learned_grad: no target statistics");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = set_train_smem();
+  if (e != cudaSuccess) return check_cuda(e, "bk_learned_grad");
+  cudaMemsetAsync(d_grad_out, 0, kNParams * sizeof(float), s);
+  mlp_train_kernel<<<(int)(n / kChunk), kTrainThreads, sizeof(TrainSmem), s>>>(
+      m->d_params, d_grad_out, d_x, d_nu, d_labels, n, m->d_stats, (int)n, 0, ~0ull, d_loss);
+  return check_cuda(cudaGetLastError(), "bk_learned_grad");
+}
+
+bk_status bk_learned_infer(const bk_learned* m, const double* d_x, const double* d_nu,
+                           float* d_out, int64_t n, bk_stream_t stream) {
+  if (m == nullptr) return set_error(BK_ERR_INVALID_ARG, "model is NULL");
+  if (!m->has_stats) return set_error(BK_ERR_NOT_LOADED, "the window network has no weights");
+  if (n < 0) return set_error(BK_ERR_INVALID_ARG, "n < 0");
+  if (n == 0) return BK_OK;
+  if (d_x == nullptr || d_nu == nullptr || d_out == nullptr)
+    return set_error(BK_ERR_INVALID_ARG, "bk_learned_infer: NULL pointer");
+  mlp_infer_kernel<<<(unsigned)((n + 127) / 128), 128, 0, (cudaStream_t)stream>>>(
+      m->d_params, m->d_stats, d_x, d_nu, d_out, n);
+  return check_cuda(cudaGetLastError(), "bk_learned_infer");
+}
+
+bk_status bk_learned_params(bk_learned* m, float* h_get, const float* h_set) {
+  if (m == nullptr) return set_error(BK_ERR_INVALID_ARG, "model is NULL");
+  cudaError_t e = cudaSuccess;
+  if (h_get != nullptr) e = cudaMemcpy(h_get, m->d_params, kNParams * sizeof(float), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && h_set != nullptr) {
+    e = cudaMemcpy(m->d_params, h_set, kNParams * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && m->has_stats) e = build_table(m, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  }
+  return check_cuda(e, "bk_learned_params");
+}
+
+bk_status bk_learned_stats(bk_learned* m, float* h_get8, const float* h_set8) {
+  if (m == nullptr) return set_error(BK_ERR_INVALID_ARG, "model is NULL");
+  cudaError_t e = cudaSuccess;
+  if (h_get8 != nullptr) e = cudaMemcpy(h_get8, m->d_stats, 8 * sizeof(float), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && h_set8 != nullptr) {
+    e = cudaMemcpy(m->d_stats, h_set8, 8 * sizeof(float), cudaMemcpyHostToDevice);
+    m->has_stats = 1;
+    if (e == cudaSuccess) e = build_table(m, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  }
+  return check_cuda(e, "bk_learned_stats");
+}
+
+bk_status bk_learned_set_margins(bk_learned* m, float rel, float abs_) {
+  if (m == nullptr || !(rel >= 0.0f) || !(abs_ >= 0.0f))
+    return set_error(BK_ERR_INVALID_ARG, "bk_learned_set_margins: need a model and margins >= 0");
+  m->margin_rel = rel;
+  m->margin_abs = abs_;
+  return BK_OK;
+}
+
+// Checkpoint: magic, n_params, step, seed, stats[8], params, adam m, adam v,
+// FNV-1a 64 checksum of everything before it.
+bk_status bk_learned_save(const bk_learned* m, const char* path) {
+  if (m == nullptr || path == nullptr) return set_error(BK_ERR_INVALID_ARG, "model or path NULL");
+  if (!m->has_stats) return set_error(BK_ERR_NOT_LOADED, "nothing to save: untrained model");
+  std::vector<float> p(kNParams), mm(kNParams), vv(kNParams), st(8);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(p.data(), m->d_params, kNParams * 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(mm.data(), m->d_m, kNParams * 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(vv.data(), m->d_v, kNParams * 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(st.data(), m->d_stats, 32, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return check_cuda(e, "bk_learned_save");
+  std::vector<unsigned char> buf;
+  auto put = [&](const void* d, size_t n) {
+    const unsigned char* c = (const unsigned char*)d;
+    buf.insert(buf.end(), c, c + n);
+  };
+  const int64_t np = kNParams, step = m->step;
+  const uint64_t seed = m->seed;
+  put(kMagic, 8);
+  put(&np, 8);
+  put(&step, 8);
+  put(&seed, 8);
+  put(st.data(), 32);
+  put(p.data(), kNParams * 4);
+  put(mm.data(), kNParams * 4);
+  put(vv.data(), kNParams * 4);
+  const uint64_t h = fnv1a(buf.data(), buf.size());
+  put(&h, 8);
+  FILE* f = std::fopen(path, "wb");
+  if (f == nullptr) return set_error(BK_ERR_INVALID_ARG, "cannot open %s for writing", path);
+  const size_t w = std::fwrite(buf.data(), 1, buf.size(), f);
+  std::fclose(f);
+  if (w != buf.size()) return set_error(BK_ERR_INVALID_ARG, "short write to %s", path);
+  return BK_OK;
+}
+
+bk_status bk_learned_load(bk_learned* m, const char* path) {
+  if (m == nullptr || path == nullptr) return set_error(BK_ERR_INVALID_ARG, "model or path NULL");
+  FILE* f = std::fopen(path, "rb");
+  if (f == nullptr) return set_error(BK_ERR_INVALID_ARG, "cannot open %s", path);
+  std::vector<unsigned char> buf;
+  unsigned char tmp[65536];
+  size_t r;
+  while ((r = std::fread(tmp, 1, sizeof(tmp), f)) > 0) buf.insert(buf.end(), tmp, tmp + r);
+  std::fclose(f);
+  const size_t expect = 8 + 8 + 8 + 8 + 32 + 3 * (size_t)kNParams * 4 + 8;
+  if (buf.size() != expect || std::memcmp(buf.data(), kMagic, 8) != 0)
+    return set_error(BK_ERR_INVALID_ARG, "%s is not a window-network checkpoint", path);
+  uint64_t h;
+  std::memcpy(&h, buf.data() + expect - 8, 8);
+  if (h != fnv1a(buf.data(), expect - 8))
+    return set_error(BK_ERR_INVALID_ARG, "%s: checksum mismatch", path);
+  int64_t np, step;
+  std::memcpy(&np, buf.data() + 8, 8);
+  std::memcpy(&step, buf.data() + 16, 8);
+  if (np != kNParams) return set_error(BK_ERR_INVALID_ARG, "%s: wrong parameter count", path);
+  std::memcpy(&m->seed, buf.data() + 24, 8);
+  const unsigned char* st = buf.data() + 32;
+  const unsigned char* p = st + 32;
+  cudaError_t e = cudaMemcpy(m->d_stats, st, 32, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(m->d_params, p, kNParams * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(m->d_m, p + kNParams * 4, kNParams * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(m->d_v, p + 2 * kNParams * 4, kNParams * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(m->d_grad, 0, kNParams * 4);
+  if (e != cudaSuccess) return check_cuda(e, "bk_learned_load");
+  m->step = step;
+  m->has_stats = 1;
+  e = build_table(m, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  return check_cuda(e, "bk_learned_load");
+}
+
+}  // extern "C"

@@ -153,26 +153,48 @@ __device__ __forceinline__ Window32 window_f32(float x, float nu, Tally& tl) {
   return w;
 }
 
+// e^y - 1 with small relative error: Taylor polynomial to y^7 for |y| < 0.35
+// (truncation < 2e-8 relative), e^y - 1 on the MUFU above (no cancellation:
+// |e^y - 1| >= 0.29 there).
+__device__ __forceinline__ float expm1_f32(float y) {
+  const float poly =
+      y * fmaf(y, fmaf(y, fmaf(y, fmaf(y, fmaf(y, fmaf(y, 1.0f / 5040.0f, 1.0f / 720.0f),
+                                                   1.0f / 120.0f), 1.0f / 24.0f), 1.0f / 6.0f),
+                       0.5f), 1.0f);
+  return fabsf(y) < 0.35f ? poly : mufu_ex2(y * kLog2ef) - 1.0f;
+}
+
 // Scaled trapezoid sum of the FP32 form, with the weights of Eq. (refined):
-//   S = sum_j c_j exp(nu (t_j - ts) - x (cosh t_j - cosh ts)) (1 + e^{-2 nu t_j}),
-// c_0 = c_N = 1/2, the exponent in the difference form, e^{-2 nu t_j} by a
-// geometric recurrence and a Kahan-compensated sum.  Returns h S.
-__device__ __forceinline__ float trapezoid_f32(float x, float nu, const Window32& w, int N,
-                                               Tally& tl) {
+//   S = sum_j c_j exp(a_j) (1 + e^{-2 nu t_j}),  c_0 = c_N = 1/2,
+//   a_j = nu tau_j - x (cosh t_j - cosh ts),  tau_j = t_j - ts = (t0 - ts) + j h.
+// Peak-relative nodes keep nu tau_j and the spacing accurate near the peak.
+// The cosh difference is written so that no large argument enters an FP32
+// exponential: with A = x e^{ts}/2 and B = x e^{-ts}/2 (from FP64),
+//   x (cosh t - cosh ts) = A expm1(tau) + B expm1(-tau),
+// and at ts = 0, x (cosh tau - 1) = 2 x sinh^2(tau/2).  (sinh(ts + tau/2) in
+// FP32 would carry an argument error of ulp(ts) ~ 1e-6 at ts ~ 10, times
+// A ~ nu in the exponent.)  e^{-2 nu t_j} follows a geometric recurrence; the
+// sum is Kahan-compensated.  The order enters as nu_hi + nu_lo (the FP64
+// order split into two floats): rounding nu itself to FP32 would integrate
+// K of a neighbouring order, off by ulp(nu) d(log K)/d nu ~ ulp(nu) ln(2 nu/x),
+// ~1e-5 at x ~ 1e-3, nu ~ 18.  Returns h S.
+__device__ __forceinline__ float trapezoid_f32(float x, float nu, float nu_lo, const Window32& w,
+                                               float Ah, float Bh, int N, Tally& tl) {
   const float h = (w.t1 - w.t0) / (float)N;
+  const float tau0 = w.t0 - w.ts;
   float W = mufu_ex2(-2.0f * kLog2ef * nu * w.t0);
   const float rho = mufu_ex2(-2.0f * kLog2ef * nu * h);
   float S = 0.0f, c = 0.0f;
   const float x2 = 2.0f * x;
   const bool at_zero = (w.ts == 0.0f);
   for (int j = 0; j <= N; ++j) {
-    const float t = fmaf((float)j, h, w.t0);
+    const float tau = fmaf((float)j, h, tau0);
     float a;
     if (at_zero) {
-      const float s = sinh_f32(0.5f * t);
-      a = fmaf(-x2 * s, s, nu * t);
+      const float sq = sinh_f32(0.5f * tau);
+      a = fmaf(nu, tau, fmaf(nu_lo, tau, -x2 * sq * sq));
     } else {
-      a = fmaf(-x2 * sinh_f32(0.5f * (t + w.ts)), sinh_f32(0.5f * (t - w.ts)), nu * (t - w.ts));
+      a = fmaf(nu, tau, fmaf(nu_lo, tau, -fmaf(Ah, expm1_f32(tau), Bh * expm1_f32(-tau))));
     }
     float f = exp_f32(a);
     f = fmaf(f, W, f);
@@ -187,12 +209,10 @@ __device__ __forceinline__ float trapezoid_f32(float x, float nu, const Window32
   return h * S;
 }
 
-// Everything of one K_nu evaluation in the FP32 form except the final
-// normalisation: returns h S (FP32) and the FP64 log-scale
-// log f_s = nu ts - x cosh(ts) - ln 2, so that K = e^{log f_s} h S.
-// Outside x in [1e-4, 1e4], nu <= 40 the FP64 window search is used.
-// On failure (node bound exceeded) returns NaN scale.
-__device__ __forceinline__ double log_scale_f32(double x64, float nu, float& hS, Tally& tl) {
+// The searched window of the FP32 form: FP32 search inside x in [1e-4, 1e4],
+// nu <= 40, the FP64 search (with the FP32 eps) outside, where FP32 sinh /
+// cosh of the window ends lose too much.
+__device__ __forceinline__ Window32 search_window_f32(double x64, float nu, Tally& tl) {
   const float x = (float)x64;
   Window32 w;
   if (x >= 1e-4f && x <= 1e4f && nu <= 40.0f) {
@@ -203,19 +223,92 @@ __device__ __forceinline__ double log_scale_f32(double x64, float nu, float& hS,
     w.t0 = (float)w64.t0;
     w.t1 = (float)w64.t1;
   }
+  return w;
+}
+
+// Everything of one K_nu evaluation in the FP32 form after the window:
+// returns h S (FP32) and the FP64 log-scale log f_s = nu ts - x cosh(ts) - ln 2,
+// so that K = e^{log f_s} h S.  x and nu stay FP64 here (nu ts reaches ~200).
+// On failure (node bound exceeded) returns a NaN scale.
+__device__ __forceinline__ double scale_from_window_f32(double x64, double nu64, const Window32& w,
+                                                        float& hS, Tally& tl) {
+  const float x = (float)x64;
+  const float nu = (float)nu64;
+  const float nu_lo = (float)(nu64 - (double)nu);
   const int N = strip_node_count(x, nu, w.t1 - w.t0, kF32Log2OverTol, kF32MaxNodes);
   if (N > kF32MaxNodes) {
     ++tl.fail;
     hS = 0.0f;
     return __longlong_as_double(0x7ff8000000000000LL);
   }
-  hS = trapezoid_f32(x, nu, w, N, tl);
+  // e^{ts} of the (FP32) peak in FP64: x cosh(ts) can be ~1e2 and enters
+  // the scale, x e^{+-ts}/2 enter the node exponents.
   double cs = 1.0;
-  if (w.ts > 0.0f) {  // cosh of the (FP32) peak in FP64: x cosh(ts) can be ~1e2
-    const double e = exp_bounded((double)w.ts);
-    cs = 0.5 * (e + 1.0 / e);
+  float Ah = 0.5f * x, Bh = 0.5f * x;
+  if (w.ts > 0.0f) {
+    const double e = exp_bounded((double)w.ts), er = 1.0 / e;
+    cs = 0.5 * (e + er);
+    Ah = (float)(0.5 * x64 * e);
+    Bh = (float)(0.5 * x64 * er);
   }
-  return fma((double)nu, (double)w.ts, -x64 * cs) - kLn2;
+  hS = trapezoid_f32(x, nu, nu_lo, w, Ah, Bh, N, tl);
+  return fma(nu64, (double)w.ts, -x64 * cs) - kLn2;
+}
+
+__device__ __forceinline__ double log_scale_f32(double x64, double nu64, float& hS, Tally& tl) {
+  return scale_from_window_f32(x64, nu64, search_window_f32(x64, (float)nu64, tl), hS, tl);
+}
+
+// ---------------------------------------------------------------------------
+// Learned window (a10).  The window network's outputs (t*, t* - t0,
+// t1 - t*, ln N) are tabulated by the inference kernel on a grid over
+// (ln x, nu) and interpolated bilinearly here; the window is widened by a
+// relative and an absolute margin and then checked:
+//   F(t1) = nu (t1 - t^) - x (cosh t1 - cosh t^) + L <= 0 and, if t0 > 0,
+//   F(t0) + ln 2 <= 0, with t^ the predicted peak and L = -log eps.
+// F bounds g(t) - g(t^) + L from above on each side (see window_f64), and
+// g(t^) <= g(t*), so a window that passes contains the eps-window of the
+// unimodal integrand; anything else takes the searched window (fallback).
+constexpr int kTabX = 512;   // ln x in [ln 1e-3, ln 140]
+constexpr int kTabNu = 256;  // nu in [0.05, 20]
+constexpr float kTabLx0 = -6.90775528f, kTabLx1 = 4.94164242f;
+constexpr float kTabNu0 = 0.05f, kTabNu1 = 20.0f;
+
+struct LearnedView {
+  const float4* table;  // kTabNu rows of kTabX entries (t*, left, right, ln N)
+  float margin_rel, margin_abs;
+};
+
+__device__ __forceinline__ bool learned_window_f32(const LearnedView& lv, float x, float nu,
+                                                   Window32& w) {
+  const float lx = kLn2f * mufu_lg2(x);
+  const float fx = (lx - kTabLx0) * ((kTabX - 1) / (kTabLx1 - kTabLx0));
+  const float fn = (nu - kTabNu0) * ((kTabNu - 1) / (kTabNu1 - kTabNu0));
+  if (!(fx >= 0.0f && fx <= (float)(kTabX - 1) && fn >= 0.0f && fn <= (float)(kTabNu - 1)))
+    return false;
+  const int ix = min((int)fx, kTabX - 2), in = min((int)fn, kTabNu - 2);
+  const float ax = fx - (float)ix, an = fn - (float)in;
+  const float4 p00 = __ldg(lv.table + in * kTabX + ix), p01 = __ldg(lv.table + in * kTabX + ix + 1);
+  const float4 p10 = __ldg(lv.table + (in + 1) * kTabX + ix);
+  const float4 p11 = __ldg(lv.table + (in + 1) * kTabX + ix + 1);
+  const float b00 = (1.0f - ax) * (1.0f - an), b01 = ax * (1.0f - an), b10 = (1.0f - ax) * an,
+              b11 = ax * an;
+  const float ts = fmaxf(b00 * p00.x + b01 * p01.x + b10 * p10.x + b11 * p11.x, 0.0f);
+  const float left = fmaxf(b00 * p00.y + b01 * p01.y + b10 * p10.y + b11 * p11.y, 0.0f);
+  const float right = fmaxf(b00 * p00.z + b01 * p01.z + b10 * p10.z + b11 * p11.z, 0.0f);
+  const float t0 = fmaxf(0.0f, ts - fmaf(left, 1.0f + lv.margin_rel, lv.margin_abs));
+  const float t1 = ts + fmaf(right, 1.0f + lv.margin_rel, lv.margin_abs);
+  const float L = kLogInvEps32;
+  const float F1 = fmaf(nu, t1 - ts, -x * dcosh_f32(t1, ts)) + L;
+  bool ok = (F1 <= 0.0f);
+  if (t0 > 0.0f) {
+    const float F0 = fmaf(nu, t0 - ts, -x * dcosh_f32(t0, ts)) + L + kLn2f;
+    ok = ok && (F0 <= 0.0f);
+  }
+  w.ts = ts;
+  w.t0 = t0;
+  w.t1 = t1;
+  return ok;
 }
 
 }  // namespace bk

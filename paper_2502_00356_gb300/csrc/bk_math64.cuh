@@ -117,6 +117,7 @@ struct Tally {
   unsigned iters;       // window-end Newton iterations
   unsigned peak_iters;  // peak Newton iterations
   unsigned fail;        // evaluations returned as NaN
+  unsigned fallback;    // learned windows rejected by the in-kernel check
 };
 
 // The window of Sec. IV-B.  ts = t_max, cs/ss = cosh/sinh(ts), [t0, t1] the

@@ -1,9 +1,9 @@
-// Kernels shared by the FP64 and FP32 forms: the bk_eval kernel, the fused
+// Kernels shared by the arithmetic forms: the bk_eval kernel, the fused
 // symmetric Matern tile writer and the m x n block writer, templated on a
-// Form policy that supplies one K_nu evaluation and one Matern entry:
-//   static double eval(double x, double nu, Tally&, unsigned& evals, double& log_k);
-//   static double matern(double xi, double yi, double xj, double yj, double sigma2,
-//                        double beta, double nu, double log_pref, Tally&, unsigned& evals);
+// Form passed by value that supplies one K_nu evaluation and one Matern entry:
+//   double eval(double x, double nu, Tally&, unsigned& evals, double& log_k) const;
+//   double matern(double xi, double yi, double xj, double yj, double sigma2,
+//                 double beta, double nu, double log_pref, Tally&, unsigned& evals) const;
 #pragma once
 
 #include <cuda_runtime.h>
@@ -29,10 +29,11 @@ __device__ __forceinline__ float to_out<float>(double v) { return (float)v; }
 __device__ __forceinline__ void flush_tally(unsigned long long* ctr, const Tally& tl,
                                             unsigned evals) {
   if (ctr == nullptr) return;
-  unsigned long long v[5] = {tl.fail, tl.nodes, tl.iters, evals, tl.peak_iters};
-  const int idx[5] = {BK_CTR_FAIL, BK_CTR_NODES, BK_CTR_ITERS, BK_CTR_EVALS, BK_CTR_PEAK_ITERS};
+  unsigned long long v[6] = {tl.fail, tl.nodes, tl.iters, evals, tl.peak_iters, tl.fallback};
+  const int idx[6] = {BK_CTR_FAIL, BK_CTR_NODES, BK_CTR_ITERS, BK_CTR_EVALS, BK_CTR_PEAK_ITERS,
+                      BK_CTR_FALLBACK};
 #pragma unroll
-  for (int k = 0; k < 5; ++k) {
+  for (int k = 0; k < 6; ++k) {
     unsigned long long a = v[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
@@ -43,10 +44,10 @@ __device__ __forceinline__ void flush_tally(unsigned long long* ctr, const Tally
 
 // The element-wise domain rules of the C-ABI around a form's evaluation.
 template <class Form>
-__device__ __forceinline__ double eval_domain(double x, double nu, Tally& tl, unsigned& evals,
-                                              double& log_k) {
+__device__ __forceinline__ double eval_domain(const Form& form, double x, double nu, Tally& tl,
+                                              unsigned& evals, double& log_k) {
   nu = fabs(nu);
-  if (x > 0.0 && x < kInf && nu < kInf) return Form::eval(x, nu, tl, evals, log_k);
+  if (x > 0.0 && x < kInf && nu < kInf) return form.eval(x, nu, tl, evals, log_k);
   if (x == 0.0 && nu == nu) {
     log_k = kInf;
     return kInf;
@@ -60,17 +61,17 @@ __device__ __forceinline__ double eval_domain(double x, double nu, Tally& tl, un
 }
 
 template <class Form, typename OutT>
-__global__ void __launch_bounds__(128) eval_kernel(const double* __restrict__ x,
+__global__ void __launch_bounds__(128) eval_kernel(const Form form, const double* __restrict__ x,
                                                    const double* __restrict__ nu,
                                                    OutT* __restrict__ out,
                                                    OutT* __restrict__ log_out, int64_t n,
                                                    unsigned long long* __restrict__ ctr) {
-  Tally tl{0u, 0u, 0u, 0u};
+  Tally tl{0u, 0u, 0u, 0u, 0u};
   unsigned evals = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     double lk;
-    const double k = eval_domain<Form>(x[i], nu[i], tl, evals, lk);
+    const double k = eval_domain<Form>(form, x[i], nu[i], tl, evals, lk);
     out[i] = to_out<OutT>(k);
     if (log_out != nullptr) log_out[i] = to_out<OutT>(lk);
   }
@@ -101,7 +102,8 @@ struct SymTileSmem {
 };
 
 template <class Form, typename OutT, int WARPS>
-__device__ __forceinline__ void sym_tile(SymTileSmem<OutT>& sm, const double* __restrict__ locs,
+__device__ __forceinline__ void sym_tile(const Form& form, SymTileSmem<OutT>& sm,
+                                         const double* __restrict__ locs,
                                          int64_t n, int64_t I, int64_t J, double sigma2,
                                          double beta, double nu, double log_pref,
                                          OutT* __restrict__ out, int64_t ld, Tally& tl,
@@ -122,8 +124,8 @@ __device__ __forceinline__ void sym_tile(SymTileSmem<OutT>& sm, const double* __
   for (int c = warp; c < kTile; c += WARPS) {
     double v = 0.0;
     if (r0 + lane < n && c0 + c < n)
-      v = Form::matern(sm.rx[lane], sm.ry[lane], sm.cx[c], sm.cy[c], sigma2, beta, nu, log_pref,
-                       tl, evals);
+      v = form.matern(sm.rx[lane], sm.ry[lane], sm.cx[c], sm.cy[c], sigma2, beta, nu, log_pref,
+                      tl, evals);
     sm.tile[lane][c] = to_out<OutT>(v);
   }
   __syncthreads();
@@ -152,17 +154,17 @@ __device__ __forceinline__ void tri_tile(int64_t t, int64_t& I, int64_t& J) {
 // Full symmetric matrix: its lower-triangle tiles visited grid-stride.
 template <class Form, typename OutT>
 __global__ void __launch_bounds__(kThreads) matern_sym_kernel(
-    const double* __restrict__ locs, int64_t n, double sigma2, double beta, double nu,
+    const Form form, const double* __restrict__ locs, int64_t n, double sigma2, double beta, double nu,
     OutT* __restrict__ out, int64_t ld, int64_t ntiles, unsigned long long* __restrict__ ctr) {
   __shared__ SymTileSmem<OutT> sm;
   const double log_pref = matern_log_prefactor(sigma2, nu);
-  Tally tl{0u, 0u, 0u, 0u};
+  Tally tl{0u, 0u, 0u, 0u, 0u};
   unsigned evals = 0;
   for (int64_t tix = blockIdx.x; tix < ntiles; tix += gridDim.x) {
     int64_t I, J;
     tri_tile(tix, I, J);
     __syncthreads();  // the previous tile's shared data is no longer read
-    sym_tile<Form, OutT, kWarps>(sm, locs, n, I, J, sigma2, beta, nu, log_pref, out, ld, tl,
+    sym_tile<Form, OutT, kWarps>(form, sm, locs, n, I, J, sigma2, beta, nu, log_pref, out, ld, tl,
                                  evals);
   }
   flush_tally(ctr, tl, evals);
@@ -171,13 +173,13 @@ __global__ void __launch_bounds__(kThreads) matern_sym_kernel(
 // General m x n block (Algorithm 3's single tile between two location sets).
 template <class Form, typename OutT>
 __global__ void __launch_bounds__(kThreads) matern_block_kernel(
-    const double* __restrict__ locs1, int64_t m, const double* __restrict__ locs2, int64_t n,
+    const Form form, const double* __restrict__ locs1, int64_t m, const double* __restrict__ locs2, int64_t n,
     double sigma2, double beta, double nu, OutT* __restrict__ out, int64_t ld, int64_t tiles_m,
     int64_t ntiles, unsigned long long* __restrict__ ctr) {
   __shared__ double s_rx[kTile], s_ry[kTile], s_cx[kTile], s_cy[kTile];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const double log_pref = matern_log_prefactor(sigma2, nu);
-  Tally tl{0u, 0u, 0u, 0u};
+  Tally tl{0u, 0u, 0u, 0u, 0u};
   unsigned evals = 0;
   for (int64_t tix = blockIdx.x; tix < ntiles; tix += gridDim.x) {
     const int64_t r0 = (tix % tiles_m) * kTile, c0 = (tix / tiles_m) * kTile;
@@ -197,7 +199,7 @@ __global__ void __launch_bounds__(kThreads) matern_block_kernel(
       const int c = warp + kWarps * k;
       const int64_t i = r0 + lane, j = c0 + c;
       if (i < m && j < n)
-        out[i + j * ld] = to_out<OutT>(Form::matern(s_rx[lane], s_ry[lane], s_cx[c], s_cy[c],
+        out[i + j * ld] = to_out<OutT>(form.matern(s_rx[lane], s_ry[lane], s_cx[c], s_cy[c],
                                                         sigma2, beta, nu, log_pref, tl, evals));
     }
   }
@@ -209,19 +211,20 @@ __global__ void __launch_bounds__(kThreads) matern_block_kernel(
 int grid_for(int64_t work_items, int per_sm);
 
 template <class Form>
-cudaError_t launch_eval_form(const double* x, const double* nu, void* out, void* log_out,
+cudaError_t launch_eval_form(const Form& form, const double* x, const double* nu, void* out, void* log_out,
                              bk_dtype out_t, int64_t n, unsigned long long* ctr, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const int grid = grid_for((n + 127) / 128, 16);
   if (out_t == BK_F64)
-    eval_kernel<Form, double><<<grid, 128, 0, s>>>(x, nu, (double*)out, (double*)log_out, n, ctr);
+    eval_kernel<Form, double><<<grid, 128, 0, s>>>(form, x, nu, (double*)out, (double*)log_out, n,
+                                                   ctr);
   else
-    eval_kernel<Form, float><<<grid, 128, 0, s>>>(x, nu, (float*)out, (float*)log_out, n, ctr);
+    eval_kernel<Form, float><<<grid, 128, 0, s>>>(form, x, nu, (float*)out, (float*)log_out, n, ctr);
   return cudaGetLastError();
 }
 
 template <class Form>
-cudaError_t launch_matern_sym_form(const double* locs, int64_t n, double sigma2, double beta,
+cudaError_t launch_matern_sym_form(const Form& form, const double* locs, int64_t n, double sigma2, double beta,
                                    double nu, void* out, int64_t ld, bk_dtype out_t,
                                    unsigned long long* ctr, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
@@ -229,16 +232,16 @@ cudaError_t launch_matern_sym_form(const double* locs, int64_t n, double sigma2,
   const int64_t ntiles = nb * (nb + 1) / 2;
   const int grid = grid_for(ntiles, 4);
   if (out_t == BK_F64)
-    matern_sym_kernel<Form, double><<<grid, kThreads, 0, s>>>(locs, n, sigma2, beta, nu,
+    matern_sym_kernel<Form, double><<<grid, kThreads, 0, s>>>(form, locs, n, sigma2, beta, nu,
                                                               (double*)out, ld, ntiles, ctr);
   else
-    matern_sym_kernel<Form, float><<<grid, kThreads, 0, s>>>(locs, n, sigma2, beta, nu,
+    matern_sym_kernel<Form, float><<<grid, kThreads, 0, s>>>(form, locs, n, sigma2, beta, nu,
                                                              (float*)out, ld, ntiles, ctr);
   return cudaGetLastError();
 }
 
 template <class Form>
-cudaError_t launch_matern_block_form(const double* locs1, int64_t m, const double* locs2,
+cudaError_t launch_matern_block_form(const Form& form, const double* locs1, int64_t m, const double* locs2,
                                      int64_t n, double sigma2, double beta, double nu, void* out,
                                      int64_t ld, bk_dtype out_t, unsigned long long* ctr,
                                      cudaStream_t s) {
@@ -248,10 +251,10 @@ cudaError_t launch_matern_block_form(const double* locs1, int64_t m, const doubl
   const int grid = grid_for(ntiles, 4);
   if (out_t == BK_F64)
     matern_block_kernel<Form, double><<<grid, kThreads, 0, s>>>(
-        locs1, m, locs2, n, sigma2, beta, nu, (double*)out, ld, tm, ntiles, ctr);
+        form, locs1, m, locs2, n, sigma2, beta, nu, (double*)out, ld, tm, ntiles, ctr);
   else
     matern_block_kernel<Form, float><<<grid, kThreads, 0, s>>>(
-        locs1, m, locs2, n, sigma2, beta, nu, (float*)out, ld, tm, ntiles, ctr);
+        form, locs1, m, locs2, n, sigma2, beta, nu, (float*)out, ld, tm, ntiles, ctr);
   return cudaGetLastError();
 }
 

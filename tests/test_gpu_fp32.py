@@ -60,6 +60,14 @@ def test_eval_f32_region_grid(dev):
     assert np.abs(np.expm1(lgot - lref)).max() <= F32_RTOL
 
 
+def test_eval_f32_small_x_large_nu(dev):
+    # the corner with the peak far out (t* ~ 10): x in [1e-3, 1e-2], nu in [12, 20]
+    x, nu = inputs.kv_pairs(6000, seed=77, x_lo=1e-3, x_hi=1e-2, nu_lo=12.0, nu_hi=20.0)
+    _, lgot = eval_f32(x, nu, dev)
+    _, lref = oracle.besselk(x, nu, return_log=True)
+    assert np.abs(np.expm1(lgot - lref)).max() <= 0.5 * F32_RTOL
+
+
 def test_eval_f32_outside_region_uses_fp64_search(dev):
     # x below 1e-4 or above 1e4 takes the FP64 window search
     x = np.array([3e-5, 5e-5, 2e4, 0.5])

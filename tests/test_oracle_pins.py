@@ -208,3 +208,58 @@ def test_matern_properties(orc):
     np.linalg.cholesky(M[np.ix_(keep, keep)])
     I, J = inputs.entry_sample(60, 200, seed=18)
     np.testing.assert_array_equal(orc.matern_entries(locs, I, J, sigma2, beta, nu), M[I, J])
+
+
+# ---------------------------------------------------------------------------
+# FP64 reference of the window network (oracle/mlp.py)
+
+def test_mlp_backward_matches_finite_differences():
+    from oracle import mlp
+    rng = np.random.default_rng(31)
+    p = rng.normal(0, 0.3, mlp.N_PARAMS)
+    U = rng.uniform(-1, 1, (17, 2))
+    T = rng.normal(0, 1, (17, 4))
+    _, g = mlp.loss_and_grad(p, U, T)
+    idx = rng.choice(mlp.N_PARAMS, 60, replace=False)
+    idx = np.concatenate([idx, [0, 127, 128, 191, 192, 8767, 8771]])  # every block edge
+    h = 1e-6
+    for i in idx:
+        e = np.zeros_like(p)
+        e[i] = h
+        fd = (mlp.loss_only(p + e, U, T) - mlp.loss_only(p - e, U, T)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-8 + 1e-6 * abs(fd)
+
+
+def test_mlp_forward_closed_forms():
+    from oracle import mlp
+    p = np.zeros(mlp.N_PARAMS)
+    W1, b1, W2, b2, W3, b3, W4, b4 = mlp.unpack(p)  # views into p
+    b4[:] = [0.5, -1.0, 2.0, 3.0]
+    y, _ = mlp.forward(p, np.array([[0.3, -0.2]]))
+    assert np.array_equal(y[0], [0.5, -1.0, 2.0, 3.0])  # all hidden units are tanh(0) = 0
+    # one path: u_x -> h1[0] -> h2[0] -> h3[0] -> y[1]
+    W1[0, 0] = 1.0
+    W2[0, 0] = 1.0
+    W3[0, 0] = 1.0
+    W4[1, 0] = 2.0
+    u = 0.4
+    y, _ = mlp.forward(p, np.array([[u, 0.9]]))
+    assert abs(y[0, 1] - (-1.0 + 2.0 * math.tanh(math.tanh(math.tanh(u))))) < 1e-15
+    assert mlp.N_PARAMS == 8772
+
+
+def test_window_labels_definition(orc):
+    # labels agree with oracle.window and N is minimal against an independent trapezoid
+    log_eps = -23 * np.log(2)
+    x = np.array([1e-3, 0.05, 0.9, 7.0, 120.0])
+    nu = np.array([15.0, 0.2, 2.5, 0.7, 3.0])
+    lab = orc.window_labels(x, nu, log_eps, 1e-6)
+    w = orc.window(x, nu, log_eps)
+    np.testing.assert_array_equal(lab[:, :4], w)
+    for (ts, t0, t1, gs, N, lref), xi, ni in zip(lab, x, nu):
+        def trap(n):
+            t = np.linspace(t0, t1, int(n) + 1)
+            f = np.exp(_g(t, xi, ni) - gs)
+            return np.log((t1 - t0) / n * (f.sum() - 0.5 * (f[0] + f[-1]))) + gs
+        assert abs(np.expm1(trap(N) - lref)) <= 1e-6 * 1.01
+        assert abs(np.expm1(trap(N - 1) - lref)) > 1e-6 * 0.99
