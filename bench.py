@@ -53,6 +53,14 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=15.0,
                    help="budget of the CPU oracle baseline sample")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-forms", action="store_true",
+                   help="skip the FP32, batched and learned-window measurements")
+    p.add_argument("--pairs", type=int, default=100_000_000,
+                   help="K_nu pairs of the learned-window evaluation workload")
+    p.add_argument("--profile-case", choices=["plain", "fp32", "learned", "learned_eval", "batched"],
+                   default=None,
+                   help="run --warmup launches plus one launch of one kernel on a small case "
+                        "(for profiler captures) and exit without a JSON line")
     return p.parse_args()
 
 
@@ -209,11 +217,190 @@ def config(n):
 
 
 # ---------------------------------------------------------------------------
+def _time(fn, stream, reps=1):
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / 1e3 / reps
+
+
+def _max_rel(got, ref, floor=1e-30):
+    big = ref.abs() >= floor
+    return float(((got.double() - ref.double()).abs() / ref.double().abs().clamp_min(floor))[big].max())
+
+
+def measure_forms(bk, inputs, dev, stream, args, plain_rate):
+    """Throughput of the other forms (outside the headline timing).  Errors
+    are stated against the plain FP64 form, which the GPU tests hold within
+    1e-10 of the oracle."""
+    import numpy as np
+    import torch
+
+    res = {}
+    ckpt = os.path.join(ROOT, "paper_2502_00356_gb300", "weights", "window_mlp.bkw")
+    net = bk.LearnedWindow(path=ckpt)
+
+    def ctr():
+        return torch.zeros(bk.BK_NUM_COUNTERS, dtype=torch.int64, device=dev)
+
+    # -- FP32 precision form: n = 40,000 jittered grid, beta = 0.05, nu ~ U(0.3, 3.5) (seed 5)
+    n3, beta3 = 40_000, 0.05
+    nu3 = float(np.random.default_rng(5).uniform(0.3, 3.5))
+    L3 = torch.as_tensor(inputs.morton_sorted(inputs.jittered_grid(n3, seed=4)), device=dev)
+    o32 = torch.empty((n3, n3), dtype=torch.float32, device=dev)
+    bk.bk_matern_tile(L3, 1.0, beta3, nu3, out=o32)
+    t = _time(lambda: bk.bk_matern_tile(L3, 1.0, beta3, nu3, out=o32), stream, 3)
+    cols = slice(0, 2000)
+    ref = bk.bk_matern_tile2(L3, L3[:, cols].contiguous(), 1.0, beta3, nu3,
+                             opts=bk.make_opts(compute=bk.BK_F64))
+    res["fp32_matern"] = {
+        "workload": f"n={n3} jittered grid, beta={beta3}, nu={nu3:.4f} (U(0.3,3.5), seed 5), FP32 out",
+        "value": n3 * n3 / t, "unit": "entries/s", "ms": 1e3 * t,
+        "max_rel_vs_fp64_form": _max_rel(o32[cols, :], ref),
+        "err_sample": "all entries of the first 2000 columns"}
+    del ref
+
+    # -- learned vs searched window vs plain FP64 on n = 40,000, nu = 1.7, beta = 0.1 (FP32 out)
+    n5, beta5, nu5 = 40_000, 0.1, 1.7
+    L5 = L3  # same 200 x 200 jittered grid (seed 4)
+    o_s = o32
+    c_s, c_l = ctr(), ctr()
+    bk.bk_matern_tile(L5, 1.0, beta5, nu5, out=o_s, opts=bk.make_opts(compute=bk.BK_F32, counters=c_s))
+    t_s = _time(lambda: bk.bk_matern_tile(L5, 1.0, beta5, nu5, out=o_s), stream, 3)
+    o_l = torch.empty_like(o_s)
+    bk.bk_matern_tile(L5, 1.0, beta5, nu5, out=o_l, opts=bk.make_opts(learned=net, counters=c_l))
+    lo = bk.make_opts(learned=net)
+    t_l = _time(lambda: bk.bk_matern_tile(L5, 1.0, beta5, nu5, out=o_l, opts=lo), stream, 3)
+    ref = bk.bk_matern_tile2(L5, L5[:, cols].contiguous(), 1.0, beta5, nu5,
+                             opts=bk.make_opts(compute=bk.BK_F64))
+    o64 = torch.empty((n5, n5), dtype=torch.float64, device=dev)
+    t_p = _time(lambda: bk.bk_matern_tile(L5, 1.0, beta5, nu5, out=o64), stream, 1)
+    del o64
+    cl, cs = c_l.cpu().numpy(), c_s.cpu().numpy()
+    res["learned_matern"] = {
+        "workload": f"n={n5} jittered grid, beta={beta5}, nu={nu5}, FP32 out",
+        "learned_value": n5 * n5 / t_l, "fp32_search_value": n5 * n5 / t_s,
+        "plain_fp64_value": n5 * n5 / t_p, "unit": "entries/s",
+        "learned_over_plain": t_p / t_l, "learned_over_fp32_search": t_s / t_l,
+        "fallback_rate": float(cl[bk.BK_CTR_FALLBACK] / max(1, cl[bk.BK_CTR_EVALS])),
+        "nodes_per_eval": {"learned": float(cl[bk.BK_CTR_NODES] / max(1, cl[bk.BK_CTR_EVALS])),
+                           "search": float(cs[bk.BK_CTR_NODES] / max(1, cs[bk.BK_CTR_EVALS]))},
+        "newton_iters_per_eval": {
+            "learned": float((cl[bk.BK_CTR_ITERS] + cl[bk.BK_CTR_PEAK_ITERS]) / max(1, cl[bk.BK_CTR_EVALS])),
+            "search": float((cs[bk.BK_CTR_ITERS] + cs[bk.BK_CTR_PEAK_ITERS]) / max(1, cs[bk.BK_CTR_EVALS]))},
+        "max_rel_vs_fp64_form": {"learned": _max_rel(o_l[cols, :], ref),
+                                 "search": _max_rel(o_s[cols, :], ref)}}
+    del o_s, o_l, o32, ref, L3
+    torch.cuda.empty_cache()
+
+    # -- learned window on 1e8 pairs: x log-uniform [1e-3, 140], nu U[0.05, 20] (seed 8)
+    npairs = args.pairs
+    xh, nh = inputs.kv_pairs(npairs, seed=8, nu_lo=0.05, nu_hi=20.0)
+    X, V = torch.as_tensor(xh, device=dev), torch.as_tensor(nh, device=dev)
+    del xh, nh
+    Y = torch.empty(npairs, dtype=torch.float32, device=dev)
+    c_e = ctr()
+    bk.bk_eval_ex(X, V, out=Y, opts=bk.make_opts(learned=net, counters=c_e))
+    t_le = _time(lambda: bk.bk_eval_ex(X, V, out=Y, opts=lo), stream, 3)
+    fo = bk.make_opts(compute=bk.BK_F32)
+    t_se = _time(lambda: bk.bk_eval_ex(X, V, out=Y, opts=fo), stream, 3)
+    sub = slice(0, 2_000_000)
+    Yd = torch.empty(2_000_000, dtype=torch.float64, device=dev)
+    t_pe = _time(lambda: bk.bk_eval(X[sub], V[sub], out=Yd), stream, 1)
+    _, ll = bk.bk_eval_ex(X[sub], V[sub], opts=lo, want_log=True)
+    _, lp = bk.bk_eval_ex(X[sub], V[sub], want_log=True)
+    ce = c_e.cpu().numpy()
+    res["learned_eval"] = {
+        "workload": f"{npairs} pairs, x log-uniform [1e-3,140], nu U[0.05,20] (seed 8), FP32 out",
+        "learned_value": npairs / t_le, "fp32_search_value": npairs / t_se,
+        "plain_fp64_value": 2_000_000 / t_pe, "unit": "K_nu evals/s",
+        "fallback_rate": float(ce[bk.BK_CTR_FALLBACK] / max(1, ce[bk.BK_CTR_EVALS])),
+        "max_rel_vs_fp64_form": float(torch.expm1((ll - lp).abs()).max()),
+        "err_sample": "the first 2,000,000 pairs (log K)"}
+    del X, V, Y, Yd
+    torch.cuda.empty_cache()
+
+    # -- batched sweep: 256 instances, n log-uniform [500, 8000], one persistent launch in a graph
+    insts = inputs.batched_instances(256)
+    entries = sum(i.n * i.n for i in insts)
+    locs = [torch.as_tensor(i.locations(), device=dev) for i in insts]
+    bres = {"workload": "256 instances, n log-uniform [500, 8000], sigma2 U[0.5,2], "
+                        "beta U[0.02,0.3], nu U[0.3,3], one launch replayed from a CUDA graph",
+            "entries": entries}
+    for name, dtype, opts in (("fp64", torch.float64, None),
+                              ("fp32", torch.float32, None),
+                              ("learned_fp32", torch.float32, bk.make_opts(learned=net))):
+        outs = [torch.empty((i.n, i.n), dtype=dtype, device=dev) for i in insts]
+        d = bk.make_descs([(L, i.sigma2, i.beta, i.nu, o) for L, i, o in zip(locs, insts, outs)])
+        plan = bk.BatchedPlan([i.n for i in insts], dtype=dtype, opts=opts)
+        plan.autotune(d, sample_tiles=20_000)
+        bk.bk_matern_batched(d, plan)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            bk.bk_matern_batched(d, plan)
+        tb = _time(g.replay, stream, 2 if name == "fp64" else 5)
+        bres[name] = {"value": entries / tb, "unit": "entries/s", "ms": 1e3 * tb,
+                      "plan": plan.info()}
+        del outs, d, g, plan
+        torch.cuda.empty_cache()
+    bres["learned_fp32_over_fp64"] = bres["learned_fp32"]["value"] / bres["fp64"]["value"]
+    res["batched"] = bres
+    res["learned_batched_over_plain_fp64_headline"] = bres["learned_fp32"]["value"] / plain_rate
+    return res
+
+
+def profile_case(args):
+    """Small single-kernel cases whose outputs still exceed the 129 MB L2."""
+    import numpy as np
+    import torch
+
+    import paper_2502_00356_gb300 as bk
+    from paper_2502_00356_gb300 import inputs
+    bk.build()
+    dev = torch.device("cuda")
+    c = args.profile_case
+    net = None
+    if c in ("learned", "learned_eval", "batched"):
+        net = bk.LearnedWindow(path=os.path.join(ROOT, "paper_2502_00356_gb300", "weights",
+                                                 "window_mlp.bkw"))
+    if c in ("plain", "fp32", "learned"):
+        n = {"plain": 6000, "fp32": 12000, "learned": 12000}[c]
+        L = torch.as_tensor(inputs.morton_sorted(inputs.jittered_grid(n, seed=4)), device=dev)
+        dtype = torch.float64 if c == "plain" else torch.float32
+        out = torch.empty((n, n), dtype=dtype, device=dev)
+        beta, nu = (0.1, 0.5) if c == "plain" else ((0.05, 2.876) if c == "fp32" else (0.1, 1.7))
+        opts = bk.make_opts(learned=net) if c == "learned" else None
+        run = lambda: bk.bk_matern_tile(L, 1.0, beta, nu, out=out, opts=opts)
+    elif c == "learned_eval":
+        xh, nh = inputs.kv_pairs(20_000_000, seed=8, nu_lo=0.05, nu_hi=20.0)
+        X, V = torch.as_tensor(xh, device=dev), torch.as_tensor(nh, device=dev)
+        Y = torch.empty(X.numel(), dtype=torch.float32, device=dev)
+        opts = bk.make_opts(learned=net)
+        run = lambda: bk.bk_eval_ex(X, V, out=Y, opts=opts)
+    else:
+        insts = inputs.batched_instances(32)
+        locs = [torch.as_tensor(i.locations(), device=dev) for i in insts]
+        outs = [torch.empty((i.n, i.n), dtype=torch.float32, device=dev) for i in insts]
+        d = bk.make_descs([(L, i.sigma2, i.beta, i.nu, o) for L, i, o in zip(locs, insts, outs)])
+        plan = bk.BatchedPlan([i.n for i in insts], dtype=torch.float32)
+        run = lambda: bk.bk_matern_batched(d, plan)
+    for _ in range(args.warmup + 1):
+        run()
+    torch.cuda.synchronize()
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.profile_case is not None:
+        profile_case(args)
         return
 
     import numpy as np
@@ -360,6 +547,12 @@ def main():
                "d2h_bytes_per_step": len(NUS) * n * n * 8, "steps": e_steps}
         del out_pin
 
+    forms = None
+    if not args.no_forms:
+        del out
+        torch.cuda.empty_cache()
+        forms = measure_forms(bk, inputs, dev, stream, args, value)
+
     cpu = None
     if rank == 0 and world == 1:
         rate, sizes, cores = oracle_rate(args.cpu_seconds, n)
@@ -380,6 +573,7 @@ def main():
             "eval_fp64": {"value": eval_rate, "unit": "K_nu evals/s",
                           "workload": "100,000 pairs, x log-uniform [1e-3,140], nu U[0.05,10]"},
             "probe": probe,
+            "forms": forms,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
