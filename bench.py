@@ -287,6 +287,7 @@ def measure_forms(bk, inputs, dev, stream, args, plain_rate):
         "plain_fp64_value": n5 * n5 / t_p, "unit": "entries/s",
         "learned_over_plain": t_p / t_l, "learned_over_fp32_search": t_s / t_l,
         "fallback_rate": float(cl[bk.BK_CTR_FALLBACK] / max(1, cl[bk.BK_CTR_EVALS])),
+        "repairs_per_eval": float(cl[bk.BK_CTR_REPAIR] / max(1, cl[bk.BK_CTR_EVALS])),
         "nodes_per_eval": {"learned": float(cl[bk.BK_CTR_NODES] / max(1, cl[bk.BK_CTR_EVALS])),
                            "search": float(cs[bk.BK_CTR_NODES] / max(1, cs[bk.BK_CTR_EVALS]))},
         "newton_iters_per_eval": {
@@ -319,6 +320,7 @@ def measure_forms(bk, inputs, dev, stream, args, plain_rate):
         "learned_value": npairs / t_le, "fp32_search_value": npairs / t_se,
         "plain_fp64_value": 2_000_000 / t_pe, "unit": "K_nu evals/s",
         "fallback_rate": float(ce[bk.BK_CTR_FALLBACK] / max(1, ce[bk.BK_CTR_EVALS])),
+        "repairs_per_eval": float(ce[bk.BK_CTR_REPAIR] / max(1, ce[bk.BK_CTR_EVALS])),
         "max_rel_vs_fp64_form": float(torch.expm1((ll - lp).abs()).max()),
         "err_sample": "the first 2,000,000 pairs (log K)"}
     del X, V, Y, Yd

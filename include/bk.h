@@ -65,12 +65,13 @@ typedef enum {
 
 /* Indices into the optional device counter array bk_opts.d_counters. */
 enum {
-  BK_CTR_FALLBACK = 0, /* learned windows rejected by the in-kernel check */
+  BK_CTR_FALLBACK = 0, /* learned windows replaced by the full window search */
   BK_CTR_FAIL = 1,     /* points returned as NaN because a search did not converge */
   BK_CTR_NODES = 2,    /* integrand evaluations (quadrature nodes) */
   BK_CTR_ITERS = 3,    /* window-end root-finder iterations */
   BK_CTR_EVALS = 4,    /* K_nu evaluations */
   BK_CTR_PEAK_ITERS = 5, /* peak (t_max) root-finder iterations */
+  BK_CTR_REPAIR = 6,   /* learned window ends moved by one Newton step after the check */
   BK_NUM_COUNTERS = 8
 };
 
@@ -210,8 +211,10 @@ bk_status bk_matern_batched(const bk_matern_desc* d_descs, int32_t count, bk_dty
  * load, kernels interpolate the table, widen the window by a relative and an
  * absolute margin and check it (the integrand at both ends must be below
  * eps times its value at the predicted peak, checked with an upper bound of
- * g); points outside the grid or failing the check use the window search and
- * are counted in BK_CTR_FALLBACK.
+ * g).  An end that fails is moved by one Newton step of the bounds search
+ * from the prediction (BK_CTR_REPAIR); points outside the grid, or whose
+ * slope does not allow that step, use the full window search
+ * (BK_CTR_FALLBACK).
  */
 typedef struct bk_learned bk_learned;
 

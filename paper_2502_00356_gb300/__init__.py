@@ -26,6 +26,7 @@ BK_ERR_UNSUPPORTED, BK_ERR_NOT_CONVERGED, BK_ERR_NOT_LOADED = 4, 5, 6
 BK_F64, BK_F32 = 0, 1
 BK_WIN_SEARCH, BK_WIN_LEARNED, BK_WIN_FIXED = 0, 1, 2
 BK_CTR_FALLBACK, BK_CTR_FAIL, BK_CTR_NODES, BK_CTR_ITERS, BK_CTR_EVALS, BK_CTR_PEAK_ITERS = 0, 1, 2, 3, 4, 5
+BK_CTR_REPAIR = 6
 BK_NUM_COUNTERS = 8
 
 #: every symbol include/bk.h declares (checked by the CPU tests)

@@ -42,7 +42,7 @@ struct BatchSmem {
   const double* locs;
   OutT* out;
   int64_t n, ld, item;
-  double sigma2, beta, nu, log_pref;
+  MaternParams mp;
 };
 
 // Persistent kernel: each CTA repeatedly takes `chunk` consecutive tiles from
@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(WARPS * 32) matern_batched_kernel(
     const int64_t* __restrict__ sizes, int64_t limit, unsigned long long* __restrict__ next,
     int chunk, unsigned long long* __restrict__ ctr) {
   __shared__ BatchSmem<OutT> sm;
-  Tally tl{0u, 0u, 0u, 0u, 0u};
+  Tally tl{0u, 0u, 0u, 0u, 0u, 0u};
   unsigned evals = 0;
   int cur = -1;
   while (true) {
@@ -80,10 +80,7 @@ __global__ void __launch_bounds__(WARPS * 32) matern_batched_kernel(
           sm.out = (OutT*)d.out;
           sm.n = d.n;
           sm.ld = d.ld;
-          sm.sigma2 = d.sigma2;
-          sm.beta = d.beta;
-          sm.nu = d.nu;
-          sm.log_pref = matern_log_prefactor(d.sigma2, d.nu);  // a1, once per instance run
+          sm.mp = matern_params(d.sigma2, d.beta, d.nu);  // a1, once per instance run
         }
         __syncthreads();
         cur = k;
@@ -91,8 +88,8 @@ __global__ void __launch_bounds__(WARPS * 32) matern_batched_kernel(
       int64_t I, J;
       tri_tile(w - __ldg(prefix + k), I, J);
       __syncthreads();
-      sym_tile<Form, OutT, WARPS>(form, sm.tile, sm.locs, sm.n, I, J, sm.sigma2, sm.beta, sm.nu,
-                                  sm.log_pref, sm.out, sm.ld, tl, evals);
+      sym_tile<Form, OutT, WARPS>(form, sm.tile, sm.locs, sm.n, I, J, sm.mp, sm.out, sm.ld, tl,
+                                  evals);
     }
   }
   flush_tally(ctr, tl, evals);
@@ -497,7 +494,7 @@ __global__ void __launch_bounds__(WARPS * 32) matern_batched_static_kernel(
   const int64_t* sizes = (const int64_t*)(scratch + kStaticSizesOff);
   const int64_t limit = prefix[count];
   __shared__ BatchSmem<OutT> sm;
-  Tally tl{0u, 0u, 0u, 0u, 0u};
+  Tally tl{0u, 0u, 0u, 0u, 0u, 0u};
   unsigned evals = 0;
   int cur = -1;
   while (true) {
@@ -518,10 +515,7 @@ __global__ void __launch_bounds__(WARPS * 32) matern_batched_static_kernel(
         sm.out = (OutT*)d.out;
         sm.n = d.n;
         sm.ld = d.ld;
-        sm.sigma2 = d.sigma2;
-        sm.beta = d.beta;
-        sm.nu = d.nu;
-        sm.log_pref = matern_log_prefactor(d.sigma2, d.nu);
+        sm.mp = matern_params(d.sigma2, d.beta, d.nu);
       }
       __syncthreads();
       cur = k;
@@ -529,8 +523,8 @@ __global__ void __launch_bounds__(WARPS * 32) matern_batched_static_kernel(
     int64_t I, J;
     tri_tile(w - prefix[k], I, J);
     __syncthreads();
-    sym_tile<Form, OutT, WARPS>(Form{}, sm.tile, sm.locs, sm.n, I, J, sm.sigma2, sm.beta, sm.nu,
-                                sm.log_pref, sm.out, sm.ld, tl, evals);
+    sym_tile<Form, OutT, WARPS>(Form{}, sm.tile, sm.locs, sm.n, I, J, sm.mp, sm.out, sm.ld, tl,
+                                evals);
   }
 }
 

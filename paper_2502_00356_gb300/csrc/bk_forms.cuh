@@ -8,12 +8,13 @@
 #include "bk.h"
 #include "bk_math32.cuh"
 #include "bk_math64.cuh"
+#include "bk_matern_common.cuh"
 
 namespace bk {
 
 struct FormF64 {
   __device__ __forceinline__ double eval(double x, double nu, Tally& tl, unsigned& evals,
-                                                double& log_k) const {
+                                         double& log_k) const {
     ++evals;
     log_k = log_kv_f64(x, nu, kPlainLog2OverTol, kPlainMaxNodes, tl);
     return exp_full(log_k);
@@ -22,44 +23,75 @@ struct FormF64 {
   // a2 + a3..a7 for one entry: distance, x = r / beta, log K_nu(x),
   // M = exp(log prefactor + nu log x + log K).  sigma^2 where r == 0
   // (Algorithm 3 tests the computed distance for exact zero).
-  __device__ __forceinline__ double matern(double xi, double yi, double xj, double yj,
-                                                  double sigma2, double beta, double nu,
-                                                  double log_pref, Tally& tl, unsigned& evals) const {
-    const double dx = xj - xi, dy = yj - yi;
+  __device__ __forceinline__ double matern(const Loc& a, const Loc& b, const MaternParams& mp,
+                                           Tally& tl, unsigned& evals) const {
+    const double dx = b.x - a.x, dy = b.y - a.y;
     const double r = sqrt(fma(dx, dx, dy * dy));
-    if (r == 0.0) return sigma2;
-    const double z = r / beta;
+    if (r == 0.0) return mp.sigma2;
+    const double z = r / mp.beta;
     ++evals;
-    const double lk = log_kv_f64(z, nu, kPlainLog2OverTol, kPlainMaxNodes, tl);
-    return exp_full(fma(nu, log_pos(z), log_pref) + lk);
+    const double lk = log_kv_f64(z, mp.nu, kPlainLog2OverTol, kPlainMaxNodes, tl);
+    return exp_full(fma(mp.nu, log_pos(z), mp.log_pref) + lk);
   }
 };
 
+// The end of one FP32-form Matern entry after the quadrature (a7): the log
+// of the entry, log prefactor + nu log x + nu ts - x - x (cosh ts - 1) - ln 2,
+// summed as a double-float and exponentiated in FP32 times h S.  FP64 is used
+// instead near r -> 0 (x < 1, where nu log x cancels against log K), when
+// x (cosh ts - 1) > 2 (its FP32 value would cost > 5e-7 absolute), and for
+// entries below ~e^-85 (beyond the float range of the FP32 path).
+__device__ __forceinline__ double matern_f32_finish(DF z, const Window32& w, const Quad32& q,
+                                                    const MaternParams& mp) {
+  if (z.hi >= 1.0f && q.xc1 <= 2.0f) {
+    const DF nu = DF{mp.nu_hi, mp.nu_lo};
+    DF a = df_add(DF{mp.log_pref_hi, mp.log_pref_lo}, df_mul(nu, df_log(z)));
+    a = df_add(a, df_mul_f(nu, w.ts));
+    a = df_add(a, df_neg(z));
+    a = df_add_f(a, -q.xc1);
+    a = df_add(a, DF{-kLn2DfHi, -kLn2DfLo});
+    if (a.hi >= -85.0f) return (double)df_exp_times(a, q.hS);
+  }
+  const double z64 = (double)z.hi + (double)z.lo;
+  const double lz = log_pos(z64);
+  return exp_fast(fma(mp.nu, lz, mp.log_pref) + log_scale_from(z64, mp.nu, w.ts, q)) *
+         (double)q.hS;
+}
+
+// a2 for the FP32 forms: x = r / beta as a double-float from the staged
+// double-float coordinates (hi is what the FP32 integrand uses).
+__device__ __forceinline__ DF matern_x_df(const Loc& a, const Loc& b, const MaternParams& mp) {
+  const DF r = df_hypot_diff(a.xh, a.xl, a.yh, a.yl, b.xh, b.xl, b.yh, b.yl);
+  if (r.hi == 0.0f) return r;
+  return df_mul(r, DF{mp.inv_beta_f, mp.inv_beta_lo});
+}
+
+// The FP32 precision form (search window).
 struct FormF32 {
-  __device__ __forceinline__ double eval(double x, double nu, Tally& tl, unsigned& evals,
-                                                double& log_k) const {
-    ++evals;
-    float hS;
-    const double scale = log_scale_f32(x, nu, hS, tl);
-    log_k = scale + (double)(kLn2f * mufu_lg2(hS));
-    return exp_split(scale) * (double)hS;
+  __device__ __forceinline__ Window32 window(float x, double x64, float nu, Tally& tl) const {
+    return search_window_f32(x64, nu, tl);
   }
 
-  // a2 in FP64; a3..a6 in FP32; a7 as the FP64 sum
-  // log prefactor + nu log x + log f_s, exponentiated and scaled by h S.
-  __device__ __forceinline__ double matern(double xi, double yi, double xj, double yj,
-                                                  double sigma2, double beta, double nu,
-                                                  double log_pref, Tally& tl, unsigned& evals) const {
-    const double dx = xj - xi, dy = yj - yi;
-    const double r = sqrt(fma(dx, dx, dy * dy));
-    if (r == 0.0) return sigma2;
-    const double z = r / beta;
+  __device__ __forceinline__ double eval(double x, double nu, Tally& tl, unsigned& evals,
+                                         double& log_k) const {
     ++evals;
-    float hS;
-    const double scale = log_scale_f32(z, nu, hS, tl);
-    // log x in FP64 near r -> 0, where nu log x cancels against log K_nu
-    const double lz = (z < 1.0) ? log_pos(z) : (double)(kLn2f * mufu_lg2((float)z));
-    return exp_split(fma(nu, lz, log_pref) + scale) * (double)hS;
+    const float xf = (float)x, nf = (float)nu, nl = (float)(nu - (double)nf);
+    const Window32 w = search_window_f32(x, nf, tl);
+    const Quad32 q = quad_f32(xf, nf, nl, w, tl);
+    const double sc = log_scale_from(x, nu, w.ts, q);
+    log_k = sc + (double)(kLn2f * mufu_lg2(q.hS));
+    return exp_fast(sc) * (double)q.hS;
+  }
+
+  // a2 as a double-float; a3..a6 in FP32 on x.hi; a7 by matern_f32_finish.
+  __device__ __forceinline__ double matern(const Loc& a, const Loc& b, const MaternParams& mp,
+                                           Tally& tl, unsigned& evals) const {
+    const DF z = matern_x_df(a, b, mp);
+    if (z.hi == 0.0f) return mp.sigma2;
+    ++evals;
+    const Window32 w = search_window_f32((double)z.hi, mp.nu_hi, tl);
+    const Quad32 q = quad_f32(z.hi, mp.nu_hi, mp.nu_lo, w, tl);
+    return matern_f32_finish(z, w, q, mp);
   }
 };
 
@@ -67,43 +99,45 @@ struct FormF32 {
 LearnedView learned_view(const bk_learned* m);
 
 // FP32 form with the learned window (a10): the window comes from the
-// tabulated network when it passes the in-kernel check, else from the search
-// (counted as a fallback).  A non-finite sum (a badly placed predicted peak
-// can overflow the scaled nodes) also falls back.
+// tabulated network, checked (and where needed repaired) in-kernel, else from
+// the search (counted as a fallback).  A badly placed predicted peak (a node
+// value more than e^2 above the value at the predicted peak, or a non-finite
+// sum) also falls back.
 struct FormF32Learned {
   LearnedView lv;
 
-  __device__ __forceinline__ double scale(double x, double nu, float& hS, Tally& tl) const {
-    Window32 w;
-    if (learned_window_f32(lv, (float)x, (float)nu, w)) {
-      const double sc = scale_from_window_f32(x, nu, w, hS, tl);
-      if (isfinite(hS) && hS > 0.0f && sc == sc) return sc;
+  __device__ __forceinline__ Quad32 quad(float x, double x64, float nu, float nu_lo, Window32& w,
+                                         Tally& tl) const {
+    if (learned_window_f32(lv, x, nu, w, tl.repairs)) {
+      const Quad32 q = quad_f32(x, nu, nu_lo, w, tl);
+      // A predicted peak more than 2 below the true one (some node exceeds it
+      // by that much) would cost FP32 accuracy in the scaled nodes.
+      if (isfinite(q.hS) && q.hS > 0.0f && q.amax <= 2.0f) return q;
     }
     ++tl.fallback;
-    return log_scale_f32(x, nu, hS, tl);
+    w = search_window_f32(x64, nu, tl);
+    return quad_f32(x, nu, nu_lo, w, tl);
   }
 
   __device__ __forceinline__ double eval(double x, double nu, Tally& tl, unsigned& evals,
                                          double& log_k) const {
     ++evals;
-    float hS;
-    const double sc = scale(x, nu, hS, tl);
-    log_k = sc + (double)(kLn2f * mufu_lg2(hS));
-    return exp_split(sc) * (double)hS;
+    const float xf = (float)x, nf = (float)nu, nl = (float)(nu - (double)nf);
+    Window32 w;
+    const Quad32 q = quad(xf, x, nf, nl, w, tl);
+    const double sc = log_scale_from(x, nu, w.ts, q);
+    log_k = sc + (double)(kLn2f * mufu_lg2(q.hS));
+    return exp_fast(sc) * (double)q.hS;
   }
 
-  __device__ __forceinline__ double matern(double xi, double yi, double xj, double yj,
-                                           double sigma2, double beta, double nu,
-                                           double log_pref, Tally& tl, unsigned& evals) const {
-    const double dx = xj - xi, dy = yj - yi;
-    const double r = sqrt(fma(dx, dx, dy * dy));
-    if (r == 0.0) return sigma2;
-    const double z = r / beta;
+  __device__ __forceinline__ double matern(const Loc& a, const Loc& b, const MaternParams& mp,
+                                           Tally& tl, unsigned& evals) const {
+    const DF z = matern_x_df(a, b, mp);
+    if (z.hi == 0.0f) return mp.sigma2;
     ++evals;
-    float hS;
-    const double sc = scale(z, nu, hS, tl);
-    const double lz = (z < 1.0) ? log_pos(z) : (double)(kLn2f * mufu_lg2((float)z));
-    return exp_split(fma(nu, lz, log_pref) + sc) * (double)hS;
+    Window32 w;
+    const Quad32 q = quad(z.hi, (double)z.hi, mp.nu_hi, mp.nu_lo, w, tl);
+    return matern_f32_finish(z, w, q, mp);
   }
 };
 

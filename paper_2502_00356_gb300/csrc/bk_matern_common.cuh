@@ -1,0 +1,56 @@
+// Per-matrix constants and staged locations shared by the Matern kernels and
+// the arithmetic forms.
+#pragma once
+
+#include <cstdint>
+
+#include "bk_math64.cuh"
+
+namespace bk {
+
+constexpr double kInf = __builtin_huge_val();
+
+// a1: log of the Matern prefactor sigma^2 / (2^{nu-1} Gamma(nu)) (Sec. III-A).
+__device__ __forceinline__ double matern_log_prefactor(double sigma2, double nu) {
+  const double ls = (sigma2 > 0.0) ? log_pos(sigma2) : -kInf;
+  return ls - (nu - 1.0) * kLn2 - lgamma(nu);
+}
+
+// Per-matrix constants of one Matern launch (a1 and the order split).
+struct MaternParams {
+  double sigma2, beta, nu, log_pref, inv_beta;
+  float inv_beta_f, nu_hi, nu_lo;  // nu = nu_hi + nu_lo (two floats)
+  float inv_beta_lo;               // 1/beta = inv_beta_f + inv_beta_lo
+  float log_pref_hi, log_pref_lo;  // a1 as two floats
+};
+
+__device__ __forceinline__ MaternParams matern_params(double sigma2, double beta, double nu) {
+  MaternParams p;
+  p.sigma2 = sigma2;
+  p.beta = beta;
+  p.nu = nu;
+  p.log_pref = matern_log_prefactor(sigma2, nu);
+  p.inv_beta = 1.0 / beta;
+  p.inv_beta_f = (float)p.inv_beta;
+  p.nu_hi = (float)nu;
+  p.nu_lo = (float)(nu - (double)p.nu_hi);
+  p.inv_beta_lo = (float)(p.inv_beta - (double)p.inv_beta_f);
+  p.log_pref_hi = (float)p.log_pref;
+  p.log_pref_lo = (float)(p.log_pref - (double)p.log_pref_hi);
+  return p;
+}
+
+// A location as staged in shared memory: FP64 coordinates and the same
+// coordinates as float pairs (hi + lo), so that FP32 forms can form exact-ish
+// differences without FP64 instructions.
+struct Loc {
+  double x, y;
+  float xh, xl, yh, yl;
+};
+
+__device__ __forceinline__ void split_f(double v, float& h, float& l) {
+  h = (float)v;
+  l = (float)(v - (double)h);
+}
+
+}  // namespace bk

@@ -179,7 +179,7 @@ __device__ __forceinline__ float expm1_f32(float y) {
 // K of a neighbouring order, off by ulp(nu) d(log K)/d nu ~ ulp(nu) ln(2 nu/x),
 // ~1e-5 at x ~ 1e-3, nu ~ 18.  Returns h S.
 __device__ __forceinline__ float trapezoid_f32(float x, float nu, float nu_lo, const Window32& w,
-                                               float Ah, float Bh, int N, Tally& tl) {
+                                               float Ah, float Bh, int N, float& amax, Tally& tl) {
   const float h = (w.t1 - w.t0) / (float)N;
   const float tau0 = w.t0 - w.ts;
   float W = mufu_ex2(-2.0f * kLog2ef * nu * w.t0);
@@ -187,6 +187,7 @@ __device__ __forceinline__ float trapezoid_f32(float x, float nu, float nu_lo, c
   float S = 0.0f, c = 0.0f;
   const float x2 = 2.0f * x;
   const bool at_zero = (w.ts == 0.0f);
+  amax = -3.0e38f;
   for (int j = 0; j <= N; ++j) {
     const float tau = fmaf((float)j, h, tau0);
     float a;
@@ -196,6 +197,7 @@ __device__ __forceinline__ float trapezoid_f32(float x, float nu, float nu_lo, c
     } else {
       a = fmaf(nu, tau, fmaf(nu_lo, tau, -fmaf(Ah, expm1_f32(tau), Bh * expm1_f32(-tau))));
     }
+    amax = fmaxf(amax, a);
     float f = exp_f32(a);
     f = fmaf(f, W, f);
     if (j == 0 || j == N) f *= 0.5f;
@@ -226,37 +228,185 @@ __device__ __forceinline__ Window32 search_window_f32(double x64, float nu, Tall
   return w;
 }
 
-// Everything of one K_nu evaluation in the FP32 form after the window:
-// returns h S (FP32) and the FP64 log-scale log f_s = nu ts - x cosh(ts) - ln 2,
-// so that K = e^{log f_s} h S.  x and nu stay FP64 here (nu ts reaches ~200).
-// On failure (node bound exceeded) returns a NaN scale.
-__device__ __forceinline__ double scale_from_window_f32(double x64, double nu64, const Window32& w,
-                                                        float& hS, Tally& tl) {
-  const float x = (float)x64;
-  const float nu = (float)nu64;
-  const float nu_lo = (float)(nu64 - (double)nu);
+// e^t for |t| < ~80 in FP32 without a large exponential argument:
+// t = k ln2 + r with ln 2 split into 16 + remaining bits (k ln2_hi exact for
+// |k| < 2^8) and e^{+-r} from the Taylor polynomial of degree 7 on
+// |r| <= ln2/2 (truncation < 6e-9 relative); returns 2^k e^r and 2^-k e^-r.
+__device__ __forceinline__ float exp_taylor7_f32(float r) {
+  return fmaf(r, fmaf(r, fmaf(r, fmaf(r, fmaf(r, fmaf(r, fmaf(r, 1.0f / 5040.0f, 1.0f / 720.0f),
+                                                          1.0f / 120.0f), 1.0f / 24.0f),
+                                            1.0f / 6.0f), 0.5f), 1.0f), 1.0f);
+}
+__device__ __forceinline__ void exp_pm_f32(float t, float& ep, float& em) {
+  const float kf = rintf(t * kLog2ef);
+  const int k = (int)kf;
+  float r = fmaf(-kf, 0.693145751953125f, t);
+  r = fmaf(-kf, 1.428606765330187e-06f, r);
+  ep = exp_taylor7_f32(r) * __int_as_float((127 + k) << 23);
+  em = exp_taylor7_f32(-r) * __int_as_float((127 - k) << 23);
+}
+
+// ---------------------------------------------------------------------------
+// Double-float arithmetic (an unevaluated sum hi + lo of two floats, ~44
+// significant bits) from error-free transformations (Knuth's two-sum, the FMA
+// two-product), so that the FP32 forms can keep distances and log-domain sums
+// accurate without FP64 instructions.
+struct DF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ DF two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return DF{s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ DF quick_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = a + b;
+  return DF{s, b - (s - a)};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const DF s = two_sum(a.hi, b.hi);
+  return quick_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+__device__ __forceinline__ DF df_add_f(DF a, float b) {
+  const DF s = two_sum(a.hi, b);
+  return quick_two_sum(s.hi, s.lo + a.lo);
+}
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const float p = a.hi * b.hi;
+  const float e = fmaf(a.hi, b.hi, -p);
+  return quick_two_sum(p, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e)));
+}
+__device__ __forceinline__ DF df_mul_f(DF a, float b) {
+  const float p = a.hi * b;
+  const float e = fmaf(a.hi, b, -p);
+  return quick_two_sum(p, fmaf(a.lo, b, e));
+}
+__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
+__device__ __forceinline__ DF df_from_double(double v) {
+  const float h = (float)v;
+  return DF{h, (float)(v - (double)h)};
+}
+
+// ln 2 as a double-float, and split for range reduction (k ln2_hi exact for
+// |k| < 2^8): ln2_hi has 16 significant bits.
+constexpr float kLn2HiF = 0.693145751953125f;
+constexpr float kLn2LoF = 1.428606765330187e-06f;
+constexpr float kLn2DfHi = 0.693147182464599609375f;  // float nearest to ln 2
+constexpr float kLn2DfLo = -1.904654323148236e-09f;   // ln 2 - kLn2DfHi
+
+// log of a double-float z > 0 (normal floats): z = 2^e m, m in [sqrt(1/2),
+// sqrt(2)), log m = 2 atanh(s), s = (m - 1)/(m + 1) from its series to s^13
+// (truncation < 1e-9 absolute), plus e ln 2 and the first-order lo term.
+__device__ __forceinline__ DF df_log(DF z) {
+  int e;
+  float m = frexpf(z.hi, &e);  // z.hi = m 2^e, m in [0.5, 1)
+  if (m < 0.70710678f) {
+    m *= 2.0f;
+    e -= 1;
+  }
+  const float s = (m - 1.0f) / (m + 1.0f), s2 = s * s;
+  const float q = fmaf(s2, fmaf(s2, fmaf(s2, fmaf(s2, fmaf(s2, fmaf(s2, 1.0f / 13.0f, 1.0f / 11.0f),
+                                                          1.0f / 9.0f), 1.0f / 7.0f), 1.0f / 5.0f),
+                                1.0f / 3.0f), 1.0f);
+  const float lm = 2.0f * s * q;
+  const float ef = (float)e;
+  DF r = quick_two_sum(ef * kLn2HiF, fmaf(ef, kLn2LoF, lm));  // e ln2_hi exact
+  return df_add_f(r, z.lo / z.hi);
+}
+
+// Distance as a double-float from the double-float coordinates: the hi-part
+// differences are made exact with two-sum, squares with the FMA two-product.
+// r.hi == 0 exactly when both FP64 coordinates agree.
+__device__ __forceinline__ DF df_hypot_diff(float axh, float axl, float ayh, float ayl, float bxh,
+                                            float bxl, float byh, float byl) {
+  DF dx = two_sum(bxh, -axh);
+  dx = two_sum(dx.hi, dx.lo + (bxl - axl));  // renormalise: the hi parts may cancel
+  DF dy = two_sum(byh, -ayh);
+  dy = two_sum(dy.hi, dy.lo + (byl - ayl));
+  DF px = DF{dx.hi * dx.hi, 0.0f};
+  px.lo = fmaf(dx.hi, dx.hi, -px.hi);
+  px.lo = fmaf(2.0f * dx.hi, dx.lo, px.lo);
+  DF py = DF{dy.hi * dy.hi, 0.0f};
+  py.lo = fmaf(dy.hi, dy.hi, -py.hi);
+  py.lo = fmaf(2.0f * dy.hi, dy.lo, py.lo);
+  const DF r2 = df_add(px, py);
+  if (r2.hi == 0.0f && dx.hi == 0.0f && dy.hi == 0.0f && dx.lo == 0.0f && dy.lo == 0.0f)
+    return DF{0.0f, 0.0f};
+  const float rh = sqrtf(r2.hi);
+  return DF{rh, (fmaf(-rh, rh, r2.hi) + r2.lo) * (0.5f / rh)};
+}
+
+// e^a * s for a double-float a with FP32 accuracy, as a float (the FP32
+// output case; underflows to 0 below the float range).
+__device__ __forceinline__ float df_exp_times(DF a, float s) {
+  if (a.hi < -103.0f) return 0.0f;
+  const float kf = rintf(a.hi * kLog2ef);
+  float r = fmaf(-kf, kLn2HiF, a.hi);
+  r = fmaf(-kf, kLn2LoF, r) + a.lo;
+  const int k = (int)kf;
+  const int k1 = k >> 1;  // split so both factors stay normal floats
+  return (exp_taylor7_f32(r) * s) * __int_as_float((127 + k1) << 23) *
+         __int_as_float((127 + k - k1) << 23);
+}
+
+// The FP32 quadrature of one evaluation on a given window: h S and
+// x (cosh ts - 1) (FP32; NaN h S when the node bound is exceeded).
+struct Quad32 {
+  float hS;
+  float xc1;   // x (cosh ts - 1) = 2 x sinh^2(ts/2)
+  float amax;  // largest node exponent g(t_j) - g(ts) (up to the e^{-2 nu t} factor)
+};
+
+__device__ __forceinline__ Quad32 quad_f32(float x, float nu, float nu_lo, const Window32& w,
+                                           Tally& tl) {
+  Quad32 q;
   const int N = strip_node_count(x, nu, w.t1 - w.t0, kF32Log2OverTol, kF32MaxNodes);
   if (N > kF32MaxNodes) {
     ++tl.fail;
-    hS = 0.0f;
-    return __longlong_as_double(0x7ff8000000000000LL);
+    q.hS = __int_as_float(0x7fc00000);
+    q.xc1 = 0.0f;
+    q.amax = 0.0f;
+    return q;
   }
-  // e^{ts} of the (FP32) peak in FP64: x cosh(ts) can be ~1e2 and enters
-  // the scale, x e^{+-ts}/2 enter the node exponents.
-  double cs = 1.0;
   float Ah = 0.5f * x, Bh = 0.5f * x;
+  q.xc1 = 0.0f;
   if (w.ts > 0.0f) {
-    const double e = exp_bounded((double)w.ts), er = 1.0 / e;
-    cs = 0.5 * (e + er);
-    Ah = (float)(0.5 * x64 * e);
-    Bh = (float)(0.5 * x64 * er);
+    float ep, em;
+    exp_pm_f32(w.ts, ep, em);
+    Ah *= ep;
+    Bh *= em;
+    const float sh = sinh_f32(0.5f * w.ts);
+    q.xc1 = 2.0f * x * sh * sh;
   }
-  hS = trapezoid_f32(x, nu, nu_lo, w, Ah, Bh, N, tl);
-  return fma(nu64, (double)w.ts, -x64 * cs) - kLn2;
+  q.hS = trapezoid_f32(x, nu, nu_lo, w, Ah, Bh, N, q.amax, tl);
+  return q;
 }
 
-__device__ __forceinline__ double log_scale_f32(double x64, double nu64, float& hS, Tally& tl) {
-  return scale_from_window_f32(x64, nu64, search_window_f32(x64, (float)nu64, tl), hS, tl);
+// log f_s = nu ts - x cosh(ts) - ln 2 in FP64 (nu ts reaches ~200): x exactly,
+// x (cosh ts - 1) from FP32 when it is below 2 (absolute error < 5e-7),
+// else from FP64 e^{ts}.
+__device__ __forceinline__ double log_scale_from(double x64, double nu64, float ts,
+                                                 const Quad32& q) {
+  double xc1 = (double)q.xc1;
+  if (q.xc1 > 2.0f) {
+    const double e = exp_bounded((double)ts);
+    const double sh = 0.5 * (e - 1.0 / e);
+    xc1 = x64 * (sh * sh) / (0.5 * (e + 1.0 / e) + 1.0);  // x (cosh - 1) = x sinh^2/(cosh + 1)
+  }
+  return fma(nu64, (double)ts, -x64) - xc1 - kLn2;
+}
+
+// e^a for a FP64 argument with FP32 accuracy (MUFU ex2 on the reduced
+// argument); NaN propagates, |a| beyond the double range is not handled.
+__device__ __forceinline__ double exp_fast(double a) {
+  double kd = fma(a, kLog2e, kRoundMagic);
+  const int k = __double2loint(kd);
+  kd -= kRoundMagic;
+  double r = fma(-kd, kLn2Hi, a);
+  r = fma(-kd, kLn2Lo, r);
+  const int k1 = k >> 1;
+  return ((double)mufu_ex2((float)r * kLog2ef) * pow2i(k1)) * pow2i(k - k1);
 }
 
 // ---------------------------------------------------------------------------
@@ -280,7 +430,7 @@ struct LearnedView {
 };
 
 __device__ __forceinline__ bool learned_window_f32(const LearnedView& lv, float x, float nu,
-                                                   Window32& w) {
+                                                   Window32& w, unsigned& repairs) {
   const float lx = kLn2f * mufu_lg2(x);
   const float fx = (lx - kTabLx0) * ((kTabX - 1) / (kTabLx1 - kTabLx0));
   const float fn = (nu - kTabNu0) * ((kTabNu - 1) / (kTabNu1 - kTabNu0));
@@ -296,19 +446,34 @@ __device__ __forceinline__ bool learned_window_f32(const LearnedView& lv, float 
   const float ts = fmaxf(b00 * p00.x + b01 * p01.x + b10 * p10.x + b11 * p11.x, 0.0f);
   const float left = fmaxf(b00 * p00.y + b01 * p01.y + b10 * p10.y + b11 * p11.y, 0.0f);
   const float right = fmaxf(b00 * p00.z + b01 * p01.z + b10 * p10.z + b11 * p11.z, 0.0f);
-  const float t0 = fmaxf(0.0f, ts - fmaf(left, 1.0f + lv.margin_rel, lv.margin_abs));
-  const float t1 = ts + fmaf(right, 1.0f + lv.margin_rel, lv.margin_abs);
+  float t0 = fmaxf(0.0f, ts - fmaf(left, 1.0f + lv.margin_rel, lv.margin_abs));
+  float t1 = ts + fmaf(right, 1.0f + lv.margin_rel, lv.margin_abs);
   const float L = kLogInvEps32;
+  // Right end.  F is concave and decreasing past its maximum at asinh(nu/x):
+  // a point with F > 0 and F' < 0 lies left of the root, and one Newton step
+  // from there lands right of it (the tangent lies above F).
   const float F1 = fmaf(nu, t1 - ts, -x * dcosh_f32(t1, ts)) + L;
-  bool ok = (F1 <= 0.0f);
+  if (F1 > 0.0f) {
+    const float Fp = fmaf(-x, sinh_f32(t1), nu);
+    if (!(Fp < 0.0f)) return false;
+    t1 -= F1 / Fp;
+    ++repairs;
+  }
+  // Left end (only when interior): G = F + ln 2 is concave and increasing on
+  // [0, ts]; from a point with G > 0 one Newton step lands left of the root.
   if (t0 > 0.0f) {
-    const float F0 = fmaf(nu, t0 - ts, -x * dcosh_f32(t0, ts)) + L + kLn2f;
-    ok = ok && (F0 <= 0.0f);
+    const float G = fmaf(nu, t0 - ts, -x * dcosh_f32(t0, ts)) + L + kLn2f;
+    if (G > 0.0f) {
+      const float Gp = fmaf(-x, sinh_f32(t0), nu);
+      if (!(Gp > 0.0f)) return false;
+      t0 = fmaxf(0.0f, t0 - G / Gp);
+      ++repairs;
+    }
   }
   w.ts = ts;
   w.t0 = t0;
   w.t1 = t1;
-  return ok;
+  return true;
 }
 
 }  // namespace bk

@@ -117,7 +117,8 @@ struct Tally {
   unsigned iters;       // window-end Newton iterations
   unsigned peak_iters;  // peak Newton iterations
   unsigned fail;        // evaluations returned as NaN
-  unsigned fallback;    // learned windows rejected by the in-kernel check
+  unsigned fallback;    // learned windows replaced by the full search
+  unsigned repairs;     // learned window ends moved by one Newton step
 };
 
 // The window of Sec. IV-B.  ts = t_max, cs/ss = cosh/sinh(ts), [t0, t1] the

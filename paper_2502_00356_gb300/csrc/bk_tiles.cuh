@@ -2,8 +2,7 @@
 // symmetric Matern tile writer and the m x n block writer, templated on a
 // Form passed by value that supplies one K_nu evaluation and one Matern entry:
 //   double eval(double x, double nu, Tally&, unsigned& evals, double& log_k) const;
-//   double matern(double xi, double yi, double xj, double yj, double sigma2,
-//                 double beta, double nu, double log_pref, Tally&, unsigned& evals) const;
+//   double matern(const Loc& a, const Loc& b, const MaternParams&, Tally&, unsigned& evals) const;
 #pragma once
 
 #include <cuda_runtime.h>
@@ -12,10 +11,10 @@
 
 #include "bk.h"
 #include "bk_math64.cuh"
+#include "bk_matern_common.cuh"
 
 namespace bk {
 
-constexpr double kInf = __builtin_huge_val();
 
 template <typename T>
 __device__ __forceinline__ T to_out(double v);
@@ -29,11 +28,12 @@ __device__ __forceinline__ float to_out<float>(double v) { return (float)v; }
 __device__ __forceinline__ void flush_tally(unsigned long long* ctr, const Tally& tl,
                                             unsigned evals) {
   if (ctr == nullptr) return;
-  unsigned long long v[6] = {tl.fail, tl.nodes, tl.iters, evals, tl.peak_iters, tl.fallback};
-  const int idx[6] = {BK_CTR_FAIL, BK_CTR_NODES, BK_CTR_ITERS, BK_CTR_EVALS, BK_CTR_PEAK_ITERS,
-                      BK_CTR_FALLBACK};
+  unsigned long long v[7] = {tl.fail,       tl.nodes,    tl.iters,  evals,
+                             tl.peak_iters, tl.fallback, tl.repairs};
+  const int idx[7] = {BK_CTR_FAIL,       BK_CTR_NODES,    BK_CTR_ITERS, BK_CTR_EVALS,
+                      BK_CTR_PEAK_ITERS, BK_CTR_FALLBACK, BK_CTR_REPAIR};
 #pragma unroll
-  for (int k = 0; k < 6; ++k) {
+  for (int k = 0; k < 7; ++k) {
     unsigned long long a = v[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(128) eval_kernel(const Form form, const double
                                                    OutT* __restrict__ out,
                                                    OutT* __restrict__ log_out, int64_t n,
                                                    unsigned long long* __restrict__ ctr) {
-  Tally tl{0u, 0u, 0u, 0u, 0u};
+  Tally tl{0u, 0u, 0u, 0u, 0u, 0u};
   unsigned evals = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -76,12 +76,6 @@ __global__ void __launch_bounds__(128) eval_kernel(const Form form, const double
     if (log_out != nullptr) log_out[i] = to_out<OutT>(lk);
   }
   flush_tally(ctr, tl, evals);
-}
-
-// a1: log of the Matern prefactor sigma^2 / (2^{nu-1} Gamma(nu)) (Sec. III-A).
-__device__ __forceinline__ double matern_log_prefactor(double sigma2, double nu) {
-  const double ls = (sigma2 > 0.0) ? log_pos(sigma2) : -kInf;
-  return ls - (nu - 1.0) * kLn2 - lgamma(nu);
 }
 
 constexpr int kTile = 32;     // tile edge (rows and columns)
@@ -97,35 +91,33 @@ constexpr int kThreads = kWarps * 32;
 // synchronise the block before the shared arrays are reused.
 template <typename OutT>
 struct SymTileSmem {
-  double rx[kTile], ry[kTile], cx[kTile], cy[kTile];
+  Loc r[kTile], c[kTile];
   OutT tile[kTile][kTile + 1];
 };
+
+__device__ __forceinline__ void stage_loc(Loc& L, const double* __restrict__ locs, int64_t n,
+                                          int64_t i) {
+  L.x = (i < n) ? locs[i] : 0.0;
+  L.y = (i < n) ? locs[n + i] : 0.0;
+  split_f(L.x, L.xh, L.xl);
+  split_f(L.y, L.yh, L.yl);
+}
 
 template <class Form, typename OutT, int WARPS>
 __device__ __forceinline__ void sym_tile(const Form& form, SymTileSmem<OutT>& sm,
                                          const double* __restrict__ locs,
-                                         int64_t n, int64_t I, int64_t J, double sigma2,
-                                         double beta, double nu, double log_pref,
+                                         int64_t n, int64_t I, int64_t J, const MaternParams& mp,
                                          OutT* __restrict__ out, int64_t ld, Tally& tl,
                                          unsigned& evals) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t r0 = I * kTile, c0 = J * kTile;
-  if (warp == 0) {
-    const int64_t i = r0 + lane;
-    sm.rx[lane] = (i < n) ? locs[i] : 0.0;
-    sm.ry[lane] = (i < n) ? locs[n + i] : 0.0;
-  } else if (warp == 1) {
-    const int64_t j = c0 + lane;
-    sm.cx[lane] = (j < n) ? locs[j] : 0.0;
-    sm.cy[lane] = (j < n) ? locs[n + j] : 0.0;
-  }
+  if (warp == 0) stage_loc(sm.r[lane], locs, n, r0 + lane);
+  else if (warp == 1) stage_loc(sm.c[lane], locs, n, c0 + lane);
   __syncthreads();
 #pragma unroll 1
   for (int c = warp; c < kTile; c += WARPS) {
     double v = 0.0;
-    if (r0 + lane < n && c0 + c < n)
-      v = form.matern(sm.rx[lane], sm.ry[lane], sm.cx[c], sm.cy[c], sigma2, beta, nu, log_pref,
-                      tl, evals);
+    if (r0 + lane < n && c0 + c < n) v = form.matern(sm.r[lane], sm.c[c], mp, tl, evals);
     sm.tile[lane][c] = to_out<OutT>(v);
   }
   __syncthreads();
@@ -157,15 +149,14 @@ __global__ void __launch_bounds__(kThreads) matern_sym_kernel(
     const Form form, const double* __restrict__ locs, int64_t n, double sigma2, double beta, double nu,
     OutT* __restrict__ out, int64_t ld, int64_t ntiles, unsigned long long* __restrict__ ctr) {
   __shared__ SymTileSmem<OutT> sm;
-  const double log_pref = matern_log_prefactor(sigma2, nu);
-  Tally tl{0u, 0u, 0u, 0u, 0u};
+  const MaternParams mp = matern_params(sigma2, beta, nu);
+  Tally tl{0u, 0u, 0u, 0u, 0u, 0u};
   unsigned evals = 0;
   for (int64_t tix = blockIdx.x; tix < ntiles; tix += gridDim.x) {
     int64_t I, J;
     tri_tile(tix, I, J);
     __syncthreads();  // the previous tile's shared data is no longer read
-    sym_tile<Form, OutT, kWarps>(form, sm, locs, n, I, J, sigma2, beta, nu, log_pref, out, ld, tl,
-                                 evals);
+    sym_tile<Form, OutT, kWarps>(form, sm, locs, n, I, J, mp, out, ld, tl, evals);
   }
   flush_tally(ctr, tl, evals);
 }
@@ -176,31 +167,22 @@ __global__ void __launch_bounds__(kThreads) matern_block_kernel(
     const Form form, const double* __restrict__ locs1, int64_t m, const double* __restrict__ locs2, int64_t n,
     double sigma2, double beta, double nu, OutT* __restrict__ out, int64_t ld, int64_t tiles_m,
     int64_t ntiles, unsigned long long* __restrict__ ctr) {
-  __shared__ double s_rx[kTile], s_ry[kTile], s_cx[kTile], s_cy[kTile];
+  __shared__ Loc s_r[kTile], s_c[kTile];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const double log_pref = matern_log_prefactor(sigma2, nu);
-  Tally tl{0u, 0u, 0u, 0u, 0u};
+  const MaternParams mp = matern_params(sigma2, beta, nu);
+  Tally tl{0u, 0u, 0u, 0u, 0u, 0u};
   unsigned evals = 0;
   for (int64_t tix = blockIdx.x; tix < ntiles; tix += gridDim.x) {
     const int64_t r0 = (tix % tiles_m) * kTile, c0 = (tix / tiles_m) * kTile;
     __syncthreads();
-    if (warp == 0) {
-      const int64_t i = r0 + lane;
-      s_rx[lane] = (i < m) ? locs1[i] : 0.0;
-      s_ry[lane] = (i < m) ? locs1[m + i] : 0.0;
-    } else if (warp == 1) {
-      const int64_t j = c0 + lane;
-      s_cx[lane] = (j < n) ? locs2[j] : 0.0;
-      s_cy[lane] = (j < n) ? locs2[n + j] : 0.0;
-    }
+    if (warp == 0) stage_loc(s_r[lane], locs1, m, r0 + lane);
+    else if (warp == 1) stage_loc(s_c[lane], locs2, n, c0 + lane);
     __syncthreads();
 #pragma unroll 1
     for (int k = 0; k < kTile / kWarps; ++k) {
       const int c = warp + kWarps * k;
       const int64_t i = r0 + lane, j = c0 + c;
-      if (i < m && j < n)
-        out[i + j * ld] = to_out<OutT>(form.matern(s_rx[lane], s_ry[lane], s_cx[c], s_cy[c],
-                                                        sigma2, beta, nu, log_pref, tl, evals));
+      if (i < m && j < n) out[i + j * ld] = to_out<OutT>(form.matern(s_r[lane], s_c[c], mp, tl, evals));
     }
   }
   flush_tally(ctr, tl, evals);
