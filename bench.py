@@ -38,7 +38,7 @@ WORKLOAD = "matern_jittered_grid_n20000_beta0.1_nu{0.5,1.5,2.3}_fp64"
 # counted from the kernel source: per quadrature node, per peak Newton
 # iteration, per window-end Newton iteration, and a fixed part per Matern
 # entry (distance, set-ups, final logs and exp) or per bare K_nu evaluation.
-FLOP_NODE, FLOP_PEAK_IT, FLOP_WIN_IT, FLOP_ENTRY_FIXED, FLOP_EVAL_FIXED = 44, 88, 48, 300, 260
+FLOP_NODE, FLOP_PEAK_IT, FLOP_WIN_IT, FLOP_ENTRY_FIXED, FLOP_EVAL_FIXED = 30, 89, 51, 170, 125
 # FP64 peak derived from the unit count and clock: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 

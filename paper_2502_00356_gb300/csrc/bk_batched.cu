@@ -53,6 +53,10 @@ __global__ void __launch_bounds__(WARPS * 32) matern_batched_kernel(
     const int64_t* __restrict__ sizes, int64_t limit, unsigned long long* __restrict__ next,
     int chunk, unsigned long long* __restrict__ ctr) {
   __shared__ BatchSmem<OutT> sm;
+  __shared__ double s_tab[16];
+  exp_table_init(s_tab);
+  Form f = form;
+  f.tab = s_tab;
   Tally tl{0u, 0u, 0u, 0u, 0u, 0u};
   unsigned evals = 0;
   int cur = -1;
@@ -88,7 +92,7 @@ __global__ void __launch_bounds__(WARPS * 32) matern_batched_kernel(
       int64_t I, J;
       tri_tile(w - __ldg(prefix + k), I, J);
       __syncthreads();
-      sym_tile<Form, OutT, WARPS>(form, sm.tile, sm.locs, sm.n, I, J, sm.mp, sm.out, sm.ld, tl,
+      sym_tile<Form, OutT, WARPS>(f, sm.tile, sm.locs, sm.n, I, J, sm.mp, sm.out, sm.ld, tl,
                                   evals);
     }
   }
@@ -494,6 +498,10 @@ __global__ void __launch_bounds__(WARPS * 32) matern_batched_static_kernel(
   const int64_t* sizes = (const int64_t*)(scratch + kStaticSizesOff);
   const int64_t limit = prefix[count];
   __shared__ BatchSmem<OutT> sm;
+  __shared__ double s_tab[16];
+  exp_table_init(s_tab);
+  Form f{};
+  f.tab = s_tab;
   Tally tl{0u, 0u, 0u, 0u, 0u, 0u};
   unsigned evals = 0;
   int cur = -1;
@@ -523,7 +531,7 @@ __global__ void __launch_bounds__(WARPS * 32) matern_batched_static_kernel(
     int64_t I, J;
     tri_tile(w - prefix[k], I, J);
     __syncthreads();
-    sym_tile<Form, OutT, WARPS>(Form{}, sm.tile, sm.locs, sm.n, I, J, sm.mp, sm.out, sm.ld, tl,
+    sym_tile<Form, OutT, WARPS>(f, sm.tile, sm.locs, sm.n, I, J, sm.mp, sm.out, sm.ld, tl,
                                 evals);
   }
 }

@@ -12,12 +12,19 @@
 
 namespace bk {
 
+// Every form carries `tab`, the block's shared-memory copy of the 2^{j/16}
+// table of exp_tab (bound by the kernels).
 struct FormF64 {
+  const double* tab;
+
   __device__ __forceinline__ double eval(double x, double nu, Tally& tl, unsigned& evals,
-                                         double& log_k) const {
+                                         double& log_k, bool want_log) const {
     ++evals;
-    log_k = log_kv_f64(x, nu, kPlainLog2OverTol, kPlainMaxNodes, tl);
-    return exp_full(log_k);
+    double hS;
+    const double sc = scale_f64(x, nu, kPlainLog2OverTol, kPlainMaxNodes, tab, hS, tl);
+    const double lh = (want_log || sc > 700.0) ? log_pos(hS) : 0.0;
+    if (want_log) log_k = sc + lh;
+    return (sc > 700.0) ? exp_full(sc + lh) : exp_full(sc) * hS;
   }
 
   // a2 + a3..a7 for one entry: distance, x = r / beta, log K_nu(x),
@@ -28,10 +35,11 @@ struct FormF64 {
     const double dx = b.x - a.x, dy = b.y - a.y;
     const double r = sqrt(fma(dx, dx, dy * dy));
     if (r == 0.0) return mp.sigma2;
-    const double z = r / mp.beta;
+    const double z = r * mp.inv_beta;
     ++evals;
-    const double lk = log_kv_f64(z, mp.nu, kPlainLog2OverTol, kPlainMaxNodes, tl);
-    return exp_full(fma(mp.nu, log_pos(z), mp.log_pref) + lk);
+    double hS;
+    const double sc = scale_f64(z, mp.nu, kPlainLog2OverTol, kPlainMaxNodes, tab, hS, tl);
+    return exp_full(fma(mp.nu, log_pos(z), mp.log_pref) + sc) * hS;
   }
 };
 
@@ -68,15 +76,13 @@ __device__ __forceinline__ DF matern_x_df(const Loc& a, const Loc& b, const Mate
 
 // The FP32 precision form (search window).
 struct FormF32 {
-  __device__ __forceinline__ Window32 window(float x, double x64, float nu, Tally& tl) const {
-    return search_window_f32(x64, nu, tl);
-  }
+  const double* tab;
 
   __device__ __forceinline__ double eval(double x, double nu, Tally& tl, unsigned& evals,
-                                         double& log_k) const {
+                                         double& log_k, bool) const {
     ++evals;
     const float xf = (float)x, nf = (float)nu, nl = (float)(nu - (double)nf);
-    const Window32 w = search_window_f32(x, nf, tl);
+    const Window32 w = search_window_f32(x, nf, tab, tl);
     const Quad32 q = quad_f32(xf, nf, nl, w, tl);
     const double sc = log_scale_from(x, nu, w.ts, q);
     log_k = sc + (double)(kLn2f * mufu_lg2(q.hS));
@@ -89,7 +95,7 @@ struct FormF32 {
     const DF z = matern_x_df(a, b, mp);
     if (z.hi == 0.0f) return mp.sigma2;
     ++evals;
-    const Window32 w = search_window_f32((double)z.hi, mp.nu_hi, tl);
+    const Window32 w = search_window_f32((double)z.hi, mp.nu_hi, tab, tl);
     const Quad32 q = quad_f32(z.hi, mp.nu_hi, mp.nu_lo, w, tl);
     return matern_f32_finish(z, w, q, mp);
   }
@@ -105,6 +111,7 @@ LearnedView learned_view(const bk_learned* m);
 // sum) also falls back.
 struct FormF32Learned {
   LearnedView lv;
+  const double* tab;
 
   __device__ __forceinline__ Quad32 quad(float x, double x64, float nu, float nu_lo, Window32& w,
                                          Tally& tl) const {
@@ -115,12 +122,12 @@ struct FormF32Learned {
       if (isfinite(q.hS) && q.hS > 0.0f && q.amax <= 2.0f) return q;
     }
     ++tl.fallback;
-    w = search_window_f32(x64, nu, tl);
+    w = search_window_f32(x64, nu, tab, tl);
     return quad_f32(x, nu, nu_lo, w, tl);
   }
 
   __device__ __forceinline__ double eval(double x, double nu, Tally& tl, unsigned& evals,
-                                         double& log_k) const {
+                                         double& log_k, bool) const {
     ++evals;
     const float xf = (float)x, nf = (float)nu, nl = (float)(nu - (double)nf);
     Window32 w;

@@ -425,13 +425,13 @@ bool learned_ready(const bk_learned* m) { return m != nullptr && m->has_stats; }
 cudaError_t launch_eval_learned(const bk_learned* m, const double* x, const double* nu, void* out,
                                 void* log_out, bk_dtype out_t, int64_t n, unsigned long long* ctr,
                                 cudaStream_t s) {
-  return launch_eval_form(FormF32Learned{learned_view(m)}, x, nu, out, log_out, out_t, n, ctr, s);
+  return launch_eval_form(FormF32Learned{learned_view(m), nullptr}, x, nu, out, log_out, out_t, n, ctr, s);
 }
 
 cudaError_t launch_matern_sym_learned(const bk_learned* m, const double* locs, int64_t n,
                                       double sigma2, double beta, double nu, void* out, int64_t ld,
                                       bk_dtype out_t, unsigned long long* ctr, cudaStream_t s) {
-  return launch_matern_sym_form(FormF32Learned{learned_view(m)}, locs, n, sigma2, beta, nu, out,
+  return launch_matern_sym_form(FormF32Learned{learned_view(m), nullptr}, locs, n, sigma2, beta, nu, out,
                                 ld, out_t, ctr, s);
 }
 
@@ -439,7 +439,7 @@ cudaError_t launch_matern_block_learned(const bk_learned* m, const double* locs1
                                         const double* locs2, int64_t n, double sigma2,
                                         double beta, double nu, void* out, int64_t ld,
                                         bk_dtype out_t, unsigned long long* ctr, cudaStream_t s) {
-  return launch_matern_block_form(FormF32Learned{learned_view(m)}, locs1, m_, locs2, n, sigma2,
+  return launch_matern_block_form(FormF32Learned{learned_view(m), nullptr}, locs1, m_, locs2, n, sigma2,
                                   beta, nu, out, ld, out_t, ctr, s);
 }
 

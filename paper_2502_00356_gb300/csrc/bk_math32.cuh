@@ -214,13 +214,14 @@ __device__ __forceinline__ float trapezoid_f32(float x, float nu, float nu_lo, c
 // The searched window of the FP32 form: FP32 search inside x in [1e-4, 1e4],
 // nu <= 40, the FP64 search (with the FP32 eps) outside, where FP32 sinh /
 // cosh of the window ends lose too much.
-__device__ __forceinline__ Window32 search_window_f32(double x64, float nu, Tally& tl) {
+__device__ __forceinline__ Window32 search_window_f32(double x64, float nu,
+                                                     const double* __restrict__ tab, Tally& tl) {
   const float x = (float)x64;
   Window32 w;
   if (x >= 1e-4f && x <= 1e4f && nu <= 40.0f) {
     w = window_f32(x, nu, tl);
   } else {
-    const Window64 w64 = window_f64(x64, (double)nu, (double)kLogInvEps32, tl);
+    const Window64 w64 = window_f64(x64, (double)nu, (double)kLogInvEps32, tab, tl);
     w.ts = (float)w64.ts;
     w.t0 = (float)w64.t0;
     w.t1 = (float)w64.t1;

@@ -110,6 +110,67 @@ __device__ __forceinline__ double log_pos(double a) {
 }
 
 // ---------------------------------------------------------------------------
+// Table-driven e^a for the hot loops (Tang's method): a = (16 k + j) ln2/16 + r,
+// |r| <= ln2/32, e^a = 2^k 2^{j/16} e^r with 2^{j/16} from a 16-entry table
+// that kernels stage in shared memory (exp_table_init) and e^r from its
+// Taylor polynomial of degree 7 (truncation < 2e-18 relative).  2^k is added
+// to the table entry's exponent field.  Valid for a in [-708, 709].
+// The table holds 2^{j/16}, j = 0..15, correctly rounded (from 50-digit values).
+static __constant__ double kExp2Tab16[16] = {
+    0x1.0000000000000p+0, 0x1.0b5586cf9890fp+0, 0x1.172b83c7d517bp+0, 0x1.2387a6e756238p+0,
+    0x1.306fe0a31b715p+0, 0x1.3dea64c123422p+0, 0x1.4bfdad5362a27p+0, 0x1.5ab07dd485429p+0,
+    0x1.6a09e667f3bcdp+0, 0x1.7a11473eb0187p+0, 0x1.8ace5422aa0dbp+0, 0x1.9c49182a3f090p+0,
+    0x1.ae89f995ad3adp+0, 0x1.c199bdd85529cp+0, 0x1.d5818dcfba487p+0, 0x1.ea4afa2a490dap+0};
+constexpr double kLog2e16 = 0x1.71547652b82fep+4;   // 16 / ln 2
+constexpr double kLn2By16Hi = 0x1.62e42fee00000p-5;  // ln2/16, 32 significant bits
+constexpr double kLn2By16Lo = 0x1.a39ef35793c76p-37; // ln2/16 - kLn2By16Hi
+
+// Fills a 16-entry shared-memory copy of the table (first 16 threads) and
+// synchronises the block.
+__device__ __forceinline__ void exp_table_init(double* tab) {
+  if (threadIdx.x < 16) tab[threadIdx.x] = kExp2Tab16[threadIdx.x];
+  __syncthreads();
+}
+
+// FP64 ops: 1 fma + 1 add (rounding), 2 fma (reduction), 7 fma (polynomial), 1 mul.
+constexpr int kExpTabOps = 12;
+__device__ __forceinline__ double exp_tab(double a, const double* __restrict__ tab) {
+  double kd = fma(a, kLog2e16, kRoundMagic);
+  const int n = __double2loint(kd);
+  kd -= kRoundMagic;
+  double r = fma(-kd, kLn2By16Hi, a);
+  r = fma(-kd, kLn2By16Lo, r);
+  double p = 1.0 / 5040.0;
+  p = fma(p, r, 1.0 / 720.0);
+  p = fma(p, r, 1.0 / 120.0);
+  p = fma(p, r, 1.0 / 24.0);
+  p = fma(p, r, 1.0 / 6.0);
+  p = fma(p, r, 0.5);
+  p = fma(p, r, 1.0);
+  p = fma(p, r, 1.0);
+  const double tj = tab[n & 15];
+  const int k = max(n >> 4, -1022);  // arguments below -708 give a tiny value, not garbage
+  return p * __hiloint2double(__double2hiint(tj) + (k << 20), __double2loint(tj));
+}
+
+// 1/a from the hardware approximation refined by Newton-Raphson steps
+// r <- r + r (1 - a r) (each doubles the correct bits; two give full precision).
+__device__ __forceinline__ double rcp_approx(double a) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(a));
+  return r;
+}
+__device__ __forceinline__ double rcp_nr2(double a) {
+  double r = rcp_approx(a);
+  r = fma(r, fma(-a, r, 1.0), r);
+  return fma(r, fma(-a, r, 1.0), r);
+}
+__device__ __forceinline__ double rcp_nr1(double a) {
+  const double r = rcp_approx(a);
+  return fma(r, fma(-a, r, 1.0), r);
+}
+
+// ---------------------------------------------------------------------------
 // Work tally of one evaluation (kept in registers; summed per warp when the
 // caller asked for counters).
 struct Tally {
@@ -132,41 +193,52 @@ struct Window64 {
   double ts, cs, t0, t1;
 };
 
+// FP32 helpers for Newton start values (only their side of the root matters).
+__device__ __forceinline__ float log_start_f32(float v) {  // ln v, ~1e-6 relative
+  float r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+  return 0.69314718f * r;
+}
+
 // a3: t_max = 0 when nu^2 <= x (g''(0) = nu^2 - x <= 0), else the root of
 // g'(t) = nu tanh(nu t) - x sinh t, which is concave on t > 0, positive just
 // right of 0 and negative at asinh(nu/x) (there nu tanh(nu t) < nu = x sinh t).
-// Safeguarded Newton inside that bracket.  Any point of the bracket is a
-// valid shift (g(t) <= g(t_max)), so hitting the iteration cap is not an
-// error; the tolerance is loose because only g(t_max) enters, to 2nd order.
-__device__ __forceinline__ void peak_f64(double x, double nu, double& ts, double& cs, Tally& tl) {
+// Safeguarded Newton inside that bracket; steps from the left that leave it
+// are clamped to its right end, from where Newton descends monotonically.
+// Any point of the bracket is a valid shift (g(t) <= g(t_max)), so hitting
+// the iteration cap is not an error.  Start values come from FP32 (the right
+// end inflated so that it stays right of the root); function values and
+// steps are FP64, reciprocals by Newton-refined hardware approximations.
+// Returns ts, cosh ts and e^{ts}.
+__device__ __forceinline__ void peak_f64(double x, double nu, const double* __restrict__ tab,
+                                         double& ts, double& cs, double& es, Tally& tl) {
   const double nu2 = nu * nu;
   if (!(nu2 > x)) {
     ts = 0.0;
     cs = 1.0;
+    es = 1.0;
     return;
   }
-  const double q = nu / x;
-  double hi = log_pos(q + sqrt(fma(q, q, 1.0)));  // asinh(nu/x)
+  const float qf = (float)nu / (float)x;
+  const float hif = log_start_f32(qf + sqrtf(fmaf(qf, qf, 1.0f)));  // asinh(nu/x)
+  double hi = fma((double)hif, 2e-5, (double)hif) + 1e-6;
   double lo = 0.0;
-  // small-t estimate from the cubic Taylor terms of g'
-  const double tc2 = (nu2 - x) / fma(nu2 * nu2, 1.0 / 3.0, x * (1.0 / 6.0));
-  double t = (tc2 < hi * hi) ? sqrt(tc2) : hi;
+  const float nu2f = (float)nu2, xf = (float)x;
+  const float tc2 = (nu2f - xf) / fmaf(nu2f * nu2f, 1.0f / 3.0f, xf * (1.0f / 6.0f));
+  double t = ((double)tc2 < hi * hi) ? (double)sqrtf(tc2) : hi;
   for (int it = 0; it < 40; ++it) {
     ++tl.peak_iters;
-    const double e = exp_bounded(t);
-    const double er = 1.0 / e;
+    const double e = exp_tab(t, tab);
+    const double er = rcp_nr2(e);
     const double sh = 0.5 * (e - er), ch = 0.5 * (e + er);
-    const double w = exp_bounded(fmax(-2.0 * nu * t, -708.0));
-    const double r1 = 1.0 / (1.0 + w);
+    const double w = exp_tab(fmax(-2.0 * nu * t, -708.0), tab);
+    const double r1 = rcp_nr2(1.0 + w);
     const double gp = fma(nu * (1.0 - w), r1, -x * sh);
     const double gpp = fma(nu2 * 4.0 * w, r1 * r1, -x * ch);
     if (gp > 0.0) lo = t; else hi = t;
-    // Past the inflection of g' (gpp < 0) a Newton step from the left lands
-    // right of the root; clamp it to the right bracket end, from where the
-    // iteration descends monotonically.  Before the inflection, bisect.
     double tn;
     if (gpp < 0.0) {
-      tn = t - gp / gpp;
+      tn = fma(-gp, rcp_nr1(gpp), t);
       if (tn > hi) tn = hi;
       if (!(tn > lo)) tn = 0.5 * (lo + hi);
     } else {
@@ -177,33 +249,38 @@ __device__ __forceinline__ void peak_f64(double x, double nu, double& ts, double
     if (fabs(dt) <= 1e-8 * t) break;
   }
   ts = t;
-  const double e = exp_bounded(t);
-  cs = 0.5 * (e + 1.0 / e);
+  es = exp_tab(t, tab);
+  cs = 0.5 * (es + rcp_nr2(es));
 }
 
 // a4: window ends.  Newton on the concave F approaches t1 from the right and
 // t0 from the left, so every iterate keeps the range at least as wide as the
-// eps-window.
-__device__ __forceinline__ Window64 window_f64(double x, double nu, double L, Tally& tl) {
+// eps-window.  Start values from FP32 bounds, inflated by 2e-5 so that they
+// stay on their side of the root.
+__device__ __forceinline__ Window64 window_f64(double x, double nu, double L,
+                                               const double* __restrict__ tab, Tally& tl) {
   Window64 w;
-  peak_f64(x, nu, w.ts, w.cs, tl);
+  double es;
+  peak_f64(x, nu, tab, w.ts, w.cs, es, tl);
   const double ts = w.ts, cs = w.cs;
-  const double ss = sqrt(fmax(cs * cs - 1.0, 0.0));
-  // ---- t1: start right of the root.  cosh t - cs >= ss d + cs d^2/2 for
-  // d = t - ts >= 0, so the root d of  L + (nu - x ss) d - x cs d^2/2 = 0 is a
-  // right bound; in the exponential regime x e^t/2 >= L + x cs + nu t is one too.
+  // ---- t1: cosh t - cs >= ss d + cs d^2/2 for d = t - ts >= 0, so the root d
+  // of L + (nu - x ss) d - x cs d^2/2 = 0 is a right bound; in the exponential
+  // regime x e^t/2 >= L + x cs + nu t is one too.
   {
-    const double a = x * cs, b = nu - x * ss;
-    double t = ts + (b + sqrt(fma(b, b, 2.0 * a * L))) / a;
-    const double tb = log_pos(2.0 * (L + a + nu * t) / x);
+    const float ssf = (float)(0.5 * (es - rcp_nr1(es)));
+    const float af = (float)(x * cs), bf = (float)nu - (float)x * ssf, Lf = (float)L;
+    const float df = (bf + sqrtf(fmaf(bf, bf, 2.0f * af * Lf))) / af;
+    double t = ts + (double)df * (1.0 + 2e-5);
+    const double tb = (double)log_start_f32(2.0f * (Lf + af + (float)nu * (float)t) / (float)x) *
+                      (1.0 + 2e-5);
     if (tb < t) t = tb;
     for (int it = 0; it < 40; ++it) {
       ++tl.iters;
-      const double e = exp_bounded(fmin(t, 709.0));
-      const double er = 1.0 / e;
+      const double e = exp_tab(fmin(t, 709.0), tab);
+      const double er = rcp_nr2(e);
       const double F = fma(nu, t - ts, -x * (0.5 * (e + er) - cs)) + L;
       const double Fp = fma(-0.5 * x, e - er, nu);
-      const double dt = F / Fp;
+      const double dt = F * rcp_nr1(Fp);
       t -= dt;
       if (fabs(dt) <= 1e-8 * t) break;
     }
@@ -216,15 +293,14 @@ __device__ __forceinline__ Window64 window_f64(double x, double nu, double L, Ta
     const double Lp = L + kLn2;
     const double G0 = fma(-nu, ts, x * (cs - 1.0)) + Lp;
     if (G0 < 0.0) {
-      double t = fmax(0.0, ts - Lp / nu);
+      double t = fmax(0.0, ts - Lp * rcp_nr1(nu));
       for (int it = 0; it < 40; ++it) {
         ++tl.iters;
-        const double e = exp_bounded(t);
-        const double er = 1.0 / e;
+        const double e = exp_tab(t, tab);
+        const double er = rcp_nr2(e);
         const double G = fma(nu, t - ts, -x * (0.5 * (e + er) - cs)) + Lp;
         const double Gp = fma(-0.5 * x, e - er, nu);
-        const double dt = G / Gp;
-        double tn = t - dt;
+        double tn = fma(-G, rcp_nr1(Gp), t);
         if (tn < 0.0) tn = 0.0;
         const bool done = fabs(tn - t) <= 1e-8 * fmax(tn, 1e-3);
         t = tn;
@@ -240,38 +316,46 @@ __device__ __forceinline__ Window64 window_f64(double x, double nu, double L, Ta
 // t_j = t_start + j H, where
 //   f(t) = e^{-x cosh t} cosh(nu t) = f_s exp(nu (t - ts) - x (cosh t - cs)) (1 + e^{-2 nu t}),
 //   f_s = e^{nu ts - x cs} / 2.
-// e^{t_j}, e^{-t_j} and e^{-2 nu t_j} follow geometric recurrences (one real
-// exp per node remains).  first/last receive the scaled end values.
+// D_j = x cosh t_j follows the three-term recurrence D_{j+1} = 2 cosh(H) D_j - D_{j-1}
+// (one FMA; its rounding error grows like j ulp / (2 sinh H)), the exponent's
+// linear part is accumulated, e^{-2 nu t_j} is geometric: one exp per node.
+// first/last receive the scaled end values.
 __device__ __forceinline__ double node_sum_f64(double t_start, double H, int count, double x,
-                                               double nu, double ts, double cs, double& first,
+                                               double nu, double ts, double cs,
+                                               const double* __restrict__ tab, double& first,
                                                double& last) {
-  double E = exp_bounded(t_start);
-  double R = 1.0 / E;
-  const double P = exp_bounded(H);
-  const double Q = 1.0 / P;
-  double W = exp_bounded(fmax(-2.0 * nu * t_start, -708.0));
-  const double rho = exp_bounded(fmax(-2.0 * nu * H, -708.0));
-  const double A0 = fma(nu, t_start - ts, x * cs);
-  const double dA = nu * H;
+  double e0 = 1.0, r0 = 1.0, W = 1.0;
+  if (t_start > 0.0) {
+    e0 = exp_tab(t_start, tab);
+    r0 = rcp_nr2(e0);
+    W = exp_tab(fmax(-2.0 * nu * t_start, -708.0), tab);
+  }
+  const double eh = exp_tab(H, tab), rh = rcp_nr2(eh);
+  const double c = eh + rh;
   const double xh = 0.5 * x;
-  double s = 0.0, jd = 0.0, f = 0.0;
+  double D0 = xh * (e0 + r0);
+  double D1 = xh * fma(e0, eh, r0 * rh);
+  const double rho = exp_tab(fmax(-2.0 * nu * H, -708.0), tab);
+  double A = fma(nu, t_start - ts, x * cs);
+  const double dA = nu * H;
+  double s = 0.0, f = 0.0;
   for (int j = 0; j < count; ++j) {
-    const double arg = fma(-xh, E + R, fma(jd, dA, A0));
-    const double ev = exp_bounded(fmax(arg, -708.0));
+    const double ev = exp_tab(A - D0, tab);
     f = fma(ev, W, ev);
     if (j == 0) first = f;
     s += f;
-    E *= P;
-    R *= Q;
+    const double D2 = fma(c, D1, -D0);
+    D0 = D1;
+    D1 = D2;
+    A += dA;
     W *= rho;
-    jd += 1.0;
   }
   last = f;
   return s;
 }
-// FP64 ops per node in node_sum_f64 (work accounting): 2 fma + 1 add (arg),
-// 1 max, exp, 1 fma + 1 add (f, s), 3 mul + 1 add (recurrences).
-constexpr int kNodeOps64 = 9 + kExpOps;
+// FP64 ops per node in node_sum_f64 (work accounting): 1 add (exponent),
+// exp, 1 fma + 1 add (f, s), 1 fma (recurrence), 1 add + 1 mul.
+constexpr int kNodeOps64 = 6 + kExpTabOps;
 
 // ---------------------------------------------------------------------------
 // a5: node count.  For f analytic in the strip |Im t| < a with
@@ -319,24 +403,34 @@ __device__ __forceinline__ int strip_node_count(float x, float nu, float width, 
 }
 
 // a6/a7: trapezoid on [t0, t1] with N intervals from the strip bound, in the
-// log domain: log K = nu ts - x cs - ln 2 + log(h S), S the weighted sum of
-// the scaled integrand (node_sum_f64).  Sets tl.fail (and returns NaN) when
-// N would exceed n_max.
-__device__ __forceinline__ double log_kv_f64(double x, double nu, float log2_over_tol, int n_max,
-                                             Tally& tl) {
-  const Window64 w = window_f64(x, nu, kLogInvEps64, tl);
+// log domain: K = e^{scale} h S with scale = nu ts - x cs - ln 2 and S the
+// weighted sum of the scaled integrand (node_sum_f64).  Returns the scale and
+// h S; sets tl.fail (and returns NaN) when N would exceed n_max.
+__device__ __forceinline__ double scale_f64(double x, double nu, float log2_over_tol, int n_max,
+                                            const double* __restrict__ tab, double& hS,
+                                            Tally& tl) {
+  const Window64 w = window_f64(x, nu, kLogInvEps64, tab, tl);
   const double width = w.t1 - w.t0;
   const int N = strip_node_count((float)x, (float)nu, (float)width, log2_over_tol, n_max);
   if (N > n_max) {
     ++tl.fail;
-    return __longlong_as_double(0x7ff8000000000000LL);
+    hS = __longlong_as_double(0x7ff8000000000000LL);
+    return hS;
   }
-  const double h = width / N;
+  const double h = width * rcp_nr2((double)N);
   double f0, fN;
-  double S = node_sum_f64(w.t0, h, N + 1, x, nu, w.ts, w.cs, f0, fN);
+  double S = node_sum_f64(w.t0, h, N + 1, x, nu, w.ts, w.cs, tab, f0, fN);
   tl.nodes += N + 1;
   S -= 0.5 * (f0 + fN);
-  return fma(nu, w.ts, -x * w.cs) - kLn2 + log_pos(h * S);
+  hS = h * S;
+  return fma(nu, w.ts, -x * w.cs) - kLn2;
+}
+
+__device__ __forceinline__ double log_kv_f64(double x, double nu, float log2_over_tol, int n_max,
+                                             const double* __restrict__ tab, Tally& tl) {
+  double hS;
+  const double sc = scale_f64(x, nu, log2_over_tol, n_max, tab, hS, tl);
+  return sc + log_pos(hS);
 }
 
 // ln(2 / tol) for the plain form: tol = 1e-13 keeps the quadrature error

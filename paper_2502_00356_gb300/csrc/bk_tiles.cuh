@@ -45,9 +45,9 @@ __device__ __forceinline__ void flush_tally(unsigned long long* ctr, const Tally
 // The element-wise domain rules of the C-ABI around a form's evaluation.
 template <class Form>
 __device__ __forceinline__ double eval_domain(const Form& form, double x, double nu, Tally& tl,
-                                              unsigned& evals, double& log_k) {
+                                              unsigned& evals, double& log_k, bool want_log) {
   nu = fabs(nu);
-  if (x > 0.0 && x < kInf && nu < kInf) return form.eval(x, nu, tl, evals, log_k);
+  if (x > 0.0 && x < kInf && nu < kInf) return form.eval(x, nu, tl, evals, log_k, want_log);
   if (x == 0.0 && nu == nu) {
     log_k = kInf;
     return kInf;
@@ -66,12 +66,17 @@ __global__ void __launch_bounds__(128) eval_kernel(const Form form, const double
                                                    OutT* __restrict__ out,
                                                    OutT* __restrict__ log_out, int64_t n,
                                                    unsigned long long* __restrict__ ctr) {
+  __shared__ double s_tab[16];
+  exp_table_init(s_tab);
+  Form f = form;
+  f.tab = s_tab;
   Tally tl{0u, 0u, 0u, 0u, 0u, 0u};
   unsigned evals = 0;
+  const bool want_log = (log_out != nullptr);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    double lk;
-    const double k = eval_domain<Form>(form, x[i], nu[i], tl, evals, lk);
+    double lk = 0.0;
+    const double k = eval_domain<Form>(f, x[i], nu[i], tl, evals, lk, want_log);
     out[i] = to_out<OutT>(k);
     if (log_out != nullptr) log_out[i] = to_out<OutT>(lk);
   }
@@ -149,6 +154,10 @@ __global__ void __launch_bounds__(kThreads) matern_sym_kernel(
     const Form form, const double* __restrict__ locs, int64_t n, double sigma2, double beta, double nu,
     OutT* __restrict__ out, int64_t ld, int64_t ntiles, unsigned long long* __restrict__ ctr) {
   __shared__ SymTileSmem<OutT> sm;
+  __shared__ double s_tab[16];
+  exp_table_init(s_tab);
+  Form f = form;
+  f.tab = s_tab;
   const MaternParams mp = matern_params(sigma2, beta, nu);
   Tally tl{0u, 0u, 0u, 0u, 0u, 0u};
   unsigned evals = 0;
@@ -156,7 +165,7 @@ __global__ void __launch_bounds__(kThreads) matern_sym_kernel(
     int64_t I, J;
     tri_tile(tix, I, J);
     __syncthreads();  // the previous tile's shared data is no longer read
-    sym_tile<Form, OutT, kWarps>(form, sm, locs, n, I, J, mp, out, ld, tl, evals);
+    sym_tile<Form, OutT, kWarps>(f, sm, locs, n, I, J, mp, out, ld, tl, evals);
   }
   flush_tally(ctr, tl, evals);
 }
@@ -168,6 +177,10 @@ __global__ void __launch_bounds__(kThreads) matern_block_kernel(
     double sigma2, double beta, double nu, OutT* __restrict__ out, int64_t ld, int64_t tiles_m,
     int64_t ntiles, unsigned long long* __restrict__ ctr) {
   __shared__ Loc s_r[kTile], s_c[kTile];
+  __shared__ double s_tab[16];
+  exp_table_init(s_tab);
+  Form f = form;
+  f.tab = s_tab;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const MaternParams mp = matern_params(sigma2, beta, nu);
   Tally tl{0u, 0u, 0u, 0u, 0u, 0u};
@@ -182,7 +195,7 @@ __global__ void __launch_bounds__(kThreads) matern_block_kernel(
     for (int k = 0; k < kTile / kWarps; ++k) {
       const int c = warp + kWarps * k;
       const int64_t i = r0 + lane, j = c0 + c;
-      if (i < m && j < n) out[i + j * ld] = to_out<OutT>(form.matern(s_r[lane], s_c[c], mp, tl, evals));
+      if (i < m && j < n) out[i + j * ld] = to_out<OutT>(f.matern(s_r[lane], s_c[c], mp, tl, evals));
     }
   }
   flush_tally(ctr, tl, evals);

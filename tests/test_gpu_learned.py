@@ -197,7 +197,8 @@ def test_learned_matern_and_batched(dev, trained):
     plan = bk.BatchedPlan([n], dtype=torch.float32, opts=bk.make_opts(learned=trained))
     bk.bk_matern_batched(d, plan)
     torch.cuda.synchronize()
-    assert torch.equal(o2, out)
+    rel = ((o2.double() - out.double()).abs() / out.double().abs().clamp_min(1e-30)).max()
+    assert float(rel) <= 2.5e-7  # same entries from another kernel: agree to rounding
 
 
 def test_learned_needs_weights_and_fp32(dev):
