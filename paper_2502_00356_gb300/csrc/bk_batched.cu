@@ -53,10 +53,8 @@ __global__ void __launch_bounds__(WARPS * 32) matern_batched_kernel(
     const int64_t* __restrict__ sizes, int64_t limit, unsigned long long* __restrict__ next,
     int chunk, unsigned long long* __restrict__ ctr) {
   __shared__ BatchSmem<OutT> sm;
-  __shared__ double s_tab[16];
-  exp_table_init(s_tab);
-  Form f = form;
-  f.tab = s_tab;
+  __shared__ double s_tab[Form::kStageTable ? kExpTabSize : 1];
+  const Form f = bind_table(form, s_tab);
   Tally tl{0u, 0u, 0u, 0u, 0u, 0u};
   unsigned evals = 0;
   int cur = -1;
@@ -498,10 +496,8 @@ __global__ void __launch_bounds__(WARPS * 32) matern_batched_static_kernel(
   const int64_t* sizes = (const int64_t*)(scratch + kStaticSizesOff);
   const int64_t limit = prefix[count];
   __shared__ BatchSmem<OutT> sm;
-  __shared__ double s_tab[16];
-  exp_table_init(s_tab);
-  Form f{};
-  f.tab = s_tab;
+  __shared__ double s_tab[Form::kStageTable ? kExpTabSize : 1];
+  const Form f = bind_table(Form{}, s_tab);
   Tally tl{0u, 0u, 0u, 0u, 0u, 0u};
   unsigned evals = 0;
   int cur = -1;

@@ -12,19 +12,39 @@
 
 namespace bk {
 
-// Every form carries `tab`, the block's shared-memory copy of the 2^{j/16}
-// table of exp_tab (bound by the kernels).
+// FP32 start values for the plain form's FP64 search: the FP32 search run
+// on the same eps (2^-52) inside x in [1e-4, 1e4], nu <= 40, where its sinh
+// and cosh stay accurate; none outside (the FP64 search then starts from
+// its own bounds).  Its iterations are FP32 work and are not tallied: the
+// plain form's counters count FP64 Newton iterations.
+__device__ __forceinline__ const Start32* plain_starts(double x, double nu, Start32& st) {
+  const float xf = (float)x;
+  if (!(xf >= 1e-4f && xf <= 1e4f && nu <= 40.0)) return nullptr;
+  Tally fp32_work{0u, 0u, 0u, 0u, 0u, 0u};
+  const Window32 w = window_f32(xf, (float)nu, (float)kLogInvEps64, fp32_work);
+  st = Start32{w.ts, w.t0, w.t1};
+  return &st;
+}
+
+// Every form carries `tab`, the 2^{j/1024} table of exp2s: the block's
+// shared-memory copy for forms whose hot loop reads it (kStageTable), else
+// the global table (read only on rare FP64 paths).  kTilesPerBlock is the
+// number of 32 x 32 tiles one block of the tile kernels computes.
 struct FormF64 {
+  static constexpr bool kStageTable = true;
+  static constexpr int kTilesPerBlock = 1;
   const double* tab;
 
   __device__ __forceinline__ double eval(double x, double nu, Tally& tl, unsigned& evals,
                                          double& log_k, bool want_log) const {
     ++evals;
+    Start32 st;
+    const Start32* sp = plain_starts(x, nu, st);
     double hS;
-    const double sc = scale_f64(x, nu, kPlainLog2OverTol, kPlainMaxNodes, tab, hS, tl);
-    const double lh = (want_log || sc > 700.0) ? log_pos(hS) : 0.0;
+    const double sc = scale_f64(x, nu, kPlainLog2OverTol, kPlainMaxNodes, tab, hS, tl, sp);
+    const double lh = (want_log || sc > 700.0) ? log_tab(hS, tab) : 0.0;
     if (want_log) log_k = sc + lh;
-    return (sc > 700.0) ? exp_full(sc + lh) : exp_full(sc) * hS;
+    return (sc > 700.0) ? exp_tab_full(sc + lh, tab) : exp_tab_full(sc, tab) * hS;
   }
 
   // a2 + a3..a7 for one entry: distance, x = r / beta, log K_nu(x),
@@ -37,9 +57,11 @@ struct FormF64 {
     if (r == 0.0) return mp.sigma2;
     const double z = r * mp.inv_beta;
     ++evals;
+    Start32 st;
+    const Start32* sp = plain_starts(z, mp.nu, st);
     double hS;
-    const double sc = scale_f64(z, mp.nu, kPlainLog2OverTol, kPlainMaxNodes, tab, hS, tl);
-    return exp_full(fma(mp.nu, log_pos(z), mp.log_pref) + sc) * hS;
+    const double sc = scale_f64(z, mp.nu, kPlainLog2OverTol, kPlainMaxNodes, tab, hS, tl, sp);
+    return exp_tab_full(fma(mp.nu, log_tab(z, tab), mp.log_pref) + sc, tab) * hS;
   }
 };
 
@@ -76,6 +98,8 @@ __device__ __forceinline__ DF matern_x_df(const Loc& a, const Loc& b, const Mate
 
 // The FP32 precision form (search window).
 struct FormF32 {
+  static constexpr bool kStageTable = false;
+  static constexpr int kTilesPerBlock = 4;
   const double* tab;
 
   __device__ __forceinline__ double eval(double x, double nu, Tally& tl, unsigned& evals,
@@ -110,6 +134,8 @@ LearnedView learned_view(const bk_learned* m);
 // value more than e^2 above the value at the predicted peak, or a non-finite
 // sum) also falls back.
 struct FormF32Learned {
+  static constexpr bool kStageTable = false;
+  static constexpr int kTilesPerBlock = 4;
   LearnedView lv;
   const double* tab;
 

@@ -2,6 +2,7 @@
 // the arithmetic forms.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 
 #include "bk_math64.cuh"
@@ -30,6 +31,25 @@ __device__ __forceinline__ MaternParams matern_params(double sigma2, double beta
   p.beta = beta;
   p.nu = nu;
   p.log_pref = matern_log_prefactor(sigma2, nu);
+  p.inv_beta = 1.0 / beta;
+  p.inv_beta_f = (float)p.inv_beta;
+  p.nu_hi = (float)nu;
+  p.nu_lo = (float)(nu - (double)p.nu_hi);
+  p.inv_beta_lo = (float)(p.inv_beta - (double)p.inv_beta_f);
+  p.log_pref_hi = (float)p.log_pref;
+  p.log_pref_lo = (float)(p.log_pref - (double)p.log_pref_hi);
+  return p;
+}
+
+// The same constants computed on the host (std::log, std::lgamma) for the
+// single-matrix launches, so that their many blocks start without per-block
+// setup arithmetic.
+inline MaternParams matern_params_host(double sigma2, double beta, double nu) {
+  MaternParams p;
+  p.sigma2 = sigma2;
+  p.beta = beta;
+  p.nu = nu;
+  p.log_pref = (sigma2 > 0.0 ? std::log(sigma2) : -kInf) - (nu - 1.0) * kLn2 - std::lgamma(nu);
   p.inv_beta = 1.0 / beta;
   p.inv_beta_f = (float)p.inv_beta;
   p.nu_hi = (float)nu;

@@ -105,10 +105,11 @@ __device__ __forceinline__ float dcosh_f32(float t, float ts) {
   return 2.0f * sinh_f32(0.5f * (t + ts)) * sinh_f32(0.5f * (t - ts));
 }
 
-// a4 in FP32 with the bound F of window_f64 (see there), eps = 2^-23.
-__device__ __forceinline__ Window32 window_f32(float x, float nu, Tally& tl) {
+// a4 in FP32 with the bound F of window_f64 (see there), L = -log eps
+// (2^-23 for the FP32 forms; 2^-52 where the plain form takes its FP64
+// Newton starts from here).
+__device__ __forceinline__ Window32 window_f32(float x, float nu, float L, Tally& tl) {
   Window32 w;
-  const float L = kLogInvEps32;
   const float ts = peak_f32(x, nu, tl);
   w.ts = ts;
   const float es = mufu_ex2(ts * kLog2ef);
@@ -219,7 +220,7 @@ __device__ __forceinline__ Window32 search_window_f32(double x64, float nu,
   const float x = (float)x64;
   Window32 w;
   if (x >= 1e-4f && x <= 1e4f && nu <= 40.0f) {
-    w = window_f32(x, nu, tl);
+    w = window_f32(x, nu, kLogInvEps32, tl);
   } else {
     const Window64 w64 = window_f64(x64, (double)nu, (double)kLogInvEps32, tab, tl);
     w.ts = (float)w64.ts;

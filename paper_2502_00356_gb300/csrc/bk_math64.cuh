@@ -110,47 +110,104 @@ __device__ __forceinline__ double log_pos(double a) {
 }
 
 // ---------------------------------------------------------------------------
-// Table-driven e^a for the hot loops (Tang's method): a = (16 k + j) ln2/16 + r,
-// |r| <= ln2/32, e^a = 2^k 2^{j/16} e^r with 2^{j/16} from a 16-entry table
-// that kernels stage in shared memory (exp_table_init) and e^r from its
-// Taylor polynomial of degree 7 (truncation < 2e-18 relative).  2^k is added
-// to the table entry's exponent field.  Valid for a in [-708, 709].
-// The table holds 2^{j/16}, j = 0..15, correctly rounded (from 50-digit values).
-static __constant__ double kExp2Tab16[16] = {
-    0x1.0000000000000p+0, 0x1.0b5586cf9890fp+0, 0x1.172b83c7d517bp+0, 0x1.2387a6e756238p+0,
-    0x1.306fe0a31b715p+0, 0x1.3dea64c123422p+0, 0x1.4bfdad5362a27p+0, 0x1.5ab07dd485429p+0,
-    0x1.6a09e667f3bcdp+0, 0x1.7a11473eb0187p+0, 0x1.8ace5422aa0dbp+0, 0x1.9c49182a3f090p+0,
-    0x1.ae89f995ad3adp+0, 0x1.c199bdd85529cp+0, 0x1.d5818dcfba487p+0, 0x1.ea4afa2a490dap+0};
-constexpr double kLog2e16 = 0x1.71547652b82fep+4;   // 16 / ln 2
-constexpr double kLn2By16Hi = 0x1.62e42fee00000p-5;  // ln2/16, 32 significant bits
-constexpr double kLn2By16Lo = 0x1.a39ef35793c76p-37; // ln2/16 - kLn2By16Hi
+// Table-driven exponential for the hot loops (Tang's method with a 1024-entry
+// table).  The kernels work in scaled units u = a K, K = 1024/ln 2, so that
+// e^a = 2^{u/1024}: u = 1024 k + j + rho (round to nearest, |rho| <= 1/2),
+// e^a = 2^k 2^{j/1024} e^{rho ln2/1024}, the last factor from its Taylor
+// polynomial of degree 3 (|rho ln2/1024| <= 3.4e-4, truncation < 6e-16
+// relative).  2^{j/1024} comes from the block's shared-memory copy of
+// kExp2Tab (exp_table_init); 2^k is added to the entry's exponent field.
+// Valid for u in [-1022 * 1024, 1023 * 1024] (a in [-708, 709]); below that
+// the result is clamped to about 2^-1022, not garbage.
+static __device__ const double kExp2Tab[1024] = {
+#include "bk_exp2_table.inc"
+};
+constexpr int kExpTabSize = 1024;
+constexpr double kExpScale = 0x1.71547652b82fep+10;  // 1024 / ln 2
+constexpr double kExpC1 = 0x1.62e42fefa39efp-11;     // ln2 / 1024
+constexpr double kExpC2 = 0x1.ebfbdff82c58fp-23;     // (ln2/1024)^2 / 2
+constexpr double kExpC3 = 0x1.c6b08d704a0c0p-35;     // (ln2/1024)^3 / 6
+constexpr double kExpC1Hi = 0x1.62e42ff000000p-11;   // ln2/1024 to 32 bits
+constexpr double kExpC1Lo = -0x1.718432a1b0e26p-45;  // ln2/1024 - kExpC1Hi
 
-// Fills a 16-entry shared-memory copy of the table (first 16 threads) and
-// synchronises the block.
+// Copies the table into a shared-memory array of kExpTabSize doubles (all
+// threads of the block take part) and synchronises the block.
 __device__ __forceinline__ void exp_table_init(double* tab) {
-  if (threadIdx.x < 16) tab[threadIdx.x] = kExp2Tab16[threadIdx.x];
+  for (int i = threadIdx.x; i < kExpTabSize; i += blockDim.x) tab[i] = kExp2Tab[i];
   __syncthreads();
 }
 
-// FP64 ops: 1 fma + 1 add (rounding), 2 fma (reduction), 7 fma (polynomial), 1 mul.
-constexpr int kExpTabOps = 12;
-__device__ __forceinline__ double exp_tab(double a, const double* __restrict__ tab) {
-  double kd = fma(a, kLog2e16, kRoundMagic);
-  const int n = __double2loint(kd);
-  kd -= kRoundMagic;
-  double r = fma(-kd, kLn2By16Hi, a);
-  r = fma(-kd, kLn2By16Lo, r);
-  double p = 1.0 / 5040.0;
-  p = fma(p, r, 1.0 / 720.0);
-  p = fma(p, r, 1.0 / 120.0);
-  p = fma(p, r, 1.0 / 24.0);
-  p = fma(p, r, 1.0 / 6.0);
-  p = fma(p, r, 0.5);
-  p = fma(p, r, 1.0);
-  p = fma(p, r, 1.0);
-  const double tj = tab[n & 15];
-  const int k = max(n >> 4, -1022);  // arguments below -708 give a tiny value, not garbage
+// 2^{u/1024} for u in scaled units.  FP64 ops: 1 add + 2 sub (rounding and
+// rho, exact), 3 fma (polynomial), 1 mul.
+constexpr int kExp2sOps = 7;
+__device__ __forceinline__ double exp2s(double u, const double* __restrict__ tab) {
+  const double v = u + kRoundMagic;
+  const int n = __double2loint(v);
+  const double rho = u - (v - kRoundMagic);
+  const double p = fma(fma(fma(kExpC3, rho, kExpC2), rho, kExpC1), rho, 1.0);
+  const double tj = tab[n & (kExpTabSize - 1)];
+  const int k = max(n >> 10, -1022);
   return p * __hiloint2double(__double2hiint(tj) + (k << 20), __double2loint(tj));
+}
+
+// e^a for a in [-708, 709] (callers clamp); one scaling multiply on top of exp2s.
+constexpr int kExpTabOps = 1 + kExp2sOps;
+__device__ __forceinline__ double exp_tab(double a, const double* __restrict__ tab) {
+  return exp2s(a * kExpScale, tab);
+}
+
+// e^a over the whole double range (NaN -> NaN, overflow -> inf, deep
+// underflow -> 0) for the final normalisation, with an exact reduction:
+// kd = round(a K), r = a - kd ln2/1024 with ln2/1024 split in two (kd times
+// the 32-bit head is exact for |kd| < 2^21), e^r from its Taylor polynomial
+// of degree 3 (|r| <= 3.4e-4, truncation < 6e-16 relative), times the table
+// entry 2^{(kd mod 1024)/1024} and 2^{floor(kd/1024)}.  |a| >= 708 goes to
+// exp_full.  FP64 ops: 1 fma + 1 sub (rounding), 2 fma (reduction),
+// 3 fma (polynomial), 1 mul.
+__device__ __forceinline__ double exp_tab_full(double a, const double* __restrict__ tab) {
+  const double v = fma(a, kExpScale, kRoundMagic);
+  if (!(fabs(a) < 708.0)) return exp_full(a);
+  const int n = __double2loint(v);
+  const double kd = v - kRoundMagic;
+  double r = fma(-kd, kExpC1Hi, a);
+  r = fma(-kd, kExpC1Lo, r);
+  const double p = fma(fma(fma(r, 1.0 / 6.0, 0.5), r, 1.0), r, 1.0);
+  const double tj = tab[n & (kExpTabSize - 1)];
+  const int k = n >> 10;
+  return p * __hiloint2double(__double2hiint(tj) + (k << 20), __double2loint(tj));
+}
+
+// log a for finite a > 0 with the same table: a = 2^e m, m in [1, 2); j =
+// round(1024 log2 m) from the FP32 hardware log of m's leading bits, so that
+// m 2^{-j/1024} = 1 + d with |d| <= 3.5e-4; log a = (1024 e + j) ln2/1024 +
+// log1p(d), log1p from its series to d^4 (truncation < 1e-18 absolute).
+// FP64 ops: 1 fma (d), 4 (series), 2 fma (assembly) and one int conversion.
+__device__ __forceinline__ double log_tab(double a, const double* __restrict__ tab) {
+  int hi = __double2hiint(a);
+  int lo = __double2loint(a);
+  int e = 0;
+  if (hi < 0x00100000) {  // subnormal: scale into the normal range
+    a *= 0x1p54;
+    e = -54;
+    hi = __double2hiint(a);
+    lo = __double2loint(a);
+  }
+  e += (hi >> 20) - 1023;
+  const int mh = hi & 0x000fffff;
+  const double m = __hiloint2double(mh | 0x3ff00000, lo);  // [1, 2)
+  const float mf = __int_as_float(0x3f800000 | (mh << 3) | ((unsigned)lo >> 29));
+  float l2;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l2) : "f"(mf));
+  const int j = __float2int_rn(l2 * 1024.0f);  // 0..1024
+  // 2^{-j/1024} = 2^{(1024 - j)/1024} / 2 (j > 0), 1 (j = 0)
+  const double tj = tab[(kExpTabSize - j) & (kExpTabSize - 1)];
+  const double tinv =
+      __hiloint2double(__double2hiint(tj) - (j > 0 ? (1 << 20) : 0), __double2loint(tj));
+  const double d = fma(m, tinv, -1.0);
+  const double q = fma(fma(d, -0.25, 1.0 / 3.0), d, -0.5);
+  const double l1p = fma(d * d, q, d);
+  const double nd = (double)(e * kExpTabSize + j);
+  return fma(nd, kExpC1Hi, fma(nd, kExpC1Lo, l1p));
 }
 
 // 1/a from the hardware approximation refined by Newton-Raphson steps
@@ -182,7 +239,7 @@ struct Tally {
   unsigned repairs;     // learned window ends moved by one Newton step
 };
 
-// The window of Sec. IV-B.  ts = t_max, cs/ss = cosh/sinh(ts), [t0, t1] the
+// The window of Sec. IV-B.  ts = t_max, cs = cosh ts, es = e^ts, [t0, t1] the
 // integration range.  The window ends are the roots of
 //   F(t) = nu (t - ts) - x (cosh t - cosh ts) + L  (+ ln 2 on the left),
 // L = -log eps.  F differs from g(t) - g(ts) + L only by
@@ -190,7 +247,13 @@ struct Tally {
 // of the peak and in [0, ln 2] left of it, so these roots enclose the
 // eps-window: the range is never narrower than the paper's.
 struct Window64 {
-  double ts, cs, t0, t1;
+  double ts, cs, es, t0, t1;
+};
+
+// FP32 start values for the FP64 Newton iterations (the FP32 search run to
+// convergence on the same F); a value <= 0 means "none" for ts and t0.
+struct Start32 {
+  float ts, t0, t1;
 };
 
 // FP32 helpers for Newton start values (only their side of the root matters).
@@ -206,12 +269,14 @@ __device__ __forceinline__ float log_start_f32(float v) {  // ln v, ~1e-6 relati
 // Safeguarded Newton inside that bracket; steps from the left that leave it
 // are clamped to its right end, from where Newton descends monotonically.
 // Any point of the bracket is a valid shift (g(t) <= g(t_max)), so hitting
-// the iteration cap is not an error.  Start values come from FP32 (the right
-// end inflated so that it stays right of the root); function values and
-// steps are FP64, reciprocals by Newton-refined hardware approximations.
-// Returns ts, cosh ts and e^{ts}.
+// the iteration cap is not an error.  The start is the FP32 root when the
+// caller has one (then Newton stops once the step is below 1e-5 relative:
+// one FP64 step), else a two-term Taylor estimate (steps below 1e-8
+// relative).  Function values and steps are FP64, reciprocals by
+// Newton-refined hardware approximations.  Returns ts, cosh ts and e^{ts}.
 __device__ __forceinline__ void peak_f64(double x, double nu, const double* __restrict__ tab,
-                                         double& ts, double& cs, double& es, Tally& tl) {
+                                         float t_start, double& ts, double& cs, double& es,
+                                         Tally& tl) {
   const double nu2 = nu * nu;
   if (!(nu2 > x)) {
     ts = 0.0;
@@ -223,9 +288,16 @@ __device__ __forceinline__ void peak_f64(double x, double nu, const double* __re
   const float hif = log_start_f32(qf + sqrtf(fmaf(qf, qf, 1.0f)));  // asinh(nu/x)
   double hi = fma((double)hif, 2e-5, (double)hif) + 1e-6;
   double lo = 0.0;
-  const float nu2f = (float)nu2, xf = (float)x;
-  const float tc2 = (nu2f - xf) / fmaf(nu2f * nu2f, 1.0f / 3.0f, xf * (1.0f / 6.0f));
-  double t = ((double)tc2 < hi * hi) ? (double)sqrtf(tc2) : hi;
+  double t, rtol;
+  if (t_start > 0.0f && (double)t_start < hi) {
+    t = (double)t_start;
+    rtol = 1e-5;
+  } else {
+    const float nu2f = (float)nu2, xf = (float)x;
+    const float tc2 = (nu2f - xf) / fmaf(nu2f * nu2f, 1.0f / 3.0f, xf * (1.0f / 6.0f));
+    t = ((double)tc2 < hi * hi) ? (double)sqrtf(tc2) : hi;
+    rtol = 1e-8;
+  }
   for (int it = 0; it < 40; ++it) {
     ++tl.peak_iters;
     const double e = exp_tab(t, tab);
@@ -246,7 +318,7 @@ __device__ __forceinline__ void peak_f64(double x, double nu, const double* __re
     }
     const double dt = tn - t;
     t = tn;
-    if (fabs(dt) <= 1e-8 * t) break;
+    if (fabs(dt) <= rtol * t) break;
   }
   ts = t;
   es = exp_tab(t, tab);
@@ -254,26 +326,35 @@ __device__ __forceinline__ void peak_f64(double x, double nu, const double* __re
 }
 
 // a4: window ends.  Newton on the concave F approaches t1 from the right and
-// t0 from the left, so every iterate keeps the range at least as wide as the
-// eps-window.  Start values from FP32 bounds, inflated by 2e-5 so that they
-// stay on their side of the root.
+// t0 from the left (after its first step, from any start), so every iterate
+// past the first keeps the range at least as wide as the eps-window.  With
+// FP32 roots as starts (inflated by 4e-6 towards their side) one FP64 step
+// meets the 1e-5 stopping rule; otherwise the starts are FP32 bounds
+// inflated by 2e-5 and the rule is 1e-8.
 __device__ __forceinline__ Window64 window_f64(double x, double nu, double L,
-                                               const double* __restrict__ tab, Tally& tl) {
+                                               const double* __restrict__ tab, Tally& tl,
+                                               const Start32* st = nullptr) {
   Window64 w;
-  double es;
-  peak_f64(x, nu, tab, w.ts, w.cs, es, tl);
-  const double ts = w.ts, cs = w.cs;
+  peak_f64(x, nu, tab, st ? st->ts : 0.0f, w.ts, w.cs, w.es, tl);
+  const double ts = w.ts, cs = w.cs, es = w.es;
   // ---- t1: cosh t - cs >= ss d + cs d^2/2 for d = t - ts >= 0, so the root d
   // of L + (nu - x ss) d - x cs d^2/2 = 0 is a right bound; in the exponential
   // regime x e^t/2 >= L + x cs + nu t is one too.
   {
-    const float ssf = (float)(0.5 * (es - rcp_nr1(es)));
-    const float af = (float)(x * cs), bf = (float)nu - (float)x * ssf, Lf = (float)L;
-    const float df = (bf + sqrtf(fmaf(bf, bf, 2.0f * af * Lf))) / af;
-    double t = ts + (double)df * (1.0 + 2e-5);
-    const double tb = (double)log_start_f32(2.0f * (Lf + af + (float)nu * (float)t) / (float)x) *
-                      (1.0 + 2e-5);
-    if (tb < t) t = tb;
+    double t, rtol;
+    if (st != nullptr && (double)st->t1 > ts) {
+      t = fma((double)st->t1, 4e-6, (double)st->t1) + 1e-6;
+      rtol = 1e-5;
+    } else {
+      const float ssf = (float)(0.5 * (es - rcp_nr1(es)));
+      const float af = (float)(x * cs), bf = (float)nu - (float)x * ssf, Lf = (float)L;
+      const float df = (bf + sqrtf(fmaf(bf, bf, 2.0f * af * Lf))) / af;
+      t = ts + (double)df * (1.0 + 2e-5);
+      const double tb =
+          (double)log_start_f32(2.0f * (Lf + af + (float)nu * (float)t) / (float)x) * (1.0 + 2e-5);
+      if (tb < t) t = tb;
+      rtol = 1e-8;
+    }
     for (int it = 0; it < 40; ++it) {
       ++tl.iters;
       const double e = exp_tab(fmin(t, 709.0), tab);
@@ -282,7 +363,7 @@ __device__ __forceinline__ Window64 window_f64(double x, double nu, double L,
       const double Fp = fma(-0.5 * x, e - er, nu);
       const double dt = F * rcp_nr1(Fp);
       t -= dt;
-      if (fabs(dt) <= 1e-8 * t) break;
+      if (fabs(dt) <= rtol * t) break;
     }
     w.t1 = t;
   }
@@ -293,7 +374,14 @@ __device__ __forceinline__ Window64 window_f64(double x, double nu, double L,
     const double Lp = L + kLn2;
     const double G0 = fma(-nu, ts, x * (cs - 1.0)) + Lp;
     if (G0 < 0.0) {
-      double t = fmax(0.0, ts - Lp * rcp_nr1(nu));
+      double t, rtol;
+      if (st != nullptr && st->t0 > 0.0f && (double)st->t0 < ts) {
+        t = fmax(0.0, fma((double)st->t0, -4e-6, (double)st->t0) - 1e-6);
+        rtol = 1e-5;
+      } else {
+        t = fmax(0.0, ts - Lp * rcp_nr1(nu));
+        rtol = 1e-8;
+      }
       for (int it = 0; it < 40; ++it) {
         ++tl.iters;
         const double e = exp_tab(t, tab);
@@ -302,7 +390,7 @@ __device__ __forceinline__ Window64 window_f64(double x, double nu, double L,
         const double Gp = fma(-0.5 * x, e - er, nu);
         double tn = fma(-G, rcp_nr1(Gp), t);
         if (tn < 0.0) tn = 0.0;
-        const bool done = fabs(tn - t) <= 1e-8 * fmax(tn, 1e-3);
+        const bool done = fabs(tn - t) <= rtol * fmax(tn, 1e-3);
         t = tn;
         if (done) break;
       }
@@ -316,10 +404,12 @@ __device__ __forceinline__ Window64 window_f64(double x, double nu, double L,
 // t_j = t_start + j H, where
 //   f(t) = e^{-x cosh t} cosh(nu t) = f_s exp(nu (t - ts) - x (cosh t - cs)) (1 + e^{-2 nu t}),
 //   f_s = e^{nu ts - x cs} / 2.
-// D_j = x cosh t_j follows the three-term recurrence D_{j+1} = 2 cosh(H) D_j - D_{j-1}
-// (one FMA; its rounding error grows like j ulp / (2 sinh H)), the exponent's
-// linear part is accumulated, e^{-2 nu t_j} is geometric: one exp per node.
-// first/last receive the scaled end values.
+// The exponent is kept in the scaled units of exp2s (times K = 1024/ln 2):
+// its linear part A_j = K (nu (t_j - ts) + x cs) is accumulated, D_j =
+// K x cosh t_j follows the three-term recurrence D_{j+1} = 2 cosh(H) D_j -
+// D_{j-1} (one FMA; its rounding error grows like j ulp / (2 sinh H)), and
+// e^{-2 nu t_j} is geometric: one exp2s per node.  first/last receive the
+// scaled end values.
 __device__ __forceinline__ double node_sum_f64(double t_start, double H, int count, double x,
                                                double nu, double ts, double cs,
                                                const double* __restrict__ tab, double& first,
@@ -332,15 +422,15 @@ __device__ __forceinline__ double node_sum_f64(double t_start, double H, int cou
   }
   const double eh = exp_tab(H, tab), rh = rcp_nr2(eh);
   const double c = eh + rh;
-  const double xh = 0.5 * x;
+  const double xh = (0.5 * kExpScale) * x;
   double D0 = xh * (e0 + r0);
   double D1 = xh * fma(e0, eh, r0 * rh);
   const double rho = exp_tab(fmax(-2.0 * nu * H, -708.0), tab);
-  double A = fma(nu, t_start - ts, x * cs);
-  const double dA = nu * H;
+  double A = kExpScale * fma(nu, t_start - ts, x * cs);
+  const double dA = kExpScale * (nu * H);
   double s = 0.0, f = 0.0;
   for (int j = 0; j < count; ++j) {
-    const double ev = exp_tab(A - D0, tab);
+    const double ev = exp2s(A - D0, tab);
     f = fma(ev, W, ev);
     if (j == 0) first = f;
     s += f;
@@ -353,9 +443,9 @@ __device__ __forceinline__ double node_sum_f64(double t_start, double H, int cou
   last = f;
   return s;
 }
-// FP64 ops per node in node_sum_f64 (work accounting): 1 add (exponent),
-// exp, 1 fma + 1 add (f, s), 1 fma (recurrence), 1 add + 1 mul.
-constexpr int kNodeOps64 = 6 + kExpTabOps;
+// FP64 ops per node in node_sum_f64 (work accounting): 1 sub (exponent),
+// exp2s, 1 fma + 1 add (f, s), 1 fma (recurrence), 1 add + 1 mul.
+constexpr int kNodeOps64 = 6 + kExp2sOps;
 
 // ---------------------------------------------------------------------------
 // a5: node count.  For f analytic in the strip |Im t| < a with
@@ -408,8 +498,8 @@ __device__ __forceinline__ int strip_node_count(float x, float nu, float width, 
 // h S; sets tl.fail (and returns NaN) when N would exceed n_max.
 __device__ __forceinline__ double scale_f64(double x, double nu, float log2_over_tol, int n_max,
                                             const double* __restrict__ tab, double& hS,
-                                            Tally& tl) {
-  const Window64 w = window_f64(x, nu, kLogInvEps64, tab, tl);
+                                            Tally& tl, const Start32* st = nullptr) {
+  const Window64 w = window_f64(x, nu, kLogInvEps64, tab, tl, st);
   const double width = w.t1 - w.t0;
   const int N = strip_node_count((float)x, (float)nu, (float)width, log2_over_tol, n_max);
   if (N > n_max) {
@@ -424,13 +514,6 @@ __device__ __forceinline__ double scale_f64(double x, double nu, float log2_over
   S -= 0.5 * (f0 + fN);
   hS = h * S;
   return fma(nu, w.ts, -x * w.cs) - kLn2;
-}
-
-__device__ __forceinline__ double log_kv_f64(double x, double nu, float log2_over_tol, int n_max,
-                                             const double* __restrict__ tab, Tally& tl) {
-  double hS;
-  const double sc = scale_f64(x, nu, log2_over_tol, n_max, tab, hS, tl);
-  return sc + log_pos(hS);
 }
 
 // ln(2 / tol) for the plain form: tol = 1e-13 keeps the quadrature error

@@ -42,6 +42,44 @@ __device__ __forceinline__ void flush_tally(unsigned long long* ctr, const Tally
 }
 
 
+// Adds the block's tallies to the caller's counters: warp sums, then one
+// shared-memory total and one global atomic per counter and block.  Every
+// thread of the block must call it.
+__device__ __forceinline__ void flush_tally_block(unsigned long long* ctr, const Tally& tl,
+                                                  unsigned evals) {
+  if (ctr == nullptr) return;
+  __shared__ unsigned long long s_acc[7];
+  if (threadIdx.x < 7) s_acc[threadIdx.x] = 0ull;
+  __syncthreads();
+  unsigned long long v[7] = {tl.fail,       tl.nodes,    tl.iters,  evals,
+                             tl.peak_iters, tl.fallback, tl.repairs};
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    unsigned long long a = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    if ((threadIdx.x & 31) == 0 && a) atomicAdd(&s_acc[k], a);
+  }
+  __syncthreads();
+  const int idx[7] = {BK_CTR_FAIL,       BK_CTR_NODES,    BK_CTR_ITERS, BK_CTR_EVALS,
+                      BK_CTR_PEAK_ITERS, BK_CTR_FALLBACK, BK_CTR_REPAIR};
+  if (threadIdx.x < 7 && s_acc[threadIdx.x]) atomicAdd(ctr + idx[threadIdx.x], s_acc[threadIdx.x]);
+}
+
+// Binds a form to its exponential table: the block's shared copy (filled
+// here, block-wide) or the global one.
+template <class Form>
+__device__ __forceinline__ Form bind_table(const Form& form, double* s_tab) {
+  Form f = form;
+  if constexpr (Form::kStageTable) {
+    exp_table_init(s_tab);
+    f.tab = s_tab;
+  } else {
+    f.tab = kExp2Tab;
+  }
+  return f;
+}
+
 // The element-wise domain rules of the C-ABI around a form's evaluation.
 template <class Form>
 __device__ __forceinline__ double eval_domain(const Form& form, double x, double nu, Tally& tl,
@@ -66,10 +104,8 @@ __global__ void __launch_bounds__(128) eval_kernel(const Form form, const double
                                                    OutT* __restrict__ out,
                                                    OutT* __restrict__ log_out, int64_t n,
                                                    unsigned long long* __restrict__ ctr) {
-  __shared__ double s_tab[16];
-  exp_table_init(s_tab);
-  Form f = form;
-  f.tab = s_tab;
+  __shared__ double s_tab[Form::kStageTable ? kExpTabSize : 1];
+  const Form f = bind_table(form, s_tab);
   Tally tl{0u, 0u, 0u, 0u, 0u, 0u};
   unsigned evals = 0;
   const bool want_log = (log_out != nullptr);
@@ -148,59 +184,70 @@ __device__ __forceinline__ void tri_tile(int64_t t, int64_t& I, int64_t& J) {
   J = t - I * (I + 1) / 2;
 }
 
-// Full symmetric matrix: its lower-triangle tiles visited grid-stride.
+// Full symmetric matrix: block b computes the lower-triangle tiles
+// [b, b + 1, ..., b + Form::kTilesPerBlock - 1] (then strides by the grid,
+// which only matters beyond 2^31 blocks).  Many short blocks let the
+// hardware block scheduler balance the uneven tile costs across the SMs.
 template <class Form, typename OutT>
 __global__ void __launch_bounds__(kThreads) matern_sym_kernel(
-    const Form form, const double* __restrict__ locs, int64_t n, double sigma2, double beta, double nu,
+    const Form form, const double* __restrict__ locs, int64_t n, const MaternParams mp,
     OutT* __restrict__ out, int64_t ld, int64_t ntiles, unsigned long long* __restrict__ ctr) {
   __shared__ SymTileSmem<OutT> sm;
-  __shared__ double s_tab[16];
-  exp_table_init(s_tab);
-  Form f = form;
-  f.tab = s_tab;
-  const MaternParams mp = matern_params(sigma2, beta, nu);
+  __shared__ double s_tab[Form::kStageTable ? kExpTabSize : 1];
+  const Form f = bind_table(form, s_tab);
   Tally tl{0u, 0u, 0u, 0u, 0u, 0u};
   unsigned evals = 0;
-  for (int64_t tix = blockIdx.x; tix < ntiles; tix += gridDim.x) {
-    int64_t I, J;
-    tri_tile(tix, I, J);
-    __syncthreads();  // the previous tile's shared data is no longer read
-    sym_tile<Form, OutT, kWarps>(f, sm, locs, n, I, J, mp, out, ld, tl, evals);
+  constexpr int kPer = Form::kTilesPerBlock;
+  for (int64_t base = (int64_t)blockIdx.x * kPer; base < ntiles; base += (int64_t)gridDim.x * kPer) {
+    const int64_t end = min(base + kPer, ntiles);
+    for (int64_t tix = base; tix < end; ++tix) {
+      int64_t I, J;
+      tri_tile(tix, I, J);
+      __syncthreads();  // the previous tile's shared data is no longer read
+      sym_tile<Form, OutT, kWarps>(f, sm, locs, n, I, J, mp, out, ld, tl, evals);
+    }
   }
-  flush_tally(ctr, tl, evals);
+  flush_tally_block(ctr, tl, evals);
 }
 
-// General m x n block (Algorithm 3's single tile between two location sets).
+// General m x n block (Algorithm 3's single tile between two location sets),
+// tiles assigned to blocks as in matern_sym_kernel.
 template <class Form, typename OutT>
 __global__ void __launch_bounds__(kThreads) matern_block_kernel(
     const Form form, const double* __restrict__ locs1, int64_t m, const double* __restrict__ locs2, int64_t n,
-    double sigma2, double beta, double nu, OutT* __restrict__ out, int64_t ld, int64_t tiles_m,
+    const MaternParams mp, OutT* __restrict__ out, int64_t ld, int64_t tiles_m,
     int64_t ntiles, unsigned long long* __restrict__ ctr) {
   __shared__ Loc s_r[kTile], s_c[kTile];
-  __shared__ double s_tab[16];
-  exp_table_init(s_tab);
-  Form f = form;
-  f.tab = s_tab;
+  __shared__ double s_tab[Form::kStageTable ? kExpTabSize : 1];
+  const Form f = bind_table(form, s_tab);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const MaternParams mp = matern_params(sigma2, beta, nu);
   Tally tl{0u, 0u, 0u, 0u, 0u, 0u};
   unsigned evals = 0;
-  for (int64_t tix = blockIdx.x; tix < ntiles; tix += gridDim.x) {
-    const int64_t r0 = (tix % tiles_m) * kTile, c0 = (tix / tiles_m) * kTile;
-    __syncthreads();
-    if (warp == 0) stage_loc(s_r[lane], locs1, m, r0 + lane);
-    else if (warp == 1) stage_loc(s_c[lane], locs2, n, c0 + lane);
-    __syncthreads();
+  constexpr int kPer = Form::kTilesPerBlock;
+  for (int64_t base = (int64_t)blockIdx.x * kPer; base < ntiles; base += (int64_t)gridDim.x * kPer) {
+    const int64_t end = min(base + kPer, ntiles);
+    for (int64_t tix = base; tix < end; ++tix) {
+      const int64_t r0 = (tix % tiles_m) * kTile, c0 = (tix / tiles_m) * kTile;
+      __syncthreads();
+      if (warp == 0) stage_loc(s_r[lane], locs1, m, r0 + lane);
+      else if (warp == 1) stage_loc(s_c[lane], locs2, n, c0 + lane);
+      __syncthreads();
 #pragma unroll 1
-    for (int k = 0; k < kTile / kWarps; ++k) {
-      const int c = warp + kWarps * k;
-      const int64_t i = r0 + lane, j = c0 + c;
-      if (i < m && j < n) out[i + j * ld] = to_out<OutT>(f.matern(s_r[lane], s_c[c], mp, tl, evals));
+      for (int k = 0; k < kTile / kWarps; ++k) {
+        const int c = warp + kWarps * k;
+        const int64_t i = r0 + lane, j = c0 + c;
+        if (i < m && j < n) out[i + j * ld] = to_out<OutT>(f.matern(s_r[lane], s_c[c], mp, tl, evals));
+      }
     }
   }
-  flush_tally(ctr, tl, evals);
+  flush_tally_block(ctr, tl, evals);
 }
 
+// Blocks for tile kernels: ceil(ntiles / per_block), capped at 2^31 - 1.
+inline int tile_grid(int64_t ntiles, int per_block) {
+  const int64_t g = (ntiles + per_block - 1) / per_block;
+  return (int)(g < 1 ? 1 : (g > 2147483647 ? 2147483647 : g));
+}
 
 // Blocks for a grid-stride launch: min(work, SMs x per_sm).
 int grid_for(int64_t work_items, int per_sm);
@@ -225,13 +272,14 @@ cudaError_t launch_matern_sym_form(const Form& form, const double* locs, int64_t
   if (n == 0) return cudaSuccess;
   const int64_t nb = (n + kTile - 1) / kTile;
   const int64_t ntiles = nb * (nb + 1) / 2;
-  const int grid = grid_for(ntiles, 4);
+  const int grid = tile_grid(ntiles, Form::kTilesPerBlock);
+  const MaternParams mp = matern_params_host(sigma2, beta, nu);
   if (out_t == BK_F64)
-    matern_sym_kernel<Form, double><<<grid, kThreads, 0, s>>>(form, locs, n, sigma2, beta, nu,
-                                                              (double*)out, ld, ntiles, ctr);
+    matern_sym_kernel<Form, double><<<grid, kThreads, 0, s>>>(form, locs, n, mp, (double*)out, ld,
+                                                              ntiles, ctr);
   else
-    matern_sym_kernel<Form, float><<<grid, kThreads, 0, s>>>(form, locs, n, sigma2, beta, nu,
-                                                             (float*)out, ld, ntiles, ctr);
+    matern_sym_kernel<Form, float><<<grid, kThreads, 0, s>>>(form, locs, n, mp, (float*)out, ld,
+                                                             ntiles, ctr);
   return cudaGetLastError();
 }
 
@@ -243,13 +291,14 @@ cudaError_t launch_matern_block_form(const Form& form, const double* locs1, int6
   if (m == 0 || n == 0) return cudaSuccess;
   const int64_t tm = (m + kTile - 1) / kTile, tn = (n + kTile - 1) / kTile;
   const int64_t ntiles = tm * tn;
-  const int grid = grid_for(ntiles, 4);
+  const int grid = tile_grid(ntiles, Form::kTilesPerBlock);
+  const MaternParams mp = matern_params_host(sigma2, beta, nu);
   if (out_t == BK_F64)
     matern_block_kernel<Form, double><<<grid, kThreads, 0, s>>>(
-        form, locs1, m, locs2, n, sigma2, beta, nu, (double*)out, ld, tm, ntiles, ctr);
+        form, locs1, m, locs2, n, mp, (double*)out, ld, tm, ntiles, ctr);
   else
     matern_block_kernel<Form, float><<<grid, kThreads, 0, s>>>(
-        form, locs1, m, locs2, n, sigma2, beta, nu, (float*)out, ld, tm, ntiles, ctr);
+        form, locs1, m, locs2, n, mp, (float*)out, ld, tm, ntiles, ctr);
   return cudaGetLastError();
 }
 
