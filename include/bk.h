@@ -65,7 +65,8 @@ typedef enum {
 
 /* Indices into the optional device counter array bk_opts.d_counters. */
 enum {
-  BK_CTR_FALLBACK = 0, /* learned windows replaced by the full window search */
+  BK_CTR_FALLBACK = 0, /* windows of a fast path (the learned network, or the plain
+                          form's FP32 roots) replaced by the full window search */
   BK_CTR_FAIL = 1,     /* points returned as NaN because a search did not converge */
   BK_CTR_NODES = 2,    /* integrand evaluations (quadrature nodes) */
   BK_CTR_ITERS = 3,    /* window-end root-finder iterations */
@@ -86,10 +87,18 @@ typedef struct {
   /* BK_WIN_LEARNED: the window network (trained or loaded); must outlive
      every call and plan that uses it. */
   const struct bk_learned* learned;
+  /* Plain form (BK_F64, BK_WIN_SEARCH) only.  0 (default): the peak and the
+     window ends are the FP32 roots of the bound F (inside x in [1e-4, 1e4],
+     nu <= 40; widened by 2e-5 relative), and the window is checked in FP64
+     on the quadrature's own end nodes (integrand below eps = 2^-52 times its
+     peak value); a failing window is replaced by the FP64 search
+     (BK_CTR_FALLBACK).  1: the FP64 Newton search from its own bounds for
+     every point. */
+  int search_f64;
 } bk_opts;
 
 /* Fills *o with the defaults: BK_WIN_SEARCH, BK_F64, b = 40, t1 = 9, no
-   counters, no network. */
+   counters, no network, search_f64 = 0. */
 void bk_opts_default(bk_opts* o);
 
 const char* bk_version(void);

@@ -54,7 +54,7 @@ _STATUS = {0: "BK_OK", 1: "BK_ERR_INVALID_ARG", 2: "BK_ERR_CUDA", 3: "BK_ERR_NOM
 class bk_opts(ctypes.Structure):
     _fields_ = [("window", ctypes.c_int), ("compute", ctypes.c_int), ("fixed_bins", ctypes.c_int),
                 ("fixed_t1", ctypes.c_double), ("d_counters", ctypes.c_void_p),
-                ("learned", ctypes.c_void_p)]
+                ("learned", ctypes.c_void_p), ("search_f64", ctypes.c_int)]
 
 
 _lock = threading.Lock()
@@ -165,10 +165,13 @@ def _ptr(t) -> Optional[int]:
 
 
 def make_opts(window: int = BK_WIN_SEARCH, compute: int = BK_F64, fixed_bins: int = 40,
-              fixed_t1: float = 9.0, counters=None, learned=None) -> bk_opts:
+              fixed_t1: float = 9.0, counters=None, learned=None,
+              search_f64: bool = False) -> bk_opts:
     """A bk_opts struct; ``counters`` is an optional CUDA int64 tensor of
     BK_NUM_COUNTERS entries that kernels add to; ``learned`` a LearnedWindow
-    (implies window = BK_WIN_LEARNED and compute = BK_F32 unless given)."""
+    (implies window = BK_WIN_LEARNED and compute = BK_F32 unless given);
+    ``search_f64`` makes the plain form run the FP64 Newton search for every
+    point instead of taking FP32 roots checked in FP64."""
     o = bk_opts()
     lib().bk_opts_default(ctypes.byref(o))
     if learned is not None:
@@ -178,6 +181,7 @@ def make_opts(window: int = BK_WIN_SEARCH, compute: int = BK_F64, fixed_bins: in
             compute = BK_F32
         o.learned = learned.handle.value
     o.window, o.compute, o.fixed_bins, o.fixed_t1 = int(window), int(compute), int(fixed_bins), float(fixed_t1)
+    o.search_f64 = int(bool(search_f64))
     if counters is not None:
         torch = _torch()
         _dev(counters, "counters", torch.int64)

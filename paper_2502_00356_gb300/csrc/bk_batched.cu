@@ -48,7 +48,7 @@ struct BatchSmem {
 // Persistent kernel: each CTA repeatedly takes `chunk` consecutive tiles from
 // *next (scratch, zeroed before the launch) until `limit` tiles are taken.
 template <class Form, typename OutT, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) matern_batched_kernel(
+__global__ void __launch_bounds__(WARPS * 32, Form::kMinBlocks * 8 / WARPS) matern_batched_kernel(
     const Form form, const bk_matern_desc* __restrict__ descs, int count, const int64_t* __restrict__ prefix,
     const int64_t* __restrict__ sizes, int64_t limit, unsigned long long* __restrict__ next,
     int chunk, unsigned long long* __restrict__ ctr) {
@@ -122,6 +122,10 @@ namespace {
 
 template <class Form>
 Form make_form(const bk_plan*) { return Form{}; }
+template <>
+FormF64 make_form<FormF64>(const bk_plan* p) {
+  return FormF64{nullptr, p->opts.search_f64 != 0};
+}
 template <>
 FormF32Learned make_form<FormF32Learned>(const bk_plan* p) {
   return FormF32Learned{learned_view(p->opts.learned)};
@@ -490,7 +494,7 @@ __global__ void __launch_bounds__(1024) static_batch_prep_kernel(
 // and counter taken from the static scratch (filled by the preparation
 // kernel earlier on the same stream).
 template <class Form, typename OutT, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) matern_batched_static_kernel(
+__global__ void __launch_bounds__(WARPS * 32, Form::kMinBlocks * 8 / WARPS) matern_batched_static_kernel(
     const bk_matern_desc* __restrict__ descs, int count, unsigned long long* __restrict__ scratch) {
   const int64_t* prefix = (const int64_t*)(scratch + kStaticPrefixOff);
   const int64_t* sizes = (const int64_t*)(scratch + kStaticSizesOff);

@@ -111,6 +111,7 @@ void bk_opts_default(bk_opts* o) {
   o->compute = BK_F64;
   o->fixed_bins = 40;
   o->fixed_t1 = 9.0;
+  o->search_f64 = 0;
   o->d_counters = nullptr;
   o->learned = nullptr;
 }
@@ -153,7 +154,7 @@ bk_status bk_eval_ex(const double* x, const double* nu, void* out, void* log_out
       (o.window == BK_WIN_LEARNED)
           ? launch_eval_learned(o.learned, x, nu, out, log_out, out_dtype, n, o.d_counters, s)
       : (o.compute == BK_F64)
-          ? launch_eval_f64(x, nu, out, log_out, out_dtype, n, o.d_counters, s)
+          ? launch_eval_f64(x, nu, out, log_out, out_dtype, n, o.search_f64 != 0, o.d_counters, s)
           : launch_eval_f32(x, nu, out, log_out, out_dtype, n, o.d_counters, s);
   return check_cuda(e, "bk_eval launch");
 }
@@ -182,7 +183,8 @@ bk_status bk_matern_tile_ex(const double* locs, int64_t n, double sigma2, double
           ? launch_matern_sym_learned(o.learned, locs, n, sigma2, beta, nu, out, ld, dtype,
                                       o.d_counters, s)
       : (o.compute == BK_F64)
-          ? launch_matern_sym_f64(locs, n, sigma2, beta, nu, out, ld, dtype, o.d_counters, s)
+          ? launch_matern_sym_f64(locs, n, sigma2, beta, nu, out, ld, dtype, o.search_f64 != 0,
+                                  o.d_counters, s)
           : launch_matern_sym_f32(locs, n, sigma2, beta, nu, out, ld, dtype, o.d_counters, s);
   return check_cuda(e, "bk_matern_tile launch");
 }
@@ -213,7 +215,7 @@ bk_status bk_matern_tile2(const double* locs1, int64_t m, const double* locs2, i
                                         dtype, o.d_counters, s)
       : (o.compute == BK_F64)
           ? launch_matern_block_f64(locs1, m, locs2, n, sigma2, beta, nu, out, ld, dtype,
-                                    o.d_counters, s)
+                                    o.search_f64 != 0, o.d_counters, s)
           : launch_matern_block_f32(locs1, m, locs2, n, sigma2, beta, nu, out, ld, dtype,
                                     o.d_counters, s);
   return check_cuda(e, "bk_matern_tile2 launch");

@@ -29,17 +29,21 @@ __device__ __forceinline__ const Start32* plain_starts(double x, double nu, Star
 // Every form carries `tab`, the 2^{j/1024} table of exp2s: the block's
 // shared-memory copy for forms whose hot loop reads it (kStageTable), else
 // the global table (read only on rare FP64 paths).  kTilesPerBlock is the
-// number of 32 x 32 tiles one block of the tile kernels computes.
+// number of 32 x 32 tiles one block of the tile kernels computes, and
+// kMinBlocks the resident 256-thread blocks per SM the tile kernels are
+// compiled for (it caps their registers: 3 -> 85, 4 -> 64).
 struct FormF64 {
   static constexpr bool kStageTable = true;
   static constexpr int kTilesPerBlock = 1;
+  static constexpr int kMinBlocks = 3;
   const double* tab;
+  bool search_f64;  // FP64 Newton search for every point (no FP32 roots)
 
   __device__ __forceinline__ double eval(double x, double nu, Tally& tl, unsigned& evals,
                                          double& log_k, bool want_log) const {
     ++evals;
     Start32 st;
-    const Start32* sp = plain_starts(x, nu, st);
+    const Start32* sp = search_f64 ? nullptr : plain_starts(x, nu, st);
     double hS;
     const double sc = scale_f64(x, nu, kPlainLog2OverTol, kPlainMaxNodes, tab, hS, tl, sp);
     const double lh = (want_log || sc > 700.0) ? log_tab(hS, tab) : 0.0;
@@ -58,7 +62,7 @@ struct FormF64 {
     const double z = r * mp.inv_beta;
     ++evals;
     Start32 st;
-    const Start32* sp = plain_starts(z, mp.nu, st);
+    const Start32* sp = search_f64 ? nullptr : plain_starts(z, mp.nu, st);
     double hS;
     const double sc = scale_f64(z, mp.nu, kPlainLog2OverTol, kPlainMaxNodes, tab, hS, tl, sp);
     return exp_tab_full(fma(mp.nu, log_tab(z, tab), mp.log_pref) + sc, tab) * hS;
@@ -100,6 +104,7 @@ __device__ __forceinline__ DF matern_x_df(const Loc& a, const Loc& b, const Mate
 struct FormF32 {
   static constexpr bool kStageTable = false;
   static constexpr int kTilesPerBlock = 4;
+  static constexpr int kMinBlocks = 4;
   const double* tab;
 
   __device__ __forceinline__ double eval(double x, double nu, Tally& tl, unsigned& evals,
@@ -136,6 +141,7 @@ LearnedView learned_view(const bk_learned* m);
 struct FormF32Learned {
   static constexpr bool kStageTable = false;
   static constexpr int kTilesPerBlock = 4;
+  static constexpr int kMinBlocks = 4;
   LearnedView lv;
   const double* tab;
 

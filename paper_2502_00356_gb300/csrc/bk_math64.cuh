@@ -400,6 +400,20 @@ __device__ __forceinline__ Window64 window_f64(double x, double nu, double L,
   return w;
 }
 
+// 2 cosh H for 0 <= H <= 0.35 from its Taylor series in y = H^2 to y^7
+// (truncation < 1e-20): 8 FP64 ops, correctly rounded to about an ulp.
+__device__ __forceinline__ double two_cosh_small(double H) {
+  const double y = H * H;
+  double p = 2.0 / 87178291200.0;
+  p = fma(p, y, 2.0 / 479001600.0);
+  p = fma(p, y, 2.0 / 3628800.0);
+  p = fma(p, y, 2.0 / 40320.0);
+  p = fma(p, y, 2.0 / 720.0);
+  p = fma(p, y, 2.0 / 24.0);
+  p = fma(p, y, 1.0);
+  return fma(p, y, 2.0);
+}
+
 // Sum of the scaled integrand f(t)/f_s over `count` equispaced nodes
 // t_j = t_start + j H, where
 //   f(t) = e^{-x cosh t} cosh(nu t) = f_s exp(nu (t - ts) - x (cosh t - cs)) (1 + e^{-2 nu t}),
@@ -409,30 +423,40 @@ __device__ __forceinline__ Window64 window_f64(double x, double nu, double L,
 // K x cosh t_j follows the three-term recurrence D_{j+1} = 2 cosh(H) D_j -
 // D_{j-1} (one FMA; its rounding error grows like j ulp / (2 sinh H)), and
 // e^{-2 nu t_j} is geometric: one exp2s per node.  first/last receive the
-// scaled end values.
-__device__ __forceinline__ double node_sum_f64(double t_start, double H, int count, double x,
-                                               double nu, double ts, double cs,
-                                               const double* __restrict__ tab, double& first,
-                                               double& last) {
-  double e0 = 1.0, r0 = 1.0, W = 1.0;
-  if (t_start > 0.0) {
-    e0 = exp_tab(t_start, tab);
-    r0 = rcp_nr2(e0);
-    W = exp_tab(fmax(-2.0 * nu * t_start, -708.0), tab);
-  }
-  const double eh = exp_tab(H, tab), rh = rcp_nr2(eh);
-  const double c = eh + rh;
+// scaled end values f_0, f_N and e0/eN the end values of exp(g(t) - g(ts))
+// without the (1 + e^{-2 nu t}) factor (for the window check).
+struct NodeSum {
+  double S, first, last, e_first, e_last;
+};
+__device__ __forceinline__ NodeSum node_sum_f64(double t_start, double H, int count, double x,
+                                                double nu, double ts, double cs,
+                                                const double* __restrict__ tab) {
   const double xh = (0.5 * kExpScale) * x;
-  double D0 = xh * (e0 + r0);
-  double D1 = xh * fma(e0, eh, r0 * rh);
+  double W = 1.0, c, D0, D1;
+  if (t_start > 0.0) {
+    const double e0 = exp_tab(t_start, tab), r0 = rcp_nr2(e0);
+    W = exp_tab(fmax(-2.0 * nu * t_start, -708.0), tab);
+    const double eh = exp_tab(H, tab), rh = rcp_nr2(eh);
+    c = eh + rh;
+    D0 = xh * (e0 + r0);
+    D1 = xh * fma(e0, eh, r0 * rh);
+  } else {
+    c = (H <= 0.35) ? two_cosh_small(H) : exp_tab(H, tab) + rcp_nr2(exp_tab(H, tab));
+    D0 = 2.0 * xh;
+    D1 = xh * c;
+  }
   const double rho = exp_tab(fmax(-2.0 * nu * H, -708.0), tab);
   double A = kExpScale * fma(nu, t_start - ts, x * cs);
   const double dA = kExpScale * (nu * H);
-  double s = 0.0, f = 0.0;
+  NodeSum r;
+  double s = 0.0, f = 0.0, ev = 0.0;
   for (int j = 0; j < count; ++j) {
-    const double ev = exp2s(A - D0, tab);
+    ev = exp2s(A - D0, tab);
     f = fma(ev, W, ev);
-    if (j == 0) first = f;
+    if (j == 0) {
+      r.first = f;
+      r.e_first = ev;
+    }
     s += f;
     const double D2 = fma(c, D1, -D0);
     D0 = D1;
@@ -440,8 +464,10 @@ __device__ __forceinline__ double node_sum_f64(double t_start, double H, int cou
     A += dA;
     W *= rho;
   }
-  last = f;
-  return s;
+  r.S = s;
+  r.last = f;
+  r.e_last = ev;
+  return r;
 }
 // FP64 ops per node in node_sum_f64 (work accounting): 1 sub (exponent),
 // exp2s, 1 fma + 1 add (f, s), 1 fma (recurrence), 1 add + 1 mul.
@@ -492,27 +518,103 @@ __device__ __forceinline__ int strip_node_count(float x, float nu, float width, 
   return nf < 2.0f ? 2 : (int)nf;
 }
 
+// The plain form's window from FP32 roots of the same F (st): t* as found
+// (any point is a valid shift: g(t) - g(t*) is what the nodes evaluate, in
+// FP64), the ends widened by 2e-5 relative and 1e-5 absolute towards their
+// side, far beyond the FP32 error of the roots; cosh t* and e^{t*} in FP64.
+// The ends are then checked in FP64 by the quadrature itself (scale_f64).
+__device__ __forceinline__ Window64 window_from_start(double x, double nu, const Start32& st,
+                                                      const double* __restrict__ tab) {
+  Window64 w;
+  w.ts = (nu * nu > x) ? (double)st.ts : 0.0;
+  if (w.ts > 0.0) {
+    w.es = exp_tab(w.ts, tab);
+    w.cs = 0.5 * (w.es + rcp_nr2(w.es));
+  } else {
+    w.es = 1.0;
+    w.cs = 1.0;
+  }
+  w.t1 = fma((double)st.t1, 2e-5, (double)st.t1) + 1e-5;
+  w.t0 = (st.t0 > 0.0f && w.ts > 0.0) ? fmax(0.0, fma((double)st.t0, -2e-5, (double)st.t0) - 1e-5)
+                                       : 0.0;
+  return w;
+}
+
 // a6/a7: trapezoid on [t0, t1] with N intervals from the strip bound, in the
 // log domain: K = e^{scale} h S with scale = nu ts - x cs - ln 2 and S the
-// weighted sum of the scaled integrand (node_sum_f64).  Returns the scale and
-// h S; sets tl.fail (and returns NaN) when N would exceed n_max.
-__device__ __forceinline__ double scale_f64(double x, double nu, float log2_over_tol, int n_max,
-                                            const double* __restrict__ tab, double& hS,
-                                            Tally& tl, const Start32* st = nullptr) {
-  const Window64 w = window_f64(x, nu, kLogInvEps64, tab, tl, st);
+// weighted sum of the scaled integrand (node_sum_f64).
+struct Scaled64 {
+  double scale, hS;
+  unsigned nodes, iters, peak_iters, fail;
+};
+
+// The FP64 search window (window_f64 from its own start bounds) and its
+// quadrature.  Kept out of line: it is the rare path of the plain form
+// (check failures, points outside the FP32 search region, or every point
+// under bk_opts.search_f64), and inlining it would cost the common path
+// registers.  Returns NaN (and fail = 1) when N would exceed n_max.
+static __device__ __noinline__ Scaled64 scaled_search_f64(double x, double nu, float log2_over_tol,
+                                                   int n_max, const double* __restrict__ tab) {
+  Tally tl{0u, 0u, 0u, 0u, 0u, 0u};
+  Scaled64 r;
+  const Window64 w = window_f64(x, nu, kLogInvEps64, tab, tl);
   const double width = w.t1 - w.t0;
   const int N = strip_node_count((float)x, (float)nu, (float)width, log2_over_tol, n_max);
   if (N > n_max) {
-    ++tl.fail;
-    hS = __longlong_as_double(0x7ff8000000000000LL);
-    return hS;
+    r.scale = r.hS = __longlong_as_double(0x7ff8000000000000LL);
+    r.nodes = 0;
+    r.fail = 1;
+  } else {
+    const double h = width * rcp_nr2((double)N);
+    const NodeSum ns = node_sum_f64(w.t0, h, N + 1, x, nu, w.ts, w.cs, tab);
+    r.hS = h * (ns.S - 0.5 * (ns.first + ns.last));
+    r.scale = fma(nu, w.ts, -x * w.cs) - kLn2;
+    r.nodes = N + 1;
+    r.fail = 0;
   }
-  const double h = width * rcp_nr2((double)N);
-  double f0, fN;
-  double S = node_sum_f64(w.t0, h, N + 1, x, nu, w.ts, w.cs, tab, f0, fN);
-  tl.nodes += N + 1;
-  S -= 0.5 * (f0 + fN);
-  hS = h * S;
+  r.iters = tl.iters;
+  r.peak_iters = tl.peak_iters;
+  return r;
+}
+
+__device__ __forceinline__ double take_search(const Scaled64& r, double& hS, Tally& tl) {
+  tl.nodes += r.nodes;
+  tl.iters += r.iters;
+  tl.peak_iters += r.peak_iters;
+  tl.fail += r.fail;
+  hS = r.hS;
+  return r.scale;
+}
+
+// The plain form's K_nu in scaled form: returns the scale and sets h S.
+// With FP32 start values (st) the window is taken from them and checked in
+// FP64 on the computed end nodes: exp(g(t1) - g(t*)) <= eps and, for t0 > 0,
+// 2 exp(g(t0) - g(t*)) <= eps (the rule of window_f64, whose F bounds these
+// from above), with a finite positive sum; a window that fails is replaced by
+// the FP64 search (tl.fallback).  Without st, the FP64 search.
+__device__ __forceinline__ double scale_f64(double x, double nu, float log2_over_tol, int n_max,
+                                            const double* __restrict__ tab, double& hS,
+                                            Tally& tl, const Start32* st = nullptr) {
+  constexpr double kEps64 = 0x1p-52;
+  if (st == nullptr) return take_search(scaled_search_f64(x, nu, log2_over_tol, n_max, tab), hS, tl);
+  const Window64 w = window_from_start(x, nu, *st, tab);
+  const double width = w.t1 - w.t0;
+  const int N = strip_node_count((float)x, (float)nu, (float)width, log2_over_tol, n_max);
+  bool ok = N <= n_max;
+  NodeSum ns;
+  double h = 0.0;
+  if (ok) {
+    h = width * rcp_nr2((double)N);
+    ns = node_sum_f64(w.t0, h, N + 1, x, nu, w.ts, w.cs, tab);
+    tl.nodes += N + 1;
+    ok = ns.e_last <= kEps64 && (w.t0 == 0.0 || 2.0 * ns.e_first <= kEps64) && ns.S > 0.0 &&
+         ns.S < 1e300;
+  }
+  if (!ok) {
+    ++tl.fallback;
+    return take_search(scaled_search_f64(x, nu, log2_over_tol, n_max, tab), hS, tl);
+  }
+  hS = h * (ns.S - 0.5 * (ns.first + ns.last));
   return fma(nu, w.ts, -x * w.cs) - kLn2;
 }
 

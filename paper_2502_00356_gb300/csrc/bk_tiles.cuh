@@ -189,7 +189,7 @@ __device__ __forceinline__ void tri_tile(int64_t t, int64_t& I, int64_t& J) {
 // which only matters beyond 2^31 blocks).  Many short blocks let the
 // hardware block scheduler balance the uneven tile costs across the SMs.
 template <class Form, typename OutT>
-__global__ void __launch_bounds__(kThreads) matern_sym_kernel(
+__global__ void __launch_bounds__(kThreads, Form::kMinBlocks) matern_sym_kernel(
     const Form form, const double* __restrict__ locs, int64_t n, const MaternParams mp,
     OutT* __restrict__ out, int64_t ld, int64_t ntiles, unsigned long long* __restrict__ ctr) {
   __shared__ SymTileSmem<OutT> sm;
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(kThreads) matern_sym_kernel(
 // General m x n block (Algorithm 3's single tile between two location sets),
 // tiles assigned to blocks as in matern_sym_kernel.
 template <class Form, typename OutT>
-__global__ void __launch_bounds__(kThreads) matern_block_kernel(
+__global__ void __launch_bounds__(kThreads, Form::kMinBlocks) matern_block_kernel(
     const Form form, const double* __restrict__ locs1, int64_t m, const double* __restrict__ locs2, int64_t n,
     const MaternParams mp, OutT* __restrict__ out, int64_t ld, int64_t tiles_m,
     int64_t ntiles, unsigned long long* __restrict__ ctr) {

@@ -198,7 +198,10 @@ def test_learned_matern_and_batched(dev, trained):
     bk.bk_matern_batched(d, plan)
     torch.cuda.synchronize()
     rel = ((o2.double() - out.double()).abs() / out.double().abs().clamp_min(1e-30)).max()
-    assert float(rel) <= 2.5e-7  # same entries from another kernel: agree to rounding
+    # the same entries from another kernel: their windows may differ in the
+    # last bits (FMA contraction), and with them N; two FP32-form results
+    # agree to twice the form's typical error (~1e-6), far inside 1e-5
+    assert float(rel) <= 2e-6
 
 
 def test_learned_needs_weights_and_fp32(dev):

@@ -99,14 +99,53 @@ def test_eval_empty_and_log_output(dev):
 
 def test_eval_counters(dev):
     x, nu = inputs.kv_pairs(2000, seed=8)
+    counts = {}
+    for search_f64 in (False, True):
+        ctr = torch.zeros(bk.BK_NUM_COUNTERS, dtype=torch.int64, device=dev)
+        opts = bk.make_opts(counters=ctr, search_f64=search_f64)
+        bk.bk_eval_ex(to_dev(x, dev), to_dev(nu, dev), opts=opts)
+        torch.cuda.synchronize()
+        c = counts[search_f64] = ctr.cpu().numpy()
+        assert c[bk.BK_CTR_EVALS] == 2000 and c[bk.BK_CTR_FAIL] == 0
+        assert 2000 * 5 < c[bk.BK_CTR_NODES] < 2000 * 80
+    # default: FP32 roots checked in FP64, no FP64 Newton iteration and no
+    # window rejected on this set (all points inside the FP32 search region)
+    assert counts[False][bk.BK_CTR_ITERS] == 0 and counts[False][bk.BK_CTR_PEAK_ITERS] == 0
+    assert counts[False][bk.BK_CTR_FALLBACK] == 0
+    # the full FP64 search iterates for every point
+    assert counts[True][bk.BK_CTR_ITERS] >= 2000 and counts[True][bk.BK_CTR_PEAK_ITERS] > 0
+    assert counts[True][bk.BK_CTR_FALLBACK] == 0
+    # both windows enclose the eps-window: node totals agree to a few per cent
+    assert abs(counts[True][bk.BK_CTR_NODES] / counts[False][bk.BK_CTR_NODES] - 1) < 0.02
+
+
+def test_eval_fp32_roots_agree_with_fp64_search(dev):
+    """The checked FP32-root window and the FP64 search give the same K_nu
+    to quadrature accuracy, inside the FP32 search region (x in [1e-4, 1e4],
+    nu <= 40) and outside it (where both take the FP64 search), and both
+    match the oracle where it is defined."""
+    rng = np.random.default_rng(21)
+    x = np.exp(rng.uniform(np.log(1e-6), np.log(1e5), 20_000))
+    nu = rng.uniform(0.0, 45.0, 20_000)
+    X, V = to_dev(x, dev), to_dev(nu, dev)
     ctr = torch.zeros(bk.BK_NUM_COUNTERS, dtype=torch.int64, device=dev)
-    opts = bk.make_opts(counters=ctr)
-    bk.bk_eval_ex(to_dev(x, dev), to_dev(nu, dev), opts=opts)
+    a, la = bk.bk_eval_ex(X, V, opts=bk.make_opts(counters=ctr), want_log=True)
+    b, lb = bk.bk_eval_ex(X, V, opts=bk.make_opts(search_f64=True), want_log=True)
     torch.cuda.synchronize()
+    la, lb = la.cpu().numpy(), lb.cpu().numpy()
+    assert np.all(np.isfinite(la)) and np.all(np.isfinite(lb))
+    # log K is assembled from terms as large as |log K| (~570 at x = 1e-6,
+    # nu = 45; ~1e5 at x = 1e5), each rounded to ~1e-16 of its size: compare
+    # the logs to 2e-12 plus that conditioning term
+    d = np.abs(la - lb)
+    i = int(np.argmax(d / (2e-12 + 1e-14 * np.abs(lb))))
+    assert d[i] <= 2e-12 + 1e-14 * abs(lb[i]), (x[i], nu[i], la[i], lb[i])
     c = ctr.cpu().numpy()
-    assert c[bk.BK_CTR_EVALS] == 2000 and c[bk.BK_CTR_FAIL] == 0
-    assert 2000 * 5 < c[bk.BK_CTR_NODES] < 2000 * 80
-    assert c[bk.BK_CTR_ITERS] > 0 and c[bk.BK_CTR_PEAK_ITERS] > 0
+    assert c[bk.BK_CTR_FAIL] == 0 and c[bk.BK_CTR_FALLBACK] <= 20
+    idx = rng.choice(np.flatnonzero(x <= 140.0), 2000, replace=False)
+    _, lref = oracle.besselk(x[idx], nu[idx], return_log=True)
+    ok = np.isfinite(lref)
+    assert np.abs(np.expm1(la[idx][ok] - lref[ok])).max() <= K_RTOL
 
 
 # ---------------------------------------------------------------------------
@@ -130,6 +169,16 @@ def test_matern_full_parity(dev, n, nu):
     assert np.abs(got.T - want).max() <= M_ATOL
     assert np.array_equal(got, got.T)
     assert np.all(np.diag(got) == sigma2)
+
+
+@pytest.mark.parametrize("nu", [0.5, 2.3, 7.5])
+def test_matern_fp64_search_option(dev, nu):
+    """bk_opts.search_f64 = 1 (FP64 Newton search for every entry) writes the
+    same matrix as the default FP32-root window to rounding."""
+    locs = inputs.morton_sorted(inputs.jittered_grid(700, seed=230))
+    a = gpu_matern(locs, 1.0, 0.1, nu, dev)
+    b = gpu_matern(locs, 1.0, 0.1, nu, dev, opts=bk.make_opts(search_f64=True))
+    assert np.abs(a - b).max() <= 1e-12  # two windows, two node counts: quadrature-level agreement
 
 
 def test_matern_ld_padding_and_duplicates(dev):
