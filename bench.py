@@ -74,6 +74,31 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+# Multi-rank host logic (weak scaling: each rank builds its own matrices, no
+# collective on the data path; the process group only carries the barrier and
+# the max over ranks of the timed region).
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ms: float, world: int, device) -> float:
+    """The largest of the ranks' times (every rank calls it; identity at 1)."""
+    if world == 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, steps: int, units_per_rank_step: float, max_ms: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * steps * units_per_rank_step / (max_ms / 1e3)
+
+
 # ---------------------------------------------------------------------------
 class ClockSampler:
     """nvidia-smi clock / throttle-reason samples taken during the timed region."""
@@ -128,9 +153,14 @@ class ClockSampler:
                 "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons, "samples": len(rows)}
 
 
+KERNEL_SOURCES = ("bk_plain.cu", "bk_math64.cuh", "bk_math32.cuh", "bk_forms.cuh", "bk_tiles.cuh",
+                  "bk_matern_common.cuh", "bk_exp2_table.inc")
+
+
 def kernel_hash():
+    """Hash of the sources the plain FP64 tile writer is compiled from."""
     h = hashlib.sha256()
-    for f in ("bk_plain.cu", "bk_math64.cuh"):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_2502_00356_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -423,8 +453,7 @@ def main():
     dev = torch.device("cuda", local)
     if rank == 0:
         bk.build()
-    if world > 1:
-        dist.barrier()
+    barrier(world)
     bk.build()  # no-op when up to date; loads after rank 0 built
 
     n = args.n
@@ -460,8 +489,7 @@ def main():
     torch.cuda.synchronize()
 
     launch_ms = [[] for _ in NUS]
-    if world > 1:
-        dist.barrier()
+    barrier(world)
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         t_start = torch.cuda.Event(enable_timing=True)
@@ -475,18 +503,12 @@ def main():
             evs.append(ev)
         t_end.record(stream)
         torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    barrier(world)
     for ev in evs:
         for k in range(len(NUS)):
             launch_ms[k].append(ev[k][0].elapsed_time(ev[k][1]))
-    total_ms = t_start.elapsed_time(t_end)
-    tmax = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    total_ms = float(tmax.item())
-    entries = world * args.steps * len(NUS) * n * n
-    value = entries / (total_ms / 1e3)
+    total_ms = max_over_ranks(t_start.elapsed_time(t_end), world, dev)
+    value = job_rate(world, args.steps, len(NUS) * n * n, total_ms)
 
     # -- roofline of the dominant kernel (the symmetric FP64 tile writer)
     mean_launch_s = statistics.mean(statistics.mean(v) for v in launch_ms) / 1e3
@@ -536,8 +558,7 @@ def main():
         out_pin = torch.empty((n, n), dtype=torch.float64).pin_memory()
         Ld = torch.empty_like(L)
         torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
+        barrier(world)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         e_steps = max(1, min(args.steps, 3))
@@ -548,10 +569,8 @@ def main():
                 out_pin.copy_(out, non_blocking=True)
         b.record(stream)
         torch.cuda.synchronize()
-        e_ms = torch.tensor([a.elapsed_time(b)], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(e_ms, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * e_steps * len(NUS) * n * n / (float(e_ms.item()) / 1e3),
+        e_ms = max_over_ranks(a.elapsed_time(b), world, dev)
+        e2e = {"value": job_rate(world, e_steps, len(NUS) * n * n, e_ms),
                "unit": "entries/s", "h2d_bytes_per_step": len(NUS) * 2 * n * 8,
                "d2h_bytes_per_step": len(NUS) * n * n * 8, "steps": e_steps}
         del out_pin
