@@ -387,6 +387,33 @@ def measure_forms(bk, inputs, dev, stream, args, plain_rate):
     bres["learned_fp32_over_fp64"] = bres["learned_fp32"]["value"] / bres["fp64"]["value"]
     res["batched"] = bres
     res["learned_batched_over_plain_fp64_headline"] = bres["learned_fp32"]["value"] / plain_rate
+    del locs
+    torch.cuda.empty_cache()
+
+    # -- the paper's refined algorithm (Algorithm 2: Temme's series below x = 0.1, the fixed
+    # window [0, 9] with b bins above) on the headline matrices, b in {16, 40, 128}
+    L2 = torch.as_tensor(inputs.morton_sorted(inputs.jittered_grid(N_LOC, seed=SEED)), device=dev)
+    o2 = torch.empty((N_LOC, N_LOC), dtype=torch.float64, device=dev)
+    cols2 = slice(0, 1000)
+    alg = {"workload": f"n={N_LOC} jittered grid, beta={BETA}, nu in {list(NUS)}, FP64 out "
+                       "(the headline matrices)",
+           "unit": "entries/s",
+           "err": "max |entry - plain FP64 form| over the first 1000 columns (entries <= 1)"}
+    refs = {nu: bk.bk_matern_tile2(L2, L2[:, cols2].contiguous(), SIGMA2, BETA, nu) for nu in NUS}
+    for bins in (16, 40, 128):
+        ts, errs = [], []
+        for nu in NUS:
+            op = bk.paper_algorithm2_opts(bins=bins)
+            bk.bk_matern_tile(L2, SIGMA2, BETA, nu, out=o2, opts=op)
+            ts.append(_time(lambda: bk.bk_matern_tile(L2, SIGMA2, BETA, nu, out=o2, opts=op),
+                            stream, 1))
+            errs.append(float((o2[cols2, :] - refs[nu]).abs().max()))
+        alg[f"b{bins}"] = {"value": len(NUS) * N_LOC * N_LOC / sum(ts),
+                           "launch_ms": [1e3 * t for t in ts], "max_abs_err": max(errs),
+                           "plain_form_speedup": plain_rate * sum(ts) / (len(NUS) * N_LOC * N_LOC)}
+    res["paper_algorithm2"] = alg
+    del o2, L2, refs
+    torch.cuda.empty_cache()
     return res
 
 
@@ -514,7 +541,7 @@ def main():
     mean_launch_s = statistics.mean(statistics.mean(v) for v in launch_ms) / 1e3
     flop_mean = float(np.mean(flop_per_launch))
     achieved = flop_mean / mean_launch_s / 1e9
-    roofline = {"bound": "alu", "kernel": "matern_sym_kernel<FormF64, double>",
+    roofline = {"bound": "alu", "kernel": "matern_sym_kernel<FormF64T<false>, double>",
                 "achieved": achieved, "peak": FP64_PEAK_GOPS, "unit": "FP64 Gop/s",
                 "frac": achieved / FP64_PEAK_GOPS,
                 "peak_source": "derived: 152 SMs x 2 FP64 ops/clk x 2.07 GHz (of derived)",

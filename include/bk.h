@@ -60,7 +60,8 @@ typedef enum { BK_F64 = 0, BK_F32 = 1 } bk_dtype;
 typedef enum {
   BK_WIN_SEARCH = 0,  /* per-point peak and bound search (Sec. IV-B) */
   BK_WIN_LEARNED = 1, /* predicted by the window network, checked, with fallback */
-  BK_WIN_FIXED = 2    /* the paper's fixed [0, t1] with b bins (Sec. IV-C) */
+  BK_WIN_FIXED = 2    /* the paper's fixed [0, t1] with b bins and no search (Algorithm 2,
+                         Sec. IV-C); plain FP64 form only */
 } bk_window;
 
 /* Indices into the optional device counter array bk_opts.d_counters. */
@@ -73,14 +74,15 @@ enum {
   BK_CTR_EVALS = 4,    /* K_nu evaluations */
   BK_CTR_PEAK_ITERS = 5, /* peak (t_max) root-finder iterations */
   BK_CTR_REPAIR = 6,   /* learned window ends moved by one Newton step after the check */
+  BK_CTR_SERIES = 7,   /* evaluations taken by Temme's series (bk_opts.series_below) */
   BK_NUM_COUNTERS = 8
 };
 
 typedef struct {
   bk_window window;  /* default BK_WIN_SEARCH */
   bk_dtype compute;  /* arithmetic of the integrand: BK_F64 (plain) or BK_F32 */
-  int fixed_bins;    /* BK_WIN_FIXED: number of bins b (paper: 40) */
-  double fixed_t1;   /* BK_WIN_FIXED: upper bound (paper: 9) */
+  int fixed_bins;    /* BK_WIN_FIXED: number of bins b, 1..100000 (paper: 40) */
+  double fixed_t1;   /* BK_WIN_FIXED: upper bound, (0, 700] (paper: 9) */
   /* Optional device array of BK_NUM_COUNTERS unsigned 64-bit counters that
      kernels add to (never reset by the library).  NULL = no counting. */
   unsigned long long* d_counters;
@@ -95,10 +97,17 @@ typedef struct {
      (BK_CTR_FALLBACK).  1: the FP64 Newton search from its own bounds for
      every point. */
   int search_f64;
+  /* Plain form (BK_F64) only: x below which K_nu(x) comes from Temme's series
+     with Campbell's forward recurrence (Sec. IV-A) instead of the integral;
+     0 (default) = never, at most 2.  The paper's refined algorithm
+     (Algorithm 2) is window = BK_WIN_FIXED, fixed_bins = 40, fixed_t1 = 9,
+     series_below = 0.1.  Evaluations taken by the series are counted in
+     BK_CTR_SERIES (their series terms in BK_CTR_NODES). */
+  double series_below;
 } bk_opts;
 
 /* Fills *o with the defaults: BK_WIN_SEARCH, BK_F64, b = 40, t1 = 9, no
-   counters, no network, search_f64 = 0. */
+   counters, no network, search_f64 = 0, series_below = 0. */
 void bk_opts_default(bk_opts* o);
 
 const char* bk_version(void);

@@ -26,7 +26,7 @@ BK_ERR_UNSUPPORTED, BK_ERR_NOT_CONVERGED, BK_ERR_NOT_LOADED = 4, 5, 6
 BK_F64, BK_F32 = 0, 1
 BK_WIN_SEARCH, BK_WIN_LEARNED, BK_WIN_FIXED = 0, 1, 2
 BK_CTR_FALLBACK, BK_CTR_FAIL, BK_CTR_NODES, BK_CTR_ITERS, BK_CTR_EVALS, BK_CTR_PEAK_ITERS = 0, 1, 2, 3, 4, 5
-BK_CTR_REPAIR = 6
+BK_CTR_REPAIR, BK_CTR_SERIES = 6, 7
 BK_NUM_COUNTERS = 8
 
 #: every symbol include/bk.h declares (checked by the CPU tests)
@@ -54,7 +54,8 @@ _STATUS = {0: "BK_OK", 1: "BK_ERR_INVALID_ARG", 2: "BK_ERR_CUDA", 3: "BK_ERR_NOM
 class bk_opts(ctypes.Structure):
     _fields_ = [("window", ctypes.c_int), ("compute", ctypes.c_int), ("fixed_bins", ctypes.c_int),
                 ("fixed_t1", ctypes.c_double), ("d_counters", ctypes.c_void_p),
-                ("learned", ctypes.c_void_p), ("search_f64", ctypes.c_int)]
+                ("learned", ctypes.c_void_p), ("search_f64", ctypes.c_int),
+                ("series_below", ctypes.c_double)]
 
 
 _lock = threading.Lock()
@@ -166,12 +167,14 @@ def _ptr(t) -> Optional[int]:
 
 def make_opts(window: int = BK_WIN_SEARCH, compute: int = BK_F64, fixed_bins: int = 40,
               fixed_t1: float = 9.0, counters=None, learned=None,
-              search_f64: bool = False) -> bk_opts:
+              search_f64: bool = False, series_below: float = 0.0) -> bk_opts:
     """A bk_opts struct; ``counters`` is an optional CUDA int64 tensor of
     BK_NUM_COUNTERS entries that kernels add to; ``learned`` a LearnedWindow
     (implies window = BK_WIN_LEARNED and compute = BK_F32 unless given);
     ``search_f64`` makes the plain form run the FP64 Newton search for every
-    point instead of taking FP32 roots checked in FP64."""
+    point instead of taking FP32 roots checked in FP64; ``series_below`` is the
+    x below which the plain form uses Temme's series (0: never).  The paper's
+    refined algorithm (Algorithm 2) is ``paper_algorithm2_opts()``."""
     o = bk_opts()
     lib().bk_opts_default(ctypes.byref(o))
     if learned is not None:
@@ -182,6 +185,7 @@ def make_opts(window: int = BK_WIN_SEARCH, compute: int = BK_F64, fixed_bins: in
         o.learned = learned.handle.value
     o.window, o.compute, o.fixed_bins, o.fixed_t1 = int(window), int(compute), int(fixed_bins), float(fixed_t1)
     o.search_f64 = int(bool(search_f64))
+    o.series_below = float(series_below)
     if counters is not None:
         torch = _torch()
         _dev(counters, "counters", torch.int64)
@@ -190,6 +194,14 @@ def make_opts(window: int = BK_WIN_SEARCH, compute: int = BK_F64, fixed_bins: in
         o.d_counters = counters.data_ptr()
     return o
 
+
+
+def paper_algorithm2_opts(bins: int = 40, t1: float = 9.0, series_below: float = 0.1,
+                          counters=None) -> bk_opts:
+    """Options for the paper's refined algorithm (Algorithm 2): Temme's series
+    below x = 0.1, else the fixed window [0, 9] with 40 bins (plain FP64)."""
+    return make_opts(window=BK_WIN_FIXED, fixed_bins=bins, fixed_t1=t1,
+                     series_below=series_below, counters=counters)
 
 def _dtype_code(torch_dtype) -> int:
     torch = _torch()

@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(WARPS * 32, Form::kMinBlocks * 8 / WARPS) mate
   __shared__ BatchSmem<OutT> sm;
   __shared__ double s_tab[Form::kStageTable ? kExpTabSize : 1];
   const Form f = bind_table(form, s_tab);
-  Tally tl{0u, 0u, 0u, 0u, 0u, 0u};
+  Tally tl{0u, 0u, 0u, 0u, 0u, 0u, 0u};
   unsigned evals = 0;
   int cur = -1;
   while (true) {
@@ -124,7 +124,15 @@ template <class Form>
 Form make_form(const bk_plan*) { return Form{}; }
 template <>
 FormF64 make_form<FormF64>(const bk_plan* p) {
-  return FormF64{nullptr, p->opts.search_f64 != 0};
+  return FormF64{nullptr, p->opts.search_f64 != 0, 0.0};
+}
+template <>
+FormF64Series make_form<FormF64Series>(const bk_plan* p) {
+  return FormF64Series{nullptr, p->opts.search_f64 != 0, p->opts.series_below};
+}
+template <>
+FormF64Fixed make_form<FormF64Fixed>(const bk_plan* p) {
+  return FormF64Fixed{nullptr, p->opts.fixed_t1, p->opts.fixed_bins, p->opts.series_below};
 }
 template <>
 FormF32Learned make_form<FormF32Learned>(const bk_plan* p) {
@@ -153,6 +161,14 @@ cudaError_t launch_batched(const bk_plan* p, const bk_matern_desc* d, int64_t li
   if (e != cudaSuccess) return e;
   const bool f64 = (p->opts.compute == BK_F64);
   const bool learned = (p->opts.window == BK_WIN_LEARNED);
+  if (p->opts.window == BK_WIN_FIXED)
+    return (p->dtype == BK_F64)
+               ? launch_batched_w<FormF64Fixed, double>(p, d, limit, warps, ctas_per_sm, chunk, s)
+               : launch_batched_w<FormF64Fixed, float>(p, d, limit, warps, ctas_per_sm, chunk, s);
+  if (f64 && p->opts.series_below > 0.0)
+    return (p->dtype == BK_F64)
+               ? launch_batched_w<FormF64Series, double>(p, d, limit, warps, ctas_per_sm, chunk, s)
+               : launch_batched_w<FormF64Series, float>(p, d, limit, warps, ctas_per_sm, chunk, s);
   if (p->dtype == BK_F64) {
     if (learned)
       return launch_batched_w<FormF32Learned, double>(p, d, limit, warps, ctas_per_sm, chunk, s);
@@ -169,7 +185,21 @@ int max_ctas_per_sm(const bk_plan* p, int warps) {
   int blocks = 0;
   const void* fn = nullptr;
   const bool f64 = (p->opts.compute == BK_F64);
-  if (p->opts.window == BK_WIN_LEARNED) {
+  if (p->opts.window == BK_WIN_FIXED) {
+    if (p->dtype == BK_F64)
+      fn = (warps == 4) ? (const void*)matern_batched_kernel<FormF64Fixed, double, 4>
+                        : (const void*)matern_batched_kernel<FormF64Fixed, double, 8>;
+    else
+      fn = (warps == 4) ? (const void*)matern_batched_kernel<FormF64Fixed, float, 4>
+                        : (const void*)matern_batched_kernel<FormF64Fixed, float, 8>;
+  } else if (f64 && p->opts.series_below > 0.0) {
+    if (p->dtype == BK_F64)
+      fn = (warps == 4) ? (const void*)matern_batched_kernel<FormF64Series, double, 4>
+                        : (const void*)matern_batched_kernel<FormF64Series, double, 8>;
+    else
+      fn = (warps == 4) ? (const void*)matern_batched_kernel<FormF64Series, float, 4>
+                        : (const void*)matern_batched_kernel<FormF64Series, float, 8>;
+  } else if (p->opts.window == BK_WIN_LEARNED) {
     if (p->dtype == BK_F64)
       fn = (warps == 4) ? (const void*)matern_batched_kernel<FormF32Learned, double, 4>
                         : (const void*)matern_batched_kernel<FormF32Learned, double, 8>;
@@ -278,13 +308,8 @@ bk_status bk_batched_plan_create(bk_plan** plan, const int64_t* sizes, int32_t c
   bk_opts o;
   bk_opts_default(&o);
   if (opts != nullptr) o = *opts; else o.compute = dtype;
-  if (o.compute != BK_F64 && o.compute != BK_F32)
-    return set_error(BK_ERR_INVALID_ARG, "opts.compute: unknown dtype %d", (int)o.compute);
-  if (o.window == BK_WIN_FIXED)
-    return set_error(BK_ERR_UNSUPPORTED, "batched: the fixed window is not built in this version");
-  if (o.window == BK_WIN_LEARNED && (o.compute != BK_F32 || !learned_ready(o.learned)))
-    return set_error(o.compute != BK_F32 ? BK_ERR_UNSUPPORTED : BK_ERR_NOT_LOADED,
-                     "batched: the learned window needs compute = BK_F32 and a network with weights");
+  const bk_status st = check_opts(&o);
+  if (st != BK_OK) return st;
   std::vector<int64_t> prefix((size_t)count + 1, 0);
   for (int32_t k = 0; k < count; ++k) {
     if (sizes[k] < 0) return set_error(BK_ERR_INVALID_ARG, "sizes[%d] < 0", (int)k);
@@ -502,7 +527,7 @@ __global__ void __launch_bounds__(WARPS * 32, Form::kMinBlocks * 8 / WARPS) mate
   __shared__ BatchSmem<OutT> sm;
   __shared__ double s_tab[Form::kStageTable ? kExpTabSize : 1];
   const Form f = bind_table(Form{}, s_tab);
-  Tally tl{0u, 0u, 0u, 0u, 0u, 0u};
+  Tally tl{0u, 0u, 0u, 0u, 0u, 0u, 0u};
   unsigned evals = 0;
   int cur = -1;
   while (true) {

@@ -49,18 +49,28 @@ int current_sm_count() {
 }
 
 namespace {
-
 bool finite(double v) { return std::isfinite(v); }
+}  // namespace
 
 bk_status check_opts(const bk_opts* o) {
   if (o->window != BK_WIN_SEARCH && o->window != BK_WIN_LEARNED && o->window != BK_WIN_FIXED)
     return set_error(BK_ERR_INVALID_ARG, "opts.window: unknown value %d", (int)o->window);
   if (o->compute != BK_F64 && o->compute != BK_F32)
     return set_error(BK_ERR_INVALID_ARG, "opts.compute: unknown dtype %d", (int)o->compute);
-  if (o->window == BK_WIN_FIXED && (o->fixed_bins < 1 || !(o->fixed_t1 > 0.0) || !finite(o->fixed_t1)))
-    return set_error(BK_ERR_INVALID_ARG, "opts: fixed window needs fixed_bins >= 1 and fixed_t1 > 0");
-  if (o->window == BK_WIN_FIXED)
-    return set_error(BK_ERR_UNSUPPORTED, "the fixed window is not built in this version");
+  if (!finite(o->series_below) || o->series_below < 0.0 || o->series_below > 2.0)
+    return set_error(BK_ERR_INVALID_ARG, "opts.series_below must be in [0, 2] (got %g)",
+                     o->series_below);
+  if (o->series_below > 0.0 && o->compute != BK_F64)
+    return set_error(BK_ERR_UNSUPPORTED, "opts.series_below needs compute = BK_F64");
+  if (o->window == BK_WIN_FIXED) {
+    if (o->fixed_bins < 1 || o->fixed_bins > 100000 || !(o->fixed_t1 > 0.0) ||
+        !(o->fixed_t1 <= 700.0))
+      return set_error(BK_ERR_INVALID_ARG,
+                       "opts: the fixed window needs 1 <= fixed_bins <= 100000 and "
+                       "0 < fixed_t1 <= 700");
+    if (o->compute != BK_F64)
+      return set_error(BK_ERR_UNSUPPORTED, "the fixed window needs compute = BK_F64");
+  }
   if (o->window == BK_WIN_LEARNED) {
     if (o->compute != BK_F32)
       return set_error(BK_ERR_UNSUPPORTED, "the learned window needs compute = BK_F32 "
@@ -70,6 +80,8 @@ bk_status check_opts(const bk_opts* o) {
   }
   return BK_OK;
 }
+
+namespace {
 
 bk_status check_dtype(bk_dtype d) {
   if (d != BK_F64 && d != BK_F32)
@@ -112,6 +124,7 @@ void bk_opts_default(bk_opts* o) {
   o->fixed_bins = 40;
   o->fixed_t1 = 9.0;
   o->search_f64 = 0;
+  o->series_below = 0.0;
   o->d_counters = nullptr;
   o->learned = nullptr;
 }
@@ -154,7 +167,7 @@ bk_status bk_eval_ex(const double* x, const double* nu, void* out, void* log_out
       (o.window == BK_WIN_LEARNED)
           ? launch_eval_learned(o.learned, x, nu, out, log_out, out_dtype, n, o.d_counters, s)
       : (o.compute == BK_F64)
-          ? launch_eval_f64(x, nu, out, log_out, out_dtype, n, o.search_f64 != 0, o.d_counters, s)
+          ? launch_eval_f64(x, nu, out, log_out, out_dtype, n, o, s)
           : launch_eval_f32(x, nu, out, log_out, out_dtype, n, o.d_counters, s);
   return check_cuda(e, "bk_eval launch");
 }
@@ -183,8 +196,7 @@ bk_status bk_matern_tile_ex(const double* locs, int64_t n, double sigma2, double
           ? launch_matern_sym_learned(o.learned, locs, n, sigma2, beta, nu, out, ld, dtype,
                                       o.d_counters, s)
       : (o.compute == BK_F64)
-          ? launch_matern_sym_f64(locs, n, sigma2, beta, nu, out, ld, dtype, o.search_f64 != 0,
-                                  o.d_counters, s)
+          ? launch_matern_sym_f64(locs, n, sigma2, beta, nu, out, ld, dtype, o, s)
           : launch_matern_sym_f32(locs, n, sigma2, beta, nu, out, ld, dtype, o.d_counters, s);
   return check_cuda(e, "bk_matern_tile launch");
 }
@@ -214,8 +226,8 @@ bk_status bk_matern_tile2(const double* locs1, int64_t m, const double* locs2, i
           ? launch_matern_block_learned(o.learned, locs1, m, locs2, n, sigma2, beta, nu, out, ld,
                                         dtype, o.d_counters, s)
       : (o.compute == BK_F64)
-          ? launch_matern_block_f64(locs1, m, locs2, n, sigma2, beta, nu, out, ld, dtype,
-                                    o.search_f64 != 0, o.d_counters, s)
+          ? launch_matern_block_f64(locs1, m, locs2, n, sigma2, beta, nu, out, ld, dtype, o,
+                                    s)
           : launch_matern_block_f32(locs1, m, locs2, n, sigma2, beta, nu, out, ld, dtype,
                                     o.d_counters, s);
   return check_cuda(e, "bk_matern_tile2 launch");

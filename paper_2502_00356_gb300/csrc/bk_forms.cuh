@@ -9,6 +9,7 @@
 #include "bk_math32.cuh"
 #include "bk_math64.cuh"
 #include "bk_matern_common.cuh"
+#include "bk_series.cuh"
 
 namespace bk {
 
@@ -20,7 +21,7 @@ namespace bk {
 __device__ __forceinline__ const Start32* plain_starts(double x, double nu, Start32& st) {
   const float xf = (float)x;
   if (!(xf >= 1e-4f && xf <= 1e4f && nu <= 40.0)) return nullptr;
-  Tally fp32_work{0u, 0u, 0u, 0u, 0u, 0u};
+  Tally fp32_work{0u, 0u, 0u, 0u, 0u, 0u, 0u};
   const Window32 w = window_f32(xf, (float)nu, (float)kLogInvEps64, fp32_work);
   st = Start32{w.ts, w.t0, w.t1};
   return &st;
@@ -32,16 +33,33 @@ __device__ __forceinline__ const Start32* plain_starts(double x, double nu, Star
 // number of 32 x 32 tiles one block of the tile kernels computes, and
 // kMinBlocks the resident 256-thread blocks per SM the tile kernels are
 // compiled for (it caps their registers: 3 -> 85, 4 -> 64).
-struct FormF64 {
+// kSeries: whether the form has the small-x series branch at all (a separate
+// instantiation, so that the default form carries no call site for it).
+template <bool kSeries>
+struct FormF64T {
   static constexpr bool kStageTable = true;
   static constexpr int kTilesPerBlock = 1;
   static constexpr int kMinBlocks = 3;
   const double* tab;
-  bool search_f64;  // FP64 Newton search for every point (no FP32 roots)
+  bool search_f64;      // FP64 Newton search for every point (no FP32 roots)
+  double series_below;  // x below which Temme's series replaces the integral (0: never)
+
+  // log K from Temme's series (Sec. IV-A), tallied.
+  __device__ __forceinline__ double series(double x, double nu, Tally& tl) const {
+    unsigned terms;
+    const double lk = series_log_k(x, nu, terms);
+    ++tl.series;
+    tl.nodes += terms;
+    return lk;
+  }
 
   __device__ __forceinline__ double eval(double x, double nu, Tally& tl, unsigned& evals,
                                          double& log_k, bool want_log) const {
     ++evals;
+    if (kSeries && x < series_below) {
+      log_k = series(x, nu, tl);
+      return exp_tab_full(log_k, tab);
+    }
     Start32 st;
     const Start32* sp = search_f64 ? nullptr : plain_starts(x, nu, st);
     double hS;
@@ -61,10 +79,70 @@ struct FormF64 {
     if (r == 0.0) return mp.sigma2;
     const double z = r * mp.inv_beta;
     ++evals;
+    if (kSeries && z < series_below)
+      return exp_tab_full(fma(mp.nu, log_tab(z, tab), mp.log_pref) + series(z, mp.nu, tl), tab);
     Start32 st;
     const Start32* sp = search_f64 ? nullptr : plain_starts(z, mp.nu, st);
     double hS;
     const double sc = scale_f64(z, mp.nu, kPlainLog2OverTol, kPlainMaxNodes, tab, hS, tl, sp);
+    return exp_tab_full(fma(mp.nu, log_tab(z, tab), mp.log_pref) + sc, tab) * hS;
+  }
+};
+
+using FormF64 = FormF64T<false>;        // the plain form
+using FormF64Series = FormF64T<true>;   // the plain form with Temme's series below a threshold
+
+// The paper's refined algorithm (Algorithm 2) in FP64: Temme's series below
+// series_below (0.1 in the paper), else the fixed window [0, t1] with `bins`
+// bins (9 and 40 in the paper; Sec. IV-C), no per-point search.
+struct FormF64Fixed {
+  static constexpr bool kStageTable = true;
+  static constexpr int kTilesPerBlock = 1;
+  static constexpr int kMinBlocks = 3;
+  const double* tab;
+  double t1;
+  int bins;
+  double series_below;
+
+  __device__ __forceinline__ double log_k_of(double x, double nu, Tally& tl, double& hS,
+                                             bool& by_series) const {
+    by_series = x < series_below;
+    if (by_series) {
+      unsigned terms;
+      const double lk = series_log_k(x, nu, terms);
+      ++tl.series;
+      tl.nodes += terms;
+      hS = 1.0;
+      return lk;
+    }
+    return fixed_scale_f64(x, nu, t1, bins, tab, hS, tl);
+  }
+
+  __device__ __forceinline__ double eval(double x, double nu, Tally& tl, unsigned& evals,
+                                         double& log_k, bool want_log) const {
+    ++evals;
+    double hS;
+    bool by_series;
+    const double sc = log_k_of(x, nu, tl, hS, by_series);
+    if (by_series) {
+      log_k = sc;
+      return exp_tab_full(sc, tab);
+    }
+    const double lh = (want_log || sc > 700.0) ? log_tab(hS, tab) : 0.0;
+    if (want_log) log_k = sc + lh;
+    return (sc > 700.0) ? exp_tab_full(sc + lh, tab) : exp_tab_full(sc, tab) * hS;
+  }
+
+  __device__ __forceinline__ double matern(const Loc& a, const Loc& b, const MaternParams& mp,
+                                           Tally& tl, unsigned& evals) const {
+    const double dx = b.x - a.x, dy = b.y - a.y;
+    const double r = sqrt(fma(dx, dx, dy * dy));
+    if (r == 0.0) return mp.sigma2;
+    const double z = r * mp.inv_beta;
+    ++evals;
+    double hS;
+    bool by_series;
+    const double sc = log_k_of(z, mp.nu, tl, hS, by_series);
     return exp_tab_full(fma(mp.nu, log_tab(z, tab), mp.log_pref) + sc, tab) * hS;
   }
 };

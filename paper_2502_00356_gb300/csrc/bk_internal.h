@@ -21,19 +21,21 @@ bk_status check_cuda(cudaError_t e, const char* what);
 
 // ---- plain FP64 form (bk_plain.cu) ----
 cudaError_t launch_eval_f64(const double* x, const double* nu, void* out, void* log_out,
-                            bk_dtype out_t, int64_t n, bool search_f64, unsigned long long* ctr,
-                            cudaStream_t s);
+                            bk_dtype out_t, int64_t n, const bk_opts& o, cudaStream_t s);
 
 // Full symmetric n x n matrix: lower-triangle tiles, each written twice.
 cudaError_t launch_matern_sym_f64(const double* locs, int64_t n, double sigma2, double beta,
                                   double nu, void* out, int64_t ld, bk_dtype out_t,
-                                  bool search_f64, unsigned long long* ctr, cudaStream_t s);
+                                  const bk_opts& o, cudaStream_t s);
 
 // General m x n block between two location sets.
 cudaError_t launch_matern_block_f64(const double* locs1, int64_t m, const double* locs2,
                                     int64_t n, double sigma2, double beta, double nu, void* out,
-                                    int64_t ld, bk_dtype out_t, bool search_f64,
-                                    unsigned long long* ctr, cudaStream_t s);
+                                    int64_t ld, bk_dtype out_t, const bk_opts& o, cudaStream_t s);
+
+// Option checks shared by every entry point that takes bk_opts (sets the
+// error message and returns the status).
+bk_status check_opts(const bk_opts* o);
 
 // ---- FP32 precision form (bk_fp32.cu) ----
 cudaError_t launch_eval_f32(const double* x, const double* nu, void* out, void* log_out,

@@ -237,6 +237,7 @@ struct Tally {
   unsigned fail;        // evaluations returned as NaN
   unsigned fallback;    // learned windows replaced by the full search
   unsigned repairs;     // learned window ends moved by one Newton step
+  unsigned series;      // evaluations taken by Temme's series (small x)
 };
 
 // The window of Sec. IV-B.  ts = t_max, cs = cosh ts, es = e^ts, [t0, t1] the
@@ -555,7 +556,7 @@ struct Scaled64 {
 // registers.  Returns NaN (and fail = 1) when N would exceed n_max.
 static __device__ __noinline__ Scaled64 scaled_search_f64(double x, double nu, float log2_over_tol,
                                                    int n_max, const double* __restrict__ tab) {
-  Tally tl{0u, 0u, 0u, 0u, 0u, 0u};
+  Tally tl{0u, 0u, 0u, 0u, 0u, 0u, 0u};
   Scaled64 r;
   const Window64 w = window_f64(x, nu, kLogInvEps64, tab, tl);
   const double width = w.t1 - w.t0;
@@ -616,6 +617,56 @@ __device__ __forceinline__ double scale_f64(double x, double nu, float log2_over
   }
   hS = h * (ns.S - 0.5 * (ns.first + ns.last));
   return fma(nu, w.ts, -x * w.cs) - kLn2;
+}
+
+// The paper's fixed window (Algorithm 2, x >= 0.1 branch, Sec. IV-C): the
+// trapezoid on [0, t1] with b bins, h = t1/b, weights 1/2 at both ends,
+// shifted by the largest node value (t_lmax).  The shift is taken at the
+// node with the largest nu t - x cosh t (g without its log(1 + e^{-2 nu t})
+// term: any shift is exact, this one keeps every scaled node <= 2).  Pass 1
+// finds it, pass 2 sums exp2s of the scaled exponents (clamped below at
+// e^-1000, far under the double range) times (1 + e^{-2 nu t}); cosh t_m by
+// the three-term recurrence, all in the scaled units of node_sum_f64.
+// Returns the scale (the shift minus ln 2) and sets h S.
+__device__ __forceinline__ double fixed_scale_f64(double x, double nu, double t1, int bins,
+                                                  const double* __restrict__ tab, double& hS,
+                                                  Tally& tl) {
+  const double h = t1 * rcp_nr2((double)bins);
+  double c;
+  if (h <= 0.35) {
+    c = two_cosh_small(h);
+  } else {
+    const double eh = exp_tab(h, tab);
+    c = eh + rcp_nr2(eh);
+  }
+  const double D0i = kExpScale * x, D1i = 0.5 * c * D0i, dA = kExpScale * (nu * h);
+  double D0 = D0i, D1 = D1i, A = 0.0, amax = -1e300;
+  for (int m = 0; m <= bins; ++m) {
+    amax = fmax(amax, A - D0);
+    const double D2 = fma(c, D1, -D0);
+    D0 = D1;
+    D1 = D2;
+    A += dA;
+  }
+  const double rho = exp_tab(fmax(-2.0 * nu * h, -708.0), tab);
+  D0 = D0i;
+  D1 = D1i;
+  A = -amax;
+  double W = 1.0, s = 0.0, f = 0.0, first = 0.0;
+  for (int m = 0; m <= bins; ++m) {
+    const double ev = exp2s(fmax(A - D0, -1000.0 * kExpScale), tab);
+    f = fma(ev, W, ev);
+    if (m == 0) first = f;
+    s += f;
+    const double D2 = fma(c, D1, -D0);
+    D0 = D1;
+    D1 = D2;
+    A += dA;
+    W *= rho;
+  }
+  tl.nodes += 2 * (bins + 1);
+  hS = h * (s - 0.5 * (first + f));
+  return amax * kExpC1 - kLn2;
 }
 
 // ln(2 / tol) for the plain form: tol = 1e-13 keeps the quadrature error

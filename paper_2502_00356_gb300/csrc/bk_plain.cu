@@ -1,7 +1,8 @@
 // Plain FP64 form: K_nu evaluation and the fused Matern tile writer
 // (distance -> r/beta -> K_nu -> normalisation -> store), Algorithm 3 and
 // Sec. IV-B, with the window search, strip-bound node count and log-domain
-// trapezoid of bk_math64.cuh.  One thread evaluates one K_nu.
+// trapezoid of bk_math64.cuh, or the paper's fixed window (Algorithm 2), and
+// Temme's series for small x when asked.  One thread evaluates one K_nu.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -17,25 +18,39 @@ int grid_for(int64_t work_items, int per_sm) {
   return (int)(work_items < cap ? (work_items > 0 ? work_items : 1) : cap);
 }
 
+// Calls launch(form) with the plain form the options select: the paper's
+// fixed window (Algorithm 2) or the searched window, each with the optional
+// series branch for small x.
+template <class Launch>
+cudaError_t with_plain_form(const bk_opts& o, Launch&& launch) {
+  if (o.window == BK_WIN_FIXED)
+    return launch(FormF64Fixed{nullptr, o.fixed_t1, o.fixed_bins, o.series_below});
+  if (o.series_below > 0.0) return launch(FormF64Series{nullptr, o.search_f64 != 0, o.series_below});
+  return launch(FormF64{nullptr, o.search_f64 != 0, 0.0});
+}
+
 cudaError_t launch_eval_f64(const double* x, const double* nu, void* out, void* log_out,
-                            bk_dtype out_t, int64_t n, bool search_f64, unsigned long long* ctr,
-                            cudaStream_t s) {
-  return launch_eval_form(FormF64{nullptr, search_f64}, x, nu, out, log_out, out_t, n, ctr, s);
+                            bk_dtype out_t, int64_t n, const bk_opts& o, cudaStream_t s) {
+  return with_plain_form(o, [&](const auto& form) {
+    return launch_eval_form(form, x, nu, out, log_out, out_t, n, o.d_counters, s);
+  });
 }
 
 cudaError_t launch_matern_sym_f64(const double* locs, int64_t n, double sigma2, double beta,
                                   double nu, void* out, int64_t ld, bk_dtype out_t,
-                                  bool search_f64, unsigned long long* ctr, cudaStream_t s) {
-  return launch_matern_sym_form(FormF64{nullptr, search_f64}, locs, n, sigma2, beta, nu, out, ld,
-                                out_t, ctr, s);
+                                  const bk_opts& o, cudaStream_t s) {
+  return with_plain_form(o, [&](const auto& form) {
+    return launch_matern_sym_form(form, locs, n, sigma2, beta, nu, out, ld, out_t, o.d_counters, s);
+  });
 }
 
 cudaError_t launch_matern_block_f64(const double* locs1, int64_t m, const double* locs2,
                                     int64_t n, double sigma2, double beta, double nu, void* out,
-                                    int64_t ld, bk_dtype out_t, bool search_f64,
-                                    unsigned long long* ctr, cudaStream_t s) {
-  return launch_matern_block_form(FormF64{nullptr, search_f64}, locs1, m, locs2, n, sigma2, beta, nu,
-                                  out, ld, out_t, ctr, s);
+                                    int64_t ld, bk_dtype out_t, const bk_opts& o, cudaStream_t s) {
+  return with_plain_form(o, [&](const auto& form) {
+    return launch_matern_block_form(form, locs1, m, locs2, n, sigma2, beta, nu, out, ld, out_t,
+                                    o.d_counters, s);
+  });
 }
 
 }  // namespace bk

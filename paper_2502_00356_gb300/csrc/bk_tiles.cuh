@@ -28,12 +28,12 @@ __device__ __forceinline__ float to_out<float>(double v) { return (float)v; }
 __device__ __forceinline__ void flush_tally(unsigned long long* ctr, const Tally& tl,
                                             unsigned evals) {
   if (ctr == nullptr) return;
-  unsigned long long v[7] = {tl.fail,       tl.nodes,    tl.iters,  evals,
-                             tl.peak_iters, tl.fallback, tl.repairs};
-  const int idx[7] = {BK_CTR_FAIL,       BK_CTR_NODES,    BK_CTR_ITERS, BK_CTR_EVALS,
-                      BK_CTR_PEAK_ITERS, BK_CTR_FALLBACK, BK_CTR_REPAIR};
+  unsigned long long v[8] = {tl.fail,       tl.nodes,    tl.iters,   evals,
+                             tl.peak_iters, tl.fallback, tl.repairs, tl.series};
+  const int idx[8] = {BK_CTR_FAIL,       BK_CTR_NODES,    BK_CTR_ITERS,  BK_CTR_EVALS,
+                      BK_CTR_PEAK_ITERS, BK_CTR_FALLBACK, BK_CTR_REPAIR, BK_CTR_SERIES};
 #pragma unroll
-  for (int k = 0; k < 7; ++k) {
+  for (int k = 0; k < 8; ++k) {
     unsigned long long a = v[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
@@ -48,22 +48,22 @@ __device__ __forceinline__ void flush_tally(unsigned long long* ctr, const Tally
 __device__ __forceinline__ void flush_tally_block(unsigned long long* ctr, const Tally& tl,
                                                   unsigned evals) {
   if (ctr == nullptr) return;
-  __shared__ unsigned long long s_acc[7];
-  if (threadIdx.x < 7) s_acc[threadIdx.x] = 0ull;
+  __shared__ unsigned long long s_acc[8];
+  if (threadIdx.x < 8) s_acc[threadIdx.x] = 0ull;
   __syncthreads();
-  unsigned long long v[7] = {tl.fail,       tl.nodes,    tl.iters,  evals,
-                             tl.peak_iters, tl.fallback, tl.repairs};
+  unsigned long long v[8] = {tl.fail,       tl.nodes,    tl.iters,   evals,
+                             tl.peak_iters, tl.fallback, tl.repairs, tl.series};
 #pragma unroll
-  for (int k = 0; k < 7; ++k) {
+  for (int k = 0; k < 8; ++k) {
     unsigned long long a = v[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
     if ((threadIdx.x & 31) == 0 && a) atomicAdd(&s_acc[k], a);
   }
   __syncthreads();
-  const int idx[7] = {BK_CTR_FAIL,       BK_CTR_NODES,    BK_CTR_ITERS, BK_CTR_EVALS,
-                      BK_CTR_PEAK_ITERS, BK_CTR_FALLBACK, BK_CTR_REPAIR};
-  if (threadIdx.x < 7 && s_acc[threadIdx.x]) atomicAdd(ctr + idx[threadIdx.x], s_acc[threadIdx.x]);
+  const int idx[8] = {BK_CTR_FAIL,       BK_CTR_NODES,    BK_CTR_ITERS,  BK_CTR_EVALS,
+                      BK_CTR_PEAK_ITERS, BK_CTR_FALLBACK, BK_CTR_REPAIR, BK_CTR_SERIES};
+  if (threadIdx.x < 8 && s_acc[threadIdx.x]) atomicAdd(ctr + idx[threadIdx.x], s_acc[threadIdx.x]);
 }
 
 // Binds a form to its exponential table: the block's shared copy (filled
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(128) eval_kernel(const Form form, const double
                                                    unsigned long long* __restrict__ ctr) {
   __shared__ double s_tab[Form::kStageTable ? kExpTabSize : 1];
   const Form f = bind_table(form, s_tab);
-  Tally tl{0u, 0u, 0u, 0u, 0u, 0u};
+  Tally tl{0u, 0u, 0u, 0u, 0u, 0u, 0u};
   unsigned evals = 0;
   const bool want_log = (log_out != nullptr);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(kThreads, Form::kMinBlocks) matern_sym_kernel(
   __shared__ SymTileSmem<OutT> sm;
   __shared__ double s_tab[Form::kStageTable ? kExpTabSize : 1];
   const Form f = bind_table(form, s_tab);
-  Tally tl{0u, 0u, 0u, 0u, 0u, 0u};
+  Tally tl{0u, 0u, 0u, 0u, 0u, 0u, 0u};
   unsigned evals = 0;
   constexpr int kPer = Form::kTilesPerBlock;
   for (int64_t base = (int64_t)blockIdx.x * kPer; base < ntiles; base += (int64_t)gridDim.x * kPer) {
@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(kThreads, Form::kMinBlocks) matern_block_kerne
   __shared__ double s_tab[Form::kStageTable ? kExpTabSize : 1];
   const Form f = bind_table(form, s_tab);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  Tally tl{0u, 0u, 0u, 0u, 0u, 0u};
+  Tally tl{0u, 0u, 0u, 0u, 0u, 0u, 0u};
   unsigned evals = 0;
   constexpr int kPer = Form::kTilesPerBlock;
   for (int64_t base = (int64_t)blockIdx.x * kPer; base < ntiles; base += (int64_t)gridDim.x * kPer) {

@@ -73,6 +73,29 @@ def test_option_checks(L):
     o.window = bk.BK_WIN_FIXED
     o.fixed_bins = 0
     assert L.bk_eval_ex(fake, fake, fake, None, 0, 5, ctypes.byref(o), None) == bk.BK_ERR_INVALID_ARG
+    o.fixed_bins = 40
+    o.fixed_t1 = 701.0
+    assert L.bk_eval_ex(fake, fake, fake, None, 0, 5, ctypes.byref(o), None) == bk.BK_ERR_INVALID_ARG
+    o.fixed_t1 = 9.0
+    o.compute = bk.BK_F32  # the fixed window is a plain FP64 form
+    assert L.bk_eval_ex(fake, fake, fake, None, 0, 5, ctypes.byref(o), None) == bk.BK_ERR_UNSUPPORTED
+    # Temme's series: x threshold in [0, 2], plain FP64 only
+    L.bk_opts_default(ctypes.byref(o))
+    for bad in (-0.1, 2.5, float("nan"), float("inf")):
+        o.series_below = bad
+        assert L.bk_eval_ex(fake, fake, fake, None, 0, 5, ctypes.byref(o), None) == bk.BK_ERR_INVALID_ARG
+    o.series_below = 0.1
+    o.compute = bk.BK_F32
+    assert L.bk_eval_ex(fake, fake, fake, None, 0, 5, ctypes.byref(o), None) == bk.BK_ERR_UNSUPPORTED
+    # n = 0 with valid options is a no-op
+    o.compute = bk.BK_F64
+    o.window = bk.BK_WIN_FIXED
+    assert L.bk_eval_ex(fake, fake, fake, None, 0, 0, ctypes.byref(o), None) == bk.BK_OK
+    # the batched plan applies the same checks
+    plan = ctypes.c_void_p()
+    sizes = (ctypes.c_int64 * 1)(10)
+    o.compute = bk.BK_F32
+    assert L.bk_batched_plan_create(ctypes.byref(plan), sizes, 1, 0, ctypes.byref(o)) == bk.BK_ERR_UNSUPPORTED
 
 
 def test_morton_order_matches_generator(L):
