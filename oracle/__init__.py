@@ -67,6 +67,7 @@ def _load():
             "oracle_besselk": (D, [D, D]),
             "oracle_besselk_batch": (None, [P, P, P, P, I64, I]),
             "oracle_besselk_temme": (D, [D, D, P]),
+            "oracle_besselk_grad_batch": (None, [P, P, P, P, P, I64, I]),
             "oracle_window": (None, [D, D, D, P]),
             "oracle_window_batch": (None, [P, P, D, P, I64, I]),
             "oracle_window_trapezoid_log_k": (D, [D, D, D, D, I64]),
@@ -126,6 +127,16 @@ def besselk(x, nu, threads: int = 0, return_log: bool = False):
     if return_log:
         return out.reshape(shape)[()], lout.reshape(shape)[()]
     return out.reshape(shape)[()]
+
+
+def besselk_grad(x, nu, threads: int = 0):
+    """(K_nu(x), dK/dx, dK/dnu) elementwise over broadcast arrays, the
+    derivatives by the integral differentiated under the sign."""
+    shape, xf, nf = _bcast(x, nu)
+    k, dx, dn = (np.empty(xf.size) for _ in range(3))
+    _load().oracle_besselk_grad_batch(_ptr(xf), _ptr(nf), _ptr(k), _ptr(dx), _ptr(dn), xf.size,
+                                      int(threads))
+    return k.reshape(shape), dx.reshape(shape), dn.reshape(shape)
 
 
 def besselk_temme(x: float, nu: float) -> float:

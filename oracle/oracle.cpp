@@ -27,6 +27,8 @@
 //  * oracle_fixed_window_log_k: the paper's refined integration branch
 //    (Algorithm 2, else-branch): fixed [0, t1], b bins, shift by the largest
 //    node value, trapezoid weights multiplying the exponential.
+//  * oracle_besselk_grad_batch: dK/dx and dK/dnu by differentiating the
+//    integral under the sign (not in the paper; for gradient-based MLE).
 //
 // Pins (tests/test_oracle_pins.py): closed forms for nu = 1/2, 3/2, 5/2,
 // recurrence Eq. (recurrence), the Wronskian with a library I_nu, small- and
@@ -308,6 +310,89 @@ void oracle_besselk_batch(const double* x, const double* nu, double* out, double
     ld r = dense_log_k((ld)xi, (ld)nu[i], &st);
     out[i] = st ? NAN : (double)expl(r);
     if (log_out) log_out[i] = st ? NAN : (double)r;
+  }
+}
+
+// Derivatives of K_nu(x), by differentiating the integral of Eq. (integral)
+// under the integral sign:
+//   -dK/dx  = int_0^inf cosh(t) e^{-x cosh t} cosh(nu t) dt,
+//    dK/dnu = int_0^inf t sinh(nu t) e^{-x cosh t} dt,
+// by the same dense trapezoid as dense_log_k (window by stepping, halving to
+// agreement) applied to the logs of these integrands, both positive for
+// x > 0, nu > 0 and even in t (so the rule on [0, T] keeps its fast
+// convergence).  kind 1: -dK/dx, kind 2: dK/dnu.  Returns the log.
+static ld log_sinh_pos(ld y) { return y + log1pl(-expl(-2.0L * y)) - kLn2; }
+
+static ld deriv_log_integrand(ld t, ld x, ld nu, int kind) {
+  if (kind == 1) return g_of(t, x, nu) + logl(coshl(t));
+  if (t == 0.0L || nu == 0.0L) return -INFINITY;
+  return logl(t) + log_sinh_pos(nu * t) - x * coshl(t);
+}
+
+static ld dense_log_deriv(ld x, ld nu, int kind, int* status) {
+  *status = 0;
+  const ld step = 1.0L / 64.0L;
+  ld gmax = deriv_log_integrand(0.0L, x, nu, kind);
+  ld T = 0.0L;
+  for (long k = 1; k <= 64L * 200L; ++k) {
+    ld t = step * (ld)k;
+    ld gt = deriv_log_integrand(t, x, nu, kind);
+    if (gt > gmax) gmax = gt;
+    if (gt < gmax - 90.0L) { T = t; break; }
+  }
+  if (T == 0.0L) { *status = 1; return NAN; }
+  ld h_start = 0.25L / powl(x * x + nu * nu + 1.0L, 0.25L);
+  if (h_start > 1.0L / 32.0L) h_start = 1.0L / 32.0L;
+  long M = (long)ceill(T / h_start);
+  if (M < 64) M = 64;
+  ld S = 0.5L * (expl(deriv_log_integrand(0.0L, x, nu, kind) - gmax) +
+                 expl(deriv_log_integrand(T, x, nu, kind) - gmax));
+  for (long m = 1; m < M; ++m)
+    S += expl(deriv_log_integrand(T * (ld)m / (ld)M, x, nu, kind) - gmax);
+  ld prev = (T / (ld)M) * S;
+  ld tol = 64.0L * LDBL_EPSILON;
+  if (tol < 1e-30L) tol = 1e-30L;
+  if (tol < 1e-17L && LDBL_MANT_DIG < 100) tol = 1e-17L;
+  int agree = 0;
+  for (int level = 0; level < 14; ++level) {
+    ld add = 0.0L;
+    for (long m = 0; m < M; ++m)
+      add += expl(deriv_log_integrand(T * (ld)(2 * m + 1) / (ld)(2 * M), x, nu, kind) - gmax);
+    S += add;
+    M *= 2;
+    ld cur = (T / (ld)M) * S;
+    if (fabsl(cur - prev) <= tol * cur) {
+      if (++agree == 2) return gmax + logl(cur);
+    } else {
+      agree = 0;
+    }
+    prev = cur;
+  }
+  *status = 1;
+  return NAN;
+}
+
+// K, dK/dx and dK/dnu (dK/dnu is odd in nu: K_{-nu} = K_nu).  NaN on failure.
+void oracle_besselk_grad_batch(const double* x, const double* nu, double* k, double* dkdx,
+                               double* dkdnu, int64_t n, int nthreads) {
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 4)
+#endif
+  for (int64_t i = 0; i < n; ++i) {
+    const ld X = (ld)x[i], V = fabsl((ld)nu[i]);
+    int s0 = 0, s1 = 0, s2 = 0;
+    const ld lk = dense_log_k(X, V, &s0);
+    const ld lx = dense_log_deriv(X, V, 1, &s1);
+    k[i] = s0 ? NAN : (double)expl(lk);
+    dkdx[i] = s1 ? NAN : (double)(-expl(lx));
+    if (V == 0.0L) {
+      dkdnu[i] = 0.0;
+    } else {
+      const ld ln = dense_log_deriv(X, V, 2, &s2);
+      const double d = s2 ? NAN : (double)expl(ln);
+      dkdnu[i] = (nu[i] < 0.0) ? -d : d;
+    }
   }
 }
 

@@ -263,3 +263,44 @@ def test_window_labels_definition(orc):
             return np.log((t1 - t0) / n * (f.sum() - 0.5 * (f[0] + f[-1]))) + gs
         assert abs(np.expm1(trap(N) - lref)) <= 1e-6 * 1.01
         assert abs(np.expm1(trap(N - 1) - lref)) > 1e-6 * 0.99
+
+
+# ---------------------------------------------------------------------------
+# Derivatives (for the gradient entry point): the integral differentiated
+# under the sign, pinned by identities and closed forms it does not use.
+
+def test_grad_x_closed_form_and_recurrence_identity(orc):
+    # d/dx of the closed form of K_{1/2}
+    x = X_GRID
+    _, dx, _ = orc.besselk_grad(x, np.full(x.size, 0.5))
+    want = -np.sqrt(np.pi / (2 * x)) * np.exp(-x) * (1 + 1 / (2 * x))
+    np.testing.assert_allclose(dx, want, rtol=1e-14, atol=0)
+    # dK_nu/dx = -(K_{nu-1} + K_{nu+1}) / 2 (from the recurrence), K_{-a} = K_a
+    rng = np.random.default_rng(41)
+    x = np.exp(rng.uniform(np.log(1e-3), np.log(140.0), 300))
+    nu = rng.uniform(0.05, 20.0, 300)
+    _, dx, _ = orc.besselk_grad(x, nu)
+    want = -0.5 * (orc.besselk(x, np.abs(nu - 1.0)) + orc.besselk(x, nu + 1.0))
+    np.testing.assert_allclose(dx, want, rtol=1e-13, atol=0)
+
+
+def test_grad_nu_closed_form_zero_and_finite_differences(orc):
+    # DLMF 10.38.7: dK_nu/dnu at nu = 1/2 is sqrt(pi/(2x)) E1(2x) e^x
+    x = X_GRID
+    _, _, dn = orc.besselk_grad(x, np.full(x.size, 0.5))
+    want = np.sqrt(np.pi / (2 * x)) * special.exp1(2 * x) * np.exp(x)
+    np.testing.assert_allclose(dn, want, rtol=1e-13, atol=0)
+    # K is even in nu: the derivative vanishes at 0 and is odd
+    _, _, d0 = orc.besselk_grad(np.array([0.01, 1.0, 50.0]), np.zeros(3))
+    assert np.all(d0 == 0.0)
+    _, _, dp = orc.besselk_grad(np.array([2.0]), np.array([3.3]))
+    _, _, dm = orc.besselk_grad(np.array([2.0]), np.array([-3.3]))
+    assert dp[0] == -dm[0] and dp[0] > 0
+    # central differences of log K in nu (step 1e-4: truncation ~1e-9)
+    rng = np.random.default_rng(42)
+    x = np.exp(rng.uniform(np.log(1e-3), np.log(140.0), 200))
+    nu = rng.uniform(0.1, 20.0, 200)
+    k, _, dn = orc.besselk_grad(x, nu)
+    _, lp = orc.besselk(x, nu + 1e-4, return_log=True)
+    _, lm = orc.besselk(x, nu - 1e-4, return_log=True)
+    np.testing.assert_allclose(dn, k * (lp - lm) / 2e-4, rtol=1e-7, atol=0)
