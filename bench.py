@@ -577,6 +577,16 @@ def main():
     b.record(stream)
     torch.cuda.synchronize()
     eval_rate = reps * X.numel() / (a.elapsed_time(b) / 1e3)
+    # K with dK/dx and dK/dnu from one quadrature, same pairs
+    G = [torch.empty_like(X) for _ in range(3)]
+    bk.bk_eval_grad(X, V, *G)
+    a.record(stream)
+    for _ in range(reps):
+        bk.bk_eval_grad(X, V, *G)
+    b.record(stream)
+    torch.cuda.synchronize()
+    grad_rate = reps * X.numel() / (a.elapsed_time(b) / 1e3)
+    del G
 
     # -- end to end through the public API with host buffers (pinned)
     e2e = None
@@ -627,7 +637,9 @@ def main():
             "failed_points": fails,
             "plain_window_fallback_rate": fallbacks / max(evals_counted, 1),
             "eval_fp64": {"value": eval_rate, "unit": "K_nu evals/s",
-                          "workload": "100,000 pairs, x log-uniform [1e-3,140], nu U[0.05,10]"},
+                          "workload": "100,000 pairs, x log-uniform [1e-3,140], nu U[0.05,10]",
+                          "with_grad_value": grad_rate,
+                          "with_grad_unit": "(K, dK/dx, dK/dnu) evals/s"},
             "probe": probe,
             "forms": forms,
         }

@@ -137,6 +137,22 @@ bk_status bk_eval(const double* x, const double* nu, double* out, int64_t n, bk_
 bk_status bk_eval_ex(const double* x, const double* nu, void* out, void* log_out,
                      bk_dtype out_dtype, int64_t n, const bk_opts* opts, bk_stream_t stream);
 
+/* Derivatives of K_nu(x) with K itself, from one quadrature (not in the
+ * paper; for gradient-based maximum likelihood): differentiating Eq.
+ * (integral) of Sec. IV-B under the integral sign,
+ *   dK/dx  = -int_0^inf cosh(t) e^{-x cosh t} cosh(nu t) dt,
+ *   dK/dnu =  int_0^inf t sinh(nu t) e^{-x cosh t} dt,
+ * evaluated on the nodes of the plain FP64 form over the union of the
+ * eps-windows of the orders nu and nu + 1 (the dK/dx integrand decays like
+ * that of K_{nu+1}).  x, nu: n FP64 values (device); k, dk_dx, dk_dnu: n FP64
+ * outputs each (device), any of them NULL to skip.  Domain: x = 0 gives
+ * (+inf, -inf, NaN), x = +inf gives zeros, x < 0, NaN or non-finite nu give
+ * NaN; dK/dnu is odd in nu.  opts: only the plain form (compute BK_F64,
+ * window BK_WIN_SEARCH, series_below 0; search_f64 and counters apply), else
+ * BK_ERR_UNSUPPORTED.  Asynchronous on `stream`; allocates nothing. */
+bk_status bk_eval_grad(const double* x, const double* nu, double* k, double* dk_dx,
+                       double* dk_dnu, int64_t n, const bk_opts* opts, bk_stream_t stream);
+
 /*
  * bk_matern_tile: the full n x n Matern matrix of `n` locations (Sec. III-A,
  * Algorithm 3), column-major with leading dimension ld >= n, written as

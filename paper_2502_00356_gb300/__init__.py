@@ -32,7 +32,7 @@ BK_NUM_COUNTERS = 8
 #: every symbol include/bk.h declares (checked by the CPU tests)
 EXPORTS = (
     "bk_opts_default", "bk_version", "bk_last_error", "bk_status_string", "bk_sync",
-    "bk_eval", "bk_eval_ex", "bk_matern_tile", "bk_matern_tile_ex", "bk_matern_tile2",
+    "bk_eval", "bk_eval_ex", "bk_eval_grad", "bk_matern_tile", "bk_matern_tile_ex", "bk_matern_tile2",
     "bk_morton_order", "bk_probe_pipe", "bk_batched_plan_create", "bk_batched_plan_destroy",
     "bk_batched_plan_info", "bk_batched_autotune", "bk_matern_batched",
     "bk_matern_batched_static", "bk_learned_create", "bk_learned_destroy", "bk_learned_train",
@@ -87,6 +87,7 @@ def lib() -> ctypes.CDLL:
             "bk_sync": (I, [P]),
             "bk_eval": (I, [P, P, P, I64, P]),
             "bk_eval_ex": (I, [P, P, P, P, I, I64, P, P]),
+            "bk_eval_grad": (I, [P, P, P, P, P, I64, P, P]),
             "bk_matern_tile": (I, [P, I64, D, D, D, P, I64, I, P]),
             "bk_matern_tile_ex": (I, [P, I64, D, D, D, P, I64, I, P, P]),
             "bk_matern_tile2": (I, [P, I64, P, I64, D, D, D, P, I64, I, P, P]),
@@ -258,6 +259,30 @@ def bk_eval_ex(x, nu, out=None, log_out=None, out_dtype=None, opts: Optional[bk_
     _check(lib().bk_eval_ex(_ptr(x), _ptr(nu), _ptr(out), _ptr(log_out), code, n, optp,
                             _stream_ptr(stream)))
     return out, log_out
+
+
+def bk_eval_grad(x, nu, k=None, dk_dx=None, dk_dnu=None, opts: Optional[bk_opts] = None,
+                 stream=None):
+    """(K_nu(x), dK/dx, dK/dnu) of the plain FP64 form from one quadrature;
+    x, nu: CUDA float64 tensors of equal size.  Returns the three tensors."""
+    torch = _torch()
+    _dev(x, "x", torch.float64)
+    _dev(nu, "nu", torch.float64)
+    n = x.numel()
+    if nu.numel() != n:
+        raise ValueError("x and nu must have the same number of elements")
+    outs = []
+    for t, name in ((k, "k"), (dk_dx, "dk_dx"), (dk_dnu, "dk_dnu")):
+        if t is None:
+            t = torch.empty(x.shape, dtype=torch.float64, device=x.device)
+        _dev(t, name, torch.float64)
+        if t.numel() != n:
+            raise ValueError(f"{name} has the wrong size")
+        outs.append(t)
+    optp = ctypes.byref(opts) if opts is not None else None
+    _check(lib().bk_eval_grad(_ptr(x), _ptr(nu), _ptr(outs[0]), _ptr(outs[1]), _ptr(outs[2]), n,
+                              optp, _stream_ptr(stream)))
+    return tuple(outs)
 
 
 def _locs(locs, name="locs"):

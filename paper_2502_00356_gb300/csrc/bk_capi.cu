@@ -172,6 +172,26 @@ bk_status bk_eval_ex(const double* x, const double* nu, void* out, void* log_out
   return check_cuda(e, "bk_eval launch");
 }
 
+bk_status bk_eval_grad(const double* x, const double* nu, double* k, double* dk_dx,
+                       double* dk_dnu, int64_t n, const bk_opts* opts, bk_stream_t stream) {
+  bk_opts o;
+  bk_opts_default(&o);
+  if (opts != nullptr) o = *opts;
+  if (n < 0) return set_error(BK_ERR_INVALID_ARG, "n must be >= 0 (got %lld)", (long long)n);
+  bk_status st = check_opts(&o);
+  if (st != BK_OK) return st;
+  if (o.compute != BK_F64 || o.window != BK_WIN_SEARCH || o.series_below != 0.0)
+    return set_error(BK_ERR_UNSUPPORTED, "bk_eval_grad: the plain form only (compute = BK_F64, "
+                                         "window = BK_WIN_SEARCH, series_below = 0)");
+  if (n == 0) return BK_OK;
+  if (x == nullptr || nu == nullptr)
+    return set_error(BK_ERR_INVALID_ARG, "x and nu must be non-NULL when n > 0");
+  if (k == nullptr && dk_dx == nullptr && dk_dnu == nullptr)
+    return set_error(BK_ERR_INVALID_ARG, "bk_eval_grad: all outputs are NULL");
+  return check_cuda(launch_eval_grad_f64(x, nu, k, dk_dx, dk_dnu, n, o, (cudaStream_t)stream),
+                    "bk_eval_grad launch");
+}
+
 bk_status bk_eval(const double* x, const double* nu, double* out, int64_t n, bk_stream_t stream) {
   return bk_eval_ex(x, nu, out, nullptr, BK_F64, n, nullptr, stream);
 }

@@ -69,6 +69,29 @@ struct FormF64T {
     return (sc > 700.0) ? exp_tab_full(sc + lh, tab) : exp_tab_full(sc, tab) * hS;
   }
 
+  // K, dK/dx and dK/dnu for finite x > 0, nu >= 0 on one set of nodes
+  // (scale3_f64): FP32 roots for the orders nu and nu + 1 as the window.
+  __device__ __forceinline__ void eval_grad(double x, double nu, Tally& tl, unsigned& evals,
+                                            double& k, double& dkdx, double& dkdnu) const {
+    ++evals;
+    Start32 st, st1;
+    const Start32* sp = search_f64 ? nullptr : plain_starts(x, nu, st);
+    const Start32* sp1 = (sp != nullptr) ? plain_starts(x, nu + 1.0, st1) : nullptr;
+    if (sp1 == nullptr) sp = nullptr;
+    double hS, hSx, hSn;
+    const double sc = scale3_f64(x, nu, tab, sp, sp1, hS, hSx, hSn, tl);
+    if (sc > 700.0) {  // e^sc alone would overflow where the products need not
+      k = exp_tab_full(sc + log_tab(hS, tab), tab);
+      dkdx = -exp_tab_full(sc + log_tab(hSx, tab), tab);
+      dkdnu = (hSn > 0.0) ? exp_tab_full(sc + log_tab(hSn, tab), tab) : 0.0;
+      return;
+    }
+    const double e = exp_tab_full(sc, tab);
+    k = e * hS;
+    dkdx = -e * hSx;
+    dkdnu = e * hSn;
+  }
+
   // a2 + a3..a7 for one entry: distance, x = r / beta, log K_nu(x),
   // M = exp(log prefactor + nu log x + log K).  sigma^2 where r == 0
   // (Algorithm 3 tests the computed distance for exact zero).

@@ -33,6 +33,10 @@ cudaError_t launch_matern_block_f64(const double* locs1, int64_t m, const double
                                     int64_t n, double sigma2, double beta, double nu, void* out,
                                     int64_t ld, bk_dtype out_t, const bk_opts& o, cudaStream_t s);
 
+// K, dK/dx, dK/dnu of the plain form (outputs may be null).
+cudaError_t launch_eval_grad_f64(const double* x, const double* nu, double* k, double* dkdx,
+                                 double* dkdnu, int64_t n, const bk_opts& o, cudaStream_t s);
+
 // Option checks shared by every entry point that takes bk_opts (sets the
 // error message and returns the status).
 bk_status check_opts(const bk_opts* o);

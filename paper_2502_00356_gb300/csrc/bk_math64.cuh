@@ -474,6 +474,11 @@ __device__ __forceinline__ NodeSum node_sum_f64(double t_start, double H, int co
 // exp2s, 1 fma + 1 add (f, s), 1 fma (recurrence), 1 add + 1 mul.
 constexpr int kNodeOps64 = 6 + kExp2sOps;
 
+// ln(2 / tol) for the plain form: tol = 1e-13 keeps the quadrature error
+// about three orders below the 1e-10 relative accuracy the form promises.
+constexpr float kPlainLog2OverTol = 30.6267f;
+constexpr int kPlainMaxNodes = 1024;
+
 // ---------------------------------------------------------------------------
 // a5: node count.  For f analytic in the strip |Im t| < a with
 // int |f(t + i s)| dt <= M(a) I for |s| < a, the trapezoid rule with step h
@@ -619,6 +624,129 @@ __device__ __forceinline__ double scale_f64(double x, double nu, float log2_over
   return fma(nu, w.ts, -x * w.cs) - kLn2;
 }
 
+// ---------------------------------------------------------------------------
+// Derivatives of K_nu(x) on the same nodes (not in the paper; for
+// gradient-based MLE).  Differentiating the integral under the sign,
+//   -dK/dx  = int cosh(t) f(t) dt,   dK/dnu = int t sinh(nu t) e^{-x cosh t} dt,
+// and with the scaled integrand of node_sum_f64,
+//   cosh(t) f/f_s = (D_j / (K x)) f_j / f_s,   t sinh(nu t) e^{-x cosh t} / f_s
+//   = t_j e^{a_j} (1 - e^{-2 nu t_j}),
+// so the node loop carries two more sums (4 more FP64 operations per node).
+// The window must hold the integrand of -dK/dx, which decays like that of
+// K_{nu+1}: it is the union of the windows of orders nu and nu + 1.
+struct NodeSum3 {
+  double S, Sx, Sn;                 // sums for K, -dK/dx (times K x), dK/dnu
+  double f0, fN, fx0, fxN, fn0, fnN;  // end terms of each sum
+  double e_first, e_last;
+};
+__device__ __forceinline__ NodeSum3 node_sum3_f64(double t_start, double H, int count, double x,
+                                                  double nu, double ts, double cs,
+                                                  const double* __restrict__ tab) {
+  const double xh = (0.5 * kExpScale) * x;
+  double W = 1.0, c, D0, D1;
+  if (t_start > 0.0) {
+    const double e0 = exp_tab(t_start, tab), r0 = rcp_nr2(e0);
+    W = exp_tab(fmax(-2.0 * nu * t_start, -708.0), tab);
+    const double eh = exp_tab(H, tab), rh = rcp_nr2(eh);
+    c = eh + rh;
+    D0 = xh * (e0 + r0);
+    D1 = xh * fma(e0, eh, r0 * rh);
+  } else {
+    c = (H <= 0.35) ? two_cosh_small(H) : exp_tab(H, tab) + rcp_nr2(exp_tab(H, tab));
+    D0 = 2.0 * xh;
+    D1 = xh * c;
+  }
+  const double rho = exp_tab(fmax(-2.0 * nu * H, -708.0), tab);
+  double A = kExpScale * fma(nu, t_start - ts, x * cs);
+  const double dA = kExpScale * (nu * H);
+  NodeSum3 r;
+  double s = 0.0, sx = 0.0, sn = 0.0, t = t_start, ev = 0.0, f = 0.0, fx = 0.0, fn = 0.0;
+  for (int j = 0; j < count; ++j) {
+    ev = exp2s(A - D0, tab);
+    f = fma(ev, W, ev);
+    fx = D0 * f;
+    fn = fma(-ev, W, ev) * t;
+    if (j == 0) {
+      r.f0 = f;
+      r.fx0 = fx;
+      r.fn0 = fn;
+      r.e_first = ev;
+    }
+    s += f;
+    sx += fx;
+    sn += fn;
+    const double D2 = fma(c, D1, -D0);
+    D0 = D1;
+    D1 = D2;
+    A += dA;
+    W *= rho;
+    t += H;
+  }
+  r.S = s;
+  r.Sx = sx;
+  r.Sn = sn;
+  r.fN = f;
+  r.fxN = fx;
+  r.fnN = fn;
+  r.e_last = ev;
+  return r;
+}
+
+// K, -dK/dx and dK/dnu in scaled form: returns the scale sc and sets
+// hS = h S, hSx = h Sx / (K x) and hSn = h Sn, so that K = e^sc hS,
+// dK/dx = -e^sc hSx, dK/dnu = e^sc hSn.  st / st1: FP32 roots for the orders
+// nu and nu + 1 (both or neither); the window is their union, checked in FP64
+// on K's end nodes as in scale_f64; without roots, or when the check fails,
+// the union of the FP64 search windows.
+__device__ __forceinline__ double scale3_f64(double x, double nu, const double* __restrict__ tab,
+                                             const Start32* st, const Start32* st1,
+                                             double& hS, double& hSx, double& hSn, Tally& tl) {
+  constexpr double kEps64 = 0x1p-52;
+  Window64 w;
+  bool check = (st != nullptr && st1 != nullptr);
+  if (check) {
+    w = window_from_start(x, nu, *st, tab);
+    const Window64 w1 = window_from_start(x, nu + 1.0, *st1, tab);
+    w.t0 = fmin(w.t0, w1.t0);
+    w.t1 = fmax(w.t1, w1.t1);
+  }
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    if (!check) {
+      w = window_f64(x, nu, kLogInvEps64, tab, tl);
+      const Window64 w1 = window_f64(x, nu + 1.0, kLogInvEps64, tab, tl);
+      w.t0 = fmin(w.t0, w1.t0);
+      w.t1 = fmax(w.t1, w1.t1);
+    }
+    const double width = w.t1 - w.t0;
+    const int N = strip_node_count((float)x, (float)(nu + 1.0), (float)width, kPlainLog2OverTol,
+                                   kPlainMaxNodes);
+    if (N > kPlainMaxNodes) {
+      if (check) {
+        ++tl.fallback;
+        check = false;
+        continue;
+      }
+      ++tl.fail;
+      hS = hSx = hSn = __longlong_as_double(0x7ff8000000000000LL);
+      return hS;
+    }
+    const double h = width * rcp_nr2((double)N);
+    const NodeSum3 ns = node_sum3_f64(w.t0, h, N + 1, x, nu, w.ts, w.cs, tab);
+    tl.nodes += N + 1;
+    if (check && !(ns.e_last <= kEps64 && (w.t0 == 0.0 || 2.0 * ns.e_first <= kEps64) &&
+                   ns.S > 0.0 && ns.S < 1e300)) {
+      ++tl.fallback;
+      check = false;
+      continue;
+    }
+    hS = h * (ns.S - 0.5 * (ns.f0 + ns.fN));
+    hSx = h * (ns.Sx - 0.5 * (ns.fx0 + ns.fxN)) * rcp_nr2(kExpScale * x);
+    hSn = h * (ns.Sn - 0.5 * (ns.fn0 + ns.fnN));
+    break;
+  }
+  return fma(nu, w.ts, -x * w.cs) - kLn2;
+}
+
 // The paper's fixed window (Algorithm 2, x >= 0.1 branch, Sec. IV-C): the
 // trapezoid on [0, t1] with b bins, h = t1/b, weights 1/2 at both ends,
 // shifted by the largest node value (t_lmax).  The shift is taken at the
@@ -669,9 +797,5 @@ __device__ __forceinline__ double fixed_scale_f64(double x, double nu, double t1
   return amax * kExpC1 - kLn2;
 }
 
-// ln(2 / tol) for the plain form: tol = 1e-13 keeps the quadrature error
-// about three orders below the 1e-10 relative accuracy the form promises.
-constexpr float kPlainLog2OverTol = 30.6267f;
-constexpr int kPlainMaxNodes = 1024;
 
 }  // namespace bk

@@ -119,6 +119,41 @@ __global__ void __launch_bounds__(128) eval_kernel(const Form form, const double
   flush_tally(ctr, tl, evals);
 }
 
+// K, dK/dx and dK/dnu of the plain form.  Domain: x = 0 gives (+inf, -inf,
+// NaN), x = +inf gives (0, 0, 0), x < 0 or NaN and non-finite nu give NaN;
+// dK/dnu is odd in nu (K_{-nu} = K_nu).  Null outputs are skipped.
+template <class Form>
+__global__ void __launch_bounds__(128) eval_grad_kernel(const Form form, const double* __restrict__ x,
+                                                        const double* __restrict__ nu,
+                                                        double* __restrict__ k,
+                                                        double* __restrict__ dkdx,
+                                                        double* __restrict__ dkdnu, int64_t n,
+                                                        unsigned long long* __restrict__ ctr) {
+  __shared__ double s_tab[Form::kStageTable ? kExpTabSize : 1];
+  const Form f = bind_table(form, s_tab);
+  Tally tl{0u, 0u, 0u, 0u, 0u, 0u, 0u};
+  unsigned evals = 0;
+  const double qnan = __longlong_as_double(0x7ff8000000000000LL);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const double xi = x[i], vi = nu[i], av = fabs(vi);
+    double kk = qnan, dx = qnan, dn = qnan;
+    if (xi > 0.0 && xi < kInf && av < kInf) {
+      f.eval_grad(xi, av, tl, evals, kk, dx, dn);
+      if (vi < 0.0) dn = -dn;
+    } else if (xi == 0.0 && av < kInf) {
+      kk = kInf;
+      dx = -kInf;
+    } else if (xi == kInf && av < kInf) {
+      kk = dx = dn = 0.0;
+    }
+    if (k != nullptr) k[i] = kk;
+    if (dkdx != nullptr) dkdx[i] = dx;
+    if (dkdnu != nullptr) dkdnu[i] = dn;
+  }
+  flush_tally(ctr, tl, evals);
+}
+
 constexpr int kTile = 32;     // tile edge (rows and columns)
 constexpr int kWarps = 8;     // 256 threads: warp w computes columns w, w+8, w+16, w+24
 constexpr int kThreads = kWarps * 32;
