@@ -553,14 +553,15 @@ def main():
     sink = torch.empty(152 * 8 * 256, dtype=torch.float64, device=dev)
     probe = {}
     for kind, name, it in ((0, "fp64_fma_tflops", 2000), (1, "fp32_fma_tflops", 20000),
-                           (2, "mufu_ex2_tops", 5000)):
+                           (2, "mufu_ex2_tops", 5000), (3, "cvt_f64_to_f32_tops", 2000),
+                           (4, "cvt_f32_to_f64_tops", 2000)):
         bk.bk_probe_pipe(kind, it // 10, 152 * 8, 256, sink)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         ops = bk.bk_probe_pipe(kind, it, 152 * 8, 256, sink)
         b.record(stream)
         torch.cuda.synchronize()
-        mult = 2 if kind in (0, 1) else 1
+        mult = 2 if kind in (0, 1) else 1  # an FMA counts 2 FLOPs
         probe[name] = ops * mult / (a.elapsed_time(b) / 1e3) / 1e12
 
     # -- secondary: bare K_nu evaluation, 100,000 pairs (x log-uniform in [1e-3,140], nu in [0.05,10])

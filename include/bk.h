@@ -313,8 +313,10 @@ bk_status bk_matern_batched_static(const bk_matern_desc* d_descs, int32_t count,
  * bk_probe_pipe: throughput probe for the roofline denominators (not part of
  * the paper's method).  Launches grid x block threads; each runs `iters`
  * trips of 8 independent operations on one pipe: kind 0 = FP64 FMA,
- * 1 = FP32 FMA, 2 = ex2.approx.f32 on the MUFU unit.  Operations per launch =
- * grid * block * iters * 8.  sink: device, grid * block doubles (written).
+ * 1 = FP32 FMA, 2 = ex2.approx.f32 on the MUFU unit, 3 = FP64 -> FP32
+ * conversion, 4 = FP32 -> FP64 conversion (each chained through integer
+ * operations).  Operations per launch = grid * block * iters * 8.  sink:
+ * device, grid * block doubles (written).
  */
 bk_status bk_probe_pipe(int kind, int64_t iters, int grid, int block, double* sink,
                         bk_stream_t stream);

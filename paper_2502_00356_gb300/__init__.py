@@ -350,8 +350,9 @@ def bk_sync(stream=None):
 
 
 def bk_probe_pipe(kind: int, iters: int, grid: int, block: int, sink, stream=None):
-    """Launch a pipe-rate probe (0 FP64 FMA, 1 FP32 FMA, 2 MUFU ex2); the caller
-    times it.  Returns the number of operations the launch performs."""
+    """Launch a pipe-rate probe (0 FP64 FMA, 1 FP32 FMA, 2 MUFU ex2, 3 FP64 -> FP32
+    conversion, 4 FP32 -> FP64 conversion); the caller times it.  Returns the
+    number of operations the launch performs."""
     torch = _torch()
     _dev(sink, "sink", torch.float64)
     if sink.numel() < grid * block:

@@ -13,6 +13,24 @@
 
 namespace bk {
 
+// The element-wise domain rules of the C-ABI around a form's evaluation.
+template <class Form>
+__device__ __forceinline__ double eval_domain(const Form& form, double x, double nu, Tally& tl,
+                                              unsigned& evals, double& log_k, bool want_log) {
+  nu = fabs(nu);
+  if (x > 0.0 && x < kInf && nu < kInf) return form.eval(x, nu, tl, evals, log_k, want_log);
+  if (x == 0.0 && nu == nu) {
+    log_k = kInf;
+    return kInf;
+  }
+  if (x == kInf && nu < kInf) {
+    log_k = -kInf;
+    return 0.0;
+  }
+  log_k = __longlong_as_double(0x7ff8000000000000LL);
+  return log_k;
+}
+
 // FP32 start values for the plain form's FP64 search: the FP32 search run
 // on the same eps (2^-52) inside x in [1e-4, 1e4], nu <= 40, where its sinh
 // and cosh stay accurate; none outside (the FP64 search then starts from
@@ -40,6 +58,7 @@ struct FormF64T {
   static constexpr bool kStageTable = true;
   static constexpr int kTilesPerBlock = 1;
   static constexpr int kMinBlocks = 3;
+  static constexpr bool kFloatEval = false;
   const double* tab;
   bool search_f64;      // FP64 Newton search for every point (no FP32 roots)
   double series_below;  // x below which Temme's series replaces the integral (0: never)
@@ -110,6 +129,20 @@ struct FormF64T {
     const double sc = scale_f64(z, mp.nu, kPlainLog2OverTol, kPlainMaxNodes, tab, hS, tl, sp);
     return exp_tab_full(fma(mp.nu, log_tab(z, tab), mp.log_pref) + sc, tab) * hS;
   }
+
+  template <typename OutT>
+  __device__ __forceinline__ OutT matern_out(const Loc& a, const Loc& b, const MaternParams& mp,
+                                             Tally& tl, unsigned& evals) const {
+    return to_out<OutT>(matern(a, b, mp, tl, evals));
+  }
+
+  template <typename OutT>
+  __device__ __forceinline__ void eval_out(double x, double nu, Tally& tl, unsigned& evals,
+                                           OutT& k, OutT& log_k, bool want_log) const {
+    double lk = 0.0;
+    k = to_out<OutT>(eval_domain(*this, x, nu, tl, evals, lk, want_log));
+    log_k = to_out<OutT>(lk);
+  }
 };
 
 using FormF64 = FormF64T<false>;        // the plain form
@@ -122,6 +155,7 @@ struct FormF64Fixed {
   static constexpr bool kStageTable = true;
   static constexpr int kTilesPerBlock = 1;
   static constexpr int kMinBlocks = 3;
+  static constexpr bool kFloatEval = false;
   const double* tab;
   double t1;
   int bins;
@@ -168,29 +202,45 @@ struct FormF64Fixed {
     const double sc = log_k_of(z, mp.nu, tl, hS, by_series);
     return exp_tab_full(fma(mp.nu, log_tab(z, tab), mp.log_pref) + sc, tab) * hS;
   }
+
+  template <typename OutT>
+  __device__ __forceinline__ OutT matern_out(const Loc& a, const Loc& b, const MaternParams& mp,
+                                             Tally& tl, unsigned& evals) const {
+    return to_out<OutT>(matern(a, b, mp, tl, evals));
+  }
+
+  template <typename OutT>
+  __device__ __forceinline__ void eval_out(double x, double nu, Tally& tl, unsigned& evals,
+                                           OutT& k, OutT& log_k, bool want_log) const {
+    double lk = 0.0;
+    k = to_out<OutT>(eval_domain(*this, x, nu, tl, evals, lk, want_log));
+    log_k = to_out<OutT>(lk);
+  }
 };
 
 // The end of one FP32-form Matern entry after the quadrature (a7): the log
-// of the entry, log prefactor + nu log x + nu ts - x - x (cosh ts - 1) - ln 2,
-// summed as a double-float and exponentiated in FP32 times h S.  FP64 is used
-// instead near r -> 0 (x < 1, where nu log x cancels against log K), when
-// x (cosh ts - 1) > 2 (its FP32 value would cost > 5e-7 absolute), and for
-// entries below ~e^-85 (beyond the float range of the FP32 path).
-__device__ __forceinline__ double matern_f32_finish(DF z, const Window32& w, const Quad32& q,
-                                                    const MaternParams& mp) {
-  if (z.hi >= 1.0f && q.xc1 <= 2.0f) {
+// of the entry, log prefactor + nu log x + nu ts - x cosh ts - ln 2, summed as
+// a double-float (df_log_scale) and exponentiated in FP32 times h S, written
+// as OutT without FP64 instructions.  FP64 is used instead near r -> 0
+// (x < 1, where nu log x cancels against log K) and, for FP64 output, for
+// entries beyond the float range.
+template <typename OutT>
+__device__ __forceinline__ OutT matern_f32_finish(DF z, const Window32& w, const Quad32& q,
+                                                  const MaternParams& mp) {
+  if (z.hi >= 1.0f) {
     const DF nu = DF{mp.nu_hi, mp.nu_lo};
     DF a = df_add(DF{mp.log_pref_hi, mp.log_pref_lo}, df_mul(nu, df_log(z)));
-    a = df_add(a, df_mul_f(nu, w.ts));
-    a = df_add(a, df_neg(z));
-    a = df_add_f(a, -q.xc1);
-    a = df_add(a, DF{-kLn2DfHi, -kLn2DfLo});
-    if (a.hi >= -85.0f) return (double)df_exp_times(a, q.hS);
+    a = df_add(a, df_log_scale(z, nu, w.ts, q));
+    if constexpr (sizeof(OutT) == sizeof(float)) {
+      return df_exp_times(a, q.hS);
+    } else {
+      if (a.hi >= -85.0f && a.hi <= 85.0f) return widen_f(df_exp_times(a, q.hS));
+    }
   }
   const double z64 = (double)z.hi + (double)z.lo;
   const double lz = log_pos(z64);
-  return exp_fast(fma(mp.nu, lz, mp.log_pref) + log_scale_from(z64, mp.nu, w.ts, q)) *
-         (double)q.hS;
+  return to_out<OutT>(exp_fast(fma(mp.nu, lz, mp.log_pref) + log_scale_from(z64, mp.nu, w.ts, q)) *
+                      (double)q.hS);
 }
 
 // a2 for the FP32 forms: x = r / beta as a double-float from the staged
@@ -201,33 +251,92 @@ __device__ __forceinline__ DF matern_x_df(const Loc& a, const Loc& b, const Mate
   return df_mul(r, DF{mp.inv_beta_f, mp.inv_beta_lo});
 }
 
+// The FP32 forms' bare evaluation (eval_out): inside x in [1e-4, 1e4],
+// nu in [2^-70, 40] the arguments are split into double-floats by integer
+// operations and the result is assembled as for the Matern entries, with no
+// FP64 instruction on the way (FP64 output widens the FP32 value exactly);
+// elsewhere, and for FP64 output beyond the float range, the form's FP64
+// normalisation (eval) and the domain rules of the C-ABI apply.
+template <class Form, typename OutT>
+__device__ __forceinline__ void eval_out_f32(const Form& f, double x, double nu, Tally& tl,
+                                             unsigned& evals, OutT& k, OutT& log_k,
+                                             bool want_log) {
+  const long long xb = __double_as_longlong(x);
+  const long long vb = __double_as_longlong(nu) & 0x7fffffffffffffffLL;
+  bool okx = false, okn = false;
+  DF xd{0.0f, 0.0f}, nd{0.0f, 0.0f};
+  if (xb > 0 && xb < 0x7ff0000000000000LL && vb < 0x7ff0000000000000LL) {
+    xd = df_from_bits(x, okx);
+    nd = df_from_bits(__longlong_as_double(vb), okn);
+  }
+  if (okx && okn && xd.hi >= 1e-4f && xd.hi <= 1e4f && nd.hi <= 40.0f) {
+    ++evals;
+    Window32 w;
+    const Quad32 q = f.quad(xd.hi, [&] { return x; }, nd.hi, nd.lo, w, tl);
+    const DF a = df_log_scale(xd, nd, w.ts, q);
+    if constexpr (sizeof(OutT) == sizeof(float)) {
+      k = df_exp_times(a, q.hS);
+      if (want_log) log_k = a.hi + (a.lo + kLn2f * mufu_lg2(q.hS));
+      return;
+    } else {
+      if (a.hi >= -85.0f && a.hi <= 85.0f) {
+        k = widen_f(df_exp_times(a, q.hS));
+        if (want_log) log_k = widen_f(a.hi) + widen_f(a.lo + kLn2f * mufu_lg2(q.hS));
+        return;
+      }
+      --evals;  // counted again by the FP64 path below
+    }
+  }
+  double lk = 0.0;
+  const double kd = eval_domain<Form>(f, x, nu, tl, evals, lk, want_log);
+  k = to_out<OutT>(kd);
+  log_k = to_out<OutT>(lk);
+}
+
 // The FP32 precision form (search window).
 struct FormF32 {
   static constexpr bool kStageTable = false;
   static constexpr int kTilesPerBlock = 4;
   static constexpr int kMinBlocks = 4;
+  static constexpr bool kFloatEval = true;
   const double* tab;
 
+  template <class X64>
+  __device__ __forceinline__ Quad32 quad(float x, X64 x64_of, float nu, float nu_lo, Window32& w,
+                                         Tally& tl) const {
+    w = search_window_f32(x, x64_of, nu, tab, tl);
+    return quad_f32(x, nu, nu_lo, w, tl);
+  }
+
+  // FP64 normalisation (outside the float path of eval_out_f32).
   __device__ __forceinline__ double eval(double x, double nu, Tally& tl, unsigned& evals,
                                          double& log_k, bool) const {
     ++evals;
     const float xf = (float)x, nf = (float)nu, nl = (float)(nu - (double)nf);
-    const Window32 w = search_window_f32(x, nf, tab, tl);
-    const Quad32 q = quad_f32(xf, nf, nl, w, tl);
+    Window32 w;
+    const Quad32 q = quad(xf, [&] { return x; }, nf, nl, w, tl);
     const double sc = log_scale_from(x, nu, w.ts, q);
     log_k = sc + (double)(kLn2f * mufu_lg2(q.hS));
     return exp_fast(sc) * (double)q.hS;
   }
 
+  template <typename OutT>
+  __device__ __forceinline__ void eval_out(double x, double nu, Tally& tl, unsigned& evals,
+                                           OutT& k, OutT& log_k, bool want_log) const {
+    eval_out_f32(*this, x, nu, tl, evals, k, log_k, want_log);
+  }
+
   // a2 as a double-float; a3..a6 in FP32 on x.hi; a7 by matern_f32_finish.
-  __device__ __forceinline__ double matern(const Loc& a, const Loc& b, const MaternParams& mp,
-                                           Tally& tl, unsigned& evals) const {
+  template <typename OutT>
+  __device__ __forceinline__ OutT matern_out(const Loc& a, const Loc& b, const MaternParams& mp,
+                                             Tally& tl, unsigned& evals) const {
     const DF z = matern_x_df(a, b, mp);
-    if (z.hi == 0.0f) return mp.sigma2;
+    if (z.hi == 0.0f) return sizeof(OutT) == sizeof(float) ? (OutT)mp.sigma2_f : (OutT)mp.sigma2;
     ++evals;
-    const Window32 w = search_window_f32((double)z.hi, mp.nu_hi, tab, tl);
-    const Quad32 q = quad_f32(z.hi, mp.nu_hi, mp.nu_lo, w, tl);
-    return matern_f32_finish(z, w, q, mp);
+    Window32 w;
+    const Quad32 q = quad(z.hi, [&] { return (double)z.hi + (double)z.lo; }, mp.nu_hi, mp.nu_lo,
+                          w, tl);
+    return matern_f32_finish<OutT>(z, w, q, mp);
   }
 };
 
@@ -243,10 +352,12 @@ struct FormF32Learned {
   static constexpr bool kStageTable = false;
   static constexpr int kTilesPerBlock = 4;
   static constexpr int kMinBlocks = 4;
+  static constexpr bool kFloatEval = true;
   LearnedView lv;
   const double* tab;
 
-  __device__ __forceinline__ Quad32 quad(float x, double x64, float nu, float nu_lo, Window32& w,
+  template <class X64>
+  __device__ __forceinline__ Quad32 quad(float x, X64 x64_of, float nu, float nu_lo, Window32& w,
                                          Tally& tl) const {
     if (learned_window_f32(lv, x, nu, w, tl.repairs)) {
       const Quad32 q = quad_f32(x, nu, nu_lo, w, tl);
@@ -255,7 +366,7 @@ struct FormF32Learned {
       if (isfinite(q.hS) && q.hS > 0.0f && q.amax <= 2.0f) return q;
     }
     ++tl.fallback;
-    w = search_window_f32(x64, nu, tab, tl);
+    w = search_window_f32(x, x64_of, nu, tab, tl);
     return quad_f32(x, nu, nu_lo, w, tl);
   }
 
@@ -264,20 +375,28 @@ struct FormF32Learned {
     ++evals;
     const float xf = (float)x, nf = (float)nu, nl = (float)(nu - (double)nf);
     Window32 w;
-    const Quad32 q = quad(xf, x, nf, nl, w, tl);
+    const Quad32 q = quad(xf, [&] { return x; }, nf, nl, w, tl);
     const double sc = log_scale_from(x, nu, w.ts, q);
     log_k = sc + (double)(kLn2f * mufu_lg2(q.hS));
     return exp_fast(sc) * (double)q.hS;
   }
 
-  __device__ __forceinline__ double matern(const Loc& a, const Loc& b, const MaternParams& mp,
-                                           Tally& tl, unsigned& evals) const {
+  template <typename OutT>
+  __device__ __forceinline__ void eval_out(double x, double nu, Tally& tl, unsigned& evals,
+                                           OutT& k, OutT& log_k, bool want_log) const {
+    eval_out_f32(*this, x, nu, tl, evals, k, log_k, want_log);
+  }
+
+  template <typename OutT>
+  __device__ __forceinline__ OutT matern_out(const Loc& a, const Loc& b, const MaternParams& mp,
+                                             Tally& tl, unsigned& evals) const {
     const DF z = matern_x_df(a, b, mp);
-    if (z.hi == 0.0f) return mp.sigma2;
+    if (z.hi == 0.0f) return sizeof(OutT) == sizeof(float) ? (OutT)mp.sigma2_f : (OutT)mp.sigma2;
     ++evals;
     Window32 w;
-    const Quad32 q = quad(z.hi, (double)z.hi, mp.nu_hi, mp.nu_lo, w, tl);
-    return matern_f32_finish(z, w, q, mp);
+    const Quad32 q = quad(z.hi, [&] { return (double)z.hi + (double)z.lo; }, mp.nu_hi, mp.nu_lo,
+                          w, tl);
+    return matern_f32_finish<OutT>(z, w, q, mp);
   }
 };
 

@@ -11,6 +11,15 @@ namespace bk {
 
 constexpr double kInf = __builtin_huge_val();
 
+// Output conversion of a double result (FP32 outputs round once).
+template <typename T>
+__device__ __forceinline__ T to_out(double v);
+template <>
+__device__ __forceinline__ double to_out<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ float to_out<float>(double v) { return (float)v; }
+
+
 // a1: log of the Matern prefactor sigma^2 / (2^{nu-1} Gamma(nu)) (Sec. III-A).
 __device__ __forceinline__ double matern_log_prefactor(double sigma2, double nu) {
   const double ls = (sigma2 > 0.0) ? log_pos(sigma2) : -kInf;
@@ -23,6 +32,7 @@ struct MaternParams {
   float inv_beta_f, nu_hi, nu_lo;  // nu = nu_hi + nu_lo (two floats)
   float inv_beta_lo;               // 1/beta = inv_beta_f + inv_beta_lo
   float log_pref_hi, log_pref_lo;  // a1 as two floats
+  float sigma2_f;                  // sigma^2 as a float (the FP32 diagonal)
 };
 
 __device__ __forceinline__ MaternParams matern_params(double sigma2, double beta, double nu) {
@@ -38,6 +48,7 @@ __device__ __forceinline__ MaternParams matern_params(double sigma2, double beta
   p.inv_beta_lo = (float)(p.inv_beta - (double)p.inv_beta_f);
   p.log_pref_hi = (float)p.log_pref;
   p.log_pref_lo = (float)(p.log_pref - (double)p.log_pref_hi);
+  p.sigma2_f = (float)sigma2;
   return p;
 }
 
@@ -57,6 +68,7 @@ inline MaternParams matern_params_host(double sigma2, double beta, double nu) {
   p.inv_beta_lo = (float)(p.inv_beta - (double)p.inv_beta_f);
   p.log_pref_hi = (float)p.log_pref;
   p.log_pref_lo = (float)(p.log_pref - (double)p.log_pref_hi);
+  p.sigma2_f = (float)sigma2;
   return p;
 }
 

@@ -214,15 +214,17 @@ __device__ __forceinline__ float trapezoid_f32(float x, float nu, float nu_lo, c
 
 // The searched window of the FP32 form: FP32 search inside x in [1e-4, 1e4],
 // nu <= 40, the FP64 search (with the FP32 eps) outside, where FP32 sinh /
-// cosh of the window ends lose too much.
-__device__ __forceinline__ Window32 search_window_f32(double x64, float nu,
+// cosh of the window ends lose too much.  x is the FP32 argument, x64 the
+// full one, produced by x64_of() only on the FP64 path (a conversion between
+// FP64 and FP32 costs an FP64-pipe slot on this GPU, like an FMA).
+template <class X64>
+__device__ __forceinline__ Window32 search_window_f32(float x, X64 x64_of, float nu,
                                                      const double* __restrict__ tab, Tally& tl) {
-  const float x = (float)x64;
   Window32 w;
   if (x >= 1e-4f && x <= 1e4f && nu <= 40.0f) {
     w = window_f32(x, nu, kLogInvEps32, tl);
   } else {
-    const Window64 w64 = window_f64(x64, (double)nu, (double)kLogInvEps32, tab, tl);
+    const Window64 w64 = window_f64(x64_of(), (double)nu, (double)kLogInvEps32, tab, tl);
     w.ts = (float)w64.ts;
     w.t0 = (float)w64.t0;
     w.t1 = (float)w64.t1;
@@ -352,6 +354,102 @@ __device__ __forceinline__ float df_exp_times(DF a, float s) {
          __int_as_float((127 + k - k1) << 23);
 }
 
+// ---------------------------------------------------------------------------
+// Conversions and functions for the FP32 forms without FP64 instructions.
+// (On this GPU FP64 <-> FP32 conversions run at the FP64 rate, 2 per clock
+// and SM, like an FMA; integer <-> FP32 conversions run on the MUFU pipe.)
+
+// A double as a double-float by integer operations: hi = v rounded to 24
+// significant bits, lo = the rest rounded to float (|v - hi - lo| <= 2^-48
+// |v|).  ok = false (and the caller takes an FP64 path) outside
+// |v| in [2^-70, 2^100] or for zero, denormal, infinite and NaN v.
+__device__ __forceinline__ DF df_from_bits(double v, bool& ok) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int e = (int)((b >> 52) & 0x7ff) - 1023;
+  ok = (e >= -70 && e <= 100);
+  const unsigned long long m = (b & 0xfffffffffffffull) | (1ull << 52);
+  unsigned long long q = (m + (1ull << 28)) >> 29;  // 24 significant bits (25 on carry)
+  const long long r = (long long)m - (long long)(q << 29);  // |r| <= 2^28
+  int eh = e;
+  if (q >> 24) {
+    q >>= 1;
+    ++eh;
+  }
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const float hi = __int_as_float((int)(sign | ((unsigned)(eh + 127) << 23) | ((unsigned)q & 0x7fffffu)));
+  // r 2^(e-52): the exponent can fall below the float range; split the scale
+  const int s1 = (e - 52) / 2, s2 = (e - 52) - s1;
+  const float lo = (float)r * __int_as_float((s1 + 127) << 23) * __int_as_float((s2 + 127) << 23);
+  return DF{hi, __int_as_float(__float_as_int(lo) ^ (int)sign)};
+}
+
+// A float as a double by integer operations (exact; denormals, infinities
+// and NaN through the conversion).
+__device__ __forceinline__ double widen_f(float f) {
+  const unsigned u = (unsigned)__float_as_int(f);
+  const unsigned ex = (u >> 23) & 0xffu;
+  if (ex == 0u && (u & 0x7fffffu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+  if (ex == 0u || ex == 0xffu) return (double)f;
+  return __hiloint2double(
+      (int)((u & 0x80000000u) | ((ex - 127u + 1023u) << 20) | ((u & 0x7fffffu) >> 3)),
+      (int)(u << 29));
+}
+
+// e^t as a double-float, ~2e-14 relative for t in [-70, 88] (below -70 the
+// low part leaves the float range and the result has FP32 accuracy): t = k ln 2 + r
+// with ln 2 split into 16 + 24 + 24 bits (k ln2_hi exact for |k| < 128, the
+// second product kept exact by the FMA), |r| <= ln2/2, e^r by its Taylor
+// series to r^11 (truncation < 7e-15) in double-float with double-float
+// coefficients up to 1/720.
+constexpr float kLn2Lo2F = 5.4979231e-14f;  // ln 2 - kLn2HiF - kLn2LoF (to float)
+__device__ __forceinline__ DF df_exp(float t) {
+  const float kf = rintf(t * kLog2ef);
+  const float r0 = fmaf(-kf, kLn2HiF, t);            // exact
+  const float p1 = kf * kLn2LoF;
+  const float p1e = fmaf(kf, kLn2LoF, -p1);
+  DF r = two_sum(r0, -p1);
+  r = df_add_f(r, -fmaf(kf, kLn2Lo2F, p1e));
+  float c = 1.0f / 39916800.0f;                        // 1/11!
+  c = fmaf(c, r.hi, 1.0f / 3628800.0f);
+  c = fmaf(c, r.hi, 1.0f / 362880.0f);
+  c = fmaf(c, r.hi, 1.0f / 40320.0f);
+  c = fmaf(c, r.hi, 1.0f / 5040.0f);                   // tail to r^7 in FP32 (its error < 1e-14)
+  DF p = df_add(df_mul_f(r, c), DF{0x1.6c16c2p-10f, -0x1.27d27ep-35f});  // + 1/720
+  p = df_add(df_mul(p, r), DF{0x1.111112p-7f, -0x1.dddddep-32f});          // + 1/120
+  p = df_add(df_mul(p, r), DF{0x1.555556p-5f, -0x1.555556p-30f});         // + 1/24
+  p = df_add(df_mul(p, r), DF{0x1.555556p-3f, -0x1.555556p-28f});         // + 1/6
+  p = df_add_f(df_mul(p, r), 0.5f);
+  p = df_add_f(df_mul(p, r), 1.0f);
+  p = df_add_f(df_mul(p, r), 1.0f);
+  const int k = (int)kf;
+  const float sc = __int_as_float((127 + k) << 23);
+  return DF{p.hi * sc, p.lo * sc};
+}
+
+// 1 / a for a double-float a > 0 (one Newton step on the FP32 reciprocal).
+__device__ __forceinline__ DF df_rcp(DF a) {
+  const float y = 1.0f / a.hi;
+  const DF e = df_add_f(df_neg(df_mul_f(a, y)), 1.0f);  // 1 - a y
+  return df_add_f(df_mul_f(e, y), y);
+}
+
+// cosh t - 1 for t >= 0 as a double-float (~1e-13 relative): for t < 1/2
+// (t^2/2)(1 + (t^2/12) q(t^2)) with q's tail in FP32, else (e^t + e^-t)/2 - 1.
+__device__ __forceinline__ DF df_cosh_m1(float t) {
+  if (t < 0.5f) {
+    // cosh t - 1 = (y/2)(1 + (y/12)(1 + y q(y))), y = t^2,
+    // q = 1/30 + y/1680 + y^2/151200 (next term below 1e-9 of q)
+    const DF y = DF{t * t, fmaf(t, t, -(t * t))};  // t^2 exactly
+    const float q = fmaf(y.hi, fmaf(y.hi, 1.0f / 151200.0f, 1.0f / 1680.0f), 1.0f / 30.0f);
+    const DF inner = df_add_f(df_mul_f(y, q), 1.0f);
+    const DF corr = df_mul(df_mul(inner, y), DF{0x1.555556p-4f, -0x1.555556p-29f});  // / 12
+    return df_mul(DF{0.5f * y.hi, 0.5f * y.lo}, df_add_f(corr, 1.0f));
+  }
+  const DF e = df_exp(t);
+  const DF c = df_add(e, df_rcp(e));  // 2 cosh t
+  return df_add_f(DF{0.5f * c.hi, 0.5f * c.lo}, -1.0f);
+}
+
 // The FP32 quadrature of one evaluation on a given window: h S and
 // x (cosh ts - 1) (FP32; NaN h S when the node bound is exceeded).
 struct Quad32 {
@@ -397,6 +495,16 @@ __device__ __forceinline__ double log_scale_from(double x64, double nu64, float 
     xc1 = x64 * (sh * sh) / (0.5 * (e + 1.0 / e) + 1.0);  // x (cosh - 1) = x sinh^2/(cosh + 1)
   }
   return fma(nu64, (double)ts, -x64) - xc1 - kLn2;
+}
+
+// The same log f_s = nu ts - x cosh(ts) - ln 2 as a double-float from the
+// double-float x and nu, without FP64 instructions: x (cosh ts - 1) from the
+// quadrature's FP32 value when it is at most 2 (absolute error < 5e-7),
+// else x times cosh ts - 1 in double-float (df_cosh_m1).
+__device__ __forceinline__ DF df_log_scale(DF x, DF nu, float ts, const Quad32& q) {
+  DF a = df_add(df_mul_f(nu, ts), df_neg(x));
+  a = (q.xc1 <= 2.0f) ? df_add_f(a, -q.xc1) : df_add(a, df_neg(df_mul(x, df_cosh_m1(ts))));
+  return df_add(a, DF{-kLn2DfHi, -kLn2DfLo});
 }
 
 // e^a for a FP64 argument with FP32 accuracy (MUFU ex2 on the reduced

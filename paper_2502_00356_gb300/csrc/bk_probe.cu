@@ -61,6 +61,46 @@ __global__ void probe_ex2(int64_t iters, double* sink) {
   sink[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// FP64 -> FP32 conversions: per trip one conversion of a double in [1, 2),
+// whose float result is turned back into a double in [1, 2) by integer
+// operations only (so the compiler cannot fold a round trip).
+__global__ void probe_cvt64(int64_t iters, double* sink) {
+  double a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = 1.0 + 1e-3 * (threadIdx.x + k);
+  for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int b = __float_as_int((float)a[k]);
+      a[k] = __hiloint2double(0x3ff00000 | ((b + 1) & 0x000fffff), b);
+    }
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += a[k];
+  sink[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+// FP32 -> FP64 conversions: per trip one conversion of a float in [1, 2),
+// whose double result is turned back into a float in [1, 2) by integer
+// operations only.
+__global__ void probe_cvt32(int64_t iters, double* sink) {
+  float a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = 1.0f + 1e-3f * (threadIdx.x + k);
+  for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int h = __double2hiint((double)a[k]);
+      a[k] = __int_as_float(0x3f800000 | ((h + 1) & 0x007fffff));
+    }
+  }
+  float s = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += a[k];
+  sink[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 }  // namespace
 }  // namespace bk
 
@@ -74,6 +114,8 @@ extern "C" bk_status bk_probe_pipe(int kind, int64_t iters, int grid, int block,
     case 0: probe_dfma<<<grid, block, 0, s>>>(iters, sink); break;
     case 1: probe_ffma<<<grid, block, 0, s>>>(iters, sink); break;
     case 2: probe_ex2<<<grid, block, 0, s>>>(iters, sink); break;
+    case 3: probe_cvt64<<<grid, block, 0, s>>>(iters, sink); break;
+    case 4: probe_cvt32<<<grid, block, 0, s>>>(iters, sink); break;
     default: return set_error(BK_ERR_INVALID_ARG, "bk_probe_pipe: unknown kind %d", kind);
   }
   return check_cuda(cudaGetLastError(), "bk_probe_pipe launch");

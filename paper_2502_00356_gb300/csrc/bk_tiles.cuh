@@ -11,17 +11,11 @@
 
 #include "bk.h"
 #include "bk_math64.cuh"
+#include "bk_forms.cuh"
 #include "bk_matern_common.cuh"
 
 namespace bk {
 
-
-template <typename T>
-__device__ __forceinline__ T to_out(double v);
-template <>
-__device__ __forceinline__ double to_out<double>(double v) { return v; }
-template <>
-__device__ __forceinline__ float to_out<float>(double v) { return (float)v; }
 
 // Adds this warp's tallies to the caller's counters (one atomic per warp and
 // counter).  Every lane of the warp must call it.
@@ -80,24 +74,6 @@ __device__ __forceinline__ Form bind_table(const Form& form, double* s_tab) {
   return f;
 }
 
-// The element-wise domain rules of the C-ABI around a form's evaluation.
-template <class Form>
-__device__ __forceinline__ double eval_domain(const Form& form, double x, double nu, Tally& tl,
-                                              unsigned& evals, double& log_k, bool want_log) {
-  nu = fabs(nu);
-  if (x > 0.0 && x < kInf && nu < kInf) return form.eval(x, nu, tl, evals, log_k, want_log);
-  if (x == 0.0 && nu == nu) {
-    log_k = kInf;
-    return kInf;
-  }
-  if (x == kInf && nu < kInf) {
-    log_k = -kInf;
-    return 0.0;
-  }
-  log_k = __longlong_as_double(0x7ff8000000000000LL);
-  return log_k;
-}
-
 template <class Form, typename OutT>
 __global__ void __launch_bounds__(128) eval_kernel(const Form form, const double* __restrict__ x,
                                                    const double* __restrict__ nu,
@@ -111,10 +87,10 @@ __global__ void __launch_bounds__(128) eval_kernel(const Form form, const double
   const bool want_log = (log_out != nullptr);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    double lk = 0.0;
-    const double k = eval_domain<Form>(f, x[i], nu[i], tl, evals, lk, want_log);
-    out[i] = to_out<OutT>(k);
-    if (log_out != nullptr) log_out[i] = to_out<OutT>(lk);
+    OutT k, lk;
+    f.template eval_out<OutT>(x[i], nu[i], tl, evals, k, lk, want_log);
+    out[i] = k;
+    if (log_out != nullptr) log_out[i] = lk;
   }
   flush_tally(ctr, tl, evals);
 }
@@ -192,9 +168,10 @@ __device__ __forceinline__ void sym_tile(const Form& form, SymTileSmem<OutT>& sm
   __syncthreads();
 #pragma unroll 1
   for (int c = warp; c < kTile; c += WARPS) {
-    double v = 0.0;
-    if (r0 + lane < n && c0 + c < n) v = form.matern(sm.r[lane], sm.c[c], mp, tl, evals);
-    sm.tile[lane][c] = to_out<OutT>(v);
+    OutT v = (OutT)0;
+    if (r0 + lane < n && c0 + c < n)
+      v = form.template matern_out<OutT>(sm.r[lane], sm.c[c], mp, tl, evals);
+    sm.tile[lane][c] = v;
   }
   __syncthreads();
 #pragma unroll
@@ -271,7 +248,7 @@ __global__ void __launch_bounds__(kThreads, Form::kMinBlocks) matern_block_kerne
       for (int k = 0; k < kTile / kWarps; ++k) {
         const int c = warp + kWarps * k;
         const int64_t i = r0 + lane, j = c0 + c;
-        if (i < m && j < n) out[i + j * ld] = to_out<OutT>(f.matern(s_r[lane], s_c[c], mp, tl, evals));
+        if (i < m && j < n) out[i + j * ld] = f.template matern_out<OutT>(s_r[lane], s_c[c], mp, tl, evals);
       }
     }
   }
