@@ -36,11 +36,11 @@ __device__ __forceinline__ double eval_domain(const Form& form, double x, double
 // and cosh stay accurate; none outside (the FP64 search then starts from
 // its own bounds).  Its iterations are FP32 work and are not tallied: the
 // plain form's counters count FP64 Newton iterations.
-__device__ __forceinline__ const Start32* plain_starts(double x, double nu, Start32& st) {
-  const float xf = (float)x;
-  if (!(xf >= 1e-4f && xf <= 1e4f && nu <= 40.0)) return nullptr;
+__device__ __forceinline__ const Start32* plain_starts(double x, float nu, Start32& st) {
+  const float xf = f32_trunc(x);
+  if (!(xf >= 1e-4f && xf <= 1e4f && nu <= 40.0f)) return nullptr;
   Tally fp32_work{0u, 0u, 0u, 0u, 0u, 0u, 0u};
-  const Window32 w = window_f32(xf, (float)nu, (float)kLogInvEps64, fp32_work);
+  const Window32 w = window_f32(xf, nu, (float)kLogInvEps64, fp32_work);
   st = Start32{w.ts, w.t0, w.t1};
   return &st;
 }
@@ -80,7 +80,7 @@ struct FormF64T {
       return exp_tab_full(log_k, tab);
     }
     Start32 st;
-    const Start32* sp = search_f64 ? nullptr : plain_starts(x, nu, st);
+    const Start32* sp = search_f64 ? nullptr : plain_starts(x, f32_trunc(nu), st);
     double hS;
     const double sc = scale_f64(x, nu, kPlainLog2OverTol, kPlainMaxNodes, tab, hS, tl, sp);
     const double lh = (want_log || sc > 700.0) ? log_tab(hS, tab) : 0.0;
@@ -94,8 +94,8 @@ struct FormF64T {
                                             double& k, double& dkdx, double& dkdnu) const {
     ++evals;
     Start32 st, st1;
-    const Start32* sp = search_f64 ? nullptr : plain_starts(x, nu, st);
-    const Start32* sp1 = (sp != nullptr) ? plain_starts(x, nu + 1.0, st1) : nullptr;
+    const Start32* sp = search_f64 ? nullptr : plain_starts(x, f32_trunc(nu), st);
+    const Start32* sp1 = (sp != nullptr) ? plain_starts(x, f32_trunc(nu + 1.0), st1) : nullptr;
     if (sp1 == nullptr) sp = nullptr;
     double hS, hSx, hSn;
     const double sc = scale3_f64(x, nu, tab, sp, sp1, hS, hSx, hSn, tl);
@@ -117,14 +117,14 @@ struct FormF64T {
   __device__ __forceinline__ double matern(const Loc& a, const Loc& b, const MaternParams& mp,
                                            Tally& tl, unsigned& evals) const {
     const double dx = b.x - a.x, dy = b.y - a.y;
-    const double r = sqrt(fma(dx, dx, dy * dy));
-    if (r == 0.0) return mp.sigma2;
-    const double z = r * mp.inv_beta;
+    const double r2 = fma(dx, dx, dy * dy);
+    if (!bits_pos(r2)) return mp.sigma2;  // r == 0 (r2 >= 0)
+    const double z = sqrt(r2) * mp.inv_beta;
     ++evals;
     if (kSeries && z < series_below)
       return exp_tab_full(fma(mp.nu, log_tab(z, tab), mp.log_pref) + series(z, mp.nu, tl), tab);
     Start32 st;
-    const Start32* sp = search_f64 ? nullptr : plain_starts(z, mp.nu, st);
+    const Start32* sp = search_f64 ? nullptr : plain_starts(z, mp.nu_hi, st);
     double hS;
     const double sc = scale_f64(z, mp.nu, kPlainLog2OverTol, kPlainMaxNodes, tab, hS, tl, sp);
     return exp_tab_full(fma(mp.nu, log_tab(z, tab), mp.log_pref) + sc, tab) * hS;

@@ -383,18 +383,6 @@ __device__ __forceinline__ DF df_from_bits(double v, bool& ok) {
   return DF{hi, __int_as_float(__float_as_int(lo) ^ (int)sign)};
 }
 
-// A float as a double by integer operations (exact; denormals, infinities
-// and NaN through the conversion).
-__device__ __forceinline__ double widen_f(float f) {
-  const unsigned u = (unsigned)__float_as_int(f);
-  const unsigned ex = (u >> 23) & 0xffu;
-  if (ex == 0u && (u & 0x7fffffu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
-  if (ex == 0u || ex == 0xffu) return (double)f;
-  return __hiloint2double(
-      (int)((u & 0x80000000u) | ((ex - 127u + 1023u) << 20) | ((u & 0x7fffffu) >> 3)),
-      (int)(u << 29));
-}
-
 // e^t as a double-float, ~2e-14 relative for t in [-70, 88] (below -70 the
 // low part leaves the float range and the result has FP32 accuracy): t = k ln 2 + r
 // with ln 2 split into 16 + 24 + 24 bits (k ln2_hi exact for |k| < 128, the

@@ -20,6 +20,39 @@ constexpr double kSqrt2 = 1.4142135623730951;
 // -log(2^-52): the paper's machine epsilon (Sec. IV-C) in the window rule.
 constexpr double kLogInvEps64 = 36.04365338911715;
 
+// ---------------------------------------------------------------------------
+// Bit-level helpers that keep work off the FP64 pipe: on this GPU FP64
+// compares and FP64 <-> FP32 conversions issue to the FP64 unit at its
+// 2-per-clock rate, like FMAs, while integer operations do not.
+
+// v > 0 for v not NaN (NaN with a clear sign bit counts as positive).
+__device__ __forceinline__ bool bits_pos(double v) { return __double_as_longlong(v) > 0; }
+// a <= b for a, b >= 0 (false when a is NaN).
+__device__ __forceinline__ bool bits_le(double a, double b) {
+  return __double_as_longlong(a) <= __double_as_longlong(b);
+}
+// v truncated to a float (23 stored significand bits); a conversion outside
+// the float normal range.
+__device__ __forceinline__ float f32_trunc(double v) {
+  const long long b = __double_as_longlong(v);
+  const int e = (int)((b >> 52) & 0x7ff) - 1023;
+  if (e < -126 || e > 127) return (float)v;
+  const unsigned hi = (unsigned)((unsigned long long)b >> 32);
+  return __int_as_float((int)((hi & 0x80000000u) | ((unsigned)(e + 127) << 23) |
+                              (unsigned)((b >> 29) & 0x7fffff)));
+}
+// A float as a double by integer operations (exact; denormals, infinities
+// and NaN through the conversion).
+__device__ __forceinline__ double widen_f(float f) {
+  const unsigned u = (unsigned)__float_as_int(f);
+  const unsigned ex = (u >> 23) & 0xffu;
+  if (ex == 0u && (u & 0x7fffffu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+  if (ex == 0u || ex == 0xffu) return (double)f;
+  return __hiloint2double(
+      (int)((u & 0x80000000u) | ((ex - 127u + 1023u) << 20) | ((u & 0x7fffffu) >> 3)),
+      (int)(u << 29));
+}
+
 __device__ __forceinline__ double pow2i(int k) {  // 2^k for k in [-1022, 1023]
   return __hiloint2double((k + 1023) << 20, 0);
 }
@@ -166,7 +199,8 @@ __device__ __forceinline__ double exp_tab(double a, const double* __restrict__ t
 // 3 fma (polynomial), 1 mul.
 __device__ __forceinline__ double exp_tab_full(double a, const double* __restrict__ tab) {
   const double v = fma(a, kExpScale, kRoundMagic);
-  if (!(fabs(a) < 708.0)) return exp_full(a);
+  if (!((__double_as_longlong(a) & 0x7fffffffffffffffLL) < 0x4086200000000000LL))  // |a| < 708
+    return exp_full(a);
   const int n = __double2loint(v);
   const double kd = v - kRoundMagic;
   double r = fma(-kd, kExpC1Hi, a);
@@ -434,7 +468,7 @@ __device__ __forceinline__ NodeSum node_sum_f64(double t_start, double H, int co
                                                 const double* __restrict__ tab) {
   const double xh = (0.5 * kExpScale) * x;
   double W = 1.0, c, D0, D1;
-  if (t_start > 0.0) {
+  if (bits_pos(t_start)) {
     const double e0 = exp_tab(t_start, tab), r0 = rcp_nr2(e0);
     W = exp_tab(fmax(-2.0 * nu * t_start, -708.0), tab);
     const double eh = exp_tab(H, tab), rh = rcp_nr2(eh);
@@ -442,7 +476,7 @@ __device__ __forceinline__ NodeSum node_sum_f64(double t_start, double H, int co
     D0 = xh * (e0 + r0);
     D1 = xh * fma(e0, eh, r0 * rh);
   } else {
-    c = (H <= 0.35) ? two_cosh_small(H) : exp_tab(H, tab) + rcp_nr2(exp_tab(H, tab));
+    c = bits_le(H, 0.35) ? two_cosh_small(H) : exp_tab(H, tab) + rcp_nr2(exp_tab(H, tab));
     D0 = 2.0 * xh;
     D1 = xh * c;
   }
@@ -524,25 +558,26 @@ __device__ __forceinline__ int strip_node_count(float x, float nu, float width, 
   return nf < 2.0f ? 2 : (int)nf;
 }
 
-// The plain form's window from FP32 roots of the same F (st): t* as found
-// (any point is a valid shift: g(t) - g(t*) is what the nodes evaluate, in
-// FP64), the ends widened by 2e-5 relative and 1e-5 absolute towards their
-// side, far beyond the FP32 error of the roots; cosh t* and e^{t*} in FP64.
+// The plain form's window from FP32 roots of the same F (st): t* as found,
+// 0 where the FP32 test found nu^2 <= x (any point is a valid shift: g(t) -
+// g(t*) is what the nodes evaluate, in FP64), the ends widened by 2e-5
+// relative and 1e-5 absolute towards their side, far beyond the FP32 error
+// of the roots; cosh t* and e^{t*} in FP64.
 // The ends are then checked in FP64 by the quadrature itself (scale_f64).
 __device__ __forceinline__ Window64 window_from_start(double x, double nu, const Start32& st,
                                                       const double* __restrict__ tab) {
   Window64 w;
-  w.ts = (nu * nu > x) ? (double)st.ts : 0.0;
-  if (w.ts > 0.0) {
+  w.ts = widen_f(st.ts);  // 0 when the FP32 search found nu^2 <= x
+  if (st.ts > 0.0f) {
     w.es = exp_tab(w.ts, tab);
     w.cs = 0.5 * (w.es + rcp_nr2(w.es));
   } else {
     w.es = 1.0;
     w.cs = 1.0;
   }
-  w.t1 = fma((double)st.t1, 2e-5, (double)st.t1) + 1e-5;
-  w.t0 = (st.t0 > 0.0f && w.ts > 0.0) ? fmax(0.0, fma((double)st.t0, -2e-5, (double)st.t0) - 1e-5)
-                                       : 0.0;
+  const double t1 = widen_f(st.t1), t0 = widen_f(st.t0);
+  w.t1 = fma(t1, 2e-5, t1) + 1e-5;
+  w.t0 = (st.t0 > 0.0f && st.ts > 0.0f) ? fmax(0.0, fma(t0, -2e-5, t0) - 1e-5) : 0.0;
   return w;
 }
 
@@ -605,7 +640,8 @@ __device__ __forceinline__ double scale_f64(double x, double nu, float log2_over
   if (st == nullptr) return take_search(scaled_search_f64(x, nu, log2_over_tol, n_max, tab), hS, tl);
   const Window64 w = window_from_start(x, nu, *st, tab);
   const double width = w.t1 - w.t0;
-  const int N = strip_node_count((float)x, (float)nu, (float)width, log2_over_tol, n_max);
+  const int N = strip_node_count(f32_trunc(x), f32_trunc(nu), f32_trunc(width), log2_over_tol,
+                                 n_max);
   bool ok = N <= n_max;
   NodeSum ns;
   double h = 0.0;
@@ -613,8 +649,9 @@ __device__ __forceinline__ double scale_f64(double x, double nu, float log2_over
     h = width * rcp_nr2((double)N);
     ns = node_sum_f64(w.t0, h, N + 1, x, nu, w.ts, w.cs, tab);
     tl.nodes += N + 1;
-    ok = ns.e_last <= kEps64 && (w.t0 == 0.0 || 2.0 * ns.e_first <= kEps64) && ns.S > 0.0 &&
-         ns.S < 1e300;
+    // e_last <= eps, (t0 == 0 or 2 e_first <= eps), 0 < S < 1e300, as integer tests
+    ok = bits_le(ns.e_last, kEps64) && (!bits_pos(w.t0) || bits_le(ns.e_first, 0.5 * kEps64)) &&
+         bits_pos(ns.S) && bits_le(ns.S, 1e300);
   }
   if (!ok) {
     ++tl.fallback;
@@ -644,7 +681,7 @@ __device__ __forceinline__ NodeSum3 node_sum3_f64(double t_start, double H, int 
                                                   const double* __restrict__ tab) {
   const double xh = (0.5 * kExpScale) * x;
   double W = 1.0, c, D0, D1;
-  if (t_start > 0.0) {
+  if (bits_pos(t_start)) {
     const double e0 = exp_tab(t_start, tab), r0 = rcp_nr2(e0);
     W = exp_tab(fmax(-2.0 * nu * t_start, -708.0), tab);
     const double eh = exp_tab(H, tab), rh = rcp_nr2(eh);
@@ -652,7 +689,7 @@ __device__ __forceinline__ NodeSum3 node_sum3_f64(double t_start, double H, int 
     D0 = xh * (e0 + r0);
     D1 = xh * fma(e0, eh, r0 * rh);
   } else {
-    c = (H <= 0.35) ? two_cosh_small(H) : exp_tab(H, tab) + rcp_nr2(exp_tab(H, tab));
+    c = bits_le(H, 0.35) ? two_cosh_small(H) : exp_tab(H, tab) + rcp_nr2(exp_tab(H, tab));
     D0 = 2.0 * xh;
     D1 = xh * c;
   }
