@@ -45,7 +45,7 @@ __device__ __forceinline__ const Start32* plain_starts(double x, float nu, Start
   return &st;
 }
 
-// Every form carries `tab`, the 2^{j/1024} table of exp2s: the block's
+// Every form carries `tab`, the 2^{j/4096} table of exp2s: the block's
 // shared-memory copy for forms whose hot loop reads it (kStageTable), else
 // the global table (read only on rare FP64 paths).  kTilesPerBlock is the
 // number of 32 x 32 tiles one block of the tile kernels computes, and

@@ -143,25 +143,29 @@ __device__ __forceinline__ double log_pos(double a) {
 }
 
 // ---------------------------------------------------------------------------
-// Table-driven exponential for the hot loops (Tang's method with a 1024-entry
-// table).  The kernels work in scaled units u = a K, K = 1024/ln 2, so that
-// e^a = 2^{u/1024}: u = 1024 k + j + rho (round to nearest, |rho| <= 1/2),
-// e^a = 2^k 2^{j/1024} e^{rho ln2/1024}, the last factor from its Taylor
-// polynomial of degree 3 (|rho ln2/1024| <= 3.4e-4, truncation < 6e-16
-// relative).  2^{j/1024} comes from the block's shared-memory copy of
-// kExp2Tab (exp_table_init); 2^k is added to the entry's exponent field.
-// Valid for u in [-1022 * 1024, 1023 * 1024] (a in [-708, 709]); below that
-// the result is clamped to about 2^-1022, not garbage.
-static __device__ const double kExp2Tab[1024] = {
+// Table-driven exponential for the hot loops (Tang's method with a 4096-entry
+// table).  The kernels work in scaled units u = a K, K = 4096/ln 2, so that
+// e^a = 2^{u/4096}: u = 4096 k + j + rho (round to nearest, |rho| <= 1/2),
+// e^a = 2^k 2^{j/4096} e^{y}, y = rho ln2/4096, |y| <= c = 8.46e-5, and e^y from
+// the quadratic 1 + y (1 + c^2/8) + y^2/2: the Taylor quadratic with the
+// cubic term's best linear replacement on [-c, c] (y^3 ~ (3c^2/4) y, the
+// Chebyshev projection), relative error below 2.6e-14.  2^{j/4096} comes from
+// the block's shared-memory copy of kExp2Tab (exp_table_init, 32 KB); 2^k is
+// added to the entry's exponent field.  Valid for u in [-1022 * 4096,
+// 1023 * 4096] (a in [-708, 709]); below that the result is clamped to about
+// 2^-1022, not garbage.
+static __device__ const double kExp2Tab[4096] = {
 #include "bk_exp2_table.inc"
 };
-constexpr int kExpTabSize = 1024;
-constexpr double kExpScale = 0x1.71547652b82fep+10;  // 1024 / ln 2
-constexpr double kExpC1 = 0x1.62e42fefa39efp-11;     // ln2 / 1024
-constexpr double kExpC2 = 0x1.ebfbdff82c58fp-23;     // (ln2/1024)^2 / 2
-constexpr double kExpC3 = 0x1.c6b08d704a0c0p-35;     // (ln2/1024)^3 / 6
-constexpr double kExpC1Hi = 0x1.62e42ff000000p-11;   // ln2/1024 to 32 bits
-constexpr double kExpC1Lo = -0x1.718432a1b0e26p-45;  // ln2/1024 - kExpC1Hi
+constexpr int kExpTabBits = 12;
+constexpr int kExpTabSize = 1 << kExpTabBits;
+constexpr double kExpScale = 0x1.71547652b82fep+12;  // 4096 / ln 2
+constexpr double kExpC1 = 0x1.62e42fefa39efp-13;     // ln2 / 4096
+constexpr double kExpK1 = 0x1.62e42ff4f7b0ap-13;     // (ln2/4096)(1 + c^2/8)
+constexpr double kExpK2 = 0x1.ebfbdff82c58fp-27;     // (ln2/4096)^2 / 2
+constexpr double kExpC3 = 0x1.c6b08d704a0c0p-41;     // (ln2/4096)^3 / 6
+constexpr double kExpC1Hi = 0x1.62e42ff000000p-13;   // ln2/4096 to 29 bits
+constexpr double kExpC1Lo = -0x1.718432a1b0e26p-47;  // ln2/4096 - kExpC1Hi
 
 // Copies the table into a shared-memory array of kExpTabSize doubles (all
 // threads of the block take part) and synchronises the block.
@@ -170,16 +174,16 @@ __device__ __forceinline__ void exp_table_init(double* tab) {
   __syncthreads();
 }
 
-// 2^{u/1024} for u in scaled units.  FP64 ops: 1 add + 2 sub (rounding and
-// rho, exact), 3 fma (polynomial), 1 mul.
-constexpr int kExp2sOps = 7;
+// 2^{u/4096} for u in scaled units.  FP64 ops: 1 add + 2 sub (rounding and
+// rho, exact), 2 fma (polynomial), 1 mul.
+constexpr int kExp2sOps = 6;
 __device__ __forceinline__ double exp2s(double u, const double* __restrict__ tab) {
   const double v = u + kRoundMagic;
   const int n = __double2loint(v);
   const double rho = u - (v - kRoundMagic);
-  const double p = fma(fma(fma(kExpC3, rho, kExpC2), rho, kExpC1), rho, 1.0);
+  const double p = fma(fma(kExpK2, rho, kExpK1), rho, 1.0);
   const double tj = tab[n & (kExpTabSize - 1)];
-  const int k = max(n >> 10, -1022);
+  const int k = max(n >> kExpTabBits, -1022);
   return p * __hiloint2double(__double2hiint(tj) + (k << 20), __double2loint(tj));
 }
 
@@ -191,12 +195,27 @@ __device__ __forceinline__ double exp_tab(double a, const double* __restrict__ t
 
 // e^a over the whole double range (NaN -> NaN, overflow -> inf, deep
 // underflow -> 0) for the final normalisation, with an exact reduction:
-// kd = round(a K), r = a - kd ln2/1024 with ln2/1024 split in two (kd times
-// the 32-bit head is exact for |kd| < 2^21), e^r from its Taylor polynomial
-// of degree 3 (|r| <= 3.4e-4, truncation < 6e-16 relative), times the table
-// entry 2^{(kd mod 1024)/1024} and 2^{floor(kd/1024)}.  |a| >= 708 goes to
+// kd = round(a K), r = a - kd ln2/4096 with ln2/4096 split in two (kd times
+// the 29-bit head is exact for |kd| < 2^23), e^r from its Taylor polynomial
+// of degree 3 (|r| <= 8.5e-5, truncation < 3e-18 relative), times the table
+// entry 2^{(kd mod 4096)/4096} and 2^{floor(kd/4096)}.  |a| >= 708 goes to
 // exp_full.  FP64 ops: 1 fma + 1 sub (rounding), 2 fma (reduction),
 // 3 fma (polynomial), 1 mul.
+// The same for |a| < 708 without the range test: the accurate exponential of
+// the set-up values of the node recurrences (e^{t0}, e^{h}, e^{-2 nu h}, ...),
+// whose relative errors the recurrences multiply by up to the node count.
+__device__ __forceinline__ double exp_acc(double a, const double* __restrict__ tab) {
+  const double v = fma(a, kExpScale, kRoundMagic);
+  const int n = __double2loint(v);
+  const double kd = v - kRoundMagic;
+  double r = fma(-kd, kExpC1Hi, a);
+  r = fma(-kd, kExpC1Lo, r);
+  const double p = fma(fma(fma(r, 1.0 / 6.0, 0.5), r, 1.0), r, 1.0);
+  const double tj = tab[n & (kExpTabSize - 1)];
+  const int k = max(n >> kExpTabBits, -1022);
+  return p * __hiloint2double(__double2hiint(tj) + (k << 20), __double2loint(tj));
+}
+
 __device__ __forceinline__ double exp_tab_full(double a, const double* __restrict__ tab) {
   const double v = fma(a, kExpScale, kRoundMagic);
   if (!((__double_as_longlong(a) & 0x7fffffffffffffffLL) < 0x4086200000000000LL))  // |a| < 708
@@ -207,15 +226,15 @@ __device__ __forceinline__ double exp_tab_full(double a, const double* __restric
   r = fma(-kd, kExpC1Lo, r);
   const double p = fma(fma(fma(r, 1.0 / 6.0, 0.5), r, 1.0), r, 1.0);
   const double tj = tab[n & (kExpTabSize - 1)];
-  const int k = n >> 10;
+  const int k = n >> kExpTabBits;
   return p * __hiloint2double(__double2hiint(tj) + (k << 20), __double2loint(tj));
 }
 
 // log a for finite a > 0 with the same table: a = 2^e m, m in [1, 2); j =
-// round(1024 log2 m) from the FP32 hardware log of m's leading bits, so that
-// m 2^{-j/1024} = 1 + d with |d| <= 3.5e-4; log a = (1024 e + j) ln2/1024 +
-// log1p(d), log1p from its series to d^4 (truncation < 1e-18 absolute).
-// FP64 ops: 1 fma (d), 4 (series), 2 fma (assembly) and one int conversion.
+// round(4096 log2 m) from the FP32 hardware log of m's leading bits, so that
+// m 2^{-j/4096} = 1 + d with |d| <= 8.5e-5; log a = (4096 e + j) ln2/4096 +
+// log1p(d), log1p from its series to d^3 (truncation < 2e-17 absolute).
+// FP64 ops: 1 fma (d), 3 (series), 2 fma (assembly) and one int conversion.
 __device__ __forceinline__ double log_tab(double a, const double* __restrict__ tab) {
   int hi = __double2hiint(a);
   int lo = __double2loint(a);
@@ -232,14 +251,13 @@ __device__ __forceinline__ double log_tab(double a, const double* __restrict__ t
   const float mf = __int_as_float(0x3f800000 | (mh << 3) | ((unsigned)lo >> 29));
   float l2;
   asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l2) : "f"(mf));
-  const int j = __float2int_rn(l2 * 1024.0f);  // 0..1024
-  // 2^{-j/1024} = 2^{(1024 - j)/1024} / 2 (j > 0), 1 (j = 0)
+  const int j = __float2int_rn(l2 * (float)kExpTabSize);  // 0..4096
+  // 2^{-j/4096} = 2^{(4096 - j)/4096} / 2 (j > 0), 1 (j = 0)
   const double tj = tab[(kExpTabSize - j) & (kExpTabSize - 1)];
   const double tinv =
       __hiloint2double(__double2hiint(tj) - (j > 0 ? (1 << 20) : 0), __double2loint(tj));
   const double d = fma(m, tinv, -1.0);
-  const double q = fma(fma(d, -0.25, 1.0 / 3.0), d, -0.5);
-  const double l1p = fma(d * d, q, d);
+  const double l1p = fma(d * d, fma(d, 1.0 / 3.0, -0.5), d);
   const double nd = (double)(e * kExpTabSize + j);
   return fma(nd, kExpC1Hi, fma(nd, kExpC1Lo, l1p));
 }
@@ -453,7 +471,7 @@ __device__ __forceinline__ double two_cosh_small(double H) {
 // t_j = t_start + j H, where
 //   f(t) = e^{-x cosh t} cosh(nu t) = f_s exp(nu (t - ts) - x (cosh t - cs)) (1 + e^{-2 nu t}),
 //   f_s = e^{nu ts - x cs} / 2.
-// The exponent is kept in the scaled units of exp2s (times K = 1024/ln 2):
+// The exponent is kept in the scaled units of exp2s (times K = 4096/ln 2):
 // its linear part A_j = K (nu (t_j - ts) + x cs) is accumulated, D_j =
 // K x cosh t_j follows the three-term recurrence D_{j+1} = 2 cosh(H) D_j -
 // D_{j-1} (one FMA; its rounding error grows like j ulp / (2 sinh H)), and
@@ -469,18 +487,18 @@ __device__ __forceinline__ NodeSum node_sum_f64(double t_start, double H, int co
   const double xh = (0.5 * kExpScale) * x;
   double W = 1.0, c, D0, D1;
   if (bits_pos(t_start)) {
-    const double e0 = exp_tab(t_start, tab), r0 = rcp_nr2(e0);
-    W = exp_tab(fmax(-2.0 * nu * t_start, -708.0), tab);
-    const double eh = exp_tab(H, tab), rh = rcp_nr2(eh);
-    c = eh + rh;
+    const double e0 = exp_acc(t_start, tab), r0 = rcp_nr2(e0);
+    W = exp_acc(fmax(-2.0 * nu * t_start, -708.0), tab);
+    const double eh = exp_acc(H, tab), rh = rcp_nr2(eh);
+    c = bits_le(H, 0.35) ? two_cosh_small(H) : eh + rh;
     D0 = xh * (e0 + r0);
     D1 = xh * fma(e0, eh, r0 * rh);
   } else {
-    c = bits_le(H, 0.35) ? two_cosh_small(H) : exp_tab(H, tab) + rcp_nr2(exp_tab(H, tab));
+    c = bits_le(H, 0.35) ? two_cosh_small(H) : exp_acc(H, tab) + rcp_nr2(exp_acc(H, tab));
     D0 = 2.0 * xh;
     D1 = xh * c;
   }
-  const double rho = exp_tab(fmax(-2.0 * nu * H, -708.0), tab);
+  const double rho = exp_acc(fmax(-2.0 * nu * H, -708.0), tab);
   double A = kExpScale * fma(nu, t_start - ts, x * cs);
   const double dA = kExpScale * (nu * H);
   NodeSum r;
@@ -506,7 +524,7 @@ __device__ __forceinline__ NodeSum node_sum_f64(double t_start, double H, int co
 }
 // FP64 ops per node in node_sum_f64 (work accounting): 1 sub (exponent),
 // exp2s, 1 fma + 1 add (f, s), 1 fma (recurrence), 1 add + 1 mul.
-constexpr int kNodeOps64 = 6 + kExp2sOps;
+constexpr int kNodeOps64 = 6 + kExp2sOps;  // 12
 
 // ln(2 / tol) for the plain form: tol = 1e-13 keeps the quadrature error
 // about three orders below the 1e-10 relative accuracy the form promises.
@@ -682,18 +700,18 @@ __device__ __forceinline__ NodeSum3 node_sum3_f64(double t_start, double H, int 
   const double xh = (0.5 * kExpScale) * x;
   double W = 1.0, c, D0, D1;
   if (bits_pos(t_start)) {
-    const double e0 = exp_tab(t_start, tab), r0 = rcp_nr2(e0);
-    W = exp_tab(fmax(-2.0 * nu * t_start, -708.0), tab);
-    const double eh = exp_tab(H, tab), rh = rcp_nr2(eh);
-    c = eh + rh;
+    const double e0 = exp_acc(t_start, tab), r0 = rcp_nr2(e0);
+    W = exp_acc(fmax(-2.0 * nu * t_start, -708.0), tab);
+    const double eh = exp_acc(H, tab), rh = rcp_nr2(eh);
+    c = bits_le(H, 0.35) ? two_cosh_small(H) : eh + rh;
     D0 = xh * (e0 + r0);
     D1 = xh * fma(e0, eh, r0 * rh);
   } else {
-    c = bits_le(H, 0.35) ? two_cosh_small(H) : exp_tab(H, tab) + rcp_nr2(exp_tab(H, tab));
+    c = bits_le(H, 0.35) ? two_cosh_small(H) : exp_acc(H, tab) + rcp_nr2(exp_acc(H, tab));
     D0 = 2.0 * xh;
     D1 = xh * c;
   }
-  const double rho = exp_tab(fmax(-2.0 * nu * H, -708.0), tab);
+  const double rho = exp_acc(fmax(-2.0 * nu * H, -708.0), tab);
   double A = kExpScale * fma(nu, t_start - ts, x * cs);
   const double dA = kExpScale * (nu * H);
   NodeSum3 r;
@@ -801,7 +819,7 @@ __device__ __forceinline__ double fixed_scale_f64(double x, double nu, double t1
   if (h <= 0.35) {
     c = two_cosh_small(h);
   } else {
-    const double eh = exp_tab(h, tab);
+    const double eh = exp_acc(h, tab);
     c = eh + rcp_nr2(eh);
   }
   const double D0i = kExpScale * x, D1i = 0.5 * c * D0i, dA = kExpScale * (nu * h);
@@ -813,7 +831,7 @@ __device__ __forceinline__ double fixed_scale_f64(double x, double nu, double t1
     D1 = D2;
     A += dA;
   }
-  const double rho = exp_tab(fmax(-2.0 * nu * h, -708.0), tab);
+  const double rho = exp_acc(fmax(-2.0 * nu * h, -708.0), tab);
   D0 = D0i;
   D1 = D1i;
   A = -amax;
