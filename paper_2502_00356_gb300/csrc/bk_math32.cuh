@@ -165,6 +165,23 @@ __device__ __forceinline__ float expm1_f32(float y) {
   return fabsf(y) < 0.35f ? poly : mufu_ex2(y * kLog2ef) - 1.0f;
 }
 
+// e^y - 1 and e^{-y} - 1 together, both with small relative error: for
+// |y| < 0.35 the Taylor polynomial p of expm1 (as in expm1_f32) and
+// e^{-y} - 1 = -p / (1 + p); above, E = e^y on the MUFU and E - 1, 1/E - 1
+// (no cancellation beyond a factor of ~3 in ulps there).  One polynomial,
+// one ex2 and one rcp instead of two expm1_f32 calls.
+__device__ __forceinline__ void expm1_pm_f32(float y, float& em, float& emn) {
+  const float p =
+      y * fmaf(y, fmaf(y, fmaf(y, fmaf(y, fmaf(y, fmaf(y, 1.0f / 5040.0f, 1.0f / 720.0f),
+                                               1.0f / 120.0f), 1.0f / 24.0f), 1.0f / 6.0f),
+                   0.5f), 1.0f);
+  const float e = mufu_ex2(y * kLog2ef);
+  const bool small = fabsf(y) < 0.35f;
+  em = small ? p : e - 1.0f;
+  const float r = mufu_rcp(small ? 1.0f + p : e);
+  emn = small ? -p * r : r - 1.0f;
+}
+
 // Scaled trapezoid sum of the FP32 form, with the weights of Eq. (refined):
 //   S = sum_j c_j exp(a_j) (1 + e^{-2 nu t_j}),  c_0 = c_N = 1/2,
 //   a_j = nu tau_j - x (cosh t_j - cosh ts),  tau_j = t_j - ts = (t0 - ts) + j h.
@@ -185,23 +202,25 @@ __device__ __forceinline__ float trapezoid_f32(float x, float nu, float nu_lo, c
   const float tau0 = w.t0 - w.ts;
   float W = mufu_ex2(-2.0f * kLog2ef * nu * w.t0);
   const float rho = mufu_ex2(-2.0f * kLog2ef * nu * h);
-  float S = 0.0f, c = 0.0f;
+  float S = 0.0f, c = 0.0f, f = 0.0f, f0 = 0.0f, jf = 0.0f;
   const float x2 = 2.0f * x;
   const bool at_zero = (w.ts == 0.0f);
   amax = -3.0e38f;
-  for (int j = 0; j <= N; ++j) {
-    const float tau = fmaf((float)j, h, tau0);
+  for (int j = 0; j <= N; ++j, jf += 1.0f) {  // jf = j exactly (float counter, no conversion)
+    const float tau = fmaf(jf, h, tau0);
     float a;
     if (at_zero) {
       const float sq = sinh_f32(0.5f * tau);
       a = fmaf(nu, tau, fmaf(nu_lo, tau, -x2 * sq * sq));
     } else {
-      a = fmaf(nu, tau, fmaf(nu_lo, tau, -fmaf(Ah, expm1_f32(tau), Bh * expm1_f32(-tau))));
+      float em, emn;
+      expm1_pm_f32(tau, em, emn);
+      a = fmaf(nu, tau, fmaf(nu_lo, tau, -fmaf(Ah, em, Bh * emn)));
     }
     amax = fmaxf(amax, a);
-    float f = exp_f32(a);
+    f = exp_f32(a);
     f = fmaf(f, W, f);
-    if (j == 0 || j == N) f *= 0.5f;
+    if (j == 0) f0 = f;
     const float y = f - c;  // Kahan
     const float s2 = S + y;
     c = (s2 - S) - y;
@@ -209,7 +228,7 @@ __device__ __forceinline__ float trapezoid_f32(float x, float nu, float nu_lo, c
     W *= rho;
   }
   tl.nodes += N + 1;
-  return h * S;
+  return h * ((S - c) - 0.5f * (f0 + f));  // end weights 1/2
 }
 
 // The searched window of the FP32 form: FP32 search inside x in [1e-4, 1e4],
