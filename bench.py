@@ -414,6 +414,28 @@ def measure_forms(bk, inputs, dev, stream, args, plain_rate):
     res["paper_algorithm2"] = alg
     del o2, L2, refs
     torch.cuda.empty_cache()
+
+    # -- downstream Gaussian log-likelihood (blocked FP64 Cholesky) on the n = 4,000 and
+    # n = 8,000 Matern matrices of the Cholesky checks (jittered grid seed 3, beta 0.1, nu 0.5)
+    ll = {"unit": "s", "workload": "jittered grid (seed 3), sigma2 1, beta 0.1, nu 0.5, "
+                                   "z ~ N(0, 1) (seed 5): matrix generation + log-likelihood"}
+    for nl in (4000, 8000):
+        Ll = torch.as_tensor(inputs.morton_sorted(inputs.jittered_grid(nl, seed=3)), device=dev)
+        zl = torch.as_tensor(np.random.default_rng(5).standard_normal(nl), device=dev)
+        ml = torch.empty((nl, nl), dtype=torch.float64, device=dev)
+        yl = torch.empty(nl, dtype=torch.float64, device=dev)
+        outl = torch.empty(3, dtype=torch.float64, device=dev)
+        bk.bk_matern_tile(Ll, SIGMA2, BETA, 0.5, out=ml)
+        bk.bk_gaussian_loglik(ml, zl, y=yl, out=outl)
+        t_gen = _time(lambda: bk.bk_matern_tile(Ll, SIGMA2, BETA, 0.5, out=ml), stream, 1)
+        t_ll = _time(lambda: bk.bk_gaussian_loglik(ml, zl, y=yl, out=outl), stream, 1)
+        bk.bk_matern_tile(Ll, SIGMA2, BETA, 0.5, out=ml)  # the last call factored ml in place
+        ll[f"n{nl}"] = {"matern_s": t_gen, "loglik_s": t_ll,
+                        "cholesky_fp64_tflops": nl ** 3 / 3 / t_ll / 1e12,
+                        "loglik": float(bk.bk_gaussian_loglik(ml, zl, y=yl, out=outl)[0])}
+        del Ll, zl, ml, yl
+        torch.cuda.empty_cache()
+    res["gaussian_loglik"] = ll
     return res
 
 

@@ -309,6 +309,25 @@ bk_status bk_learned_load(bk_learned* model, const char* path);
 bk_status bk_matern_batched_static(const bk_matern_desc* d_descs, int32_t count, bk_dtype dtype,
                                    bk_stream_t stream);
 
+/* Gaussian log-likelihood of observations z under the covariance matrix a
+ * (the step that consumes the generated matrix in the maximum-likelihood
+ * loop the paper accelerates, Sec. II; not part of the paper's method):
+ *   l = -1/2 (z^T a^{-1} z + log det a + n log 2 pi),
+ * by an in-place blocked Cholesky a = L L^T in FP64 (64 x 64 tiles),
+ * log det a = 2 sum log L_ii and the forward substitution L y = z
+ * (z^T a^{-1} z = y^T y).
+ *   a:   n x n column-major FP64 (device), ld >= n; only the lower triangle
+ *        is read, and it is overwritten by L (the upper triangle is untouched)
+ *   z:   n FP64 observations (device, read only)
+ *   y:   n FP64 workspace (device); receives L^{-1} z
+ *   out: 3 FP64 (device): [l, log det a, z^T a^{-1} z]
+ * A matrix that is not positive definite (a pivot <= 0) gives NaN in out and
+ * adds 1 to BK_CTR_FAIL when opts carries counters (other options are
+ * ignored).  n = 0 writes zeros.  n <= 65535 * 64.  Asynchronous on
+ * `stream` (about 5 launches per 64 rows); allocates nothing. */
+bk_status bk_gaussian_loglik(double* a, int64_t n, int64_t ld, const double* z, double* y,
+                             double* out, const bk_opts* opts, bk_stream_t stream);
+
 /*
  * bk_probe_pipe: throughput probe for the roofline denominators (not part of
  * the paper's method).  Launches grid x block threads; each runs `iters`

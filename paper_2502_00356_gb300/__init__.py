@@ -32,7 +32,7 @@ BK_NUM_COUNTERS = 8
 #: every symbol include/bk.h declares (checked by the CPU tests)
 EXPORTS = (
     "bk_opts_default", "bk_version", "bk_last_error", "bk_status_string", "bk_sync",
-    "bk_eval", "bk_eval_ex", "bk_eval_grad", "bk_matern_tile", "bk_matern_tile_ex", "bk_matern_tile2",
+    "bk_eval", "bk_eval_ex", "bk_eval_grad", "bk_gaussian_loglik", "bk_matern_tile", "bk_matern_tile_ex", "bk_matern_tile2",
     "bk_morton_order", "bk_probe_pipe", "bk_batched_plan_create", "bk_batched_plan_destroy",
     "bk_batched_plan_info", "bk_batched_autotune", "bk_matern_batched",
     "bk_matern_batched_static", "bk_learned_create", "bk_learned_destroy", "bk_learned_train",
@@ -88,6 +88,7 @@ def lib() -> ctypes.CDLL:
             "bk_eval": (I, [P, P, P, I64, P]),
             "bk_eval_ex": (I, [P, P, P, P, I, I64, P, P]),
             "bk_eval_grad": (I, [P, P, P, P, P, I64, P, P]),
+            "bk_gaussian_loglik": (I, [P, I64, I64, P, P, P, P, P]),
             "bk_matern_tile": (I, [P, I64, D, D, D, P, I64, I, P]),
             "bk_matern_tile_ex": (I, [P, I64, D, D, D, P, I64, I, P, P]),
             "bk_matern_tile2": (I, [P, I64, P, I64, D, D, D, P, I64, I, P, P]),
@@ -283,6 +284,31 @@ def bk_eval_grad(x, nu, k=None, dk_dx=None, dk_dnu=None, opts: Optional[bk_opts]
     _check(lib().bk_eval_grad(_ptr(x), _ptr(nu), _ptr(outs[0]), _ptr(outs[1]), _ptr(outs[2]), n,
                               optp, _stream_ptr(stream)))
     return tuple(outs)
+
+
+def bk_gaussian_loglik(a, z, y=None, out=None, opts: Optional[bk_opts] = None, stream=None):
+    """Gaussian log-likelihood of z under the covariance ``a`` (CUDA float64,
+    viewed column-major like the Matern outputs: shape (n, ld), its lower
+    triangle overwritten by the Cholesky factor).  Returns ``out`` =
+    [l, log det a, z^T a^{-1} z] (CUDA float64, 3)."""
+    torch = _torch()
+    _dev(a, "a", torch.float64)
+    _dev(z, "z", torch.float64)
+    if a.dim() != 2:
+        raise ValueError("a must be 2-D (n, ld)")
+    n, ld = a.shape[0], a.shape[1]
+    if z.numel() != n:
+        raise ValueError("z must have n elements")
+    if y is None:
+        y = torch.empty(n, dtype=torch.float64, device=a.device)
+    if out is None:
+        out = torch.empty(3, dtype=torch.float64, device=a.device)
+    _dev(y, "y", torch.float64)
+    _dev(out, "out", torch.float64)
+    optp = ctypes.byref(opts) if opts is not None else None
+    _check(lib().bk_gaussian_loglik(_ptr(a), n, ld, _ptr(z), _ptr(y), _ptr(out), optp,
+                                    _stream_ptr(stream)))
+    return out
 
 
 def _locs(locs, name="locs"):

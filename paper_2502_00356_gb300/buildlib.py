@@ -36,8 +36,8 @@ def _sources():
 
 def _inputs():
     return (_sources() + glob.glob(os.path.join(CSRC, "*.cuh"))
-            + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(INCLUDE, "*.h"))
-            + [os.path.abspath(__file__)])
+            + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.inc"))
+            + glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)])
 
 
 def up_to_date() -> bool:

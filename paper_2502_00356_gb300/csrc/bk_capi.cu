@@ -192,6 +192,26 @@ bk_status bk_eval_grad(const double* x, const double* nu, double* k, double* dk_
                     "bk_eval_grad launch");
 }
 
+bk_status bk_gaussian_loglik(double* a, int64_t n, int64_t ld, const double* z, double* y,
+                             double* out, const bk_opts* opts, bk_stream_t stream) {
+  bk_opts o;
+  bk_opts_default(&o);
+  if (opts != nullptr) o = *opts;
+  bk_status st = check_opts(&o);
+  if (st != BK_OK) return st;
+  if (out == nullptr) return set_error(BK_ERR_INVALID_ARG, "out is NULL");
+  if (n < 0) return set_error(BK_ERR_INVALID_ARG, "n must be >= 0 (got %lld)", (long long)n);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n == 0)
+    return check_cuda(cudaMemsetAsync(out, 0, 3 * sizeof(double), s), "bk_gaussian_loglik");
+  if ((st = check_matrix(a, n, n, ld)) != BK_OK) return st;
+  if (z == nullptr || y == nullptr) return set_error(BK_ERR_INVALID_ARG, "z and y must be non-NULL");
+  if (n > (int64_t)65535 * 64)
+    return set_error(BK_ERR_INVALID_ARG, "n too large for the tile grid (max %lld)",
+                     (long long)65535 * 64);
+  return check_cuda(launch_loglik(a, n, ld, z, y, out, o.d_counters, s), "bk_gaussian_loglik");
+}
+
 bk_status bk_eval(const double* x, const double* nu, double* out, int64_t n, bk_stream_t stream) {
   return bk_eval_ex(x, nu, out, nullptr, BK_F64, n, nullptr, stream);
 }

@@ -37,6 +37,11 @@ cudaError_t launch_matern_block_f64(const double* locs1, int64_t m, const double
 cudaError_t launch_eval_grad_f64(const double* x, const double* nu, double* k, double* dkdx,
                                  double* dkdnu, int64_t n, const bk_opts& o, cudaStream_t s);
 
+// The Gaussian log-likelihood steps (Cholesky, log det, forward
+// substitution, reduction) on `s`; see bk_gaussian_loglik.
+cudaError_t launch_loglik(double* a, int64_t n, int64_t ld, const double* z, double* y,
+                          double* out, unsigned long long* ctr, cudaStream_t s);
+
 // Option checks shared by every entry point that takes bk_opts (sets the
 // error message and returns the status).
 bk_status check_opts(const bk_opts* o);
