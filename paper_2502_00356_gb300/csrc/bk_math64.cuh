@@ -187,6 +187,34 @@ __device__ __forceinline__ double exp2s(double u, const double* __restrict__ tab
   return p * __hiloint2double(__double2hiint(tj) + (k << 20), __double2loint(tj));
 }
 
+// exp2s for the node loops (every node exponent of an eps-window has
+// |u| < 3e5): the nearest integer n of u is found on the FP32 and integer
+// pipes from u's leading 23 significand bits (a float built from the bit
+// pattern, rounded with the float magic number 1.5 2^23), and only kd = n
+// (rebuilt exactly from the integer by one FP64 subtraction) and rho = u - kd
+// use the FP64 pipe: 5 FP64 operations instead of 6.  The float's truncation
+// can put n off the nearest integer by up to a float ulp (1/32 at |u| < 2^18):
+// |rho| <= 0.53 keeps the polynomial's error below 3e-14.  |u| >= 2^22 is
+// clamped to 4e6 on the integer side (a result of about 2^-977 for negative
+// u; NaN stays NaN through rho).
+constexpr int kExp2sNodeOps = 5;
+__device__ __forceinline__ double exp2s_node(double u, const double* __restrict__ tab) {
+  const int hi = __double2hiint(u);
+  const int ex = (hi >> 20) & 0x7ff;  // biased exponent of u
+  const int mant = ((hi & 0x000fffff) << 3) | (int)((unsigned)__double2loint(u) >> 29);
+  const float mag = (ex < 1003) ? 0.0f                                // |u| < 2^-20: n = 0
+                    : (ex > 1044) ? 4.0e6f                            // |u| >= 2^22: clamp
+                                  : __int_as_float(((ex - 896) << 23) | mant);
+  const float uf = __int_as_float(__float_as_int(mag) | (hi & (int)0x80000000));
+  const int n = __float_as_int(uf + 12582912.0f) - 0x4b400000;  // round to nearest
+  const double kd = __hiloint2double(0x43380000, n ^ (int)0x80000000) - 0x1.8000080000000p+52;
+  const double rho = u - kd;
+  const double p = fma(fma(kExpK2, rho, kExpK1), rho, 1.0);
+  const double tj = tab[n & (kExpTabSize - 1)];
+  const int k = max(n >> kExpTabBits, -1022);
+  return p * __hiloint2double(__double2hiint(tj) + (k << 20), __double2loint(tj));
+}
+
 // e^a for a in [-708, 709] (callers clamp); one scaling multiply on top of exp2s.
 constexpr int kExpTabOps = 1 + kExp2sOps;
 __device__ __forceinline__ double exp_tab(double a, const double* __restrict__ tab) {
@@ -504,7 +532,7 @@ __device__ __forceinline__ NodeSum node_sum_f64(double t_start, double H, int co
   NodeSum r;
   double s = 0.0, f = 0.0, ev = 0.0;
   for (int j = 0; j < count; ++j) {
-    ev = exp2s(A - D0, tab);
+    ev = exp2s_node(A - D0, tab);
     f = fma(ev, W, ev);
     if (j == 0) {
       r.first = f;
@@ -523,8 +551,8 @@ __device__ __forceinline__ NodeSum node_sum_f64(double t_start, double H, int co
   return r;
 }
 // FP64 ops per node in node_sum_f64 (work accounting): 1 sub (exponent),
-// exp2s, 1 fma + 1 add (f, s), 1 fma (recurrence), 1 add + 1 mul.
-constexpr int kNodeOps64 = 6 + kExp2sOps;  // 12
+// exp2s_node, 1 fma + 1 add (f, s), 1 fma (recurrence), 1 add + 1 mul.
+constexpr int kNodeOps64 = 6 + kExp2sNodeOps;  // 11
 
 // ln(2 / tol) for the plain form: tol = 1e-13 keeps the quadrature error
 // about three orders below the 1e-10 relative accuracy the form promises.
@@ -717,7 +745,7 @@ __device__ __forceinline__ NodeSum3 node_sum3_f64(double t_start, double H, int 
   NodeSum3 r;
   double s = 0.0, sx = 0.0, sn = 0.0, t = t_start, ev = 0.0, f = 0.0, fx = 0.0, fn = 0.0;
   for (int j = 0; j < count; ++j) {
-    ev = exp2s(A - D0, tab);
+    ev = exp2s_node(A - D0, tab);
     f = fma(ev, W, ev);
     fx = D0 * f;
     fn = fma(-ev, W, ev) * t;
