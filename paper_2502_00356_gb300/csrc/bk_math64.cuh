@@ -531,6 +531,7 @@ __device__ __forceinline__ NodeSum node_sum_f64(double t_start, double H, int co
   const double dA = kExpScale * (nu * H);
   NodeSum r;
   double s = 0.0, f = 0.0, ev = 0.0;
+#pragma unroll 2  // two nodes' exponentials in flight per warp (measured +0.4 % over 1 and 4)
   for (int j = 0; j < count; ++j) {
     ev = exp2s_node(A - D0, tab);
     f = fma(ev, W, ev);
