@@ -415,8 +415,9 @@ bk_status bk_batched_autotune(bk_plan* plan, const bk_matern_desc* d_descs, int6
   const int chunk_c[2] = {1, 4};
   bk_status st = BK_OK;
   for (int wi = 0; wi < 2 && st == BK_OK; ++wi) {
-    const int maxc = max_ctas_per_sm(plan, warps_c[wi]);
-    for (int c = 1; c <= std::min(maxc, 8) && st == BK_OK; c *= 2) {
+    // CTAs per SM: 1, 2, 4, ... below the occupancy limit, and the limit itself
+    const int maxc = std::min(max_ctas_per_sm(plan, warps_c[wi]), 8);
+    for (int c = 1; c <= maxc && st == BK_OK; c = (c * 2 > maxc && c < maxc) ? maxc : c * 2) {
       for (int ci = 0; ci < 2 && st == BK_OK; ++ci) {
         float ms = 0.0f;
         for (int rep = 0; rep < 2; ++rep) {  // the first run warms the shape up
