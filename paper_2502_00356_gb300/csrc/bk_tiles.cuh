@@ -74,28 +74,89 @@ __device__ __forceinline__ Form bind_table(const Form& form, double* s_tab) {
   return f;
 }
 
+// Cost-ordering key of one (x, nu) pair from its bit patterns alone (no
+// FP64 instruction): |x| to 1/8 of an octave in the high bits, |nu| to 1/8 of
+// an octave below.  Pairs with close keys have similar windows, node counts
+// and search paths.
+__device__ __forceinline__ unsigned eval_cost_key(double x, double nu) {
+  const unsigned kx = ((unsigned)__double2hiint(x) >> 17) & 0x3fffu;   // exponent + 3 bits
+  const unsigned kn = ((unsigned)__double2hiint(nu) >> 17) & 0x3fffu;
+  return (kx << 14) | kn;
+}
+
+// Orders a round of 128 pairs (base .. base + 127) by eval_cost_key with a
+// bitonic sort in shared memory and returns the pair thread t evaluates, so
+// that a warp's 32 lanes take similar paths through the search and the node
+// loop (random pairs otherwise leave most lanes idle while the slowest
+// finishes).  Each pair's arithmetic is unchanged; results go back to their
+// own positions.  Every thread of the 128-thread block must call it.
+__device__ __forceinline__ int64_t sorted_pair(const double* __restrict__ x,
+                                               const double* __restrict__ nu, int64_t base,
+                                               int64_t n, unsigned* s_key, unsigned char* s_idx) {
+  constexpr int kB = 128;
+  const int t = threadIdx.x;
+  const int64_t i0 = base + t;
+  __syncthreads();  // the previous round's order is no longer read
+  s_key[t] = (i0 < n) ? eval_cost_key(x[i0], nu[i0]) : 0xffffffffu;
+  s_idx[t] = (unsigned char)t;
+  for (int size = 2; size <= kB; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      __syncthreads();
+      const int j = t ^ stride;
+      if (j > t) {
+        const bool up = ((t & size) == 0);
+        const unsigned a = s_key[t], b = s_key[j];
+        if ((a > b) == up) {
+          s_key[t] = b;
+          s_key[j] = a;
+          const unsigned char ia = s_idx[t];
+          s_idx[t] = s_idx[j];
+          s_idx[j] = ia;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  return base + s_idx[t];
+}
+
+// Bare evaluations, 128 per block and round.  The FP64 forms sort each round
+// by cost (sorted_pair); the FP32 forms, whose lanes diverge less and whose
+// evaluations are short, take the pairs in order.
 template <class Form, typename OutT>
 __global__ void __launch_bounds__(128) eval_kernel(const Form form, const double* __restrict__ x,
                                                    const double* __restrict__ nu,
                                                    OutT* __restrict__ out,
                                                    OutT* __restrict__ log_out, int64_t n,
                                                    unsigned long long* __restrict__ ctr) {
+  constexpr int kB = 128;
+  constexpr bool kSort = !Form::kFloatEval;
   __shared__ double s_tab[Form::kStageTable ? kExpTabSize : 1];
+  __shared__ unsigned s_key[kSort ? kB : 1];
+  __shared__ unsigned char s_idx[kSort ? kB : 1];
   const Form f = bind_table(form, s_tab);
   Tally tl{0u, 0u, 0u, 0u, 0u, 0u, 0u};
   unsigned evals = 0;
   const bool want_log = (log_out != nullptr);
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    OutT k, lk;
-    f.template eval_out<OutT>(x[i], nu[i], tl, evals, k, lk, want_log);
-    out[i] = k;
-    if (log_out != nullptr) log_out[i] = lk;
+  for (int64_t base = (int64_t)blockIdx.x * kB; base < n; base += (int64_t)gridDim.x * kB) {
+    int64_t i;
+    if constexpr (kSort) {
+      i = sorted_pair(x, nu, base, n, s_key, s_idx);
+    } else {
+      i = base + threadIdx.x;
+    }
+    if (i < n) {
+      OutT k, lk;
+      f.template eval_out<OutT>(x[i], nu[i], tl, evals, k, lk, want_log);
+      out[i] = k;
+      if (log_out != nullptr) log_out[i] = lk;
+    }
   }
   flush_tally(ctr, tl, evals);
 }
 
-// K, dK/dx and dK/dnu of the plain form.  Domain: x = 0 gives (+inf, -inf,
+// K, dK/dx and dK/dnu of the plain form, 128 pairs per block and round in
+// cost order (sorted_pair).  Domain: x = 0 gives (+inf, -inf,
 // NaN), x = +inf gives (0, 0, 0), x < 0 or NaN and non-finite nu give NaN;
 // dK/dnu is odd in nu (K_{-nu} = K_nu).  Null outputs are skipped.
 template <class Form>
@@ -105,13 +166,17 @@ __global__ void __launch_bounds__(128) eval_grad_kernel(const Form form, const d
                                                         double* __restrict__ dkdx,
                                                         double* __restrict__ dkdnu, int64_t n,
                                                         unsigned long long* __restrict__ ctr) {
+  constexpr int kB = 128;
   __shared__ double s_tab[Form::kStageTable ? kExpTabSize : 1];
+  __shared__ unsigned s_key[kB];
+  __shared__ unsigned char s_idx[kB];
   const Form f = bind_table(form, s_tab);
   Tally tl{0u, 0u, 0u, 0u, 0u, 0u, 0u};
   unsigned evals = 0;
   const double qnan = __longlong_as_double(0x7ff8000000000000LL);
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+  for (int64_t base = (int64_t)blockIdx.x * kB; base < n; base += (int64_t)gridDim.x * kB) {
+    const int64_t i = sorted_pair(x, nu, base, n, s_key, s_idx);
+    if (i >= n) continue;
     const double xi = x[i], vi = nu[i], av = fabs(vi);
     double kk = qnan, dx = qnan, dn = qnan;
     if (xi > 0.0 && xi < kInf && av < kInf) {
