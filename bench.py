@@ -34,15 +34,20 @@ METRIC = "K_ν evals/s, Matérn entries/s (1 GB300): plain FP64 vs learned/FP32,
 N_LOC, BETA, SIGMA2, NUS, SEED = 20_000, 0.1, 1.0, (0.5, 1.5, 2.3), 2
 WORKLOAD = "matern_jittered_grid_n20000_beta0.1_nu{0.5,1.5,2.3}_fp64"
 
-# FP64 work model of the plain form in FP64 pipe operations (one per thread
-# and instruction: fma, add, mul, compare), counted from the kernel source:
-# per quadrature node (one table exp plus the recurrences), per FP64 peak
-# Newton iteration, per FP64 window-end Newton iteration (these run only for
-# windows the FP64 check rejects, or outside the FP32 search region), and a
-# fixed part per Matern entry (distance, cosh t*, set-ups, end checks, log x,
-# final exp) or per bare K_nu evaluation.  The FP32 Newton iterations that
-# place the window run on the FP32/MUFU pipes and are not counted.
-OPS_NODE, OPS_PEAK_IT, OPS_WIN_IT, OPS_ENTRY_FIXED, OPS_EVAL_FIXED = 11, 54, 31, 90, 75
+# FP64 work model of the plain form in FP64 arithmetic operations (one per
+# thread and DFMA/DADD/DMUL): 8 per quadrature node of the common loop (the
+# table exponential's 4, its product with the cosh(nu t) factor, the
+# summing FMA and the two three-term recurrences; windows outside that loop's
+# conditions take 11 and are counted at 8), per FP64 peak Newton iteration
+# and per FP64 window-end Newton iteration (these run only for windows the
+# check rejects, or outside the FP32 search region), and a fixed part per
+# Matern entry (distance, square root, window ends, step, set-ups, log x and
+# the final exponential).  The fixed part is ncu's executed DFMA + DADD + DMUL
+# per entry minus 8 x nodes per entry on the n = 6000 case of the same kernel
+# (81, 87, 88 for nu = 0.5, 1.5, 2.3; the mean).  The FP32 Newton iterations
+# that place the window and the FP32 window check run on the FP32/MUFU pipes
+# and are not counted.
+OPS_NODE, OPS_PEAK_IT, OPS_WIN_IT, OPS_ENTRY_FIXED = 8, 54, 31, 85
 # FP64 pipe peak from the unit count and clock: 152 SMs x 2 DFMA/clk x 2.07 GHz
 # (1.26 TFLOP/s counting an FMA as two FLOPs).
 FP64_PEAK_GOPS = 152 * 2 * 2.07e9 / 1e9
@@ -513,6 +518,7 @@ def main():
 
     # -- work accounting pass (untimed): nodes / iterations per launch
     flop_per_launch = []
+    work = []
     fails = fallbacks = evals_counted = 0
     for nu in NUS:
         ctr = torch.zeros(bk.BK_NUM_COUNTERS, dtype=torch.int64, device=dev)
@@ -521,6 +527,10 @@ def main():
         fails += int(c[bk.BK_CTR_FAIL])
         fallbacks += int(c[bk.BK_CTR_FALLBACK])
         evals_counted += int(c[bk.BK_CTR_EVALS])
+        work.append({"nu": nu, "nodes_per_entry": float(c[bk.BK_CTR_NODES] / max(1, c[bk.BK_CTR_EVALS])),
+                     "iters_per_entry": float(c[bk.BK_CTR_ITERS] / max(1, c[bk.BK_CTR_EVALS])),
+                     "peak_iters_per_entry": float(c[bk.BK_CTR_PEAK_ITERS]
+                                                   / max(1, c[bk.BK_CTR_EVALS]))})
         flop_per_launch.append(OPS_NODE * c[bk.BK_CTR_NODES] + OPS_PEAK_IT * c[bk.BK_CTR_PEAK_ITERS]
                                + OPS_WIN_IT * c[bk.BK_CTR_ITERS] + OPS_ENTRY_FIXED * c[bk.BK_CTR_EVALS])
     torch.cuda.synchronize()
@@ -569,7 +579,8 @@ def main():
                 "peak_source": "derived: 152 SMs x 2 FP64 ops/clk x 2.07 GHz (of derived)",
                 "traffic": profiled_traffic(n),
                 "algorithmic_fp64_ops_per_launch": flop_mean,
-                "algorithmic_bytes_per_launch": n * n * 8 + 16 * n}
+                "algorithmic_bytes_per_launch": n * n * 8 + 16 * n,
+                "work": work}
 
     # -- pipe probes (context for the peak)
     sink = torch.empty(152 * 8 * 256, dtype=torch.float64, device=dev)

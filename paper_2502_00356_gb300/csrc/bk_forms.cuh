@@ -41,7 +41,7 @@ __device__ __forceinline__ const Start32* plain_starts(double x, float nu, Start
   if (!(xf >= 1e-4f && xf <= 1e4f && nu <= 40.0f)) return nullptr;
   Tally fp32_work{0u, 0u, 0u, 0u, 0u, 0u, 0u};
   const Window32 w = window_f32(xf, nu, (float)kLogInvEps64, fp32_work);
-  st = Start32{w.ts, w.t0, w.t1};
+  st = Start32{w.ts, w.t0, w.t1, w.cs};
   return &st;
 }
 

@@ -61,6 +61,7 @@ __device__ __forceinline__ double exp_split(double a) {
 
 struct Window32 {
   float ts, t0, t1;
+  float cs;  // cosh ts (window_f32 only)
 };
 
 // a3 in FP32: the same bracketed Newton as peak_f64 (g' concave on t > 0,
@@ -114,6 +115,7 @@ __device__ __forceinline__ Window32 window_f32(float x, float nu, float L, Tally
   w.ts = ts;
   const float es = mufu_ex2(ts * kLog2ef);
   const float cs = 0.5f * (es + mufu_rcp(es));
+  w.cs = cs;
   const float ss = sinh_f32(ts);
   {
     const float a = x * cs, b = nu - x * ss;

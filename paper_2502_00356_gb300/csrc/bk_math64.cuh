@@ -31,15 +31,18 @@ __device__ __forceinline__ bool bits_pos(double v) { return __double_as_longlong
 __device__ __forceinline__ bool bits_le(double a, double b) {
   return __double_as_longlong(a) <= __double_as_longlong(b);
 }
-// v truncated to a float (23 stored significand bits); a conversion outside
-// the float normal range.
+// v truncated to a float (23 stored significand bits) by integer operations
+// only (no conversion on the FP64 pipe): magnitudes below 2^-126 give a
+// signed zero, above the float range a signed infinity, NaN a NaN.
 __device__ __forceinline__ float f32_trunc(double v) {
   const long long b = __double_as_longlong(v);
-  const int e = (int)((b >> 52) & 0x7ff) - 1023;
-  if (e < -126 || e > 127) return (float)v;
   const unsigned hi = (unsigned)((unsigned long long)b >> 32);
-  return __int_as_float((int)((hi & 0x80000000u) | ((unsigned)(e + 127) << 23) |
-                              (unsigned)((b >> 29) & 0x7fffff)));
+  const int e = (int)((hi >> 20) & 0x7ff) - 1023;
+  const unsigned sign = hi & 0x80000000u;
+  const unsigned mant = (unsigned)((b >> 29) & 0x7fffff);
+  const unsigned big = sign | 0x7f800000u | ((e == 1024 && (b & 0xfffffffffffffLL) != 0) ? 0x400000u : 0u);
+  const unsigned r = (e < -126) ? sign : (e > 127) ? big : (sign | ((unsigned)(e + 127) << 23) | mant);
+  return __uint_as_float(r);
 }
 // A float as a double by integer operations (exact; denormals, infinities
 // and NaN through the conversion).
@@ -215,6 +218,25 @@ __device__ __forceinline__ double exp2s_node(double u, const double* __restrict_
   return p * __hiloint2double(__double2hiint(tj) + (k << 20), __double2loint(tj));
 }
 
+// exp2s_node split into its polynomial p (|rho| <= 0.53) and the scaled
+// table value T = 2^{k + j/4096}, 2^{u/4096} = p T, for loops that fold the
+// final product into an FMA: 4 FP64 operations.
+__device__ __forceinline__ void exp2s_node_parts(double u, const double* __restrict__ tab,
+                                                 double& p, double& T) {
+  const int hi = __double2hiint(u);
+  const int ex = (hi >> 20) & 0x7ff;
+  const int mant = ((hi & 0x000fffff) << 3) | (int)((unsigned)__double2loint(u) >> 29);
+  const float mag = (ex < 1003) ? 0.0f : (ex > 1044) ? 4.0e6f : __int_as_float(((ex - 896) << 23) | mant);
+  const float uf = __int_as_float(__float_as_int(mag) | (hi & (int)0x80000000));
+  const int n = __float_as_int(uf + 12582912.0f) - 0x4b400000;
+  const double kd = __hiloint2double(0x43380000, n ^ (int)0x80000000) - 0x1.8000080000000p+52;
+  const double rho = u - kd;
+  p = fma(fma(kExpK2, rho, kExpK1), rho, 1.0);
+  const double tj = tab[n & (kExpTabSize - 1)];
+  const int k = max(n >> kExpTabBits, -1022);
+  T = __hiloint2double(__double2hiint(tj) + (k << 20), __double2loint(tj));
+}
+
 // e^a for a in [-708, 709] (callers clamp); one scaling multiply on top of exp2s.
 constexpr int kExpTabOps = 1 + kExp2sOps;
 __device__ __forceinline__ double exp_tab(double a, const double* __restrict__ tab) {
@@ -334,7 +356,7 @@ struct Window64 {
 // FP32 start values for the FP64 Newton iterations (the FP32 search run to
 // convergence on the same F); a value <= 0 means "none" for ts and t0.
 struct Start32 {
-  float ts, t0, t1;
+  float ts, t0, t1, cs;  // cs: cosh ts as the FP32 search computed it
 };
 
 // FP32 helpers for Newton start values (only their side of the root matters).
@@ -555,6 +577,117 @@ __device__ __forceinline__ NodeSum node_sum_f64(double t_start, double H, int co
 // exp2s_node, 1 fma + 1 add (f, s), 1 fma (recurrence), 1 add + 1 mul.
 constexpr int kNodeOps64 = 6 + kExp2sNodeOps;  // 11
 
+// 2 cosh v for v >= 0: two_cosh_small up to 0.35, e^v + e^{-v} above.  The
+// choice is made once for the active lanes of the warp (a vote): lanes of a
+// warp mostly agree, and a per-lane select would evaluate both sides.
+__device__ __forceinline__ double two_cosh_warp(double v, const double* __restrict__ tab) {
+  const bool small = bits_le(v, 0.35);
+  const unsigned act = __activemask();
+  if (__all_sync(act, small)) return two_cosh_small(v);
+  const double e = exp_acc(v, tab), big = e + rcp_nr2(e);
+  if (!__any_sync(act, small)) return big;
+  return small ? two_cosh_small(v) : big;
+}
+
+// The same sum without centring, for the checked windows of scale_f64:
+//   f(t_j) = (e^{nu t_start} / 2) e^{-x cosh t_j} C_j,
+//   C_j = e^{nu (t_j - t_start)} (1 + e^{-2 nu t_j}) = 2 e^{-nu t_start} cosh(nu t_j),
+// where C_j follows its own three-term recurrence C_{j+1} = 2 cosh(nu H) C_j
+// - C_{j-1}.  A node costs the exponential of -D_j, its product with C_j,
+// the sum and the two recurrences: 8 FP64 operations instead of 11, and the
+// set-up needs neither cosh t* nor the centring exponentials.  Each factor must stay in
+// the double range on its own, x cosh t_j <= 690 (exp2s_node's argument
+// below 2^22) and nu (t_j - t_start) <= 600, and the C recurrence amplifies
+// rounding with the node count; cosh_loop_ok states the conditions.  Returns S = sum_j e^{-x cosh t_j} C_j and the end terms.
+struct NodeSumC {
+  double S, first, last;
+};
+__device__ __forceinline__ NodeSumC node_sum_cosh(double t_start, double H, int count, double x,
+                                                  double nu, const double* __restrict__ tab) {
+  const double xh = (0.5 * kExpScale) * x;
+  const double th = nu * H;
+  double c, D0, D1, cn, C0, C1;
+  if (bits_pos(t_start)) {
+    const double e0 = exp_acc(t_start, tab), r0 = rcp_nr2(e0);
+    const double eh = exp_acc(H, tab), rh = rcp_nr2(eh);
+    c = bits_le(H, 0.35) ? two_cosh_small(H) : eh + rh;
+    D0 = xh * (e0 + r0);
+    D1 = xh * fma(e0, eh, r0 * rh);
+    const double W = exp_acc(fmax(-2.0 * nu * t_start, -708.0), tab);
+    const double en = exp_acc(th, tab), rn = rcp_nr2(en);
+    cn = bits_le(th, 0.35) ? two_cosh_small(th) : en + rn;
+    C0 = 1.0 + W;
+    C1 = fma(W, rn, en);  // e^{nu H} + e^{-2 nu t_start} e^{-nu H}
+  } else {
+    c = two_cosh_warp(H, tab);
+    D0 = 2.0 * xh;
+    D1 = xh * c;
+    cn = two_cosh_warp(th, tab);
+    C0 = 2.0;
+    C1 = cn;
+  }
+  // node j's term is p_j (T_j C_j) with 2^{-D_j/4096} = p_j T_j: the sum
+  // takes it by one FMA (8 FP64 operations per node); the end terms are
+  // formed once
+  NodeSumC r;
+  double p, q;
+  {
+    double T;
+    exp2s_node_parts(-D0, tab, p, T);
+    q = T * C0;
+    r.first = p * q;
+  }
+  double s = r.first;
+#pragma unroll 2
+  for (int j = 1; j < count; ++j) {
+    const double D2 = fma(c, D1, -D0);
+    D0 = D1;
+    D1 = D2;
+    const double C2 = fma(cn, C1, -C0);
+    C0 = C1;
+    C1 = C2;
+    double T;
+    exp2s_node_parts(-D0, tab, p, T);
+    q = T * C0;
+    s = fma(p, q, s);
+  }
+  r.S = s;
+  r.last = p * q;
+  return r;
+}
+// FP64 ops per node of node_sum_cosh: exp2s_node_parts (4), 1 mul (T C),
+// 1 fma (sum), 2 fma (recurrences).
+constexpr int kNodeOps64Cosh = 8;
+
+// Whether node_sum_cosh may take a window [t0, t1] of N intervals (FP32
+// tests on truncated copies).  Rounding in the C recurrence (each step's,
+// and that of 2 cosh(nu h)) reaches node j amplified by about
+// sum_k (1 - e^{-2 nu h k}) / (2 sinh(nu h)) <= min(j^2 / 2, j / (2 nu h)),
+// so its relative error stays below about u N^2 min(1, 1 / (nu (t1 - t0))),
+// u = 2^-53; the test keeps that under 2^16 u ~ 7e-12 (every window of up to
+// 256 intervals passes).  Range: x cosh t1 <= 690 (cosh t <= (e^t + 1)/2)
+// and nu (t1 - t0) <= 600.  NaN fails.
+__device__ __forceinline__ bool cosh_loop_ok(float x, float nu, float t0, float t1, int N) {
+  const float nw = nu * (t1 - t0), nf = (float)N;
+  constexpr float kLog2ef_ = 1.44269504f;
+  float e1;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e1) : "f"(t1 * kLog2ef_));
+  return nf * nf <= 65536.0f * fmaxf(nw, 1.0f) && nw <= 600.0f && x * (e1 + 1.0f) <= 1380.0f;
+}
+
+// log2 v of a positive finite double to about 1e-6, on the integer, FP32 and
+// MUFU pipes: the exponent field plus lg2 of the leading 23 significand bits.
+__device__ __forceinline__ float log2_f64_approx(double v) {
+  const int hi = __double2hiint(v);
+  const float m = __int_as_float(0x3f800000 | ((hi & 0x000fffff) << 3) |
+                                 (int)((unsigned)__double2loint(v) >> 29));
+  float lm;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lm) : "f"(m));
+  // the unbiased exponent as a float, exactly, by the magic-number trick
+  const float e = __int_as_float(0x4b400000 + ((hi >> 20) & 0x7ff)) - 12583935.0f;
+  return e + lm;
+}
+
 // ln(2 / tol) for the plain form: tol = 1e-13 keeps the quadrature error
 // about three orders below the 1e-10 relative accuracy the form promises.
 constexpr float kPlainLog2OverTol = 30.6267f;
@@ -610,7 +743,8 @@ __device__ __forceinline__ int strip_node_count(float x, float nu, float width, 
 // g(t*) is what the nodes evaluate, in FP64), the ends widened by 2e-5
 // relative and 1e-5 absolute towards their side, far beyond the FP32 error
 // of the roots; cosh t* and e^{t*} in FP64.
-// The ends are then checked in FP64 by the quadrature itself (scale_f64).
+// The ends are then checked on the computed end nodes (scale3_f64; scale_f64
+// widens its ends the same way).
 __device__ __forceinline__ Window64 window_from_start(double x, double nu, const Start32& st,
                                                       const double* __restrict__ tab) {
   Window64 w;
@@ -674,38 +808,76 @@ __device__ __forceinline__ double take_search(const Scaled64& r, double& hS, Tal
   return r.scale;
 }
 
-// The plain form's K_nu in scaled form: returns the scale and sets h S.
-// With FP32 start values (st) the window is taken from them and checked in
-// FP64 on the computed end nodes: exp(g(t1) - g(t*)) <= eps and, for t0 > 0,
-// 2 exp(g(t0) - g(t*)) <= eps (the rule of window_f64, whose F bounds these
-// from above), with a finite positive sum; a window that fails is replaced by
-// the FP64 search (tl.fallback).  Without st, the FP64 search.
+// The plain form's K_nu in scaled form: returns the scale and sets h S
+// (K = e^{scale} h S).  With FP32 start values (st) the window is taken from
+// them (the ends widened as in window_from_start) and checked on the
+// computed end nodes against the rule of window_f64, whose F bounds these
+// from above: e(t1) <= eps and, for t0 > 0, 2 e(t0) <= eps, where e(t) =
+// exp(g(t) - g(t*)) with g(t) = nu t - x cosh t, and a finite positive sum.
+// A window that fails is replaced by the FP64 search (tl.fallback); without
+// st, the FP64 search.
+//  - node_sum_cosh where cosh_loop_ok: scale nu t0 - ln 2.  The check takes
+//    log2 e(t) = log2 f_t - log2(1 + e^{-2 nu t}) - (nu (t* - t0) - x cosh t*)
+//    log2 e from the exact FP64 end terms f_t and FP32 values of the rest
+//    (cosh t* as the FP32 search computed it): error below about 3e-4 in
+//    log2 e, i.e. the thresholds hold to a factor 2^{3e-4}.
+//  - node_sum_f64 elsewhere (centred at t*, cosh t* in FP64): scale
+//    nu t* - x cosh t* - ln 2, the check on its FP64 end values.
 __device__ __forceinline__ double scale_f64(double x, double nu, float log2_over_tol, int n_max,
                                             const double* __restrict__ tab, double& hS,
                                             Tally& tl, const Start32* st = nullptr) {
   constexpr double kEps64 = 0x1p-52;
   if (st == nullptr) return take_search(scaled_search_f64(x, nu, log2_over_tol, n_max, tab), hS, tl);
-  const Window64 w = window_from_start(x, nu, *st, tab);
-  const double width = w.t1 - w.t0;
-  const int N = strip_node_count(f32_trunc(x), f32_trunc(nu), f32_trunc(width), log2_over_tol,
-                                 n_max);
-  bool ok = N <= n_max;
-  NodeSum ns;
-  double h = 0.0;
-  if (ok) {
-    h = width * rcp_nr2((double)N);
-    ns = node_sum_f64(w.t0, h, N + 1, x, nu, w.ts, w.cs, tab);
+  const double t1r = widen_f(st->t1), t0r = widen_f(st->t0);
+  const double t1 = fma(t1r, 2e-5, t1r) + 1e-5;
+  const double t0 = (st->t0 > 0.0f && st->ts > 0.0f) ? fmax(0.0, fma(t0r, -2e-5, t0r) - 1e-5) : 0.0;
+  const double width = t1 - t0;
+  const float xf = f32_trunc(x), nuf = f32_trunc(nu), t0f = f32_trunc(t0), t1f = f32_trunc(t1);
+  const int N = strip_node_count(xf, nuf, f32_trunc(width), log2_over_tol, n_max);
+  if (N <= n_max) {
+    const double h = width * rcp_nr2((double)N);
     tl.nodes += N + 1;
-    // e_last <= eps, (t0 == 0 or 2 e_first <= eps), 0 < S < 1e300, as integer tests
-    ok = bits_le(ns.e_last, kEps64) && (!bits_pos(w.t0) || bits_le(ns.e_first, 0.5 * kEps64)) &&
-         bits_pos(ns.S) && bits_le(ns.S, 1e300);
+    if (cosh_loop_ok(xf, nuf, t0f, t1f, N)) {
+      const NodeSumC ns = node_sum_cosh(t0, h, N + 1, x, nu, tab);
+      constexpr float kL2e = 1.44269504f;
+      const float G = fmaf(nuf, st->ts - t0f, -xf * st->cs) * kL2e;  // log2 of the peak term
+      float w1;
+      asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(w1) : "f"(-2.0f * kL2e * nuf * t1f));
+      float lw1;
+      asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lw1) : "f"(1.0f + w1));
+      bool ok = bits_pos(ns.last) && log2_f64_approx(ns.last) - lw1 - G <= -52.0f &&
+                bits_pos(ns.S) && bits_le(ns.S, 1e300);
+      if (bits_pos(t0)) {
+        float w0, lw0;
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(w0) : "f"(-2.0f * kL2e * nuf * t0f));
+        asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lw0) : "f"(1.0f + w0));
+        ok = ok && bits_pos(ns.first) && log2_f64_approx(ns.first) - lw0 - G <= -53.0f;
+      }
+      if (ok) {
+        hS = h * (ns.S - 0.5 * (ns.first + ns.last));
+        return fma(nu, t0, -kLn2);
+      }
+    } else {
+      Window64 w;
+      w.ts = widen_f(st->ts);  // 0 when the FP32 search found nu^2 <= x
+      if (st->ts > 0.0f) {
+        w.es = exp_tab(w.ts, tab);
+        w.cs = 0.5 * (w.es + rcp_nr2(w.es));
+      } else {
+        w.es = 1.0;
+        w.cs = 1.0;
+      }
+      const NodeSum ns = node_sum_f64(t0, h, N + 1, x, nu, w.ts, w.cs, tab);
+      // e_last <= eps, (t0 == 0 or 2 e_first <= eps), 0 < S < 1e300, as integer tests
+      if (bits_le(ns.e_last, kEps64) && (!bits_pos(t0) || bits_le(ns.e_first, 0.5 * kEps64)) &&
+          bits_pos(ns.S) && bits_le(ns.S, 1e300)) {
+        hS = h * (ns.S - 0.5 * (ns.first + ns.last));
+        return fma(nu, w.ts, -x * w.cs) - kLn2;
+      }
+    }
   }
-  if (!ok) {
-    ++tl.fallback;
-    return take_search(scaled_search_f64(x, nu, log2_over_tol, n_max, tab), hS, tl);
-  }
-  hS = h * (ns.S - 0.5 * (ns.first + ns.last));
-  return fma(nu, w.ts, -x * w.cs) - kLn2;
+  ++tl.fallback;
+  return take_search(scaled_search_f64(x, nu, log2_over_tol, n_max, tab), hS, tl);
 }
 
 // ---------------------------------------------------------------------------

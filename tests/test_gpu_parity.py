@@ -70,6 +70,35 @@ def test_eval_full_size_sampled(dev):
     assert_rel(got[idx], oracle.besselk(x[idx], nu[idx]), K_RTOL)
 
 
+def test_eval_node_loop_regions(dev):
+    """Both quadrature loops of the plain form and the switch between them:
+    the uncentred loop with the cosh(nu t) recurrence (most windows) and the
+    centred loop (x cosh t1 > 690, many nodes at nu (t1 - t0) small, nu
+    (t1 - t0) > 600, the FP64 search).  Beyond the 1e-10 requirement, log K
+    must agree with the oracle to 1e-12 + 2e-15 |log K| (the rounding of a
+    log assembled from terms as large as |log K|), so that an error growing
+    in either recurrence would show."""
+    rng = np.random.default_rng(41)
+    m = 4000
+    sets = {
+        "large x": (np.exp(rng.uniform(np.log(100.0), np.log(3000.0), m)), rng.uniform(0, 30, m)),
+        "small nu": (np.exp(rng.uniform(np.log(1e-4), np.log(2.0), m)), rng.uniform(0, 0.03, m)),
+        "large nu": (np.exp(rng.uniform(np.log(1e-3), np.log(140.0), m)), rng.uniform(10, 40, m)),
+        "region": inputs.kv_pairs(m, seed=42),
+    }
+    for name, (x, nu) in sets.items():
+        for search_f64 in (False, True):
+            _, lout = bk.bk_eval_ex(to_dev(x, dev), to_dev(nu, dev), want_log=True,
+                                    opts=bk.make_opts(search_f64=search_f64))
+            torch.cuda.synchronize()
+            got = lout.cpu().numpy()
+            _, want = oracle.besselk(x, nu, return_log=True)
+            err = np.abs(got - want)
+            bound = 1e-12 + 2e-15 * np.abs(want)
+            i = int(np.argmax(err / bound))
+            assert np.all(err <= bound), (name, search_f64, x[i], nu[i], err[i])
+
+
 def test_eval_domain_edges(dev):
     x = np.array([0.0, -1.0, np.nan, np.inf, 2.0, 2.0, 1e-3, 0.5])
     nu = np.array([1.0, 1.0, 1.0, 1.0, -3.3, np.nan, 20.0, 0.0])
