@@ -44,16 +44,29 @@ __device__ __forceinline__ float f32_trunc(double v) {
   const unsigned r = (e < -126) ? sign : (e > 127) ? big : (sign | ((unsigned)(e + 127) << 23) | mant);
   return __uint_as_float(r);
 }
-// A float as a double by integer operations (exact; denormals, infinities
-// and NaN through the conversion).
+// A float as a double by integer operations only (exact for every input:
+// subnormals are normalised, infinities and NaN payloads kept), so that no
+// conversion is issued on the FP64 pipe.
 __device__ __forceinline__ double widen_f(float f) {
   const unsigned u = (unsigned)__float_as_int(f);
-  const unsigned ex = (u >> 23) & 0xffu;
-  if (ex == 0u && (u & 0x7fffffu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
-  if (ex == 0u || ex == 0xffu) return (double)f;
-  return __hiloint2double(
-      (int)((u & 0x80000000u) | ((ex - 127u + 1023u) << 20) | ((u & 0x7fffffu) >> 3)),
-      (int)(u << 29));
+  const unsigned sign = u & 0x80000000u, ex = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  unsigned hi, lo;
+  if (ex == 0xffu) {  // infinity, NaN
+    hi = sign | 0x7ff00000u | (m >> 3);
+    lo = m << 29;
+  } else if (ex != 0u) {
+    hi = sign | ((ex + 896u) << 20) | (m >> 3);
+    lo = m << 29;
+  } else if (m == 0u) {
+    hi = sign;
+    lo = 0u;
+  } else {  // m 2^-149 with its leading bit at p
+    const int p = 31 - __clz((int)m);
+    const unsigned long long mm = ((unsigned long long)m << (52 - p)) & 0xfffffffffffffULL;
+    hi = sign | ((unsigned)(p - 149 + 1023) << 20) | (unsigned)(mm >> 32);
+    lo = (unsigned)mm;
+  }
+  return __hiloint2double((int)hi, (int)lo);
 }
 
 __device__ __forceinline__ double pow2i(int k) {  // 2^k for k in [-1022, 1023]
@@ -828,14 +841,18 @@ __device__ __forceinline__ double scale_f64(double x, double nu, float log2_over
                                             Tally& tl, const Start32* st = nullptr) {
   constexpr double kEps64 = 0x1p-52;
   if (st == nullptr) return take_search(scaled_search_f64(x, nu, log2_over_tol, n_max, tab), hS, tl);
-  const double t1r = widen_f(st->t1), t0r = widen_f(st->t0);
-  const double t1 = fma(t1r, 2e-5, t1r) + 1e-5;
-  const double t0 = (st->t0 > 0.0f && st->ts > 0.0f) ? fmax(0.0, fma(t0r, -2e-5, t0r) - 1e-5) : 0.0;
-  const double width = t1 - t0;
-  const float xf = f32_trunc(x), nuf = f32_trunc(nu), t0f = f32_trunc(t0), t1f = f32_trunc(t1);
-  const int N = strip_node_count(xf, nuf, f32_trunc(width), log2_over_tol, n_max);
+  // The window's geometry in FP32, taken exactly to FP64: the ends widened by
+  // 2e-5 relative and 1e-5 absolute (as window_from_start), h = (t1 - t0)/N
+  // rounded to a float.  The trapezoid rule of step h over [t0, t0 + N h]
+  // needs nothing more of h: its end node lies within ~1e-7 relative of t1,
+  // inside the widening, and the check reads the computed end terms.
+  const float t1f = fmaf(st->t1, 2e-5f, st->t1) + 1e-5f;
+  const float t0f = (st->t0 > 0.0f && st->ts > 0.0f) ? fmaxf(0.0f, fmaf(st->t0, -2e-5f, st->t0) - 1e-5f)
+                                                     : 0.0f;
+  const float xf = f32_trunc(x), nuf = f32_trunc(nu), wf = t1f - t0f;
+  const int N = strip_node_count(xf, nuf, wf, log2_over_tol, n_max);
   if (N <= n_max) {
-    const double h = width * rcp_nr2((double)N);
+    const double t0 = widen_f(t0f), h = widen_f(__fdividef(wf, (float)N));
     tl.nodes += N + 1;
     if (cosh_loop_ok(xf, nuf, t0f, t1f, N)) {
       const NodeSumC ns = node_sum_cosh(t0, h, N + 1, x, nu, tab);
