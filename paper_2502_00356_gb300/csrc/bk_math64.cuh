@@ -231,20 +231,27 @@ __device__ __forceinline__ double exp2s_node(double u, const double* __restrict_
   return p * __hiloint2double(__double2hiint(tj) + (k << 20), __double2loint(tj));
 }
 
-// exp2s_node split into its polynomial p (|rho| <= 0.53) and the scaled
-// table value T = 2^{k + j/4096}, 2^{u/4096} = p T, for loops that fold the
-// final product into an FMA: 4 FP64 operations.
-__device__ __forceinline__ void exp2s_node_parts(double u, const double* __restrict__ tab,
-                                                 double& p, double& T) {
-  const int hi = __double2hiint(u);
-  const int ex = (hi >> 20) & 0x7ff;
-  const int mant = ((hi & 0x000fffff) << 3) | (int)((unsigned)__double2loint(u) >> 29);
-  const float mag = (ex < 1003) ? 0.0f : (ex > 1044) ? 4.0e6f : __int_as_float(((ex - 896) << 23) | mant);
-  const float uf = __int_as_float(__float_as_int(mag) | (hi & (int)0x80000000));
-  const int n = __float_as_int(uf + 12582912.0f) - 0x4b400000;
-  const double kd = __hiloint2double(0x43380000, n ^ (int)0x80000000) - 0x1.8000080000000p+52;
-  const double rho = u - kd;
-  p = fma(fma(kExpK2, rho, kExpK1), rho, 1.0);
+// 2^{-D/4096} for 0 <= D < 2^22 (a node loop's x cosh t in scaled units),
+// split into its polynomial p and the scaled table value T, 2^{-D/4096} =
+// p T, for loops that fold the final product into an FMA.  m = round(D) is
+// taken exactly from D's 53-bit significand on the integer pipe, rho = D - m
+// (|rho| <= 1/2, exact), p = 1 - K1 rho + K2 rho^2 (relative error below
+// 2.6e-14, as exp2s) and the table index and exponent from -m, so that no
+// negated copy of D is formed: 4 FP64 operations.  Callers keep D below
+// 2^22; a finite D above gives some value below 2^-990 (m is clamped to
+// 2^22), NaN gives NaN.
+__device__ __forceinline__ void exp2s_neg_parts(double D, const double* __restrict__ tab,
+                                                double& p, double& T) {
+  const long long b = __double_as_longlong(D);
+  const int e = (int)((b >> 52) & 0x7ff) - 1023;
+  const long long sig = (b & 0xfffffffffffffLL) | 0x10000000000000LL;
+  const int sh = 52 - min(max(e, -2), 21);  // 31 .. 54 (D < 1/2 gives m = 0)
+  int m = (int)((sig + (1LL << (sh - 1))) >> sh);
+  m = (e > 21) ? (1 << 22) : m;
+  const double kd = __hiloint2double(0x43380000, m ^ (int)0x80000000) - 0x1.8000080000000p+52;
+  const double rho = D - kd;
+  p = fma(fma(kExpK2, rho, -kExpK1), rho, 1.0);
+  const int n = -m;
   const double tj = tab[n & (kExpTabSize - 1)];
   const int k = max(n >> kExpTabBits, -1022);
   T = __hiloint2double(__double2hiint(tj) + (k << 20), __double2loint(tj));
@@ -646,7 +653,7 @@ __device__ __forceinline__ NodeSumC node_sum_cosh(double t_start, double H, int 
   double p, q;
   {
     double T;
-    exp2s_node_parts(-D0, tab, p, T);
+    exp2s_neg_parts(D0, tab, p, T);
     q = T * C0;
     r.first = p * q;
   }
@@ -660,7 +667,7 @@ __device__ __forceinline__ NodeSumC node_sum_cosh(double t_start, double H, int 
     C0 = C1;
     C1 = C2;
     double T;
-    exp2s_node_parts(-D0, tab, p, T);
+    exp2s_neg_parts(D0, tab, p, T);
     q = T * C0;
     s = fma(p, q, s);
   }
@@ -668,7 +675,7 @@ __device__ __forceinline__ NodeSumC node_sum_cosh(double t_start, double H, int 
   r.last = p * q;
   return r;
 }
-// FP64 ops per node of node_sum_cosh: exp2s_node_parts (4), 1 mul (T C),
+// FP64 ops per node of node_sum_cosh: exp2s_neg_parts (4), 1 mul (T C),
 // 1 fma (sum), 2 fma (recurrences).
 constexpr int kNodeOps64Cosh = 8;
 
