@@ -69,6 +69,21 @@ __device__ __forceinline__ double widen_f(float f) {
   return __hiloint2double((int)hi, (int)lo);
 }
 
+// sqrt a for a > 0: an FP32 reciprocal square root of a's leading bits as
+// the seed (relative error ~2^-22), then two Newton-Heron steps in FP64,
+// s <- s + (a - s^2) h with h = 1/(2 s0) from the seed: the error squares
+// to ~2^-44 and then falls below the final rounding (within an ulp).  4 FP64
+// operations; a outside [2^-120, 2^120] takes the library square root.
+__device__ __forceinline__ double sqrt_pos(double a) {
+  const float af = f32_trunc(a);
+  if (!(af >= 0x1p-120f && af <= 0x1p120f)) return sqrt(a);
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(af));
+  const double s0 = widen_f(af * y), h = widen_f(0.5f * y);
+  const double s1 = fma(fma(-s0, s0, a), h, s0);
+  return fma(fma(-s1, s1, a), h, s1);
+}
+
 __device__ __forceinline__ double pow2i(int k) {  // 2^k for k in [-1022, 1023]
   return __hiloint2double((k + 1023) << 20, 0);
 }
@@ -597,16 +612,34 @@ __device__ __forceinline__ NodeSum node_sum_f64(double t_start, double H, int co
 // exp2s_node, 1 fma + 1 add (f, s), 1 fma (recurrence), 1 add + 1 mul.
 constexpr int kNodeOps64 = 6 + kExp2sNodeOps;  // 11
 
-// 2 cosh v for v >= 0: two_cosh_small up to 0.35, e^v + e^{-v} above.  The
-// choice is made once for the active lanes of the warp (a vote): lanes of a
-// warp mostly agree, and a per-lane select would evaluate both sides.
+// 2 cosh v for 0 <= v <= 0.75 from its Taylor series in y = v^2 to y^9
+// (truncation < 2e-18): 10 FP64 ops.
+__device__ __forceinline__ double two_cosh_mid(double v) {
+  const double y = v * v;
+  double p = 2.0 / 6402373705728000.0;
+  p = fma(p, y, 2.0 / 20922789888000.0);
+  p = fma(p, y, 2.0 / 87178291200.0);
+  p = fma(p, y, 2.0 / 479001600.0);
+  p = fma(p, y, 2.0 / 3628800.0);
+  p = fma(p, y, 2.0 / 40320.0);
+  p = fma(p, y, 2.0 / 720.0);
+  p = fma(p, y, 2.0 / 24.0);
+  p = fma(p, y, 1.0);
+  return fma(p, y, 2.0);
+}
+
+// 2 cosh v for v >= 0: two_cosh_small up to 0.35 (8 FP64 ops), two_cosh_mid
+// up to 0.75 (10), e^v + e^{-v} above (13).  The tier is chosen once for the
+// active lanes of the warp (a vote): lanes of a warp mostly agree, and a
+// per-lane select would evaluate several tiers.
 __device__ __forceinline__ double two_cosh_warp(double v, const double* __restrict__ tab) {
-  const bool small = bits_le(v, 0.35);
+  const bool small = bits_le(v, 0.35), mid = bits_le(v, 0.75);
   const unsigned act = __activemask();
   if (__all_sync(act, small)) return two_cosh_small(v);
+  if (__all_sync(act, mid)) return two_cosh_mid(v);
   const double e = exp_acc(v, tab), big = e + rcp_nr2(e);
-  if (!__any_sync(act, small)) return big;
-  return small ? two_cosh_small(v) : big;
+  if (!__any_sync(act, mid)) return big;
+  return mid ? two_cosh_mid(v) : big;
 }
 
 // The same sum without centring, for the checked windows of scale_f64:
