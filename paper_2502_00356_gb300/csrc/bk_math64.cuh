@@ -774,16 +774,23 @@ static __constant__ float kStripMu[16] = {
     6.631101466e-01f, 7.570198201e-01f, 8.532695255e-01f, 9.509323257e-01f};
 
 // Returns N in [2, n_max], or n_max + 1 when the bound asks for more nodes.
+// a / (ln(2/tol) + nu lam(a) + x mu(a)) is quasi-concave in a (a linear
+// numerator over a positive convex denominator), so its samples rise to one
+// maximum and then fall: the scan starts at the widest strip, where the
+// maximum lies for most points (the last or second-to-last sample on the
+// Matern workloads), and stops at the first decrease.  Every a gives a valid
+// bound, so a stop at a rounding-level wiggle can only cost a node, not
+// accuracy.  The index is the same for all lanes still scanning, so the
+// constant-memory reads stay uniform.
 __device__ __forceinline__ int strip_node_count(float x, float nu, float width, float log2_over_tol,
                                                 int n_max) {
-  float bn = 0.0f, bd = 1.0f;
-#pragma unroll
-  for (int k = 0; k < 16; ++k) {
+  float bn = kStripA[15];
+  float bd = fmaf(nu, kStripLam[15], fmaf(x, kStripMu[15], log2_over_tol));
+  for (int k = 14; k >= 0; --k) {
     const float d = fmaf(nu, kStripLam[k], fmaf(x, kStripMu[k], log2_over_tol));
-    if (kStripA[k] * bd > bn * d) {
-      bn = kStripA[k];
-      bd = d;
-    }
+    if (!(kStripA[k] * bd > bn * d)) break;
+    bn = kStripA[k];
+    bd = d;
   }
   const float h = 6.28318531f * bn / bd;
   const float nf = ceilf(width / h);
