@@ -35,19 +35,20 @@ N_LOC, BETA, SIGMA2, NUS, SEED = 20_000, 0.1, 1.0, (0.5, 1.5, 2.3), 2
 WORKLOAD = "matern_jittered_grid_n20000_beta0.1_nu{0.5,1.5,2.3}_fp64"
 
 # FP64 work model of the plain form in FP64 arithmetic operations (one per
-# thread and DFMA/DADD/DMUL): 8 per quadrature node of the common loop (the
-# table exponential's 4, its product with the cosh(nu t) factor, the
-# summing FMA and the two three-term recurrences; windows outside that loop's
-# conditions take 11 and are counted at 8), per FP64 peak Newton iteration
-# and per FP64 window-end Newton iteration (these run only for windows the
-# check rejects, or outside the FP32 search region), and a fixed part per
-# Matern entry (distance, square root, window ends, step, set-ups, log x and
-# the final exponential).  The fixed part is ncu's executed DFMA + DADD + DMUL
-# per entry minus 8 x nodes per entry on the n = 6000 case of the same kernel
+# thread and DFMA/DADD/DMUL): 6 per quadrature node of the common loop (the
+# table exponential's polynomial, 2, with its rounding and remainder on the
+# integer pipe; its product with the cosh(nu t) factor; the summing FMA; the
+# two three-term recurrences; windows outside that loop's conditions take 11
+# and are counted at 6), per FP64 peak Newton iteration and per FP64
+# window-end Newton iteration (these run only for windows the check rejects,
+# or outside the FP32 search region), and a fixed part per Matern entry
+# (distance, square root, set-ups, end terms, log x and the final
+# exponential).  The fixed part is ncu's executed DFMA + DADD + DMUL per
+# entry minus 6 x nodes per entry on the n = 6000 case of the same kernel
 # (54, 55, 56 for nu = 0.5, 1.5, 2.3; the mean).  The FP32 Newton iterations
 # that place the window and the FP32 window check run on the FP32/MUFU pipes
 # and are not counted.
-OPS_NODE, OPS_PEAK_IT, OPS_WIN_IT, OPS_ENTRY_FIXED = 8, 54, 31, 55
+OPS_NODE, OPS_PEAK_IT, OPS_WIN_IT, OPS_ENTRY_FIXED = 6, 54, 31, 55
 # FP64 pipe peak from the unit count and clock: 152 SMs x 2 DFMA/clk x 2.07 GHz
 # (1.26 TFLOP/s counting an FMA as two FLOPs).
 FP64_PEAK_GOPS = 152 * 2 * 2.07e9 / 1e9

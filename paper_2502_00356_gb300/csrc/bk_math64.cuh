@@ -248,23 +248,40 @@ __device__ __forceinline__ double exp2s_node(double u, const double* __restrict_
 
 // 2^{-D/4096} for 0 <= D < 2^22 (a node loop's x cosh t in scaled units),
 // split into its polynomial p and the scaled table value T, 2^{-D/4096} =
-// p T, for loops that fold the final product into an FMA.  m = round(D) is
-// taken exactly from D's 53-bit significand on the integer pipe, rho = D - m
-// (|rho| <= 1/2, exact), p = 1 - K1 rho + K2 rho^2 (relative error below
-// 2.6e-14, as exp2s) and the table index and exponent from -m, so that no
-// negated copy of D is formed: 4 FP64 operations.  Callers keep D below
-// 2^22; a finite D above gives some value below 2^-990 (m is clamped to
-// 2^22), NaN gives NaN.
+// p T, for loops that fold the final product into an FMA.  The rounding
+// m = round(D) and the remainder rho = D - m (|rho| <= 1/2) are both taken
+// exactly from D's 53-bit significand on the integer pipe: with sh the
+// position of D's binary point in it, m = (sig + 2^(sh-1)) >> sh and
+// rho 2^sh = ((sig + 2^(sh-1)) mod 2^sh) - 2^(sh-1), an integer below 2^53
+// in magnitude that is normalised into a double by its leading-bit position.
+// p = 1 - K1 rho + K2 rho^2 (relative error below 2.6e-14, as exp2s) is then
+// the only FP64 work: 2 operations.  The table index and exponent come from
+// -m, so that no negated copy of D is formed.  Callers keep D below 2^22; a
+// finite D above gives some value below 2^-990 (m is clamped to 2^22), NaN
+// gives NaN.
 __device__ __forceinline__ void exp2s_neg_parts(double D, const double* __restrict__ tab,
                                                 double& p, double& T) {
   const long long b = __double_as_longlong(D);
   const int e = (int)((b >> 52) & 0x7ff) - 1023;
   const long long sig = (b & 0xfffffffffffffLL) | 0x10000000000000LL;
   const int sh = 52 - min(max(e, -2), 21);  // 31 .. 54 (D < 1/2 gives m = 0)
-  int m = (int)((sig + (1LL << (sh - 1))) >> sh);
-  m = (e > 21) ? (1 << 22) : m;
-  const double kd = __hiloint2double(0x43380000, m ^ (int)0x80000000) - 0x1.8000080000000p+52;
-  const double rho = D - kd;
+  const long long half = 1LL << (sh - 1);
+  const long long t = sig + half;
+  int m = (int)(t >> sh);
+  const long long R = (t & ((half << 1) - 1)) - half;  // rho 2^sh
+  // R as a double times 2^-sh: sign, leading-bit position L of |R| (L <= 53),
+  // the bits below it as the significand
+  const unsigned long long A = (unsigned long long)(R < 0 ? -R : R);
+  const int L = 63 - __clzll((long long)A);
+  const unsigned long long frac = (L <= 52) ? ((A << (52 - L)) & 0xfffffffffffffULL) : 0ULL;
+  const unsigned long long rb = ((unsigned long long)(R < 0) << 63) |
+                                ((unsigned long long)(L - sh + 1023) << 52) | frac;
+  double rho = (A == 0ULL) ? 0.0 : __longlong_as_double((long long)rb);
+  rho = (e < -2) ? D : rho;  // D < 1/4 (and 0): m = 0, rho = D
+  if (e > 21) {              // out of range for the callers: clamp, keep NaN
+    m = 1 << 22;
+    rho = D;
+  }
   p = fma(fma(kExpK2, rho, -kExpK1), rho, 1.0);
   const int n = -m;
   const double tj = tab[n & (kExpTabSize - 1)];
@@ -680,7 +697,7 @@ __device__ __forceinline__ NodeSumC node_sum_cosh(double t_start, double H, int 
     C1 = cn;
   }
   // node j's term is p_j (T_j C_j) with 2^{-D_j/4096} = p_j T_j: the sum
-  // takes it by one FMA (8 FP64 operations per node); the end terms are
+  // takes it by one FMA (6 FP64 operations per node); the end terms are
   // formed once
   NodeSumC r;
   double p, q;
@@ -708,9 +725,9 @@ __device__ __forceinline__ NodeSumC node_sum_cosh(double t_start, double H, int 
   r.last = p * q;
   return r;
 }
-// FP64 ops per node of node_sum_cosh: exp2s_neg_parts (4), 1 mul (T C),
+// FP64 ops per node of node_sum_cosh: exp2s_neg_parts (2), 1 mul (T C),
 // 1 fma (sum), 2 fma (recurrences).
-constexpr int kNodeOps64Cosh = 8;
+constexpr int kNodeOps64Cosh = 6;
 
 // Whether node_sum_cosh may take a window [t0, t1] of N intervals (FP32
 // tests on truncated copies).  Rounding in the C recurrence (each step's,
