@@ -38,7 +38,7 @@ WORKLOAD = "matern_jittered_grid_n20000_beta0.1_nu{0.5,1.5,2.3}_fp64"
 # thread and DFMA/DADD/DMUL): 6 per quadrature node of the common loop (the
 # table exponential's polynomial, 2, with its rounding and remainder on the
 # integer pipe; its product with the cosh(nu t) factor; the summing FMA; the
-# two three-term recurrences; windows outside that loop's conditions take 11
+# two three-term recurrences; windows outside that loop's conditions take 9
 # and are counted at 6), per FP64 peak Newton iteration and per FP64
 # window-end Newton iteration (these run only for windows the check rejects,
 # or outside the FP32 search region), and a fixed part per Matern entry

@@ -218,28 +218,51 @@ __device__ __forceinline__ double exp2s(double u, const double* __restrict__ tab
   return p * __hiloint2double(__double2hiint(tj) + (k << 20), __double2loint(tj));
 }
 
+// For 0 <= v < 2^22: M = round(v) and rho = v - M (|rho| <= 1/2), both
+// exact and on the integer pipe.  With sh the position of v's binary point
+// in its 53-bit significand sig, M = (sig + 2^(sh-1)) >> sh and
+// rho 2^sh = ((sig + 2^(sh-1)) mod 2^sh) - 2^(sh-1), an integer below 2^53 in
+// magnitude, normalised into a double by its leading-bit position.  v < 1/4
+// (and 0) gives M = 0, rho = v.  Out of range (v >= 2^22) gives
+// M = 4,000,000 and rho = v, so that exp2s_node stays finite for finite
+// arguments; NaN gives rho = NaN.
+__device__ __forceinline__ void round_rem(double v, int& M, double& rho) {
+  const long long b = __double_as_longlong(v);
+  const int e = (int)((b >> 52) & 0x7ff) - 1023;
+  const long long sig = (b & 0xfffffffffffffLL) | 0x10000000000000LL;
+  const int sh = 52 - min(max(e, -2), 21);  // 31 .. 54
+  const long long half = 1LL << (sh - 1);
+  const long long t = sig + half;
+  M = (int)(t >> sh);
+  const long long R = (t & ((half << 1) - 1)) - half;  // rho 2^sh
+  const unsigned long long A = (unsigned long long)(R < 0 ? -R : R);
+  const int L = 63 - __clzll((long long)A);  // leading bit (L <= 53)
+  const unsigned long long frac = (L <= 52) ? ((A << (52 - L)) & 0xfffffffffffffULL) : 0ULL;
+  const unsigned long long rb = ((unsigned long long)(R < 0) << 63) |
+                                ((unsigned long long)(L - sh + 1023) << 52) | frac;
+  rho = (A == 0ULL) ? 0.0 : __longlong_as_double((long long)rb);
+  rho = (e < -2) ? v : rho;
+  if (e > 21) {
+    M = 4000000;
+    rho = v;
+  }
+}
+
 // exp2s for the node loops (every node exponent of an eps-window has
-// |u| < 3e5): the nearest integer n of u is found on the FP32 and integer
-// pipes from u's leading 23 significand bits (a float built from the bit
-// pattern, rounded with the float magic number 1.5 2^23), and only kd = n
-// (rebuilt exactly from the integer by one FP64 subtraction) and rho = u - kd
-// use the FP64 pipe: 5 FP64 operations instead of 6.  The float's truncation
-// can put n off the nearest integer by up to a float ulp (1/32 at |u| < 2^18):
-// |rho| <= 0.53 keeps the polynomial's error below 3e-14.  |u| >= 2^22 is
-// clamped to 4e6 on the integer side (a result of about 2^-977 for negative
-// u; NaN stays NaN through rho).
-constexpr int kExp2sNodeOps = 5;
+// |u| < 3e5): the nearest integer n of u and rho = u - n come from round_rem
+// of |u| on the integer pipe (signs restored by integer operations), so that
+// only the polynomial and the final product use the FP64 pipe: 3 FP64
+// operations instead of 6.  |u| >= 2^22 gives some finite value (about
+// 2^{+-976}); NaN stays NaN.
+constexpr int kExp2sNodeOps = 3;
 __device__ __forceinline__ double exp2s_node(double u, const double* __restrict__ tab) {
-  const int hi = __double2hiint(u);
-  const int ex = (hi >> 20) & 0x7ff;  // biased exponent of u
-  const int mant = ((hi & 0x000fffff) << 3) | (int)((unsigned)__double2loint(u) >> 29);
-  const float mag = (ex < 1003) ? 0.0f                                // |u| < 2^-20: n = 0
-                    : (ex > 1044) ? 4.0e6f                            // |u| >= 2^22: clamp
-                                  : __int_as_float(((ex - 896) << 23) | mant);
-  const float uf = __int_as_float(__float_as_int(mag) | (hi & (int)0x80000000));
-  const int n = __float_as_int(uf + 12582912.0f) - 0x4b400000;  // round to nearest
-  const double kd = __hiloint2double(0x43380000, n ^ (int)0x80000000) - 0x1.8000080000000p+52;
-  const double rho = u - kd;
+  const long long ub = __double_as_longlong(u);
+  int M;
+  double r;
+  round_rem(__longlong_as_double(ub & 0x7fffffffffffffffLL), M, r);
+  const bool neg = ub < 0;
+  const int n = neg ? -M : M;
+  const double rho = __longlong_as_double(__double_as_longlong(r) ^ (ub & (long long)0x8000000000000000ULL));
   const double p = fma(fma(kExpK2, rho, kExpK1), rho, 1.0);
   const double tj = tab[n & (kExpTabSize - 1)];
   const int k = max(n >> kExpTabBits, -1022);
@@ -627,7 +650,7 @@ __device__ __forceinline__ NodeSum node_sum_f64(double t_start, double H, int co
 }
 // FP64 ops per node in node_sum_f64 (work accounting): 1 sub (exponent),
 // exp2s_node, 1 fma + 1 add (f, s), 1 fma (recurrence), 1 add + 1 mul.
-constexpr int kNodeOps64 = 6 + kExp2sNodeOps;  // 11
+constexpr int kNodeOps64 = 6 + kExp2sNodeOps;  // 9
 
 // 2 cosh v for 0 <= v <= 0.75 from its Taylor series in y = v^2 to y^9
 // (truncation < 2e-18): 10 FP64 ops.
@@ -664,11 +687,13 @@ __device__ __forceinline__ double two_cosh_warp(double v, const double* __restri
 //   C_j = e^{nu (t_j - t_start)} (1 + e^{-2 nu t_j}) = 2 e^{-nu t_start} cosh(nu t_j),
 // where C_j follows its own three-term recurrence C_{j+1} = 2 cosh(nu H) C_j
 // - C_{j-1}.  A node costs the exponential of -D_j, its product with C_j,
-// the sum and the two recurrences: 8 FP64 operations instead of 11, and the
-// set-up needs neither cosh t* nor the centring exponentials.  Each factor must stay in
-// the double range on its own, x cosh t_j <= 690 (exp2s_node's argument
-// below 2^22) and nu (t_j - t_start) <= 600, and the C recurrence amplifies
-// rounding with the node count; cosh_loop_ok states the conditions.  Returns S = sum_j e^{-x cosh t_j} C_j and the end terms.
+// the sum and the two recurrences: 6 FP64 operations instead of the
+// centred loop's 9, and the set-up needs neither cosh t* nor the centring
+// exponentials.  Each factor must stay in the double range on its own,
+// x cosh t_j <= 690 (the exponential's argument below 2^22) and
+// nu (t_j - t_start) <= 600, and the C recurrence amplifies rounding with the
+// node count; cosh_loop_ok states the conditions.  Returns
+// S = sum_j e^{-x cosh t_j} C_j and the end terms.
 struct NodeSumC {
   double S, first, last;
 };

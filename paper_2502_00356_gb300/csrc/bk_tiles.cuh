@@ -124,7 +124,7 @@ __device__ __forceinline__ int64_t sorted_pair(const double* __restrict__ x,
 // by cost (sorted_pair); the FP32 forms, whose lanes diverge less and whose
 // evaluations are short, take the pairs in order.
 template <class Form, typename OutT>
-__global__ void __launch_bounds__(128) eval_kernel(const Form form, const double* __restrict__ x,
+__global__ void __launch_bounds__(128, 6) eval_kernel(const Form form, const double* __restrict__ x,
                                                    const double* __restrict__ nu,
                                                    OutT* __restrict__ out,
                                                    OutT* __restrict__ log_out, int64_t n,
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(128) eval_kernel(const Form form, const double
 // NaN), x = +inf gives (0, 0, 0), x < 0 or NaN and non-finite nu give NaN;
 // dK/dnu is odd in nu (K_{-nu} = K_nu).  Null outputs are skipped.
 template <class Form>
-__global__ void __launch_bounds__(128) eval_grad_kernel(const Form form, const double* __restrict__ x,
+__global__ void __launch_bounds__(128, 4) eval_grad_kernel(const Form form, const double* __restrict__ x,
                                                         const double* __restrict__ nu,
                                                         double* __restrict__ k,
                                                         double* __restrict__ dkdx,
