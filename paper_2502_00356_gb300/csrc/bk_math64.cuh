@@ -318,17 +318,15 @@ __device__ __forceinline__ double exp_tab(double a, const double* __restrict__ t
   return exp2s(a * kExpScale, tab);
 }
 
-// e^a over the whole double range (NaN -> NaN, overflow -> inf, deep
-// underflow -> 0) for the final normalisation, with an exact reduction:
-// kd = round(a K), r = a - kd ln2/4096 with ln2/4096 split in two (kd times
-// the 29-bit head is exact for |kd| < 2^23), e^r from its Taylor polynomial
-// of degree 3 (|r| <= 8.5e-5, truncation < 3e-18 relative), times the table
-// entry 2^{(kd mod 4096)/4096} and 2^{floor(kd/4096)}.  |a| >= 708 goes to
-// exp_full.  FP64 ops: 1 fma + 1 sub (rounding), 2 fma (reduction),
-// 3 fma (polynomial), 1 mul.
-// The same for |a| < 708 without the range test: the accurate exponential of
+// e^a for |a| < 708 with an exact reduction: kd = round(a K),
+// r = a - kd ln2/4096 with ln2/4096 split in two (kd times the 29-bit head is
+// exact for |kd| < 2^23), e^r from its Taylor polynomial of degree 3
+// (|r| <= 8.5e-5, truncation < 3e-18 relative), times the table entry
+// 2^{(kd mod 4096)/4096} and 2^{floor(kd/4096)}: the accurate exponential of
 // the set-up values of the node recurrences (e^{t0}, e^{h}, e^{-2 nu h}, ...),
 // whose relative errors the recurrences multiply by up to the node count.
+// FP64 ops: 1 fma + 1 sub (rounding), 2 fma (reduction), 3 fma
+// (polynomial), 1 mul.
 __device__ __forceinline__ double exp_acc(double a, const double* __restrict__ tab) {
   const double v = fma(a, kExpScale, kRoundMagic);
   const int n = __double2loint(v);
@@ -341,25 +339,40 @@ __device__ __forceinline__ double exp_acc(double a, const double* __restrict__ t
   return p * __hiloint2double(__double2hiint(tj) + (k << 20), __double2loint(tj));
 }
 
+// 2^{u/4096} for |u| < 2^22 with e^r from its Taylor cubic (|r| <= 8.5e-5,
+// truncation < 3e-18 relative): the rounding and remainder of u on the
+// integer pipe (round_rem, signs restored by integer operations), then 4 FP64
+// operations.
+__device__ __forceinline__ double exp2s_cubic(double u, const double* __restrict__ tab) {
+  const long long ub = __double_as_longlong(u);
+  int M;
+  double r;
+  round_rem(__longlong_as_double(ub & 0x7fffffffffffffffLL), M, r);
+  const int n = (ub < 0) ? -M : M;
+  const double rho =
+      __longlong_as_double(__double_as_longlong(r) ^ (ub & (long long)0x8000000000000000ULL));
+  const double p = fma(fma(fma(kExpC3, rho, kExpK2), rho, kExpC1), rho, 1.0);
+  const double tj = tab[n & (kExpTabSize - 1)];
+  const int k = max(n >> kExpTabBits, -1022);
+  return p * __hiloint2double(__double2hiint(tj) + (k << 20), __double2loint(tj));
+}
+
+// e^a over the whole double range for the final normalisations: u = a K
+// rounded to a double, then exp2s_cubic.  The rounding of u costs at most
+// |a| 2^-53 relative, the same order as the rounding a itself carries from
+// the sums that formed it: 5 FP64 operations.  |a| >= 708 goes to exp_full
+// (NaN -> NaN, overflow -> inf, deep underflow -> 0).
 __device__ __forceinline__ double exp_tab_full(double a, const double* __restrict__ tab) {
-  const double v = fma(a, kExpScale, kRoundMagic);
   if (!((__double_as_longlong(a) & 0x7fffffffffffffffLL) < 0x4086200000000000LL))  // |a| < 708
     return exp_full(a);
-  const int n = __double2loint(v);
-  const double kd = v - kRoundMagic;
-  double r = fma(-kd, kExpC1Hi, a);
-  r = fma(-kd, kExpC1Lo, r);
-  const double p = fma(fma(fma(r, 1.0 / 6.0, 0.5), r, 1.0), r, 1.0);
-  const double tj = tab[n & (kExpTabSize - 1)];
-  const int k = n >> kExpTabBits;
-  return p * __hiloint2double(__double2hiint(tj) + (k << 20), __double2loint(tj));
+  return exp2s_cubic(a * kExpScale, tab);
 }
 
 // log a for finite a > 0 with the same table: a = 2^e m, m in [1, 2); j =
 // round(4096 log2 m) from the FP32 hardware log of m's leading bits, so that
 // m 2^{-j/4096} = 1 + d with |d| <= 8.5e-5; log a = (4096 e + j) ln2/4096 +
 // log1p(d), log1p from its series to d^3 (truncation < 2e-17 absolute).
-// FP64 ops: 1 fma (d), 3 (series), 2 fma (assembly) and one int conversion.
+// FP64 ops: 1 fma (d), 3 (series), 1 fma (assembly).
 __device__ __forceinline__ double log_tab(double a, const double* __restrict__ tab) {
   int hi = __double2hiint(a);
   int lo = __double2loint(a);
@@ -383,8 +396,11 @@ __device__ __forceinline__ double log_tab(double a, const double* __restrict__ t
       __hiloint2double(__double2hiint(tj) - (j > 0 ? (1 << 20) : 0), __double2loint(tj));
   const double d = fma(m, tinv, -1.0);
   const double l1p = fma(d * d, fma(d, 1.0 / 3.0, -0.5), d);
-  const double nd = (double)(e * kExpTabSize + j);
-  return fma(nd, kExpC1Hi, fma(nd, kExpC1Lo, l1p));
+  // 4096 e + j as a double without an FP64-pipe conversion (|.| < 2^23 is
+  // exact in a float); one FMA with ln2/4096 rounded (error below |log a|
+  // 2^-53, the order of the result's own rounding)
+  const double nd = widen_f(__int2float_rn(e * kExpTabSize + j));
+  return fma(nd, kExpC1, l1p);
 }
 
 // 1/a from the hardware approximation refined by Newton-Raphson steps
@@ -579,13 +595,14 @@ __device__ __forceinline__ Window64 window_f64(double x, double nu, double L,
 }
 
 // 2 cosh H for 0 <= H <= 0.35 from its Taylor series in y = H^2 to y^7
-// (truncation < 1e-20): 8 FP64 ops, correctly rounded to about an ulp.
+// (truncation < 1e-20), correctly rounded to about an ulp.  The terms from
+// y^5 on (below 1.6e-11) are summed in FP32 (their rounding is below 1e-18):
+// 6 FP64 operations.
 __device__ __forceinline__ double two_cosh_small(double H) {
   const double y = H * H;
-  double p = 2.0 / 87178291200.0;
-  p = fma(p, y, 2.0 / 479001600.0);
-  p = fma(p, y, 2.0 / 3628800.0);
-  p = fma(p, y, 2.0 / 40320.0);
+  const float yf = f32_trunc(y);
+  const float q = fmaf(fmaf(yf, 2.0f / 87178291200.0f, 2.0f / 479001600.0f), yf, 2.0f / 3628800.0f);
+  double p = fma(widen_f(q), y, 2.0 / 40320.0);
   p = fma(p, y, 2.0 / 720.0);
   p = fma(p, y, 2.0 / 24.0);
   p = fma(p, y, 1.0);
@@ -653,14 +670,15 @@ __device__ __forceinline__ NodeSum node_sum_f64(double t_start, double H, int co
 constexpr int kNodeOps64 = 6 + kExp2sNodeOps;  // 9
 
 // 2 cosh v for 0 <= v <= 0.75 from its Taylor series in y = v^2 to y^9
-// (truncation < 2e-18): 10 FP64 ops.
+// (truncation < 2e-18); the terms from y^6 on (below 1.3e-10) in FP32: 7 FP64
+// operations.
 __device__ __forceinline__ double two_cosh_mid(double v) {
   const double y = v * v;
-  double p = 2.0 / 6402373705728000.0;
-  p = fma(p, y, 2.0 / 20922789888000.0);
-  p = fma(p, y, 2.0 / 87178291200.0);
-  p = fma(p, y, 2.0 / 479001600.0);
-  p = fma(p, y, 2.0 / 3628800.0);
+  const float yf = f32_trunc(y);
+  float q = fmaf(yf, 2.0f / 6402373705728000.0f, 2.0f / 20922789888000.0f);
+  q = fmaf(q, yf, 2.0f / 87178291200.0f);
+  q = fmaf(q, yf, 2.0f / 479001600.0f);
+  double p = fma(widen_f(q), y, 2.0 / 3628800.0);
   p = fma(p, y, 2.0 / 40320.0);
   p = fma(p, y, 2.0 / 720.0);
   p = fma(p, y, 2.0 / 24.0);
@@ -668,8 +686,8 @@ __device__ __forceinline__ double two_cosh_mid(double v) {
   return fma(p, y, 2.0);
 }
 
-// 2 cosh v for v >= 0: two_cosh_small up to 0.35 (8 FP64 ops), two_cosh_mid
-// up to 0.75 (10), e^v + e^{-v} above (13).  The tier is chosen once for the
+// 2 cosh v for v >= 0: two_cosh_small up to 0.35 (6 FP64 ops), two_cosh_mid
+// up to 0.75 (7), e^v + e^{-v} above (13).  The tier is chosen once for the
 // active lanes of the warp (a vote): lanes of a warp mostly agree, and a
 // per-lane select would evaluate several tiers.
 __device__ __forceinline__ double two_cosh_warp(double v, const double* __restrict__ tab) {
@@ -961,7 +979,7 @@ __device__ __forceinline__ double scale_f64(double x, double nu, float log2_over
       }
       if (ok) {
         hS = h * (ns.S - 0.5 * (ns.first + ns.last));
-        return fma(nu, t0, -kLn2);
+        return bits_pos(t0) ? fma(nu, t0, -kLn2) : -kLn2;
       }
     } else {
       Window64 w;
