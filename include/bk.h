@@ -340,6 +340,27 @@ bk_status bk_gaussian_loglik(double* a, int64_t n, int64_t ld, const double* z, 
 bk_status bk_probe_pipe(int kind, int64_t iters, int grid, int block, double* sink,
                         bk_stream_t stream);
 
+/*
+ * bk_math_probe: evaluates one of the plain form's device math helpers on n
+ * inputs, as the kernels compute it (a test hook for those helpers, not part
+ * of the paper's method).  fn:
+ *   0  e^a by the final normalisations' exponential (any a; |a| >= 708 takes
+ *      the range-checked path)
+ *   1  log a for finite a > 0 (subnormals included)
+ *   2  2^{u/4096} by the centred node loop's exponential, |u| < 2^22
+ *   3  2^{-D/4096} by the uncentred node loop's exponential, 0 <= D < 2^22
+ *   4  round(v) and v - round(v) for 0 <= v < 2^22 (halves round up), taken
+ *      on the integer pipe: out[2i] = round(v), out[2i + 1] = the remainder
+ *   5  2 cosh v for v >= 0 (the series tiers and the exponential path)
+ *   6  sqrt a for a > 0
+ *   7  e^a by the accurate set-up exponential, |a| < 708
+ * in: device, n doubles; out: device, n doubles (2n for fn 4).  Inputs
+ * outside a function's stated domain give unspecified values (no fault).
+ * Errors: BK_ERR_INVALID_ARG for an unknown fn, n < 0 or null pointers with
+ * n > 0.
+ */
+bk_status bk_math_probe(int fn, const double* in, double* out, int64_t n, bk_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

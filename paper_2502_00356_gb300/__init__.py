@@ -33,7 +33,7 @@ BK_NUM_COUNTERS = 8
 EXPORTS = (
     "bk_opts_default", "bk_version", "bk_last_error", "bk_status_string", "bk_sync",
     "bk_eval", "bk_eval_ex", "bk_eval_grad", "bk_gaussian_loglik", "bk_matern_tile", "bk_matern_tile_ex", "bk_matern_tile2",
-    "bk_morton_order", "bk_probe_pipe", "bk_batched_plan_create", "bk_batched_plan_destroy",
+    "bk_morton_order", "bk_probe_pipe", "bk_math_probe", "bk_batched_plan_create", "bk_batched_plan_destroy",
     "bk_batched_plan_info", "bk_batched_autotune", "bk_matern_batched",
     "bk_matern_batched_static", "bk_learned_create", "bk_learned_destroy", "bk_learned_train",
     "bk_learned_grad", "bk_learned_infer", "bk_learned_params", "bk_learned_stats",
@@ -94,6 +94,7 @@ def lib() -> ctypes.CDLL:
             "bk_matern_tile2": (I, [P, I64, P, I64, D, D, D, P, I64, I, P, P]),
             "bk_morton_order": (I, [P, I64, P]),
             "bk_probe_pipe": (I, [I, I64, I, I, P, P]),
+            "bk_math_probe": (I, [I, P, P, I64, P]),
             "bk_batched_plan_create": (I, [P, P, ctypes.c_int32, I, P]),
             "bk_batched_plan_destroy": (I, [P]),
             "bk_batched_plan_info": (I, [P, P, P, P, P, P]),
@@ -386,6 +387,24 @@ def bk_probe_pipe(kind: int, iters: int, grid: int, block: int, sink, stream=Non
     _check(lib().bk_probe_pipe(int(kind), int(iters), int(grid), int(block), _ptr(sink),
                                _stream_ptr(stream)))
     return grid * block * iters * 8
+
+
+MATH_PROBE_FNS = {"exp": 0, "log": 1, "exp2s_node": 2, "exp2s_neg": 3, "round_rem": 4,
+                  "two_cosh": 5, "sqrt": 6, "exp_acc": 7}
+
+
+def bk_math_probe(fn, x, stream=None):
+    """Evaluate one of the plain form's device math helpers (MATH_PROBE_FNS)
+    on a CUDA float64 tensor; "round_rem" returns an (n, 2) tensor of
+    (round(v), v - round(v))."""
+    torch = _torch()
+    _dev(x, "x", torch.float64)
+    k = MATH_PROBE_FNS[fn] if isinstance(fn, str) else int(fn)
+    x = x.contiguous()
+    n = x.numel()
+    out = torch.empty(2 * n if k == 4 else n, dtype=torch.float64, device=x.device)
+    _check(lib().bk_math_probe(k, _ptr(x), _ptr(out), n, _stream_ptr(stream)))
+    return out.view(n, 2) if k == 4 else out.view(x.shape)
 
 
 # ---------------------------------------------------------------------------

@@ -252,8 +252,9 @@ __device__ __forceinline__ void round_rem(double v, int& M, double& rho) {
 // |u| < 3e5): the nearest integer n of u and rho = u - n come from round_rem
 // of |u| on the integer pipe (signs restored by integer operations), so that
 // only the polynomial and the final product use the FP64 pipe: 3 FP64
-// operations instead of 6.  |u| >= 2^22 gives some finite value (about
-// 2^{+-976}); NaN stays NaN.
+// operations instead of 6.  Accurate for u in [-1022 * 4096, 1023 * 4096];
+// below, the exponent is clamped at -1022 (a result near 2^-1022), and
+// |u| >= 2^22 gives some finite value (about 2^{+-976}); NaN stays NaN.
 constexpr int kExp2sNodeOps = 3;
 __device__ __forceinline__ double exp2s_node(double u, const double* __restrict__ tab) {
   const long long ub = __double_as_longlong(u);
@@ -279,9 +280,11 @@ __device__ __forceinline__ double exp2s_node(double u, const double* __restrict_
 // in magnitude that is normalised into a double by its leading-bit position.
 // p = 1 - K1 rho + K2 rho^2 (relative error below 2.6e-14, as exp2s) is then
 // the only FP64 work: 2 operations.  The table index and exponent come from
-// -m, so that no negated copy of D is formed.  Callers keep D below 2^22; a
-// finite D above gives some value below 2^-990 (m is clamped to 2^22), NaN
-// gives NaN.
+// -m, so that no negated copy of D is formed.  Accurate for D <= 1022 * 4096
+// (results down to 2^-1022; the node loops keep D below 4.08e6); above, the
+// exponent is clamped at -1022 (a result near 2^-1022, not garbage), and a
+// finite D >= 2^22 gives some value below 2^-990 (m is clamped to 2^22).
+// NaN gives NaN.
 __device__ __forceinline__ void exp2s_neg_parts(double D, const double* __restrict__ tab,
                                                 double& p, double& T) {
   const long long b = __double_as_longlong(D);
@@ -358,9 +361,9 @@ __device__ __forceinline__ double exp2s_cubic(double u, const double* __restrict
 }
 
 // e^a over the whole double range for the final normalisations: u = a K
-// rounded to a double, then exp2s_cubic.  The rounding of u costs at most
-// |a| 2^-53 relative, the same order as the rounding a itself carries from
-// the sums that formed it: 5 FP64 operations.  |a| >= 708 goes to exp_full
+// rounded to a double, then exp2s_cubic.  The roundings of u and of K cost
+// at most 1.3e-16 |a| relative, the order of the rounding a itself carries
+// from the sums that formed it: 5 FP64 operations.  |a| >= 708 goes to exp_full
 // (NaN -> NaN, overflow -> inf, deep underflow -> 0).
 __device__ __forceinline__ double exp_tab_full(double a, const double* __restrict__ tab) {
   if (!((__double_as_longlong(a) & 0x7fffffffffffffffLL) < 0x4086200000000000LL))  // |a| < 708

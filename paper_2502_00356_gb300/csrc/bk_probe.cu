@@ -7,6 +7,7 @@
 #include <cstdint>
 
 #include "bk_internal.h"
+#include "bk_math64.cuh"
 
 namespace bk {
 namespace {
@@ -101,6 +102,39 @@ __global__ void probe_cvt32(int64_t iters, double* sink) {
   sink[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// The plain form's math helpers on an array of inputs (bk_math_probe), with
+// the exponential table read from global memory.
+__global__ void math_probe_kernel(int fn, const double* __restrict__ in, double* __restrict__ out,
+                                  int64_t n) {
+  const double* tab = kExp2Tab;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const double v = in[i];
+    switch (fn) {
+      case 0: out[i] = exp_tab_full(v, tab); break;
+      case 1: out[i] = log_tab(v, tab); break;
+      case 2: out[i] = exp2s_node(v, tab); break;
+      case 3: {
+        double p, T;
+        exp2s_neg_parts(v, tab, p, T);
+        out[i] = p * T;
+        break;
+      }
+      case 4: {
+        int M;
+        double r;
+        round_rem(v, M, r);
+        out[2 * i] = (double)M;
+        out[2 * i + 1] = r;
+        break;
+      }
+      case 5: out[i] = two_cosh_warp(v, tab); break;
+      case 6: out[i] = sqrt_pos(v); break;
+      default: out[i] = exp_acc(v, tab); break;
+    }
+  }
+}
+
 }  // namespace
 }  // namespace bk
 
@@ -119,4 +153,17 @@ extern "C" bk_status bk_probe_pipe(int kind, int64_t iters, int grid, int block,
     default: return set_error(BK_ERR_INVALID_ARG, "bk_probe_pipe: unknown kind %d", kind);
   }
   return check_cuda(cudaGetLastError(), "bk_probe_pipe launch");
+}
+
+extern "C" bk_status bk_math_probe(int fn, const double* in, double* out, int64_t n,
+                                   bk_stream_t stream) {
+  using namespace bk;
+  if (fn < 0 || fn > 7) return set_error(BK_ERR_INVALID_ARG, "bk_math_probe: unknown fn %d", fn);
+  if (n < 0 || (n > 0 && (in == nullptr || out == nullptr)))
+    return set_error(BK_ERR_INVALID_ARG, "bk_math_probe: bad arguments");
+  if (n == 0) return BK_OK;
+  const int64_t blocks = (n + 255) / 256;
+  const int grid = (int)(blocks < 152 * 8 ? blocks : 152 * 8);
+  math_probe_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(fn, in, out, n);
+  return check_cuda(cudaGetLastError(), "bk_math_probe launch");
 }
