@@ -703,6 +703,23 @@ __device__ __forceinline__ double two_cosh_warp(double v, const double* __restri
   return mid ? two_cosh_mid(v) : big;
 }
 
+// 2 cosh(h) for the quantised steps h = 2^e (1 + k/256), e = -12..0,
+// k = 0..255 (index (e + 12) 256 + k), correctly rounded (gen_cosh_table.py).
+static __device__ const double kCoshTab[3328] = {
+#include "bk_cosh_table.inc"
+};
+
+// The step h rounded up to 8 significand bits (hq >= h: N hq still covers the
+// window, and the strip bound's error grows by at most e^{2 pi a/h 2^-8},
+// a factor 1.13 at tol = 1e-13) and its index in kCoshTab, or -1 when hq is
+// outside [2^-12, 2).
+__device__ __forceinline__ float quantise_step(float h, int& idx) {
+  const int up = (__float_as_int(h) + 0x7fff) & ~0x7fff;
+  const int i = (up >> 15) - ((127 - 12) << 8);
+  idx = (h > 0.0f && i >= 0 && i < 3328) ? i : -1;
+  return __int_as_float(up);
+}
+
 // The same sum without centring, for the checked windows of scale_f64:
 //   f(t_j) = (e^{nu t_start} / 2) e^{-x cosh t_j} C_j,
 //   C_j = e^{nu (t_j - t_start)} (1 + e^{-2 nu t_j}) = 2 e^{-nu t_start} cosh(nu t_j),
@@ -719,7 +736,8 @@ struct NodeSumC {
   double S, first, last;
 };
 __device__ __forceinline__ NodeSumC node_sum_cosh(double t_start, double H, int count, double x,
-                                                  double nu, const double* __restrict__ tab) {
+                                                  double nu, const double* __restrict__ tab,
+                                                  int cosh_idx) {
   const double xh = (0.5 * kExpScale) * x;
   const double th = nu * H;
   double c, D0, D1, cn, C0, C1;
@@ -735,7 +753,7 @@ __device__ __forceinline__ NodeSumC node_sum_cosh(double t_start, double H, int 
     C0 = 1.0 + W;
     C1 = fma(W, rn, en);  // e^{nu H} + e^{-2 nu t_start} e^{-nu H}
   } else {
-    c = two_cosh_warp(H, tab);
+    c = (cosh_idx >= 0) ? kCoshTab[cosh_idx] : two_cosh_warp(H, tab);
     D0 = 2.0 * xh;
     D1 = xh * c;
     cn = two_cosh_warp(th, tab);
@@ -953,23 +971,27 @@ __device__ __forceinline__ double scale_f64(double x, double nu, float log2_over
   if (st == nullptr) return take_search(scaled_search_f64(x, nu, log2_over_tol, n_max, tab), hS, tl);
   // The window's geometry in FP32, taken exactly to FP64: the ends widened by
   // 2e-5 relative and 1e-5 absolute (as window_from_start), h = (t1 - t0)/N
-  // rounded to a float.  The trapezoid rule of step h over [t0, t0 + N h]
-  // needs nothing more of h: its end node lies within ~1e-7 relative of t1,
-  // inside the widening, and the check reads the computed end terms.
+  // rounded up to 8 significand bits (quantise_step, so that 2 cosh h comes
+  // from kCoshTab).  The trapezoid rule of step h over [t0, t0 + N h] needs
+  // nothing more of h: its last node lies at most 0.4 % beyond t1, and the
+  // check reads the computed end terms.
   const float t1f = fmaf(st->t1, 2e-5f, st->t1) + 1e-5f;
   const float t0f = (st->t0 > 0.0f && st->ts > 0.0f) ? fmaxf(0.0f, fmaf(st->t0, -2e-5f, st->t0) - 1e-5f)
                                                      : 0.0f;
   const float xf = f32_trunc(x), nuf = f32_trunc(nu), wf = t1f - t0f;
   const int N = strip_node_count(xf, nuf, wf, log2_over_tol, n_max);
   if (N <= n_max) {
-    const double t0 = widen_f(t0f), h = widen_f(__fdividef(wf, (float)N));
+    int cosh_idx;
+    const float hq = quantise_step(__fdividef(wf, (float)N), cosh_idx);
+    const float tnf = fmaf((float)N, hq, t0f);  // the last node
+    const double t0 = widen_f(t0f), h = widen_f(hq);
     tl.nodes += N + 1;
-    if (cosh_loop_ok(xf, nuf, t0f, t1f, N)) {
-      const NodeSumC ns = node_sum_cosh(t0, h, N + 1, x, nu, tab);
+    if (cosh_loop_ok(xf, nuf, t0f, tnf, N)) {
+      const NodeSumC ns = node_sum_cosh(t0, h, N + 1, x, nu, tab, cosh_idx);
       constexpr float kL2e = 1.44269504f;
       const float G = fmaf(nuf, st->ts - t0f, -xf * st->cs) * kL2e;  // log2 of the peak term
       float w1;
-      asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(w1) : "f"(-2.0f * kL2e * nuf * t1f));
+      asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(w1) : "f"(-2.0f * kL2e * nuf * tnf));
       float lw1;
       asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lw1) : "f"(1.0f + w1));
       bool ok = bits_pos(ns.last) && log2_f64_approx(ns.last) - lw1 - G <= -52.0f &&
