@@ -62,6 +62,8 @@ struct FormF64T {
   const double* tab;
   bool search_f64;      // FP64 Newton search for every point (no FP32 roots)
   double series_below;  // x below which Temme's series replaces the integral (0: never)
+  const double* cnu = nullptr;  // 2 cosh(nu h) on kCoshTab's steps for the launch's nu, or null
+  static constexpr bool kCoshNuTable = true;
 
   // log K from Temme's series (Sec. IV-A), tallied.
   __device__ __forceinline__ double series(double x, double nu, Tally& tl) const {
@@ -126,7 +128,7 @@ struct FormF64T {
     Start32 st;
     const Start32* sp = search_f64 ? nullptr : plain_starts(z, mp.nu_hi, st);
     double hS;
-    const double sc = scale_f64(z, mp.nu, kPlainLog2OverTol, kPlainMaxNodes, tab, hS, tl, sp);
+    const double sc = scale_f64(z, mp.nu, kPlainLog2OverTol, kPlainMaxNodes, tab, hS, tl, sp, cnu);
     return exp_tab_full(fma(mp.nu, log_tab(z, tab), mp.log_pref) + sc, tab) * hS;
   }
 
@@ -156,6 +158,7 @@ struct FormF64Fixed {
   static constexpr int kTilesPerBlock = 1;
   static constexpr int kMinBlocks = 3;
   static constexpr bool kFloatEval = false;
+  static constexpr bool kCoshNuTable = false;
   const double* tab;
   double t1;
   int bins;

@@ -705,7 +705,8 @@ __device__ __forceinline__ double two_cosh_warp(double v, const double* __restri
 
 // 2 cosh(h) for the quantised steps h = 2^e (1 + k/256), e = -12..0,
 // k = 0..255 (index (e + 12) 256 + k), correctly rounded (gen_cosh_table.py).
-static __device__ const double kCoshTab[3328] = {
+constexpr int kCoshTabSize = 3328;
+static __device__ const double kCoshTab[kCoshTabSize] = {
 #include "bk_cosh_table.inc"
 };
 
@@ -718,6 +719,14 @@ __device__ __forceinline__ float quantise_step(float h, int& idx) {
   const int i = (up >> 15) - ((127 - 12) << 8);
   idx = (h > 0.0f && i >= 0 && i < 3328) ? i : -1;
   return __int_as_float(up);
+}
+
+// 2 cosh(nu h_k) for the steps of kCoshTab (h_k = 2^e (1 + j/256), k =
+// (e + 12) 256 + j), as node_sum_cosh would compute it: the per-launch table
+// of the Matern tile writers, whose nu is fixed.
+__device__ __forceinline__ double cosh_nu_entry(double nu, int k, const double* __restrict__ tab) {
+  const double h = __hiloint2double(((k >> 8) - 12 + 1023) << 20 | ((k & 255) << 12), 0);
+  return two_cosh_warp(nu * h, tab);
 }
 
 // The same sum without centring, for the checked windows of scale_f64:
@@ -735,9 +744,11 @@ __device__ __forceinline__ float quantise_step(float h, int& idx) {
 struct NodeSumC {
   double S, first, last;
 };
+// cosh_idx: the step's index in kCoshTab (or -1); cnu: a table of
+// 2 cosh(nu h) on the same steps for this nu (or null).
 __device__ __forceinline__ NodeSumC node_sum_cosh(double t_start, double H, int count, double x,
                                                   double nu, const double* __restrict__ tab,
-                                                  int cosh_idx) {
+                                                  int cosh_idx, const double* __restrict__ cnu) {
   const double xh = (0.5 * kExpScale) * x;
   const double th = nu * H;
   double c, D0, D1, cn, C0, C1;
@@ -756,7 +767,7 @@ __device__ __forceinline__ NodeSumC node_sum_cosh(double t_start, double H, int 
     c = (cosh_idx >= 0) ? kCoshTab[cosh_idx] : two_cosh_warp(H, tab);
     D0 = 2.0 * xh;
     D1 = xh * c;
-    cn = two_cosh_warp(th, tab);
+    cn = (cosh_idx >= 0 && cnu != nullptr) ? cnu[cosh_idx] : two_cosh_warp(th, tab);
     C0 = 2.0;
     C1 = cn;
   }
@@ -966,7 +977,8 @@ __device__ __forceinline__ double take_search(const Scaled64& r, double& hS, Tal
 //    nu t* - x cosh t* - ln 2, the check on its FP64 end values.
 __device__ __forceinline__ double scale_f64(double x, double nu, float log2_over_tol, int n_max,
                                             const double* __restrict__ tab, double& hS,
-                                            Tally& tl, const Start32* st = nullptr) {
+                                            Tally& tl, const Start32* st = nullptr,
+                                            const double* __restrict__ cnu = nullptr) {
   constexpr double kEps64 = 0x1p-52;
   if (st == nullptr) return take_search(scaled_search_f64(x, nu, log2_over_tol, n_max, tab), hS, tl);
   // The window's geometry in FP32, taken exactly to FP64: the ends widened by
@@ -987,7 +999,7 @@ __device__ __forceinline__ double scale_f64(double x, double nu, float log2_over
     const double t0 = widen_f(t0f), h = widen_f(hq);
     tl.nodes += N + 1;
     if (cosh_loop_ok(xf, nuf, t0f, tnf, N)) {
-      const NodeSumC ns = node_sum_cosh(t0, h, N + 1, x, nu, tab, cosh_idx);
+      const NodeSumC ns = node_sum_cosh(t0, h, N + 1, x, nu, tab, cosh_idx, cnu);
       constexpr float kL2e = 1.44269504f;
       const float G = fmaf(nuf, st->ts - t0f, -xf * st->cs) * kL2e;  // log2 of the peak term
       float w1;

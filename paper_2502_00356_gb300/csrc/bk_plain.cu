@@ -13,6 +13,39 @@
 
 namespace bk {
 
+namespace {
+
+// Fills the per-launch table of 2 cosh(nu h) on kCoshTab's steps.
+__global__ void __launch_bounds__(256) cosh_nu_table_kernel(double nu, double* __restrict__ out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < kCoshTabSize) out[k] = cosh_nu_entry(nu, k, kExp2Tab);
+}
+
+// Runs launch(form) for a Matern tile writer of the searched-window form with
+// form.cnu pointing at a table of 2 cosh(nu h) for this launch's nu, in
+// stream-ordered memory on s (allocated, filled and freed on s, so that the
+// sequence can be captured in a graph).  Without the memory the kernels
+// compute the values themselves; forms without the table run as they are.
+template <class Form, class Launch>
+cudaError_t with_cosh_nu_table(Form form, double nu, cudaStream_t s, Launch&& launch) {
+  if constexpr (Form::kCoshNuTable) {
+    double* cnu = nullptr;
+    if (cudaMallocAsync((void**)&cnu, kCoshTabSize * sizeof(double), s) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return launch(form);
+    }
+    cosh_nu_table_kernel<<<(kCoshTabSize + 255) / 256, 256, 0, s>>>(nu, cnu);
+    form.cnu = cnu;
+    const cudaError_t e = launch(form);
+    const cudaError_t f = cudaFreeAsync(cnu, s);
+    return e != cudaSuccess ? e : f;
+  } else {
+    return launch(form);
+  }
+}
+
+}  // namespace
+
 int grid_for(int64_t work_items, int per_sm) {
   const int64_t cap = (int64_t)current_sm_count() * per_sm;
   return (int)(work_items < cap ? (work_items > 0 ? work_items : 1) : cap);
@@ -39,17 +72,23 @@ cudaError_t launch_eval_f64(const double* x, const double* nu, void* out, void* 
 cudaError_t launch_matern_sym_f64(const double* locs, int64_t n, double sigma2, double beta,
                                   double nu, void* out, int64_t ld, bk_dtype out_t,
                                   const bk_opts& o, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
   return with_plain_form(o, [&](const auto& form) {
-    return launch_matern_sym_form(form, locs, n, sigma2, beta, nu, out, ld, out_t, o.d_counters, s);
+    return with_cosh_nu_table(form, nu, s, [&](const auto& f) {
+      return launch_matern_sym_form(f, locs, n, sigma2, beta, nu, out, ld, out_t, o.d_counters, s);
+    });
   });
 }
 
 cudaError_t launch_matern_block_f64(const double* locs1, int64_t m, const double* locs2,
                                     int64_t n, double sigma2, double beta, double nu, void* out,
                                     int64_t ld, bk_dtype out_t, const bk_opts& o, cudaStream_t s) {
+  if (m == 0 || n == 0) return cudaSuccess;
   return with_plain_form(o, [&](const auto& form) {
-    return launch_matern_block_form(form, locs1, m, locs2, n, sigma2, beta, nu, out, ld, out_t,
-                                    o.d_counters, s);
+    return with_cosh_nu_table(form, nu, s, [&](const auto& f) {
+      return launch_matern_block_form(f, locs1, m, locs2, n, sigma2, beta, nu, out, ld, out_t,
+                                      o.d_counters, s);
+    });
   });
 }
 
