@@ -302,6 +302,7 @@ struct FormF32 {
   static constexpr int kTilesPerBlock = 4;
   static constexpr int kMinBlocks = 4;
   static constexpr bool kFloatEval = true;
+  static constexpr bool kCoshNuTable = false;
   const double* tab;
 
   template <class X64>
@@ -356,6 +357,7 @@ struct FormF32Learned {
   static constexpr int kTilesPerBlock = 4;
   static constexpr int kMinBlocks = 4;
   static constexpr bool kFloatEval = true;
+  static constexpr bool kCoshNuTable = false;
   LearnedView lv;
   const double* tab;
 
