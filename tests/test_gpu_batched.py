@@ -90,6 +90,31 @@ def test_batched_graph_capture_and_replay(dev):
         assert torch.equal(a, it[4])
 
 
+def test_batched_fp64_replay_follows_new_parameters(dev):
+    """The FP64 plan's per-instance tables of 2 cosh(nu h) are filled from
+    the descriptors at every launch: a captured graph replayed after the
+    descriptors' nu (and beta, sigma2) changed in place gives the single-call
+    results for the new parameters."""
+    items = make_batch(SMALL, dev, torch.float64)
+    d = bk.make_descs(items)
+    plan = bk.BatchedPlan([it[0].shape[1] for it in items], dtype=torch.float64)
+    bk.bk_matern_batched(d, plan)  # one eager run before capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        bk.bk_matern_batched(d, plan)
+    for shift in (0.0, 0.37, 1.9):
+        changed = [(L, s2 * (1 + shift), be * (1 + 0.5 * shift), nu + shift, out)
+                   for (L, s2, be, nu, out) in items]
+        d.copy_(bk.make_descs(changed))
+        for it in items:
+            it[4].fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        for it in changed:
+            assert same(it[4], single(it)), f"nu={it[3]} differs after replay"
+
+
 def test_batched_autotune_keeps_results(dev, tmp_path, monkeypatch):
     monkeypatch.setenv("BK_AUTOTUNE_CACHE", str(tmp_path / "tune.txt"))
     items = make_batch(SMALL, dev, torch.float64)

@@ -210,6 +210,32 @@ def test_matern_fp64_search_option(dev, nu):
     assert np.abs(a - b).max() <= 1e-12  # two windows, two node counts: quadrature-level agreement
 
 
+def test_matern_graph_capture(dev):
+    """bk_matern_tile captured in a CUDA graph (its per-call table of
+    2 cosh(nu h) lives in stream-ordered memory, which capture turns into
+    graph allocations) replays to the eager result, twice."""
+    n = 700
+    L = to_dev(inputs.morton_sorted(inputs.jittered_grid(n, seed=240)), dev)
+    eager = torch.empty((n, n), dtype=torch.float64, device=dev)
+    bk.bk_matern_tile(L, 1.1, 0.1, 1.5, out=eager)
+    torch.cuda.synchronize()
+    out = torch.empty_like(eager)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):  # a warm-up on the capture stream
+        bk.bk_matern_tile(L, 1.1, 0.1, 1.5, out=out)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        bk.bk_matern_tile(L, 1.1, 0.1, 1.5, out=out)
+    for _ in range(2):
+        out.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(out, eager)
+
+
 def test_matern_ld_padding_and_duplicates(dev):
     locs = inputs.jittered_grid(40, seed=31)
     locs[:, 7] = locs[:, 3]
