@@ -55,7 +55,7 @@ class bk_opts(ctypes.Structure):
     _fields_ = [("window", ctypes.c_int), ("compute", ctypes.c_int), ("fixed_bins", ctypes.c_int),
                 ("fixed_t1", ctypes.c_double), ("d_counters", ctypes.c_void_p),
                 ("learned", ctypes.c_void_p), ("search_f64", ctypes.c_int),
-                ("series_below", ctypes.c_double)]
+                ("series_below", ctypes.c_double), ("d_cosh_table", ctypes.c_void_p)]
 
 
 _lock = threading.Lock()
@@ -320,6 +320,27 @@ def _locs(locs, name="locs"):
     return locs.shape[1]
 
 
+BK_COSH_TABLE_LEN = 3328
+
+
+def _with_cosh_table(opts, device):
+    """A copy of ``opts`` (default options when None) whose d_cosh_table is a
+    scratch tensor from torch's caching allocator on the current stream (so
+    the library allocates nothing and graph capture takes it from the graph's
+    pool); returns (opts, tensor keeping the scratch alive)."""
+    torch = _torch()
+    if opts is None:
+        o = bk_opts()
+        lib().bk_opts_default(ctypes.byref(o))
+    else:
+        o = bk_opts.from_buffer_copy(opts)
+    table = None
+    if not o.d_cosh_table:
+        table = torch.empty(BK_COSH_TABLE_LEN, dtype=torch.float64, device=device)
+        o.d_cosh_table = table.data_ptr()
+    return o, table
+
+
 def bk_matern_tile(locs, sigma2: float, beta: float, nu: float, out=None, dtype=None,
                    opts: Optional[bk_opts] = None, stream=None):
     """Full n x n Matern matrix of SoA locations (2, n).  ``out`` is a CUDA
@@ -334,9 +355,10 @@ def bk_matern_tile(locs, sigma2: float, beta: float, nu: float, out=None, dtype=
     if out.dim() != 2 or out.shape[0] != n or out.shape[1] < n:
         raise ValueError("out must be (n, ld) with ld >= n")
     ld = out.shape[1]
-    optp = ctypes.byref(opts) if opts is not None else None
+    o, table = _with_cosh_table(opts, locs.device)
     _check(lib().bk_matern_tile_ex(_ptr(locs), n, float(sigma2), float(beta), float(nu), _ptr(out),
-                                   ld, code, optp, _stream_ptr(stream)))
+                                   ld, code, ctypes.byref(o), _stream_ptr(stream)))
+    del table  # stream-ordered reuse by torch's allocator is safe after the launch
     return out
 
 
@@ -353,9 +375,9 @@ def bk_matern_tile2(locs1, locs2, sigma2: float, beta: float, nu: float, out=Non
     _dev(out, "out")
     if out.dim() != 2 or out.shape[0] != n or out.shape[1] < m:
         raise ValueError("out must be (n, ld) with ld >= m")
-    optp = ctypes.byref(opts) if opts is not None else None
+    o, table = _with_cosh_table(opts, locs1.device)
     _check(lib().bk_matern_tile2(_ptr(locs1), m, _ptr(locs2), n, float(sigma2), float(beta),
-                                 float(nu), _ptr(out), out.shape[1], code, optp,
+                                 float(nu), _ptr(out), out.shape[1], code, ctypes.byref(o),
                                  _stream_ptr(stream)))
     return out
 

@@ -127,6 +127,7 @@ void bk_opts_default(bk_opts* o) {
   o->series_below = 0.0;
   o->d_counters = nullptr;
   o->learned = nullptr;
+  o->d_cosh_table = nullptr;
 }
 
 const char* bk_version(void) { return "libbesselk 0.1.0 (sm_103a)"; }

@@ -22,26 +22,21 @@ __global__ void __launch_bounds__(256) cosh_nu_table_kernel(double nu, double* _
 }
 
 // Runs launch(form) for a Matern tile writer of the searched-window form with
-// form.cnu pointing at a table of 2 cosh(nu h) for this launch's nu, in
-// stream-ordered memory on s (allocated, filled and freed on s, so that the
-// sequence can be captured in a graph).  Without the memory the kernels
-// compute the values themselves; forms without the table run as they are.
+// form.cnu pointing at the caller's table (bk_opts.d_cosh_table), first
+// filled on s with 2 cosh(nu h) for this launch's nu.  Without a table the
+// kernels compute the values themselves; forms without the table run as
+// they are.  Allocates nothing.
 template <class Form, class Launch>
-cudaError_t with_cosh_nu_table(Form form, double nu, cudaStream_t s, Launch&& launch) {
+cudaError_t with_cosh_nu_table(Form form, double nu, double* table, cudaStream_t s,
+                               Launch&& launch) {
   if constexpr (Form::kCoshNuTable) {
-    double* cnu = nullptr;
-    if (cudaMallocAsync((void**)&cnu, kCoshTabSize * sizeof(double), s) != cudaSuccess) {
-      (void)cudaGetLastError();
-      return launch(form);
+    if (table != nullptr) {
+      static_assert(kCoshTabSize == BK_COSH_TABLE_LEN, "table length");
+      cosh_nu_table_kernel<<<(kCoshTabSize + 255) / 256, 256, 0, s>>>(nu, table);
+      form.cnu = table;
     }
-    cosh_nu_table_kernel<<<(kCoshTabSize + 255) / 256, 256, 0, s>>>(nu, cnu);
-    form.cnu = cnu;
-    const cudaError_t e = launch(form);
-    const cudaError_t f = cudaFreeAsync(cnu, s);
-    return e != cudaSuccess ? e : f;
-  } else {
-    return launch(form);
   }
+  return launch(form);
 }
 
 }  // namespace
@@ -74,7 +69,7 @@ cudaError_t launch_matern_sym_f64(const double* locs, int64_t n, double sigma2, 
                                   const bk_opts& o, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   return with_plain_form(o, [&](const auto& form) {
-    return with_cosh_nu_table(form, nu, s, [&](const auto& f) {
+    return with_cosh_nu_table(form, nu, o.d_cosh_table, s, [&](const auto& f) {
       return launch_matern_sym_form(f, locs, n, sigma2, beta, nu, out, ld, out_t, o.d_counters, s);
     });
   });
@@ -85,7 +80,7 @@ cudaError_t launch_matern_block_f64(const double* locs1, int64_t m, const double
                                     int64_t ld, bk_dtype out_t, const bk_opts& o, cudaStream_t s) {
   if (m == 0 || n == 0) return cudaSuccess;
   return with_plain_form(o, [&](const auto& form) {
-    return with_cosh_nu_table(form, nu, s, [&](const auto& f) {
+    return with_cosh_nu_table(form, nu, o.d_cosh_table, s, [&](const auto& f) {
       return launch_matern_block_form(f, locs1, m, locs2, n, sigma2, beta, nu, out, ld, out_t,
                                       o.d_counters, s);
     });
