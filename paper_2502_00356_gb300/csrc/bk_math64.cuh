@@ -729,6 +729,19 @@ __device__ __forceinline__ double cosh_nu_entry(double nu, int k, const double* 
   return two_cosh_warp(nu * h, tab);
 }
 
+// log2 v of a positive finite double to about 1e-6, on the integer, FP32 and
+// MUFU pipes: the exponent field plus lg2 of the leading 23 significand bits.
+__device__ __forceinline__ float log2_f64_approx(double v) {
+  const int hi = __double2hiint(v);
+  const float m = __int_as_float(0x3f800000 | ((hi & 0x000fffff) << 3) |
+                                 (int)((unsigned)__double2loint(v) >> 29));
+  float lm;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lm) : "f"(m));
+  // the unbiased exponent as a float, exactly, by the magic-number trick
+  const float e = __int_as_float(0x4b400000 + ((hi >> 20) & 0x7ff)) - 12583935.0f;
+  return e + lm;
+}
+
 // The same sum without centring, for the checked windows of scale_f64:
 //   f(t_j) = (e^{nu t_start} / 2) e^{-x cosh t_j} C_j,
 //   C_j = e^{nu (t_j - t_start)} (1 + e^{-2 nu t_j}) = 2 e^{-nu t_start} cosh(nu t_j),
@@ -742,17 +755,23 @@ __device__ __forceinline__ double cosh_nu_entry(double nu, int k, const double* 
 // node count; cosh_loop_ok states the conditions.  Returns
 // S = sum_j e^{-x cosh t_j} C_j and the end terms.
 struct NodeSumC {
-  double S, first, last;
+  double S;                   // the trapezoid sum, end weights 1/2 included
+  float l2_first, l2_last;    // log2 of the unweighted end terms (window check)
+  bool pos;                   // the last term's factors are positive
 };
 // cosh_idx: the step's index in kCoshTab (or -1); cnu: a table of
-// 2 cosh(nu h) on the same steps for this nu (or null).
+// 2 cosh(nu h) on the same steps for this nu (or null).  The weights 1/2 of
+// the end nodes are folded into their terms (at t_start = 0, C_0/2 = 1), and
+// the end terms' logs for the window check come from the factors on the
+// FP32/integer pipes, so the ends cost no extra FP64 products.
 __device__ __forceinline__ NodeSumC node_sum_cosh(double t_start, double H, int count, double x,
                                                   double nu, const double* __restrict__ tab,
                                                   int cosh_idx, const double* __restrict__ cnu) {
   const double xh = (0.5 * kExpScale) * x;
   const double th = nu * H;
-  double c, D0, D1, cn, C0, C1;
-  if (bits_pos(t_start)) {
+  const bool start_pos = bits_pos(t_start);
+  double c, D0, D1, cn, C0, C1, C0h = 1.0;
+  if (start_pos) {
     const double e0 = exp_acc(t_start, tab), r0 = rcp_nr2(e0);
     const double eh = exp_acc(H, tab), rh = rcp_nr2(eh);
     c = bits_le(H, 0.35) ? two_cosh_small(H) : eh + rh;
@@ -762,6 +781,7 @@ __device__ __forceinline__ NodeSumC node_sum_cosh(double t_start, double H, int 
     const double en = exp_acc(th, tab), rn = rcp_nr2(en);
     cn = bits_le(th, 0.35) ? two_cosh_small(th) : en + rn;
     C0 = 1.0 + W;
+    C0h = fma(W, 0.5, 0.5);
     C1 = fma(W, rn, en);  // e^{nu H} + e^{-2 nu t_start} e^{-nu H}
   } else {
     c = (cosh_idx >= 0) ? kCoshTab[cosh_idx] : two_cosh_warp(H, tab);
@@ -772,32 +792,39 @@ __device__ __forceinline__ NodeSumC node_sum_cosh(double t_start, double H, int 
     C1 = cn;
   }
   // node j's term is p_j (T_j C_j) with 2^{-D_j/4096} = p_j T_j: the sum
-  // takes it by one FMA (6 FP64 operations per node); the end terms are
-  // formed once
+  // takes it by one FMA (6 FP64 operations per node)
   NodeSumC r;
-  double p, q;
-  {
-    double T;
-    exp2s_neg_parts(D0, tab, p, T);
-    q = T * C0;
-    r.first = p * q;
+  double p, T;
+  exp2s_neg_parts(D0, tab, p, T);
+  double s = p * T;  // the first term times 1/2 (C_0 / 2 = 1 at t_start = 0)
+  r.l2_first = 0.0f;
+  if (start_pos) {
+    s *= C0h;
+    float l2p;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l2p) : "f"(f32_trunc(p)));
+    r.l2_first = l2p + log2_f64_approx(T) + log2_f64_approx(C0h) + 1.0f;
   }
-  double s = r.first;
 #pragma unroll 2
-  for (int j = 1; j < count; ++j) {
+  for (int j = 1; j < count - 1; ++j) {
     const double D2 = fma(c, D1, -D0);
     D0 = D1;
     D1 = D2;
     const double C2 = fma(cn, C1, -C0);
     C0 = C1;
     C1 = C2;
-    double T;
     exp2s_neg_parts(D0, tab, p, T);
-    q = T * C0;
-    s = fma(p, q, s);
+    s = fma(p, T * C0, s);
+  }
+  {  // the last node (D_N, C_N after the loop), weight 1/2; count >= 3
+    exp2s_neg_parts(D1, tab, p, T);
+    const double qh = T * (0.5 * C1);
+    s = fma(p, qh, s);
+    float l2p;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l2p) : "f"(f32_trunc(p)));
+    r.l2_last = l2p + log2_f64_approx(qh) + 1.0f;
+    r.pos = bits_pos(qh) && bits_pos(p);
   }
   r.S = s;
-  r.last = p * q;
   return r;
 }
 // FP64 ops per node of node_sum_cosh: exp2s_neg_parts (2), 1 mul (T C),
@@ -820,18 +847,6 @@ __device__ __forceinline__ bool cosh_loop_ok(float x, float nu, float t0, float 
   return nf * nf <= 65536.0f * fmaxf(nw, 1.0f) && nw <= 600.0f && x * (e1 + 1.0f) <= 1380.0f;
 }
 
-// log2 v of a positive finite double to about 1e-6, on the integer, FP32 and
-// MUFU pipes: the exponent field plus lg2 of the leading 23 significand bits.
-__device__ __forceinline__ float log2_f64_approx(double v) {
-  const int hi = __double2hiint(v);
-  const float m = __int_as_float(0x3f800000 | ((hi & 0x000fffff) << 3) |
-                                 (int)((unsigned)__double2loint(v) >> 29));
-  float lm;
-  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lm) : "f"(m));
-  // the unbiased exponent as a float, exactly, by the magic-number trick
-  const float e = __int_as_float(0x4b400000 + ((hi >> 20) & 0x7ff)) - 12583935.0f;
-  return e + lm;
-}
 
 // ln(2 / tol) for the plain form: tol = 1e-13 keeps the quadrature error
 // about three orders below the 1e-10 relative accuracy the form promises.
@@ -1006,16 +1021,16 @@ __device__ __forceinline__ double scale_f64(double x, double nu, float log2_over
       asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(w1) : "f"(-2.0f * kL2e * nuf * tnf));
       float lw1;
       asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lw1) : "f"(1.0f + w1));
-      bool ok = bits_pos(ns.last) && log2_f64_approx(ns.last) - lw1 - G <= -52.0f &&
-                bits_pos(ns.S) && bits_le(ns.S, 1e300);
+      bool ok = ns.pos && ns.l2_last - lw1 - G <= -52.0f && bits_pos(ns.S) &&
+                bits_le(ns.S, 1e300);
       if (bits_pos(t0)) {
         float w0, lw0;
         asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(w0) : "f"(-2.0f * kL2e * nuf * t0f));
         asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lw0) : "f"(1.0f + w0));
-        ok = ok && bits_pos(ns.first) && log2_f64_approx(ns.first) - lw0 - G <= -53.0f;
+        ok = ok && ns.l2_first - lw0 - G <= -53.0f;
       }
       if (ok) {
-        hS = h * (ns.S - 0.5 * (ns.first + ns.last));
+        hS = h * ns.S;
         return bits_pos(t0) ? fma(nu, t0, -kLn2) : -kLn2;
       }
     } else {
