@@ -323,15 +323,18 @@ def _locs(locs, name="locs"):
 BK_COSH_TABLE_LEN = 3328
 
 
-def _with_cosh_table(opts, device):
-    """A copy of ``opts`` (default options when None) whose d_cosh_table is a
-    scratch tensor from torch's caching allocator on the current stream (so
-    the library allocates nothing and graph capture takes it from the graph's
-    pool); returns (opts, tensor keeping the scratch alive)."""
+def _with_cosh_table(opts, device, dtype_code):
+    """A copy of ``opts`` whose d_cosh_table is a scratch tensor from torch's
+    caching allocator on the current stream (so the library allocates nothing
+    and graph capture takes it from the graph's pool); returns (opts, tensor
+    keeping the scratch alive).  ``opts`` None means the C defaults for a
+    NULL options pointer: default options with compute = the output dtype
+    (FP32 output takes the FP32 precision form)."""
     torch = _torch()
     if opts is None:
         o = bk_opts()
         lib().bk_opts_default(ctypes.byref(o))
+        o.compute = int(dtype_code)
     else:
         o = bk_opts.from_buffer_copy(opts)
     table = None
@@ -355,7 +358,7 @@ def bk_matern_tile(locs, sigma2: float, beta: float, nu: float, out=None, dtype=
     if out.dim() != 2 or out.shape[0] != n or out.shape[1] < n:
         raise ValueError("out must be (n, ld) with ld >= n")
     ld = out.shape[1]
-    o, table = _with_cosh_table(opts, locs.device)
+    o, table = _with_cosh_table(opts, locs.device, code)
     _check(lib().bk_matern_tile_ex(_ptr(locs), n, float(sigma2), float(beta), float(nu), _ptr(out),
                                    ld, code, ctypes.byref(o), _stream_ptr(stream)))
     del table  # stream-ordered reuse by torch's allocator is safe after the launch
@@ -375,7 +378,7 @@ def bk_matern_tile2(locs1, locs2, sigma2: float, beta: float, nu: float, out=Non
     _dev(out, "out")
     if out.dim() != 2 or out.shape[0] != n or out.shape[1] < m:
         raise ValueError("out must be (n, ld) with ld >= m")
-    o, table = _with_cosh_table(opts, locs1.device)
+    o, table = _with_cosh_table(opts, locs1.device, code)
     _check(lib().bk_matern_tile2(_ptr(locs1), m, _ptr(locs2), n, float(sigma2), float(beta),
                                  float(nu), _ptr(out), out.shape[1], code, ctypes.byref(o),
                                  _stream_ptr(stream)))

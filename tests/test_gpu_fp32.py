@@ -175,3 +175,24 @@ def test_matern_f32_cholesky_8000(dev):
             assert int(info32) == 0, f"nu={nu}: FP32 matrix failed where the rounded FP64 one factors"
         if nu <= 1.5:
             assert int(info32) == 0
+
+
+def test_default_form_follows_output_dtype(dev):
+    """Without options, FP32 output selects the FP32 precision form (the C
+    entry points' default for a NULL options pointer, mirrored by the
+    binding): the same bits as asking for compute = BK_F32 explicitly, and
+    not the plain form's FP32-rounded matrix."""
+    n = 500
+    L = torch.as_tensor(inputs.morton_sorted(inputs.jittered_grid(n, seed=251)), device=dev)
+    default = bk.bk_matern_tile(L, 1.0, 0.1, 1.3, dtype=torch.float32)
+    f32 = bk.bk_matern_tile(L, 1.0, 0.1, 1.3, dtype=torch.float32,
+                            opts=bk.make_opts(compute=bk.BK_F32))
+    plain = bk.bk_matern_tile(L, 1.0, 0.1, 1.3, dtype=torch.float32,
+                              opts=bk.make_opts(compute=bk.BK_F64))
+    torch.cuda.synchronize()
+    assert torch.equal(default, f32)
+    assert not torch.equal(default, plain)
+    d2 = bk.bk_matern_tile2(L, L, 1.0, 0.1, 1.3, dtype=torch.float32)
+    torch.cuda.synchronize()
+    assert torch.equal(d2, f32)
+
