@@ -74,14 +74,19 @@ __device__ __forceinline__ Form bind_table(const Form& form, double* s_tab) {
   return f;
 }
 
-// Cost-ordering key of one (x, nu) pair from its bit patterns alone (no
-// FP64 instruction): |x| to 1/8 of an octave in the high bits, |nu| to 1/8 of
-// an octave below.  Pairs with close keys have similar windows, node counts
-// and search paths.
+// A pair's sorting key for the bare evaluations: an estimate of its node
+// count, monotone in the two things that set it, the window's width (which
+// grows like ln(1 + 74/x) past the peak, 74 = 2 log(1/eps)) and the
+// strip-bound step (which shrinks like 1/(30 + 3 nu)); in FP32 on truncated
+// copies.  Positive floats order like their bit patterns.  Any key is valid:
+// it only groups pairs of similar cost into warps.
 __device__ __forceinline__ unsigned eval_cost_key(double x, double nu) {
-  const unsigned kx = ((unsigned)__double2hiint(x) >> 17) & 0x3fffu;   // exponent + 3 bits
-  const unsigned kn = ((unsigned)__double2hiint(nu) >> 17) & 0x3fffu;
-  return (kx << 14) | kn;
+  const float xf = f32_trunc(x), nf = fabsf(f32_trunc(nu));
+  float r, l2;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(xf));
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l2) : "f"(fmaf(74.0f, r, 1.0f)));
+  const float est = (l2 + 1.5f) * fmaf(3.0f, nf, 30.0f);
+  return (est > 0.0f && est < 3.0e38f) ? __float_as_uint(est) : 0xfffffffeu;
 }
 
 // Orders a round of 128 pairs (base .. base + 127) by eval_cost_key with a
