@@ -167,11 +167,17 @@ KERNEL_SOURCES = ("bk_plain.cu", "bk_math64.cuh", "bk_math32.cuh", "bk_forms.cuh
 
 
 def kernel_hash():
-    """Hash of the sources the plain FP64 tile writer is compiled from."""
+    """Hash of the sources the plain FP64 tile writer is compiled from, with
+    comments removed and whitespace collapsed (so that it changes with the
+    compiled code, not with its documentation)."""
+    import re
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_2502_00356_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2502_00356_gb300", "csrc", f)) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -985,9 +985,10 @@ __device__ __forceinline__ double take_search(const Scaled64& r, double& hS, Tal
 // st, the FP64 search.
 //  - node_sum_cosh where cosh_loop_ok: scale nu t0 - ln 2.  The check takes
 //    log2 e(t) = log2 f_t - log2(1 + e^{-2 nu t}) - (nu (t* - t0) - x cosh t*)
-//    log2 e from the exact FP64 end terms f_t and FP32 values of the rest
-//    (cosh t* as the FP32 search computed it): error below about 3e-4 in
-//    log2 e, i.e. the thresholds hold to a factor 2^{3e-4}.
+//    log2 e with log2 f_t from the end term's FP64 factors (to ~5e-7) and
+//    FP32 values of the rest (cosh t* as the FP32 search computed it):
+//    error below about 3e-4 in log2 e, i.e. the thresholds hold to a factor
+//    2^{3e-4}.
 //  - node_sum_f64 elsewhere (centred at t*, cosh t* in FP64): scale
 //    nu t* - x cosh t* - ln 2, the check on its FP64 end values.
 __device__ __forceinline__ double scale_f64(double x, double nu, float log2_over_tol, int n_max,
