@@ -19,6 +19,9 @@ Functions and the passages they follow:
 * ``fixed_window_log_k``: the paper's fixed-window branch of Algorithm 2.
 * ``mlp_*``: FP64 reference forward/backward of the window network (see
   ``mlp.py``).
+
+``alg2_error_map.py`` (a script beside this package) tabulates the error of
+the paper's Algorithm 2 over its region from these functions alone.
 """
 from __future__ import annotations
 
