@@ -562,7 +562,6 @@ template <class Form, typename OutT, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, Form::kMinBlocks * 8 / WARPS) matern_batched_static_kernel(
     const bk_matern_desc* __restrict__ descs, int count, unsigned long long* __restrict__ scratch) {
   const int64_t* prefix = (const int64_t*)(scratch + kStaticPrefixOff);
-  const int64_t* sizes = (const int64_t*)(scratch + kStaticSizesOff);
   const int64_t limit = prefix[count];
   __shared__ BatchSmem<OutT> sm;
   __shared__ double s_tab[Form::kStageTable ? kExpTabSize : 1];
@@ -581,8 +580,12 @@ __global__ void __launch_bounds__(WARPS * 32, Form::kMinBlocks * 8 / WARPS) mate
       __syncthreads();
       if (threadIdx.x == 0) {
         bk_matern_desc d = descs[k];
-        const bool ok = d.n == sizes[k] && d.ld >= d.n && d.locs != nullptr &&
-                        d.out != nullptr && d.beta > 0.0 && d.nu > 0.0 && d.sigma2 >= 0.0;
+        // sizes[k] was copied from this descriptor by the preparation kernel,
+        // so only the descriptor's own fields need checking here.  There are
+        // no counters on this path: a skipped descriptor leaves its output
+        // untouched and is not reported.
+        const bool ok = d.n >= 0 && d.ld >= d.n && d.locs != nullptr && d.out != nullptr &&
+                        d.beta > 0.0 && d.nu > 0.0 && d.sigma2 >= 0.0;
         if (!ok) d.n = 0;  // an invalid descriptor is skipped
         sm.locs = d.locs;
         sm.out = (OutT*)d.out;
@@ -601,28 +604,17 @@ __global__ void __launch_bounds__(WARPS * 32, Form::kMinBlocks * 8 / WARPS) mate
   }
 }
 
-std::mutex g_static_mutex;
-unsigned long long* g_static_addr[64] = {nullptr};
-
 // Device address of the scratch on the current device.  The array's name in
-// host code is only a host-side handle, so it is resolved once per device
-// with cudaGetSymbolAddress (this first call also loads the library's device
-// code on that device).
+// host code is only a host-side handle, so the address is looked up with
+// cudaGetSymbolAddress on every call (a host-side lookup once the library's
+// device code is loaded on the device; the first call on a device also loads
+// it there).  Not caching it keeps the address right after the context is
+// torn down and created again (cudaDeviceReset), when the array may move.
 bk_status static_scratch_address(unsigned long long** out) {
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return check_cuda(e, "bk_matern_batched_static: cudaGetDevice");
-  if (dev < 0 || dev >= 64)
-    return set_error(BK_ERR_UNSUPPORTED, "bk_matern_batched_static: device %d out of range", dev);
-  std::lock_guard<std::mutex> lk(g_static_mutex);
-  if (g_static_addr[dev] == nullptr) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess)
-      return check_cuda(e, "bk_matern_batched_static: cudaGetSymbolAddress");
-    g_static_addr[dev] = (unsigned long long*)p;
-  }
-  *out = g_static_addr[dev];
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+  if (e != cudaSuccess) return check_cuda(e, "bk_matern_batched_static: cudaGetSymbolAddress");
+  *out = (unsigned long long*)p;
   return BK_OK;
 }
 

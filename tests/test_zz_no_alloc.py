@@ -87,3 +87,41 @@ def test_static_rejects_too_many_instances(dev):
         bk.bk_matern_batched_static(d_big, big)
     assert err.value.status == bk.BK_ERR_INVALID_ARG
     assert "4096" in str(err.value)
+
+
+def test_static_skips_an_invalid_descriptor(dev):
+    """An invalid descriptor (beta < 0) is skipped without a report: its
+    NaN-filled output stays NaN and the other instances still match."""
+    ref = with_plan(BATCH_B, dev, torch.float64)
+    items = batch(BATCH_B, dev, torch.float64)
+    bad = 2
+    L, s2, _, nu, out = items[bad]
+    items[bad] = (L, s2, -0.1, nu, out)
+    bk.bk_matern_batched_static(bk.make_descs(items), len(items), dtype=torch.float64)
+    torch.cuda.synchronize()
+    for k, (it, r) in enumerate(zip(items, ref)):
+        if k == bad:
+            assert bool(torch.isnan(it[4]).all())
+        else:
+            assert float((it[4] - r).abs().max()) <= F64_ATOL
+
+
+def test_static_call_allocates_no_device_memory(dev):
+    """Free device memory (cudaMemGetInfo) is the same before and after a
+    call larger than any before it, once both forms' kernels are loaded."""
+    small = batch(BATCH_A, dev, torch.float64)
+    small32 = batch(BATCH_A, dev, torch.float32)
+    big = [inputs.MaternInstance(n, 900 + k, 1.0, 0.1, 0.7 + 0.2 * k)
+           for k, n in enumerate([1500, 900, 2100, 64, 700])]
+    big64 = batch(big, dev, torch.float64)
+    big32 = batch(big, dev, torch.float32)
+    descs = [bk.make_descs(x) for x in (small, small32, big64, big32)]
+    bk.bk_matern_batched_static(descs[0], len(small), dtype=torch.float64)  # loads the kernels
+    bk.bk_matern_batched_static(descs[1], len(small32), dtype=torch.float32)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    bk.bk_matern_batched_static(descs[2], len(big64), dtype=torch.float64)
+    bk.bk_matern_batched_static(descs[3], len(big32), dtype=torch.float32)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert not bool(torch.isnan(big64[2][4]).any())
