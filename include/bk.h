@@ -194,6 +194,42 @@ bk_status bk_matern_tile2(const double* locs1, int64_t m, const double* locs2, i
                           bk_dtype dtype, const bk_opts* opts, bk_stream_t stream);
 
 /*
+ * bk_matern_tile_host: the matrix of bk_matern_tile_ex delivered to HOST
+ * memory, with the host <-> device transfers inside the call (Sec. III-A,
+ * Algorithm 3; the paper's matrices are consumed by a host-side runtime).
+ *   h_locs:  HOST, 2n doubles (SoA), copied into d_work on `stream`.
+ *   h_out:   HOST, ld * n elements of dtype, column-major, ld >= n.
+ *   mode:    BK_HOST_AUTO or BK_HOST_STAGED (below).
+ *   d_work:  DEVICE workspace, 256-byte aligned, caller-owned; one workspace
+ *            must not serve two calls that can overlap on the GPU.
+ * BK_HOST_AUTO: when the device can address h_out (cudaHostGetDevicePointer
+ * accepts it: page-locked memory from cudaHostAlloc, cudaMallocHost or
+ * cudaHostRegister, and on GB300, whose GPU reaches host page tables through
+ * ATS, pageable memory as well), the tile writer stores the matrix straight
+ * into h_out over the GPU-CPU link (NVLink-C2C) and d_work needs only
+ * bk_matern_tile_host_workspace(n, dtype, 0) bytes (locations and the plain
+ * form's 2 cosh(nu h) table).  Otherwise, and always with BK_HOST_STAGED,
+ * the matrix is staged in d_work, which then needs
+ * bk_matern_tile_host_workspace(n, dtype, 1) bytes: it is generated in up to
+ * 16 panels of block-columns, and each finished panel's columns are copied to
+ * h_out on a library-owned copy stream (one per device, created on first use
+ * with its events) while later panels are generated; with pageable h_out each
+ * copy blocks the calling thread until it is done.  Either way `stream` waits
+ * for the last write to h_out before any later work: h_out is complete once
+ * `stream` reaches the end of the call (e.g. after bk_sync(stream)).  Options
+ * as bk_matern_tile_ex (opts == NULL: compute = dtype).  Not for stream
+ * capture.  Allocates no device memory.  Errors: BK_ERR_INVALID_ARG for bad
+ * sizes, parameters, mode, NULL pointers or an unaligned workspace;
+ * BK_ERR_NOMEM when work_bytes is too small for the way h_out is written.
+ */
+enum { BK_HOST_AUTO = 0, BK_HOST_STAGED = 1 };
+size_t bk_matern_tile_host_workspace(int64_t n, bk_dtype dtype, int staged);
+bk_status bk_matern_tile_host(const double* h_locs, int64_t n, double sigma2, double beta,
+                              double nu, void* h_out, int64_t ld, bk_dtype dtype,
+                              const bk_opts* opts, int mode, void* d_work, size_t work_bytes,
+                              bk_stream_t stream);
+
+/*
  * bk_morton_order (host only): perm[k] = index of the k-th location in
  * Z-order (Sec. IV-D orders locations so that a tile holds nearby points).
  * Coordinates are quantised to 16 bits over [0, 1] (clamped), x on the even
@@ -309,15 +345,20 @@ bk_status bk_learned_load(bk_learned* model, const char* path);
  * Its scratch (work list and tile counter) is a fixed array compiled into the
  * library, held by every GPU that loads the library until the process exits;
  * it fits at most 4096 instances (count > 4096 is BK_ERR_INVALID_ARG).
- * The first call on a device resolves that array's device address (this also
- * loads the library's device code there), so make the first call on each
- * device before any stream capture.  All calls share the one array and each
- * call rewrites it (work list, counter zeroed) before use: calls that can
- * overlap on the GPU (other streams, other host threads) race with each
- * other and must be ordered by the caller.  Descriptors as for
- * bk_matern_batched; dtype picks the output type and the form (compute =
- * dtype); an invalid descriptor is skipped.  Launch shape fixed (8 warps,
- * 2 CTAs per SM).  Enqueues two kernels on `stream` and does not synchronise.
+ * Every call looks up that array's device address on the current device
+ * (cudaGetSymbolAddress; the first call on a device also loads the library's
+ * device code there), so make the first call on each device before any
+ * stream capture.  All calls share the one array and each call rewrites it
+ * (work list, counter zeroed) before use: calls that can overlap on the GPU
+ * (other streams, other host threads) race with each other and must be
+ * ordered by the caller.  Descriptors as for bk_matern_batched; dtype picks
+ * the output type and the form (compute = dtype).  There are no counters on
+ * this path: an invalid descriptor (n < 0, ld < n, NULL pointers, beta or
+ * nu <= 0, sigma2 < 0) is skipped without a report and its output is left
+ * untouched.  The FP64 form here computes 2 cosh(nu h) inside the node loop
+ * (a plan keeps per-instance tables of it), so it is somewhat slower than
+ * bk_matern_batched with a plan.  Launch shape fixed (8 warps, 2 CTAs per
+ * SM).  Enqueues two kernels on `stream` and does not synchronise.
  */
 bk_status bk_matern_batched_static(const bk_matern_desc* d_descs, int32_t count, bk_dtype dtype,
                                    bk_stream_t stream);

@@ -28,11 +28,13 @@ BK_WIN_SEARCH, BK_WIN_LEARNED, BK_WIN_FIXED = 0, 1, 2
 BK_CTR_FALLBACK, BK_CTR_FAIL, BK_CTR_NODES, BK_CTR_ITERS, BK_CTR_EVALS, BK_CTR_PEAK_ITERS = 0, 1, 2, 3, 4, 5
 BK_CTR_REPAIR, BK_CTR_SERIES = 6, 7
 BK_NUM_COUNTERS = 8
+BK_HOST_AUTO, BK_HOST_STAGED = 0, 1
 
 #: every symbol include/bk.h declares (checked by the CPU tests)
 EXPORTS = (
     "bk_opts_default", "bk_version", "bk_last_error", "bk_status_string", "bk_sync",
     "bk_eval", "bk_eval_ex", "bk_eval_grad", "bk_gaussian_loglik", "bk_matern_tile", "bk_matern_tile_ex", "bk_matern_tile2",
+    "bk_matern_tile_host", "bk_matern_tile_host_workspace",
     "bk_morton_order", "bk_probe_pipe", "bk_math_probe", "bk_batched_plan_create", "bk_batched_plan_destroy",
     "bk_batched_plan_info", "bk_batched_autotune", "bk_matern_batched",
     "bk_matern_batched_static", "bk_learned_create", "bk_learned_destroy", "bk_learned_train",
@@ -92,6 +94,8 @@ def lib() -> ctypes.CDLL:
             "bk_matern_tile": (I, [P, I64, D, D, D, P, I64, I, P]),
             "bk_matern_tile_ex": (I, [P, I64, D, D, D, P, I64, I, P, P]),
             "bk_matern_tile2": (I, [P, I64, P, I64, D, D, D, P, I64, I, P, P]),
+            "bk_matern_tile_host": (I, [P, I64, D, D, D, P, I64, I, P, I, P, ctypes.c_size_t, P]),
+            "bk_matern_tile_host_workspace": (ctypes.c_size_t, [I64, I, I]),
             "bk_morton_order": (I, [P, I64, P]),
             "bk_probe_pipe": (I, [I, I64, I, I, P, P]),
             "bk_math_probe": (I, [I, P, P, I64, P]),
@@ -362,6 +366,49 @@ def bk_matern_tile(locs, sigma2: float, beta: float, nu: float, out=None, dtype=
     _check(lib().bk_matern_tile_ex(_ptr(locs), n, float(sigma2), float(beta), float(nu), _ptr(out),
                                    ld, code, ctypes.byref(o), _stream_ptr(stream)))
     del table  # stream-ordered reuse by torch's allocator is safe after the launch
+    return out
+
+
+def matern_tile_host_workspace(n: int, dtype=None, staged: bool = True) -> int:
+    """Bytes of device workspace bk_matern_tile_host needs for n locations:
+    staged=True for pageable output (the matrix passes through the
+    workspace), False for page-locked output (written directly)."""
+    torch = _torch()
+    return int(lib().bk_matern_tile_host_workspace(int(n), _dtype_code(dtype or torch.float64),
+                                                   int(bool(staged))))
+
+
+def bk_matern_tile_host(locs, sigma2: float, beta: float, nu: float, out, work,
+                        opts: Optional[bk_opts] = None, staged: bool = False, stream=None):
+    """The n x n Matern matrix of HOST locations ``locs`` (a (2, n) float64 CPU
+    tensor) written into the HOST tensor ``out`` ((n, ld) row-major =
+    column-major n x n, float64 or float32), with ``work`` a CUDA uint8 tensor
+    of at least matern_tile_host_workspace(n, staged=...) bytes.  By default
+    the kernel stores into ``out`` directly when the device can address it;
+    ``staged=True`` generates the matrix in ``work`` and copies finished
+    panels out.  Asynchronous on ``stream``: ``out`` is complete once the
+    stream has reached the end of the call.  Returns ``out``."""
+    torch = _torch()
+    if not isinstance(locs, torch.Tensor) or locs.is_cuda or locs.dtype != torch.float64:
+        raise TypeError("locs must be a float64 CPU tensor")
+    if locs.dim() != 2 or locs.shape[0] != 2 or not locs.is_contiguous():
+        raise ValueError("locs must be a contiguous (2, n) tensor (structure of arrays)")
+    n = locs.shape[1]
+    if not isinstance(out, torch.Tensor) or out.is_cuda or not out.is_contiguous():
+        raise TypeError("out must be a contiguous CPU tensor")
+    if out.dim() != 2 or out.shape[0] != n or out.shape[1] < n:
+        raise ValueError("out must be (n, ld) with ld >= n")
+    code = _dtype_code(out.dtype)
+    _dev(work, "work")
+    o = opts
+    if o is None:
+        o = bk_opts()
+        lib().bk_opts_default(ctypes.byref(o))
+        o.compute = code
+    _check(lib().bk_matern_tile_host(_ptr(locs), n, float(sigma2), float(beta), float(nu),
+                                     _ptr(out), out.shape[1], code, ctypes.byref(o),
+                                     BK_HOST_STAGED if staged else BK_HOST_AUTO, _ptr(work),
+                                     work.numel() * work.element_size(), _stream_ptr(stream)))
     return out
 
 

@@ -18,8 +18,9 @@ cudaError_t launch_eval_f32(const double* x, const double* nu, void* out, void* 
 
 cudaError_t launch_matern_sym_f32(const double* locs, int64_t n, double sigma2, double beta,
                                   double nu, void* out, int64_t ld, bk_dtype out_t,
-                                  unsigned long long* ctr, cudaStream_t s) {
-  return launch_matern_sym_form(FormF32{nullptr}, locs, n, sigma2, beta, nu, out, ld, out_t, ctr, s);
+                                  unsigned long long* ctr, cudaStream_t s, const SymRange& range) {
+  return launch_matern_sym_form(FormF32{nullptr}, locs, n, sigma2, beta, nu, out, ld, out_t, ctr, s,
+                                range);
 }
 
 cudaError_t launch_matern_block_f32(const double* locs1, int64_t m, const double* locs2,

@@ -19,6 +19,15 @@ bk_status set_error(bk_status st, const char* fmt, ...);
 // Converts a CUDA error into BK_ERR_CUDA with a message (BK_OK if none).
 bk_status check_cuda(cudaError_t e, const char* what);
 
+// A range of block-columns [j0, j1) of a symmetric matrix (32-wide blocks),
+// written in block-column order; j1 < 0 means the whole matrix.  fill_table:
+// whether a launch of the plain form refills the caller's 2 cosh(nu h) table
+// (a caller writing several ranges of one matrix fills it with the first).
+struct SymRange {
+  int64_t j0 = 0, j1 = -1;
+  bool fill_table = true;
+};
+
 // ---- plain FP64 form (bk_plain.cu) ----
 cudaError_t launch_eval_f64(const double* x, const double* nu, void* out, void* log_out,
                             bk_dtype out_t, int64_t n, const bk_opts& o, cudaStream_t s);
@@ -26,7 +35,8 @@ cudaError_t launch_eval_f64(const double* x, const double* nu, void* out, void* 
 // Full symmetric n x n matrix: lower-triangle tiles, each written twice.
 cudaError_t launch_matern_sym_f64(const double* locs, int64_t n, double sigma2, double beta,
                                   double nu, void* out, int64_t ld, bk_dtype out_t,
-                                  const bk_opts& o, cudaStream_t s);
+                                  const bk_opts& o, cudaStream_t s,
+                                  const SymRange& range = SymRange{});
 
 // General m x n block between two location sets.
 cudaError_t launch_matern_block_f64(const double* locs1, int64_t m, const double* locs2,
@@ -51,7 +61,8 @@ cudaError_t launch_eval_f32(const double* x, const double* nu, void* out, void* 
                             bk_dtype out_t, int64_t n, unsigned long long* ctr, cudaStream_t s);
 cudaError_t launch_matern_sym_f32(const double* locs, int64_t n, double sigma2, double beta,
                                   double nu, void* out, int64_t ld, bk_dtype out_t,
-                                  unsigned long long* ctr, cudaStream_t s);
+                                  unsigned long long* ctr, cudaStream_t s,
+                                  const SymRange& range = SymRange{});
 cudaError_t launch_matern_block_f32(const double* locs1, int64_t m, const double* locs2,
                                     int64_t n, double sigma2, double beta, double nu, void* out,
                                     int64_t ld, bk_dtype out_t, unsigned long long* ctr,
@@ -64,7 +75,8 @@ cudaError_t launch_eval_learned(const bk_learned* m, const double* x, const doub
                                 cudaStream_t s);
 cudaError_t launch_matern_sym_learned(const bk_learned* m, const double* locs, int64_t n,
                                       double sigma2, double beta, double nu, void* out, int64_t ld,
-                                      bk_dtype out_t, unsigned long long* ctr, cudaStream_t s);
+                                      bk_dtype out_t, unsigned long long* ctr, cudaStream_t s,
+                                      const SymRange& range = SymRange{});
 cudaError_t launch_matern_block_learned(const bk_learned* m, const double* locs1, int64_t m_,
                                         const double* locs2, int64_t n, double sigma2,
                                         double beta, double nu, void* out, int64_t ld,

@@ -430,9 +430,10 @@ cudaError_t launch_eval_learned(const bk_learned* m, const double* x, const doub
 
 cudaError_t launch_matern_sym_learned(const bk_learned* m, const double* locs, int64_t n,
                                       double sigma2, double beta, double nu, void* out, int64_t ld,
-                                      bk_dtype out_t, unsigned long long* ctr, cudaStream_t s) {
+                                      bk_dtype out_t, unsigned long long* ctr, cudaStream_t s,
+                                      const SymRange& range) {
   return launch_matern_sym_form(FormF32Learned{learned_view(m), nullptr}, locs, n, sigma2, beta, nu, out,
-                                ld, out_t, ctr, s);
+                                ld, out_t, ctr, s, range);
 }
 
 cudaError_t launch_matern_block_learned(const bk_learned* m, const double* locs1, int64_t m_,

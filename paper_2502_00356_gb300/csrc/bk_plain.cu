@@ -26,13 +26,15 @@ __global__ void __launch_bounds__(256) cosh_nu_table_kernel(double nu, double* _
 // filled on s with 2 cosh(nu h) for this launch's nu.  Without a table the
 // kernels compute the values themselves; forms without the table run as
 // they are.  Allocates nothing.
+// fill = false: the table already holds this nu's values (an earlier launch
+// for the same matrix filled it on s).
 template <class Form, class Launch>
 cudaError_t with_cosh_nu_table(Form form, double nu, double* table, cudaStream_t s,
-                               Launch&& launch) {
+                               Launch&& launch, bool fill = true) {
   if constexpr (Form::kCoshNuTable) {
     if (table != nullptr) {
       static_assert(kCoshTabSize == BK_COSH_TABLE_LEN, "table length");
-      cosh_nu_table_kernel<<<(kCoshTabSize + 255) / 256, 256, 0, s>>>(nu, table);
+      if (fill) cosh_nu_table_kernel<<<(kCoshTabSize + 255) / 256, 256, 0, s>>>(nu, table);
       form.cnu = table;
     }
   }
@@ -66,12 +68,16 @@ cudaError_t launch_eval_f64(const double* x, const double* nu, void* out, void* 
 
 cudaError_t launch_matern_sym_f64(const double* locs, int64_t n, double sigma2, double beta,
                                   double nu, void* out, int64_t ld, bk_dtype out_t,
-                                  const bk_opts& o, cudaStream_t s) {
+                                  const bk_opts& o, cudaStream_t s, const SymRange& range) {
   if (n == 0) return cudaSuccess;
   return with_plain_form(o, [&](const auto& form) {
-    return with_cosh_nu_table(form, nu, o.d_cosh_table, s, [&](const auto& f) {
-      return launch_matern_sym_form(f, locs, n, sigma2, beta, nu, out, ld, out_t, o.d_counters, s);
-    });
+    return with_cosh_nu_table(
+        form, nu, o.d_cosh_table, s,
+        [&](const auto& f) {
+          return launch_matern_sym_form(f, locs, n, sigma2, beta, nu, out, ld, out_t,
+                                        o.d_counters, s, range);
+        },
+        range.fill_table);
   });
 }
 

@@ -10,6 +10,7 @@
 #include <cstdint>
 
 #include "bk.h"
+#include "bk_internal.h"
 #include "bk_math64.cuh"
 #include "bk_forms.cuh"
 #include "bk_matern_common.cuh"
@@ -266,14 +267,35 @@ __device__ __forceinline__ void tri_tile(int64_t t, int64_t& I, int64_t& J) {
   J = t - I * (I + 1) / 2;
 }
 
+// Lower-triangle tiles in block-column order: with nb block rows, tile
+// number T = off(J) + (I - J), off(J) = J nb - J (J - 1)/2, for I >= J.
+// After the tiles of block-columns 0 .. J - 1 every entry in a row or a
+// column below 32 J is final, which is what lets a caller copy finished
+// panels while the next ones are computed.
+__device__ __forceinline__ int64_t col_tile_offset(int64_t J, int64_t nb) {
+  return J * nb - J * (J - 1) / 2;
+}
+__device__ __forceinline__ void col_tile(int64_t T, int64_t nb, int64_t& I, int64_t& J) {
+  const double b = 2.0 * (double)nb + 1.0;
+  J = (int64_t)(0.5 * (b - sqrt(fmax(b * b - 8.0 * (double)T, 0.0))));
+  if (J < 0) J = 0;
+  while (J > 0 && col_tile_offset(J, nb) > T) --J;
+  while (col_tile_offset(J + 1, nb) <= T) ++J;
+  I = J + (T - col_tile_offset(J, nb));
+}
+
 // Full symmetric matrix: block b computes the lower-triangle tiles
 // [b, b + 1, ..., b + Form::kTilesPerBlock - 1] (then strides by the grid,
 // which only matters beyond 2^31 blocks).  Many short blocks let the
 // hardware block scheduler balance the uneven tile costs across the SMs.
+// col_base < 0: the whole triangle in row order (tri_tile); else tile tix is
+// number col_base + tix of the block-column order (col_tile), for writing a
+// range of block-columns.
 template <class Form, typename OutT>
 __global__ void __launch_bounds__(kThreads, Form::kMinBlocks) matern_sym_kernel(
     const Form form, const double* __restrict__ locs, int64_t n, const MaternParams mp,
-    OutT* __restrict__ out, int64_t ld, int64_t ntiles, unsigned long long* __restrict__ ctr) {
+    OutT* __restrict__ out, int64_t ld, int64_t ntiles, unsigned long long* __restrict__ ctr,
+    int64_t col_base) {
   __shared__ SymTileSmem<OutT> sm;
   __shared__ double s_tab[Form::kStageTable ? kExpTabSize : 1];
   const Form f = bind_table(form, s_tab);
@@ -284,7 +306,8 @@ __global__ void __launch_bounds__(kThreads, Form::kMinBlocks) matern_sym_kernel(
     const int64_t end = min(base + kPer, ntiles);
     for (int64_t tix = base; tix < end; ++tix) {
       int64_t I, J;
-      tri_tile(tix, I, J);
+      if (col_base < 0) tri_tile(tix, I, J);
+      else col_tile(col_base + tix, (n + kTile - 1) / kTile, I, J);
       __syncthreads();  // the previous tile's shared data is no longer read
       sym_tile<Form, OutT, kWarps>(f, sm, locs, n, I, J, mp, out, ld, tl, evals);
     }
@@ -350,18 +373,25 @@ cudaError_t launch_eval_form(const Form& form, const double* x, const double* nu
 template <class Form>
 cudaError_t launch_matern_sym_form(const Form& form, const double* locs, int64_t n, double sigma2, double beta,
                                    double nu, void* out, int64_t ld, bk_dtype out_t,
-                                   unsigned long long* ctr, cudaStream_t s) {
+                                   unsigned long long* ctr, cudaStream_t s,
+                                   const SymRange& range = SymRange{}) {
   if (n == 0) return cudaSuccess;
   const int64_t nb = (n + kTile - 1) / kTile;
-  const int64_t ntiles = nb * (nb + 1) / 2;
+  int64_t ntiles = nb * (nb + 1) / 2, col_base = -1;
+  if (range.j1 >= 0) {  // block-columns [j0, j1) in block-column order
+    const int64_t j0 = range.j0 < 0 ? 0 : range.j0, j1 = range.j1 < nb ? range.j1 : nb;
+    if (j1 <= j0) return cudaSuccess;
+    col_base = j0 * nb - j0 * (j0 - 1) / 2;
+    ntiles = (j1 * nb - j1 * (j1 - 1) / 2) - col_base;
+  }
   const int grid = tile_grid(ntiles, Form::kTilesPerBlock);
   const MaternParams mp = matern_params_host(sigma2, beta, nu);
   if (out_t == BK_F64)
     matern_sym_kernel<Form, double><<<grid, kThreads, 0, s>>>(form, locs, n, mp, (double*)out, ld,
-                                                              ntiles, ctr);
+                                                              ntiles, ctr, col_base);
   else
     matern_sym_kernel<Form, float><<<grid, kThreads, 0, s>>>(form, locs, n, mp, (float*)out, ld,
-                                                             ntiles, ctr);
+                                                             ntiles, ctr, col_base);
   return cudaGetLastError();
 }
 

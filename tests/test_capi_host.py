@@ -148,3 +148,28 @@ def test_batched_host_checks(L):
     assert L.bk_matern_batched(fake, 2, 0, None, None) == bk.BK_ERR_INVALID_ARG
     assert L.bk_batched_plan_destroy(None) == bk.BK_OK
     assert bk._desc_dtype().itemsize == 56
+
+
+def test_matern_tile_host_checks(L):
+    """bk_matern_tile_host: the workspace size and the host-side argument
+    checks (all fail before any CUDA call)."""
+    P = ctypes.c_void_p
+    fake = P(0x1000)          # 256-byte aligned, never dereferenced
+    odd = P(0x1008)
+    need = L.bk_matern_tile_host_workspace(100, bk.BK_F64, 1)
+    small = L.bk_matern_tile_host_workspace(100, bk.BK_F64, 0)
+    assert need >= 100 * 100 * 8 + small
+    assert small >= 2 * 100 * 8 + bk.BK_COSH_TABLE_LEN * 8
+    assert L.bk_matern_tile_host_workspace(100, bk.BK_F32, 1) < need
+    assert L.bk_matern_tile_host_workspace(-1, bk.BK_F64, 1) == 0
+    host = lambda *a: L.bk_matern_tile_host(*a[:9], 0, *a[9:])
+    assert host(fake, 100, 1.0, 0.1, 0.5, fake, 100, 0, None, fake, small - 1, None) == bk.BK_ERR_NOMEM
+    assert host(fake, 100, 1.0, 0.1, 0.5, fake, 100, 0, None, odd, need, None) == bk.BK_ERR_INVALID_ARG
+    assert host(fake, 100, 1.0, 0.1, 0.5, fake, 99, 0, None, fake, need, None) == bk.BK_ERR_INVALID_ARG
+    assert host(fake, 100, 1.0, -0.1, 0.5, fake, 100, 0, None, fake, need, None) == bk.BK_ERR_INVALID_ARG
+    assert host(None, 100, 1.0, 0.1, 0.5, fake, 100, 0, None, fake, need, None) == bk.BK_ERR_INVALID_ARG
+    assert host(fake, 100, 1.0, 0.1, 0.5, fake, 100, 5, None, fake, need, None) == bk.BK_ERR_INVALID_ARG
+    assert host(fake, -1, 1.0, 0.1, 0.5, fake, 100, 0, None, fake, need, None) == bk.BK_ERR_INVALID_ARG
+    assert host(None, 0, 1.0, 0.1, 0.5, None, 0, 0, None, None, 0, None) == bk.BK_OK
+    assert L.bk_matern_tile_host(fake, 100, 1.0, 0.1, 0.5, fake, 100, 0, None, 7, fake, need,
+                                 None) == bk.BK_ERR_INVALID_ARG
