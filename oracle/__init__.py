@@ -17,6 +17,9 @@ Functions and the passages they follow:
 * ``matern_entries`` / ``matern_block``: the Matern covariance of Sec. III-A
   with sigma^2 where r == 0 (Algorithm 3).
 * ``fixed_window_log_k``: the paper's fixed-window branch of Algorithm 2.
+* ``besselk_f64`` / ``matern_entries_f64``: the same dense trapezoid in FP64
+  (one template with the long double version), for samples of 10^5..10^6
+  points where software binary128 (aarch64) would take minutes.
 * ``mlp_*``: FP64 reference forward/backward of the window network (see
   ``mlp.py``).
 
@@ -80,6 +83,8 @@ def _load():
             "oracle_fixed_window_log_k": (D, [D, D, D, I64]),
             "oracle_matern_entries": (None, [P, I64, P, P, I64, D, D, D, P, I]),
             "oracle_matern_block": (None, [P, I64, P, I64, D, D, D, P, I64, I]),
+            "oracle_besselk_batch_f64": (None, [P, P, P, P, I64, I]),
+            "oracle_matern_entries_f64": (None, [P, I64, P, P, I64, D, D, D, P, I]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -127,6 +132,18 @@ def besselk(x, nu, threads: int = 0, return_log: bool = False):
     out = np.empty_like(xa)
     lout = np.empty_like(xa)
     _load().oracle_besselk_batch(_ptr(xa), _ptr(na), _ptr(out), _ptr(lout), xa.size, int(threads))
+    if return_log:
+        return out.reshape(shape)[()], lout.reshape(shape)[()]
+    return out.reshape(shape)[()]
+
+
+def besselk_f64(x, nu, threads: int = 0, return_log: bool = False):
+    """K_nu(x) by the FP64 instance of the dense trapezoid (OpenMP)."""
+    shape, xa, na = _bcast(x, nu)
+    out = np.empty_like(xa)
+    lout = np.empty_like(xa)
+    _load().oracle_besselk_batch_f64(_ptr(xa), _ptr(na), _ptr(out), _ptr(lout), xa.size,
+                                     int(threads))
     if return_log:
         return out.reshape(shape)[()], lout.reshape(shape)[()]
     return out.reshape(shape)[()]
@@ -198,6 +215,23 @@ def matern_entries(locs: np.ndarray, I, J, sigma2: float, beta: float, nu: float
     out = np.empty(I.size, dtype=np.float64)
     _load().oracle_matern_entries(_ptr(locs), n, _ptr(I), _ptr(J), I.size, float(sigma2),
                                   float(beta), float(nu), _ptr(out), int(threads))
+    return out
+
+
+def matern_entries_f64(locs: np.ndarray, I, J, sigma2: float, beta: float, nu: float,
+                       threads: int = 0) -> np.ndarray:
+    """Entries M[I[k], J[k]] by the FP64 instance of the oracle."""
+    locs = _f64(locs)
+    assert locs.ndim == 2 and locs.shape[0] == 2
+    n = locs.shape[1]
+    I = np.ascontiguousarray(np.asarray(I, dtype=np.int64))
+    J = np.ascontiguousarray(np.asarray(J, dtype=np.int64))
+    assert I.shape == J.shape
+    if I.size and (I.min() < 0 or J.min() < 0 or I.max() >= n or J.max() >= n):
+        raise IndexError("entry index out of range")
+    out = np.empty(I.size, dtype=np.float64)
+    _load().oracle_matern_entries_f64(_ptr(locs), n, _ptr(I), _ptr(J), I.size, float(sigma2),
+                                      float(beta), float(nu), _ptr(out), int(threads))
     return out
 
 

@@ -44,6 +44,8 @@
 #include <omp.h>
 #endif
 
+#include <limits>
+
 typedef long double ld;
 
 static const ld kLn2 = 0.693147180559945309417232121458176568075500134L;
@@ -54,72 +56,87 @@ static const ld kEulerGamma = 0.577215664901532860606512090082402431042159336L;
 // Eq. (logintegrand): g(t) = log cosh(nu t) - x cosh t.
 // log cosh(y) is written as |y| + log(1 + e^{-2|y|}) - log 2 so that it does
 // not overflow for large |nu t|.
-static ld log_cosh(ld y) {
-  y = fabsl(y);
-  return y + log1pl(expl(-2.0L * y)) - kLn2;
+// Written once for a real type R (long double for the oracle proper; double
+// for the FP64 instance used on large samples), with std:: functions, whose
+// long double overloads are expl, log1pl, coshl, ...
+template <typename R>
+static R log_cosh_t(R y) {
+  y = std::fabs(y);
+  return y + std::log1p(std::exp(R(-2) * y)) - R(kLn2);
 }
 
-static ld g_of(ld t, ld x, ld nu) { return log_cosh(nu * t) - x * coshl(t); }
+template <typename R>
+static R g_of_t(R t, R x, R nu) { return log_cosh_t<R>(nu * t) - x * std::cosh(t); }
+
+static ld log_cosh(ld y) { return log_cosh_t<ld>(y); }
+static ld g_of(ld t, ld x, ld nu) { return g_of_t<ld>(t, x, nu); }
 
 // g'(t) = nu tanh(nu t) - x sinh t.
 static ld gprime_of(ld t, ld x, ld nu) { return nu * tanhl(nu * t) - x * sinhl(t); }
 
 // ---------------------------------------------------------------------------
 // K_nu(x) by the dense trapezoid rule.  Returns log K; *status = 0 on success,
-// 1 if the window search or the halving loop did not finish.
-static ld dense_log_k(ld x, ld nu, int* status) {
+// 1 if the window search or the halving loop did not finish.  R is the real
+// type of every step (long double: the oracle proper; double: its FP64
+// instance, for samples too large for software binary128 on aarch64).
+template <typename R>
+static R dense_log_k_t(R x, R nu, int* status) {
   *status = 0;
-  nu = fabsl(nu);  // K_{-nu} = K_nu: the integrand only depends on |nu|.
+  nu = std::fabs(nu);  // K_{-nu} = K_nu: the integrand only depends on |nu|.
 
   // Window [0, T]: walk outward in steps of 1/64 keeping the running maximum
   // of g; stop once g has fallen 90 below it.  Before the peak g increases
   // (it is unimodal), so the stop can only happen past the peak.  The part
   // beyond T is below e^{-90} of the peak value.
-  const ld step = 1.0L / 64.0L;
-  ld gmax = g_of(0.0L, x, nu);
-  ld T = 0.0L;
+  const R step = R(1) / R(64);
+  R gmax = g_of_t<R>(R(0), x, nu);
+  R T = R(0);
   for (long k = 1; k <= 64L * 200L; ++k) {
-    ld t = step * (ld)k;
-    ld gt = g_of(t, x, nu);
+    R t = step * (R)k;
+    R gt = g_of_t<R>(t, x, nu);
     if (gt > gmax) gmax = gt;
-    if (gt < gmax - 90.0L) { T = t; break; }
+    if (gt < gmax - R(90)) { T = t; break; }
   }
-  if (T == 0.0L) { *status = 1; return NAN; }
+  if (T == R(0)) { *status = 1; return NAN; }
 
   // The narrowest feature of the integrand is the peak, whose width is at
   // least (x^2 + nu^2)^{-1/4} (|g''| at the peak is at most x cosh t*,
   // and x sinh t* <= nu there).  Start with a step well below both that
   // width and 1/32, then halve.
-  ld h_start = 0.25L / powl(x * x + nu * nu + 1.0L, 0.25L);
-  if (h_start > 1.0L / 32.0L) h_start = 1.0L / 32.0L;
-  long M = (long)ceill(T / h_start);
+  R h_start = R(0.25) / std::pow(x * x + nu * nu + R(1), R(0.25));
+  if (h_start > R(1) / R(32)) h_start = R(1) / R(32);
+  long M = (long)std::ceil(T / h_start);
   if (M < 64) M = 64;
 
   // Trapezoid on M intervals: endpoints weight 1/2, interior weight 1.  The
   // terms are exp(g(t) - gmax) so nothing overflows; K = e^{gmax} h S.
-  ld S = 0.5L * (expl(g_of(0.0L, x, nu) - gmax) + expl(g_of(T, x, nu) - gmax));
+  R S = R(0.5) * (std::exp(g_of_t<R>(R(0), x, nu) - gmax) + std::exp(g_of_t<R>(T, x, nu) - gmax));
   for (long m = 1; m < M; ++m) {
-    ld t = T * (ld)m / (ld)M;
-    S += expl(g_of(t, x, nu) - gmax);
+    R t = T * (R)m / (R)M;
+    S += std::exp(g_of_t<R>(t, x, nu) - gmax);
   }
-  ld prev = (T / (ld)M) * S;
+  R prev = (T / (R)M) * S;
 
-  ld tol = 64.0L * LDBL_EPSILON;
-  if (tol < 1e-30L) tol = 1e-30L;
-  if (tol < 1e-17L && LDBL_MANT_DIG < 100) tol = 1e-17L;
+  // Two successive halvings must agree to 64 units of the type's epsilon
+  // (at least 1e-30; 1e-17 for the x87 80-bit type).
+  R tol = R(64) * std::numeric_limits<R>::epsilon();
+  if (tol < R(1e-30)) tol = R(1e-30);
+  if (tol < R(1e-17) && std::numeric_limits<R>::digits > 53 &&
+      std::numeric_limits<R>::digits < 100)
+    tol = R(1e-17);
   int agree = 0;
   for (int level = 0; level < 14; ++level) {
     // Halving adds the midpoints of the current intervals.
-    ld add = 0.0L;
+    R add = R(0);
     for (long m = 0; m < M; ++m) {
-      ld t = T * (ld)(2 * m + 1) / (ld)(2 * M);
-      add += expl(g_of(t, x, nu) - gmax);
+      R t = T * (R)(2 * m + 1) / (R)(2 * M);
+      add += std::exp(g_of_t<R>(t, x, nu) - gmax);
     }
     S += add;
     M *= 2;
-    ld cur = (T / (ld)M) * S;
-    if (fabsl(cur - prev) <= tol * cur) {
-      if (++agree == 2) return gmax + logl(cur);
+    R cur = (T / (R)M) * S;
+    if (std::fabs(cur - prev) <= tol * cur) {
+      if (++agree == 2) return gmax + std::log(cur);
     } else {
       agree = 0;
     }
@@ -128,6 +145,8 @@ static ld dense_log_k(ld x, ld nu, int* status) {
   *status = 1;
   return NAN;
 }
+
+static ld dense_log_k(ld x, ld nu, int* status) { return dense_log_k_t<ld>(x, nu, status); }
 
 // ---------------------------------------------------------------------------
 // Temme's series, Sec. IV-A, for |mu| <= 1/2, giving K_mu and K_{mu+1}.
@@ -560,6 +579,48 @@ void oracle_matern_block(const double* locs1, int64_t m, const double* locs2, in
                        (ld)sigma2, (ld)beta, (ld)nu, &st);
       out[i + j * ld_] = st ? NAN : (double)v;
     }
+}
+
+// The FP64 instance of the oracle (dense_log_k_t<double>): K_nu(x) and its
+// log for large samples; agrees with the long double oracle to about 1e-13
+// relative over the region of Sec. IV-C (pinned in the tests).
+void oracle_besselk_batch_f64(const double* x, const double* nu, double* out, double* log_out,
+                              int64_t n, int nthreads) {
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+  for (int64_t i = 0; i < n; ++i) {
+    const double xi = x[i];
+    if (xi == 0.0) { out[i] = INFINITY; if (log_out) log_out[i] = INFINITY; continue; }
+    if (!(xi > 0.0)) { out[i] = NAN; if (log_out) log_out[i] = NAN; continue; }
+    int st = 0;
+    const double r = dense_log_k_t<double>(xi, nu[i], &st);
+    out[i] = st ? NAN : std::exp(r);
+    if (log_out) log_out[i] = st ? NAN : r;
+  }
+}
+
+// Matern entries (I[k], J[k]) by the FP64 instance: the steps of matern_ld
+// in double.
+void oracle_matern_entries_f64(const double* locs, int64_t n, const int64_t* I, const int64_t* J,
+                               int64_t m, double sigma2, double beta, double nu, double* out,
+                               int nthreads) {
+  const double logc = std::log(sigma2) - (nu - 1.0) * (double)kLn2 - std::lgamma(nu);
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+  for (int64_t k = 0; k < m; ++k) {
+    const int64_t i = I[k], j = J[k];
+    const double dx = locs[j] - locs[i], dy = locs[n + j] - locs[n + i];
+    const double r = std::sqrt(dx * dx + dy * dy);
+    if (r == 0.0) { out[k] = sigma2; continue; }
+    const double z = r / beta;
+    int st = 0;
+    const double logk = dense_log_k_t<double>(z, nu, &st);
+    out[k] = st ? NAN : std::exp(logc + nu * std::log(z) + logk);
+  }
 }
 
 int oracle_max_threads(void) {

@@ -345,3 +345,47 @@ def test_empirical_upper_bound_algorithm1(orc):
 
     assert max_ae(c["t1"]) <= c["ae_bound"]
     assert max_ae(6.5) > c["ae_bound"]
+
+
+# ---------------------------------------------------------------------------
+# The FP64 instance of the dense trapezoid (the same template as the long
+# double oracle, in double), used for the 10^5..10^6-point error samples of
+# the benchmark.  Pinned on its own against the closed forms and the
+# recurrence, and against the long double oracle over the region.
+@pytest.mark.parametrize("order2", [1, 3, 5])
+def test_f64_instance_closed_forms(orc, order2):
+    got = orc.besselk_f64(X_GRID, order2 / 2)
+    np.testing.assert_allclose(got, k_half_closed(X_GRID, order2), rtol=5e-14, atol=0)
+
+
+def test_f64_instance_recurrence_and_symmetry(orc):
+    rng = np.random.default_rng(12)
+    x = np.exp(rng.uniform(np.log(1e-3), np.log(140), 40))
+    nu = rng.uniform(1.0, 12.0, 40)
+    km, k0, kp = orc.besselk_f64(x, nu - 1), orc.besselk_f64(x, nu), orc.besselk_f64(x, nu + 1)
+    np.testing.assert_allclose(kp, km + (2 * nu / x) * k0, rtol=5e-14)
+    assert np.array_equal(orc.besselk_f64(x, nu), orc.besselk_f64(x, -nu))
+
+
+def test_f64_instance_matches_long_double(orc):
+    rng = np.random.default_rng(13)
+    x = np.exp(rng.uniform(np.log(1e-3), np.log(140), 300))
+    nu = rng.uniform(0.0, 20.0, 300)
+    _, l64 = orc.besselk_f64(x, nu, return_log=True)
+    _, lld = orc.besselk(x, nu, return_log=True)
+    assert np.all(np.abs(l64 - lld) <= 1e-13 + 1e-15 * np.abs(lld))
+
+
+def test_f64_instance_matern_entries(orc):
+    locs = inputs.jittered_grid(300, seed=19)
+    I, J = inputs.entry_sample(300, 400, seed=20, near_fraction=0.1)
+    for nu in (0.5, 1.7, 3.2):
+        a = orc.matern_entries_f64(locs, I, J, 1.3, 0.05, nu)
+        b = orc.matern_entries(locs, I, J, 1.3, 0.05, nu)
+        np.testing.assert_allclose(a, b, rtol=1e-13, atol=1e-300)
+    dx = locs[0][I] - locs[0][J]
+    dy = locs[1][I] - locs[1][J]
+    z = np.sqrt(dx * dx + dy * dy) / 0.05
+    want = np.where(z == 0, 1.3, 1.3 * np.exp(-z))
+    np.testing.assert_allclose(orc.matern_entries_f64(locs, I, J, 1.3, 0.05, 0.5), want,
+                               rtol=5e-14, atol=0)
