@@ -228,12 +228,12 @@ struct FormF64Fixed {
 // (x < 1, where nu log x cancels against log K) and, for FP64 output, for
 // entries beyond the float range.
 template <typename OutT>
-__device__ __forceinline__ OutT matern_f32_finish(DF z, const Window32& w, const Quad32& q,
+__device__ __forceinline__ OutT matern_f32_finish(DF z, const Quad32& q,
                                                   const MaternParams& mp) {
   if (z.hi >= 1.0f) {
     const DF nu = DF{mp.nu_hi, mp.nu_lo};
     DF a = df_add(DF{mp.log_pref_hi, mp.log_pref_lo}, df_mul(nu, df_log(z)));
-    a = df_add(a, df_log_scale(z, nu, w.ts, q));
+    a = df_add(a, df_log_scale(z, nu, q));
     if constexpr (sizeof(OutT) == sizeof(float)) {
       return df_exp_times(a, q.hS);
     } else {
@@ -242,7 +242,7 @@ __device__ __forceinline__ OutT matern_f32_finish(DF z, const Window32& w, const
   }
   const double z64 = (double)z.hi + (double)z.lo;
   const double lz = log_pos(z64);
-  return to_out<OutT>(exp_fast(fma(mp.nu, lz, mp.log_pref) + log_scale_from(z64, mp.nu, w.ts, q)) *
+  return to_out<OutT>(exp_fast(fma(mp.nu, lz, mp.log_pref) + log_scale_from(z64, mp.nu, q)) *
                       (double)q.hS);
 }
 
@@ -276,7 +276,7 @@ __device__ __forceinline__ void eval_out_f32(const Form& f, double x, double nu,
     ++evals;
     Window32 w;
     const Quad32 q = f.quad(xd.hi, [&] { return x; }, nd.hi, nd.lo, w, tl);
-    const DF a = df_log_scale(xd, nd, w.ts, q);
+    const DF a = df_log_scale(xd, nd, q);
     if constexpr (sizeof(OutT) == sizeof(float)) {
       k = df_exp_times(a, q.hS);
       if (want_log) log_k = a.hi + (a.lo + kLn2f * mufu_lg2(q.hS));
@@ -319,7 +319,7 @@ struct FormF32 {
     const float xf = (float)x, nf = (float)nu, nl = (float)(nu - (double)nf);
     Window32 w;
     const Quad32 q = quad(xf, [&] { return x; }, nf, nl, w, tl);
-    const double sc = log_scale_from(x, nu, w.ts, q);
+    const double sc = log_scale_from(x, nu, q);
     log_k = sc + (double)(kLn2f * mufu_lg2(q.hS));
     return exp_fast(sc) * (double)q.hS;
   }
@@ -340,7 +340,7 @@ struct FormF32 {
     Window32 w;
     const Quad32 q = quad(z.hi, [&] { return (double)z.hi + (double)z.lo; }, mp.nu_hi, mp.nu_lo,
                           w, tl);
-    return matern_f32_finish<OutT>(z, w, q, mp);
+    return matern_f32_finish<OutT>(z, q, mp);
   }
 };
 
@@ -381,7 +381,7 @@ struct FormF32Learned {
     const float xf = (float)x, nf = (float)nu, nl = (float)(nu - (double)nf);
     Window32 w;
     const Quad32 q = quad(xf, [&] { return x; }, nf, nl, w, tl);
-    const double sc = log_scale_from(x, nu, w.ts, q);
+    const double sc = log_scale_from(x, nu, q);
     log_k = sc + (double)(kLn2f * mufu_lg2(q.hS));
     return exp_fast(sc) * (double)q.hS;
   }
@@ -401,7 +401,7 @@ struct FormF32Learned {
     Window32 w;
     const Quad32 q = quad(z.hi, [&] { return (double)z.hi + (double)z.lo; }, mp.nu_hi, mp.nu_lo,
                           w, tl);
-    return matern_f32_finish<OutT>(z, w, q, mp);
+    return matern_f32_finish<OutT>(z, q, mp);
   }
 };
 

@@ -186,39 +186,33 @@ __device__ __forceinline__ void expm1_pm_f32(float y, float& em, float& emn) {
 
 // Scaled trapezoid sum of the FP32 form, with the weights of Eq. (refined):
 //   S = sum_j c_j exp(a_j) (1 + e^{-2 nu t_j}),  c_0 = c_N = 1/2,
-//   a_j = nu tau_j - x (cosh t_j - cosh ts),  tau_j = t_j - ts = (t0 - ts) + j h.
-// Peak-relative nodes keep nu tau_j and the spacing accurate near the peak.
-// The cosh difference is written so that no large argument enters an FP32
-// exponential: with A = x e^{ts}/2 and B = x e^{-ts}/2 (from FP64),
-//   x (cosh t - cosh ts) = A expm1(tau) + B expm1(-tau),
-// and at ts = 0, x (cosh tau - 1) = 2 x sinh^2(tau/2).  (sinh(ts + tau/2) in
-// FP32 would carry an argument error of ulp(ts) ~ 1e-6 at ts ~ 10, times
-// A ~ nu in the exponent.)  e^{-2 nu t_j} follows a geometric recurrence; the
-// sum is Kahan-compensated.  The order enters as nu_hi + nu_lo (the FP64
-// order split into two floats): rounding nu itself to FP32 would integrate
-// K of a neighbouring order, off by ulp(nu) d(log K)/d nu ~ ulp(nu) ln(2 nu/x),
-// ~1e-5 at x ~ 1e-3, nu ~ 18.  Returns h S.
-__device__ __forceinline__ float trapezoid_f32(float x, float nu, float nu_lo, const Window32& w,
-                                               float Ah, float Bh, int N, float& amax, Tally& tl) {
-  const float h = (w.t1 - w.t0) / (float)N;
-  const float tau0 = w.t0 - w.ts;
-  float W = mufu_ex2(-2.0f * kLog2ef * nu * w.t0);
+//   a_j = nu tau_j - x (cosh t_j - cosh s),  tau_j = t_j - s = (t0 - s) + j h,
+// centred on the shift point s (a grid point next to the peak, see
+// shift_f32; any s is exact, it only scales the terms).  Peak-relative nodes
+// keep nu tau_j and the spacing accurate near the peak.  The cosh difference
+// is written so that no large argument enters an FP32 exponential and
+// nothing cancels, for every s >= 0 alike: with em = e^tau - 1 and
+// emn = e^{-tau} - 1 (so em emn = -(em + emn)), D = x sinh s and
+// B = x e^{-s}/2,
+//   x (cosh t - cosh s) = x e^s/2 em + B emn = em (D - B emn),
+// where D - B emn >= D/2 > 0 for t >= 0 (tau >= -s).  e^{-2 nu t_j} follows
+// a geometric recurrence; the sum is Kahan-compensated.  The order enters as
+// nu_hi + nu_lo (the FP64 order split into two floats): rounding nu itself to
+// FP32 would integrate K of a neighbouring order, off by ulp(nu) d(log K)/d nu
+// ~ ulp(nu) ln(2 nu/x), ~1e-5 at x ~ 1e-3, nu ~ 18.  Returns h S.
+__device__ __forceinline__ float trapezoid_f32(float nu, float nu_lo, float t0, float t1, float s,
+                                               float B, float D, int N, float& amax, Tally& tl) {
+  const float h = (t1 - t0) / (float)N;
+  const float tau0 = t0 - s;
+  float W = mufu_ex2(-2.0f * kLog2ef * nu * t0);
   const float rho = mufu_ex2(-2.0f * kLog2ef * nu * h);
   float S = 0.0f, c = 0.0f, f = 0.0f, f0 = 0.0f, jf = 0.0f;
-  const float x2 = 2.0f * x;
-  const bool at_zero = (w.ts == 0.0f);
   amax = -3.0e38f;
   for (int j = 0; j <= N; ++j, jf += 1.0f) {  // jf = j exactly (float counter, no conversion)
     const float tau = fmaf(jf, h, tau0);
-    float a;
-    if (at_zero) {
-      const float sq = sinh_f32(0.5f * tau);
-      a = fmaf(nu, tau, fmaf(nu_lo, tau, -x2 * sq * sq));
-    } else {
-      float em, emn;
-      expm1_pm_f32(tau, em, emn);
-      a = fmaf(nu, tau, fmaf(nu_lo, tau, -fmaf(Ah, em, Bh * emn)));
-    }
+    float em, emn;
+    expm1_pm_f32(tau, em, emn);
+    const float a = fmaf(nu, tau, fmaf(nu_lo, tau, -em * fmaf(-B, emn, D)));
     amax = fmaxf(amax, a);
     f = exp_f32(a);
     f = fmaf(f, W, f);
@@ -459,13 +453,48 @@ __device__ __forceinline__ DF df_cosh_m1(float t) {
   return df_add_f(DF{0.5f * c.hi, 0.5f * c.lo}, -1.0f);
 }
 
-// The FP32 quadrature of one evaluation on a given window: h S and
-// x (cosh ts - 1) (FP32; NaN h S when the node bound is exceeded).
+// The FP32 quadrature of one evaluation on a given window: h S, the shift
+// point s its terms are centred on and cosh s - 1 there (NaN h S when the
+// node bound is exceeded).
 struct Quad32 {
   float hS;
-  float xc1;   // x (cosh ts - 1) = 2 x sinh^2(ts/2)
-  float amax;  // largest node exponent g(t_j) - g(ts) (up to the e^{-2 nu t} factor)
+  float ts;    // the shift point s (the window's peak rounded to the grid of kPeakTab)
+  DF cm1;      // cosh s - 1 as a double-float
+  float amax;  // largest node exponent g(t_j) - g(s) (up to the e^{-2 nu t} factor)
 };
+
+// The shift points of the FP32 quadrature: the peak ts rounded to the grid
+// k/64 (k <= 1024), where kPeakTab holds cosh s - 1 (double-float), sinh s
+// and e^{-s} (gen_peak_table.py).  Any shift point is exact (it scales the
+// terms, and log K adds it back); one within 1/128 of the peak keeps the
+// largest scaled term at e^{|g''| / 32768} ~ 1.  The table takes the place
+// of per-evaluation FP32 exponentials of ts and of a double-float cosh ts - 1.
+constexpr int kPeakTabSize = 1025;
+static __device__ const float4 kPeakTab[kPeakTabSize] = {
+#include "bk_peak_table.inc"
+};
+
+// s, cosh s - 1, D = x sinh s and B = x e^{-s}/2 for the peak ts: from the
+// table on its grid, else (ts >= 16, or not a number) at ts itself from FP32
+// and double-float exponentials.
+__device__ __forceinline__ void shift_f32(float x, float ts, float& s, DF& cm1, float& B,
+                                          float& D) {
+  if (ts >= 0.0f && ts < 16.0f) {
+    const float r = rintf(ts * 64.0f);
+    s = r * 0.015625f;
+    const float4 e = __ldg(&kPeakTab[__float2int_rn(r)]);
+    cm1 = DF{e.x, e.y};
+    D = x * e.z;
+    B = 0.5f * x * e.w;
+  } else {
+    s = ts;
+    float ep, emx;
+    exp_pm_f32(ts, ep, emx);
+    B = 0.5f * x * emx;
+    D = 0.5f * x * (ep - emx);  // no cancellation at ts >= 16
+    cm1 = df_cosh_m1(ts);
+  }
+}
 
 __device__ __forceinline__ Quad32 quad_f32(float x, float nu, float nu_lo, const Window32& w,
                                            Tally& tl) {
@@ -474,45 +503,29 @@ __device__ __forceinline__ Quad32 quad_f32(float x, float nu, float nu_lo, const
   if (N > kF32MaxNodes) {
     ++tl.fail;
     q.hS = __int_as_float(0x7fc00000);
-    q.xc1 = 0.0f;
+    q.ts = w.ts;
+    q.cm1 = DF{0.0f, 0.0f};
     q.amax = 0.0f;
     return q;
   }
-  float Ah = 0.5f * x, Bh = 0.5f * x;
-  q.xc1 = 0.0f;
-  if (w.ts > 0.0f) {
-    float ep, em;
-    exp_pm_f32(w.ts, ep, em);
-    Ah *= ep;
-    Bh *= em;
-    const float sh = sinh_f32(0.5f * w.ts);
-    q.xc1 = 2.0f * x * sh * sh;
-  }
-  q.hS = trapezoid_f32(x, nu, nu_lo, w, Ah, Bh, N, q.amax, tl);
+  float B, D;
+  shift_f32(x, w.ts, q.ts, q.cm1, B, D);
+  q.hS = trapezoid_f32(nu, nu_lo, w.t0, w.t1, q.ts, B, D, N, q.amax, tl);
   return q;
 }
 
-// log f_s = nu ts - x cosh(ts) - ln 2 in FP64 (nu ts reaches ~200): x exactly,
-// x (cosh ts - 1) from FP32 when it is below 2 (absolute error < 5e-7),
-// else from FP64 e^{ts}.
-__device__ __forceinline__ double log_scale_from(double x64, double nu64, float ts,
-                                                 const Quad32& q) {
-  double xc1 = (double)q.xc1;
-  if (q.xc1 > 2.0f) {
-    const double e = exp_bounded((double)ts);
-    const double sh = 0.5 * (e - 1.0 / e);
-    xc1 = x64 * (sh * sh) / (0.5 * (e + 1.0 / e) + 1.0);  // x (cosh - 1) = x sinh^2/(cosh + 1)
-  }
-  return fma(nu64, (double)ts, -x64) - xc1 - kLn2;
+// log f_s = nu s - x cosh(s) - ln 2 in FP64 (nu s reaches ~200), s the
+// quadrature's shift point.
+__device__ __forceinline__ double log_scale_from(double x64, double nu64, const Quad32& q) {
+  const double xc1 = x64 * ((double)q.cm1.hi + (double)q.cm1.lo);
+  return fma(nu64, (double)q.ts, -x64) - xc1 - kLn2;
 }
 
-// The same log f_s = nu ts - x cosh(ts) - ln 2 as a double-float from the
-// double-float x and nu, without FP64 instructions: x (cosh ts - 1) from the
-// quadrature's FP32 value when it is at most 2 (absolute error < 5e-7),
-// else x times cosh ts - 1 in double-float (df_cosh_m1).
-__device__ __forceinline__ DF df_log_scale(DF x, DF nu, float ts, const Quad32& q) {
-  DF a = df_add(df_mul_f(nu, ts), df_neg(x));
-  a = (q.xc1 <= 2.0f) ? df_add_f(a, -q.xc1) : df_add(a, df_neg(df_mul(x, df_cosh_m1(ts))));
+// The same log f_s = nu s - x cosh(s) - ln 2 as a double-float from the
+// double-float x and nu, without FP64 instructions.
+__device__ __forceinline__ DF df_log_scale(DF x, DF nu, const Quad32& q) {
+  DF a = df_add(df_mul_f(nu, q.ts), df_neg(x));
+  a = df_add(a, df_neg(df_mul(x, q.cm1)));
   return df_add(a, DF{-kLn2DfHi, -kLn2DfLo});
 }
 

@@ -61,3 +61,29 @@ def test_rgamma_coefficients_are_the_generators():
     for z in (0.1, 0.37, 0.5, -0.45):
         s = sum(ck * z ** k for k, ck in enumerate(c))
         assert abs(s * math.gamma(z) - 1.0) <= 1e-14
+
+
+def test_peak_table_is_the_generators():
+    """kPeakTab: (cosh s - 1) as hi + lo, sinh s, e^-s at s = k/64."""
+    import struct
+    gen = load("gen_peak_table")
+    with open(os.path.join(CSRC, "bk_peak_table.inc")) as f:
+        rows = [line for line in f if line.strip().startswith("{")]
+    vals = gen.values()
+    assert len(rows) == len(vals) == 1025
+
+    def lit(tok):
+        tok = tok.strip().rstrip("f")
+        return 0.0 if tok in ("0.0", "-0.0") else float.fromhex(tok)
+
+    f32 = lambda v: struct.unpack("f", struct.pack("f", v))[0]
+    ulp32 = lambda v: math.ldexp(1.0, math.frexp(v)[1] - 24)  # float spacing at v
+    for k in range(0, 1025, 7):
+        got = tuple(lit(t) for t in rows[k].strip().strip("{},").split(","))
+        assert got == vals[k]
+        s = k / 64.0
+        cm1 = 2.0 * math.sinh(s / 2) ** 2  # cosh s - 1 without cancellation
+        assert abs((got[0] + got[1]) - cm1) <= 1e-13 * max(cm1, 1e-300)
+        assert all(v == f32(v) for v in got)  # every entry is a float
+        assert abs(got[2] - math.sinh(s)) <= ulp32(math.sinh(s)) if k else got[2] == 0.0
+        assert abs(got[3] - math.exp(-s)) <= ulp32(math.exp(-s))
