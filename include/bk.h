@@ -113,13 +113,25 @@ typedef struct {
      overlap on the GPU.  NULL (default): the kernels compute the values.
      No call allocates either way. */
   double* d_cosh_table;
+  /* Bare evaluations (bk_eval_ex) of the FP32 forms only: lanes that share
+     one evaluation's quadrature nodes, 1, 2, 4 or 8 (the node loops of a
+     warp's 32 evaluations then run in `lanes` passes on groups of that many
+     lanes, partial sums combined by a compensated shuffle reduction).
+     0 (default): the choice bk_eval_autotune made for this device, form and
+     output dtype in this process, else BK_EVAL_LANES_DEFAULT.  Other entry
+     points ignore it (the Matern writers' warps evaluate 32 neighbouring
+     entries of similar cost, one per lane). */
+  int lanes;
 } bk_opts;
+
+/* lanes per evaluation when bk_opts.lanes is 0 and nothing was autotuned. */
+#define BK_EVAL_LANES_DEFAULT 1
 
 /* Length (doubles) of bk_opts.d_cosh_table. */
 #define BK_COSH_TABLE_LEN 3328
 
 /* Fills *o with the defaults: BK_WIN_SEARCH, BK_F64, b = 40, t1 = 9, no
-   counters, no network, search_f64 = 0, series_below = 0. */
+   counters, no network, search_f64 = 0, series_below = 0, lanes = 0. */
 void bk_opts_default(bk_opts* o);
 
 const char* bk_version(void);
@@ -148,6 +160,20 @@ bk_status bk_eval(const double* x, const double* nu, double* out, int64_t n, bk_
  */
 bk_status bk_eval_ex(const double* x, const double* nu, void* out, void* log_out,
                      bk_dtype out_dtype, int64_t n, const bk_opts* opts, bk_stream_t stream);
+
+/*
+ * bk_eval_autotune: times bk_eval_ex of the FP32 forms (opts->compute =
+ * BK_F32, searched or learned window) with 1, 2, 4 and 8 lanes per
+ * evaluation on the first min(n, 2^20) pairs of the caller's x, nu (device,
+ * as bk_eval_ex; out receives results), keeps the fastest for this device,
+ * form and output dtype (used by later calls with opts->lanes == 0) and
+ * returns it in *best_lanes (host).  The lane split is the multi-threaded
+ * evaluation of K_nu that Sec. VI names as future work, on the node loop of
+ * Algorithm 2.  Synchronises `stream`; allocates no device memory.  Errors:
+ * BK_ERR_UNSUPPORTED for the FP64 forms, BK_ERR_INVALID_ARG as bk_eval_ex.
+ */
+bk_status bk_eval_autotune(const double* x, const double* nu, void* out, bk_dtype out_dtype,
+                           int64_t n, const bk_opts* opts, bk_stream_t stream, int* best_lanes);
 
 /* Derivatives of K_nu(x) with K itself, from one quadrature (not in the
  * paper; for gradient-based maximum likelihood): differentiating Eq.

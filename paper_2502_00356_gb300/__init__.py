@@ -33,7 +33,7 @@ BK_HOST_AUTO, BK_HOST_STAGED = 0, 1
 #: every symbol include/bk.h declares (checked by the CPU tests)
 EXPORTS = (
     "bk_opts_default", "bk_version", "bk_last_error", "bk_status_string", "bk_sync",
-    "bk_eval", "bk_eval_ex", "bk_eval_grad", "bk_gaussian_loglik", "bk_matern_tile", "bk_matern_tile_ex", "bk_matern_tile2",
+    "bk_eval", "bk_eval_ex", "bk_eval_grad", "bk_eval_autotune", "bk_gaussian_loglik", "bk_matern_tile", "bk_matern_tile_ex", "bk_matern_tile2",
     "bk_matern_tile_host", "bk_matern_tile_host_workspace",
     "bk_morton_order", "bk_probe_pipe", "bk_math_probe", "bk_batched_plan_create", "bk_batched_plan_destroy",
     "bk_batched_plan_info", "bk_batched_autotune", "bk_matern_batched",
@@ -57,7 +57,8 @@ class bk_opts(ctypes.Structure):
     _fields_ = [("window", ctypes.c_int), ("compute", ctypes.c_int), ("fixed_bins", ctypes.c_int),
                 ("fixed_t1", ctypes.c_double), ("d_counters", ctypes.c_void_p),
                 ("learned", ctypes.c_void_p), ("search_f64", ctypes.c_int),
-                ("series_below", ctypes.c_double), ("d_cosh_table", ctypes.c_void_p)]
+                ("series_below", ctypes.c_double), ("d_cosh_table", ctypes.c_void_p),
+                ("lanes", ctypes.c_int)]
 
 
 _lock = threading.Lock()
@@ -90,6 +91,7 @@ def lib() -> ctypes.CDLL:
             "bk_eval": (I, [P, P, P, I64, P]),
             "bk_eval_ex": (I, [P, P, P, P, I, I64, P, P]),
             "bk_eval_grad": (I, [P, P, P, P, P, I64, P, P]),
+            "bk_eval_autotune": (I, [P, P, P, I, I64, P, P, P]),
             "bk_gaussian_loglik": (I, [P, I64, I64, P, P, P, P, P]),
             "bk_matern_tile": (I, [P, I64, D, D, D, P, I64, I, P]),
             "bk_matern_tile_ex": (I, [P, I64, D, D, D, P, I64, I, P, P]),
@@ -174,7 +176,7 @@ def _ptr(t) -> Optional[int]:
 
 def make_opts(window: int = BK_WIN_SEARCH, compute: int = BK_F64, fixed_bins: int = 40,
               fixed_t1: float = 9.0, counters=None, learned=None,
-              search_f64: bool = False, series_below: float = 0.0) -> bk_opts:
+              search_f64: bool = False, series_below: float = 0.0, lanes: int = 0) -> bk_opts:
     """A bk_opts struct; ``counters`` is an optional CUDA int64 tensor of
     BK_NUM_COUNTERS entries that kernels add to; ``learned`` a LearnedWindow
     (implies window = BK_WIN_LEARNED and compute = BK_F32 unless given);
@@ -193,6 +195,7 @@ def make_opts(window: int = BK_WIN_SEARCH, compute: int = BK_F64, fixed_bins: in
     o.window, o.compute, o.fixed_bins, o.fixed_t1 = int(window), int(compute), int(fixed_bins), float(fixed_t1)
     o.search_f64 = int(bool(search_f64))
     o.series_below = float(series_below)
+    o.lanes = int(lanes)
     if counters is not None:
         torch = _torch()
         _dev(counters, "counters", torch.int64)
@@ -265,6 +268,22 @@ def bk_eval_ex(x, nu, out=None, log_out=None, out_dtype=None, opts: Optional[bk_
     _check(lib().bk_eval_ex(_ptr(x), _ptr(nu), _ptr(out), _ptr(log_out), code, n, optp,
                             _stream_ptr(stream)))
     return out, log_out
+
+
+def bk_eval_autotune(x, nu, out, opts: bk_opts, stream=None) -> int:
+    """Times the FP32 forms' bare evaluation with 1, 2, 4 and 8 lanes per
+    evaluation on (up to 2^20 of) these pairs, keeps the fastest for later
+    calls with lanes = 0 in this process and returns it (synchronises)."""
+    torch = _torch()
+    _dev(x, "x", torch.float64)
+    _dev(nu, "nu", torch.float64)
+    _dev(out, "out")
+    if nu.numel() != x.numel() or out.numel() != x.numel():
+        raise ValueError("x, nu and out must have the same number of elements")
+    best = ctypes.c_int(0)
+    _check(lib().bk_eval_autotune(_ptr(x), _ptr(nu), _ptr(out), _dtype_code(out.dtype), x.numel(),
+                                  ctypes.byref(opts), _stream_ptr(stream), ctypes.byref(best)))
+    return best.value
 
 
 def bk_eval_grad(x, nu, k=None, dk_dx=None, dk_dnu=None, opts: Optional[bk_opts] = None,

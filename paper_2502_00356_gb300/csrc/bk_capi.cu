@@ -18,6 +18,10 @@ namespace bk {
 
 namespace {
 thread_local char g_err[512] = "";
+// lanes per evaluation chosen by bk_eval_autotune, per device, FP32 form
+// (searched, learned window) and output dtype; 0 = not tuned.
+std::mutex g_lanes_mutex;
+int g_eval_lanes[64][2][2] = {};
 std::mutex g_sm_mutex;
 int g_sm_count[64] = {0};
 }  // namespace
@@ -52,6 +56,17 @@ namespace {
 bool finite(double v) { return std::isfinite(v); }
 }  // namespace
 
+int eval_lanes(const bk_opts& o, bk_dtype out_dtype) {
+  if (o.lanes != 0) return o.lanes;
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64) {
+    std::lock_guard<std::mutex> lk(g_lanes_mutex);
+    const int t = g_eval_lanes[dev][o.window == BK_WIN_LEARNED ? 1 : 0][out_dtype == BK_F32 ? 1 : 0];
+    if (t != 0) return t;
+  }
+  return BK_EVAL_LANES_DEFAULT;
+}
+
 bk_status check_opts(const bk_opts* o) {
   if (o->window != BK_WIN_SEARCH && o->window != BK_WIN_LEARNED && o->window != BK_WIN_FIXED)
     return set_error(BK_ERR_INVALID_ARG, "opts.window: unknown value %d", (int)o->window);
@@ -71,6 +86,8 @@ bk_status check_opts(const bk_opts* o) {
     if (o->compute != BK_F64)
       return set_error(BK_ERR_UNSUPPORTED, "the fixed window needs compute = BK_F64");
   }
+  if (o->lanes != 0 && o->lanes != 1 && o->lanes != 2 && o->lanes != 4 && o->lanes != 8)
+    return set_error(BK_ERR_INVALID_ARG, "opts.lanes must be 0, 1, 2, 4 or 8 (got %d)", o->lanes);
   if (o->window == BK_WIN_LEARNED) {
     if (o->compute != BK_F32)
       return set_error(BK_ERR_UNSUPPORTED, "the learned window needs compute = BK_F32 "
@@ -128,6 +145,7 @@ void bk_opts_default(bk_opts* o) {
   o->d_counters = nullptr;
   o->learned = nullptr;
   o->d_cosh_table = nullptr;
+  o->lanes = 0;
 }
 
 const char* bk_version(void) { return "libbesselk 0.1.0 (sm_103a)"; }
@@ -164,13 +182,68 @@ bk_status bk_eval_ex(const double* x, const double* nu, void* out, void* log_out
   if (x == nullptr || nu == nullptr || out == nullptr)
     return set_error(BK_ERR_INVALID_ARG, "x, nu and out must be non-NULL when n > 0");
   cudaStream_t s = (cudaStream_t)stream;
+  const int lanes = eval_lanes(o, out_dtype);
   const cudaError_t e =
       (o.window == BK_WIN_LEARNED)
-          ? launch_eval_learned(o.learned, x, nu, out, log_out, out_dtype, n, o.d_counters, s)
+          ? launch_eval_learned(o.learned, x, nu, out, log_out, out_dtype, n, o.d_counters, s,
+                                lanes)
       : (o.compute == BK_F64)
           ? launch_eval_f64(x, nu, out, log_out, out_dtype, n, o, s)
-          : launch_eval_f32(x, nu, out, log_out, out_dtype, n, o.d_counters, s);
+          : launch_eval_f32(x, nu, out, log_out, out_dtype, n, o.d_counters, s, lanes);
   return check_cuda(e, "bk_eval launch");
+}
+
+bk_status bk_eval_autotune(const double* x, const double* nu, void* out, bk_dtype out_dtype,
+                           int64_t n, const bk_opts* opts, bk_stream_t stream, int* best_lanes) {
+  bk_opts o;
+  bk_opts_default(&o);
+  if (opts != nullptr) o = *opts;
+  if (o.compute != BK_F32 || o.window == BK_WIN_FIXED)
+    return set_error(BK_ERR_UNSUPPORTED, "bk_eval_autotune: FP32 forms only (compute = BK_F32)");
+  if (best_lanes == nullptr) return set_error(BK_ERR_INVALID_ARG, "best_lanes is NULL");
+  if (n < 1) return set_error(BK_ERR_INVALID_ARG, "bk_eval_autotune needs n >= 1");
+  const int64_t m = n < ((int64_t)1 << 20) ? n : ((int64_t)1 << 20);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  if (e != cudaSuccess) {
+    if (a) cudaEventDestroy(a);
+    return check_cuda(e, "bk_eval_autotune: cudaEventCreate");
+  }
+  int best = 0;
+  float best_ms = 0.0f;
+  bk_status st = BK_OK;
+  for (int lanes : {1, 2, 4, 8}) {
+    o.lanes = lanes;
+    for (int rep = 0; rep < 4 && st == BK_OK; ++rep) {  // one warm-up, three timed
+      if (rep == 1) cudaEventRecord(a, s);
+      st = bk_eval_ex(x, nu, out, nullptr, out_dtype, m, &o, stream);
+    }
+    if (st != BK_OK) break;
+    cudaEventRecord(b, s);
+    e = cudaEventSynchronize(b);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    if (e != cudaSuccess) {
+      st = check_cuda(e, "bk_eval_autotune: timing");
+      break;
+    }
+    if (best == 0 || ms < best_ms) {
+      best = lanes;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (st != BK_OK) return st;
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64) {
+    std::lock_guard<std::mutex> lk(g_lanes_mutex);
+    g_eval_lanes[dev][o.window == BK_WIN_LEARNED ? 1 : 0][out_dtype == BK_F32 ? 1 : 0] = best;
+  }
+  *best_lanes = best;
+  return BK_OK;
 }
 
 bk_status bk_eval_grad(const double* x, const double* nu, double* k, double* dk_dx,

@@ -254,28 +254,68 @@ __device__ __forceinline__ DF matern_x_df(const Loc& a, const Loc& b, const Mate
   return df_mul(r, DF{mp.inv_beta_f, mp.inv_beta_lo});
 }
 
-// The FP32 forms' bare evaluation (eval_out): inside x in [1e-4, 1e4],
-// nu in [2^-70, 40] the arguments are split into double-floats by integer
+// The FP32 forms' bare evaluation: inside x in [1e-4, 1e4], nu in
+// [2^-70, 40] the arguments are split into double-floats by integer
 // operations and the result is assembled as for the Matern entries, with no
 // FP64 instruction on the way (FP64 output widens the FP32 value exactly);
 // elsewhere, and for FP64 output beyond the float range, the form's FP64
-// normalisation (eval) and the domain rules of the C-ABI apply.
-template <class Form, typename OutT>
-__device__ __forceinline__ void eval_out_f32(const Form& f, double x, double nu, Tally& tl,
-                                             unsigned& evals, OutT& k, OutT& log_k,
-                                             bool want_log) {
+// normalisation (eval) and the domain rules of the C-ABI apply.  The node
+// loops of the warp's 32 evaluations run on groups of L lanes
+// (coop_trapezoid_f32).  The learned form's check (a finite
+// positive sum, no node more than e^2 above the predicted peak) is taken after
+// the first pass; evaluations that fail it, or whose predicted window was
+// unusable, take the searched window in a second pass (only when some lane
+// of the warp needs one).  Every lane of the warp must call it; `valid` is
+// false for lanes without a pair.
+template <int L, class Form, typename OutT>
+__device__ __forceinline__ void eval_out_f32_coop(const Form& f, bool valid, double x, double nu,
+                                                  Tally& tl, unsigned& evals, OutT& k,
+                                                  OutT& log_k, bool want_log) {
   const long long xb = __double_as_longlong(x);
   const long long vb = __double_as_longlong(nu) & 0x7fffffffffffffffLL;
   bool okx = false, okn = false;
   DF xd{0.0f, 0.0f}, nd{0.0f, 0.0f};
-  if (xb > 0 && xb < 0x7ff0000000000000LL && vb < 0x7ff0000000000000LL) {
+  if (valid && xb > 0 && xb < 0x7ff0000000000000LL && vb < 0x7ff0000000000000LL) {
     xd = df_from_bits(x, okx);
     nd = df_from_bits(__longlong_as_double(vb), okn);
   }
-  if (okx && okn && xd.hi >= 1e-4f && xd.hi <= 1e4f && nd.hi <= 40.0f) {
+  const bool fast = okx && okn && xd.hi >= 1e-4f && xd.hi <= 1e4f && nd.hi <= 40.0f;
+  auto x64_of = [&] { return x; };
+  Window32 w;
+  Quad32 q;
+  q.hS = 0.0f;
+  q.amax = 0.0f;
+  Job32 jb = no_job32();
+  bool need_search = false;
+  if (fast) {
     ++evals;
-    Window32 w;
-    const Quad32 q = f.quad(xd.hi, [&] { return x; }, nd.hi, nd.lo, w, tl);
+    if (f.first_window(xd.hi, x64_of, nd.hi, w, tl)) jb = job_f32(xd.hi, nd.hi, nd.lo, w, q, tl);
+    else need_search = true;
+  }
+  float hS, amax;
+  coop_trapezoid_f32<L>(jb, hS, amax);
+  if (jb.N >= 0) {
+    q.hS = hS;
+    q.amax = amax;
+  }
+  if constexpr (Form::kChecked) {
+    if (fast && !(isfinite(q.hS) && q.hS > 0.0f && q.amax <= 2.0f)) need_search = true;
+    if (__any_sync(0xffffffffu, need_search)) {
+      Job32 jb2 = no_job32();
+      if (need_search) {
+        ++tl.fallback;
+        w = search_window_f32(xd.hi, x64_of, nd.hi, f.tab, tl);
+        jb2 = job_f32(xd.hi, nd.hi, nd.lo, w, q, tl);
+      }
+      coop_trapezoid_f32<L>(jb2, hS, amax);
+      if (jb2.N >= 0) {
+        q.hS = hS;
+        q.amax = amax;
+      }
+    }
+  }
+  if (!valid) return;
+  if (fast) {
     const DF a = df_log_scale(xd, nd, q);
     if constexpr (sizeof(OutT) == sizeof(float)) {
       k = df_exp_times(a, q.hS);
@@ -296,6 +336,62 @@ __device__ __forceinline__ void eval_out_f32(const Form& f, double x, double nu,
   log_k = to_out<OutT>(lk);
 }
 
+// One Matern entry of the FP32 forms with the structure of eval_out_f32_coop
+// (one lane per entry): the window and job of every lane, the node loop, then
+// the learned form's check, and the searched window for the entries that
+// fail it in a second pass taken only when some lane of the warp needs one.
+// Every lane of the warp must call it; `valid` is false outside the matrix
+// (the result is then 0 and unused).
+template <class Form, typename OutT>
+__device__ __forceinline__ OutT matern_out_f32_coop(const Form& f, bool valid, const Loc& a,
+                                                    const Loc& b, const MaternParams& mp,
+                                                    Tally& tl, unsigned& evals) {
+  DF z{0.0f, 0.0f};
+  if (valid) z = matern_x_df(a, b, mp);
+  const bool work = valid && z.hi != 0.0f;  // r == 0 gives sigma^2 (Algorithm 3)
+  auto x64_of = [&] { return (double)z.hi + (double)z.lo; };
+  Window32 w;
+  Quad32 q;
+  q.hS = 0.0f;
+  q.amax = 0.0f;
+  Job32 jb = no_job32();
+  bool need_search = false;
+  if (work) {
+    ++evals;
+    if (f.first_window(z.hi, x64_of, mp.nu_hi, w, tl))
+      jb = job_f32(z.hi, mp.nu_hi, mp.nu_lo, w, q, tl);
+    else
+      need_search = true;
+  }
+  float hS, amax;
+  coop_trapezoid_f32<1>(jb, hS, amax);
+  if (jb.N >= 0) {
+    q.hS = hS;
+    q.amax = amax;
+  }
+  if constexpr (Form::kChecked) {
+    if (work && !(isfinite(q.hS) && q.hS > 0.0f && q.amax <= 2.0f)) need_search = true;
+    if (__any_sync(0xffffffffu, need_search)) {
+      Job32 jb2 = no_job32();
+      if (need_search) {
+        ++tl.fallback;
+        w = search_window_f32(z.hi, x64_of, mp.nu_hi, f.tab, tl);
+        jb2 = job_f32(z.hi, mp.nu_hi, mp.nu_lo, w, q, tl);
+      }
+      coop_trapezoid_f32<1>(jb2, hS, amax);
+      if (jb2.N >= 0) {
+        q.hS = hS;
+        q.amax = amax;
+      }
+    }
+  }
+  if (!work) {
+    if (!valid) return (OutT)0;
+    return sizeof(OutT) == sizeof(float) ? (OutT)mp.sigma2_f : (OutT)mp.sigma2;
+  }
+  return matern_f32_finish<OutT>(z, q, mp);
+}
+
 // The FP32 precision form (search window).
 struct FormF32 {
   static constexpr bool kStageTable = false;
@@ -303,6 +399,7 @@ struct FormF32 {
   static constexpr int kMinBlocks = 4;
   static constexpr bool kFloatEval = true;
   static constexpr bool kCoshNuTable = false;
+  static constexpr bool kChecked = false;  // the searched window needs no check
   const double* tab;
 
   template <class X64>
@@ -312,7 +409,15 @@ struct FormF32 {
     return quad_f32(x, nu, nu_lo, w, tl);
   }
 
-  // FP64 normalisation (outside the float path of eval_out_f32).
+  // The window tried first by the lane-split evaluation (eval_out_f32_coop).
+  template <class X64>
+  __device__ __forceinline__ bool first_window(float x, X64 x64_of, float nu, Window32& w,
+                                               Tally& tl) const {
+    w = search_window_f32(x, x64_of, nu, tab, tl);
+    return true;
+  }
+
+  // FP64 normalisation (outside the float path of eval_out_f32_coop).
   __device__ __forceinline__ double eval(double x, double nu, Tally& tl, unsigned& evals,
                                          double& log_k, bool) const {
     ++evals;
@@ -324,11 +429,6 @@ struct FormF32 {
     return exp_fast(sc) * (double)q.hS;
   }
 
-  template <typename OutT>
-  __device__ __forceinline__ void eval_out(double x, double nu, Tally& tl, unsigned& evals,
-                                           OutT& k, OutT& log_k, bool want_log) const {
-    eval_out_f32(*this, x, nu, tl, evals, k, log_k, want_log);
-  }
 
   // a2 as a double-float; a3..a6 in FP32 on x.hi; a7 by matern_f32_finish.
   template <typename OutT>
@@ -358,8 +458,15 @@ struct FormF32Learned {
   static constexpr int kMinBlocks = 4;
   static constexpr bool kFloatEval = true;
   static constexpr bool kCoshNuTable = false;
+  static constexpr bool kChecked = true;  // quadratures of predicted windows are checked
   LearnedView lv;
   const double* tab;
+
+  template <class X64>
+  __device__ __forceinline__ bool first_window(float x, X64, float nu, Window32& w,
+                                               Tally& tl) const {
+    return learned_window_f32(lv, x, nu, w, tl.repairs);
+  }
 
   template <class X64>
   __device__ __forceinline__ Quad32 quad(float x, X64 x64_of, float nu, float nu_lo, Window32& w,
@@ -386,11 +493,6 @@ struct FormF32Learned {
     return exp_fast(sc) * (double)q.hS;
   }
 
-  template <typename OutT>
-  __device__ __forceinline__ void eval_out(double x, double nu, Tally& tl, unsigned& evals,
-                                           OutT& k, OutT& log_k, bool want_log) const {
-    eval_out_f32(*this, x, nu, tl, evals, k, log_k, want_log);
-  }
 
   template <typename OutT>
   __device__ __forceinline__ OutT matern_out(const Loc& a, const Loc& b, const MaternParams& mp,

@@ -12,8 +12,9 @@
 namespace bk {
 
 cudaError_t launch_eval_f32(const double* x, const double* nu, void* out, void* log_out,
-                            bk_dtype out_t, int64_t n, unsigned long long* ctr, cudaStream_t s) {
-  return launch_eval_form(FormF32{nullptr}, x, nu, out, log_out, out_t, n, ctr, s);
+                            bk_dtype out_t, int64_t n, unsigned long long* ctr, cudaStream_t s,
+                            int lanes) {
+  return launch_eval_form(FormF32{nullptr}, x, nu, out, log_out, out_t, n, ctr, s, lanes);
 }
 
 cudaError_t launch_matern_sym_f32(const double* locs, int64_t n, double sigma2, double beta,

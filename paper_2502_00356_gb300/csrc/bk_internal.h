@@ -56,9 +56,14 @@ cudaError_t launch_loglik(double* a, int64_t n, int64_t ld, const double* z, dou
 // error message and returns the status).
 bk_status check_opts(const bk_opts* o);
 
+// Lanes per evaluation of the FP32 forms' bare evaluations: opts.lanes, else
+// bk_eval_autotune's choice for the current device, else the default.
+int eval_lanes(const bk_opts& o, bk_dtype out_dtype);
+
 // ---- FP32 precision form (bk_fp32.cu) ----
 cudaError_t launch_eval_f32(const double* x, const double* nu, void* out, void* log_out,
-                            bk_dtype out_t, int64_t n, unsigned long long* ctr, cudaStream_t s);
+                            bk_dtype out_t, int64_t n, unsigned long long* ctr, cudaStream_t s,
+                            int lanes);
 cudaError_t launch_matern_sym_f32(const double* locs, int64_t n, double sigma2, double beta,
                                   double nu, void* out, int64_t ld, bk_dtype out_t,
                                   unsigned long long* ctr, cudaStream_t s,
@@ -72,7 +77,7 @@ cudaError_t launch_matern_block_f32(const double* locs1, int64_t m, const double
 bool learned_ready(const bk_learned* m);
 cudaError_t launch_eval_learned(const bk_learned* m, const double* x, const double* nu, void* out,
                                 void* log_out, bk_dtype out_t, int64_t n, unsigned long long* ctr,
-                                cudaStream_t s);
+                                cudaStream_t s, int lanes);
 cudaError_t launch_matern_sym_learned(const bk_learned* m, const double* locs, int64_t n,
                                       double sigma2, double beta, double nu, void* out, int64_t ld,
                                       bk_dtype out_t, unsigned long long* ctr, cudaStream_t s,

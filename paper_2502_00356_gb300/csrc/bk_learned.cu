@@ -424,8 +424,9 @@ bool learned_ready(const bk_learned* m) { return m != nullptr && m->has_stats; }
 
 cudaError_t launch_eval_learned(const bk_learned* m, const double* x, const double* nu, void* out,
                                 void* log_out, bk_dtype out_t, int64_t n, unsigned long long* ctr,
-                                cudaStream_t s) {
-  return launch_eval_form(FormF32Learned{learned_view(m), nullptr}, x, nu, out, log_out, out_t, n, ctr, s);
+                                cudaStream_t s, int lanes) {
+  return launch_eval_form(FormF32Learned{learned_view(m), nullptr}, x, nu, out, log_out, out_t, n,
+                          ctr, s, lanes);
 }
 
 cudaError_t launch_matern_sym_learned(const bk_learned* m, const double* locs, int64_t n,

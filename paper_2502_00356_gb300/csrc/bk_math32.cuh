@@ -184,49 +184,6 @@ __device__ __forceinline__ void expm1_pm_f32(float y, float& em, float& emn) {
   emn = small ? -p * r : r - 1.0f;
 }
 
-// Scaled trapezoid sum of the FP32 form, with the weights of Eq. (refined):
-//   S = sum_j c_j exp(a_j) (1 + e^{-2 nu t_j}),  c_0 = c_N = 1/2,
-//   a_j = nu tau_j - x (cosh t_j - cosh s),  tau_j = t_j - s = (t0 - s) + j h,
-// centred on the shift point s (a grid point next to the peak, see
-// shift_f32; any s is exact, it only scales the terms).  Peak-relative nodes
-// keep nu tau_j and the spacing accurate near the peak.  The cosh difference
-// is written so that no large argument enters an FP32 exponential and
-// nothing cancels, for every s >= 0 alike: with em = e^tau - 1 and
-// emn = e^{-tau} - 1 (so em emn = -(em + emn)), D = x sinh s and
-// B = x e^{-s}/2,
-//   x (cosh t - cosh s) = x e^s/2 em + B emn = em (D - B emn),
-// where D - B emn >= D/2 > 0 for t >= 0 (tau >= -s).  e^{-2 nu t_j} follows
-// a geometric recurrence; the sum is Kahan-compensated.  The order enters as
-// nu_hi + nu_lo (the FP64 order split into two floats): rounding nu itself to
-// FP32 would integrate K of a neighbouring order, off by ulp(nu) d(log K)/d nu
-// ~ ulp(nu) ln(2 nu/x), ~1e-5 at x ~ 1e-3, nu ~ 18.  Returns h S.
-__device__ __forceinline__ float trapezoid_f32(float nu, float nu_lo, float t0, float t1, float s,
-                                               float B, float D, int N, float& amax, Tally& tl) {
-  const float h = (t1 - t0) / (float)N;
-  const float tau0 = t0 - s;
-  float W = mufu_ex2(-2.0f * kLog2ef * nu * t0);
-  const float rho = mufu_ex2(-2.0f * kLog2ef * nu * h);
-  float S = 0.0f, c = 0.0f, f = 0.0f, f0 = 0.0f, jf = 0.0f;
-  amax = -3.0e38f;
-  for (int j = 0; j <= N; ++j, jf += 1.0f) {  // jf = j exactly (float counter, no conversion)
-    const float tau = fmaf(jf, h, tau0);
-    float em, emn;
-    expm1_pm_f32(tau, em, emn);
-    const float a = fmaf(nu, tau, fmaf(nu_lo, tau, -em * fmaf(-B, emn, D)));
-    amax = fmaxf(amax, a);
-    f = exp_f32(a);
-    f = fmaf(f, W, f);
-    if (j == 0) f0 = f;
-    const float y = f - c;  // Kahan
-    const float s2 = S + y;
-    c = (s2 - S) - y;
-    S = s2;
-    W *= rho;
-  }
-  tl.nodes += N + 1;
-  return h * ((S - c) - 0.5f * (f0 + f));  // end weights 1/2
-}
-
 // The searched window of the FP32 form: FP32 search inside x in [1e-4, 1e4],
 // nu <= 40, the FP64 search (with the FP32 eps) outside, where FP32 sinh /
 // cosh of the window ends lose too much.  x is the FP32 argument, x64 the
@@ -357,9 +314,12 @@ __device__ __forceinline__ DF df_hypot_diff(float axh, float axl, float ayh, flo
 }
 
 // e^a * s for a double-float a with FP32 accuracy, as a float (the FP32
-// output case; underflows to 0 below the float range).
+// output case; underflows to 0 below the float range and overflows to
+// s * inf above it, where the two power-of-two factors would leave the
+// exponent field).
 __device__ __forceinline__ float df_exp_times(DF a, float s) {
   if (a.hi < -103.0f) return 0.0f;
+  if (a.hi > 100.0f) return s * __int_as_float(0x7f800000);
   const float kf = rintf(a.hi * kLog2ef);
   float r = fmaf(-kf, kLn2HiF, a.hi);
   r = fmaf(-kf, kLn2LoF, r) + a.lo;
@@ -496,21 +456,148 @@ __device__ __forceinline__ void shift_f32(float x, float ts, float& s, DF& cm1, 
   }
 }
 
-__device__ __forceinline__ Quad32 quad_f32(float x, float nu, float nu_lo, const Window32& w,
-                                           Tally& tl) {
-  Quad32 q;
+// ---------------------------------------------------------------------------
+// The FP32 quadrature (a6).  The scaled trapezoid sum, with the weights of
+// Eq. (refined):
+//   S = sum_j c_j exp(a_j) (1 + e^{-2 nu t_j}),  c_0 = c_N = 1/2,
+//   a_j = nu tau_j - x (cosh t_j - cosh s),  tau_j = t_j - s = (t0 - s) + j h,
+// centred on the shift point s (a grid point next to the peak, see
+// shift_f32; any s is exact, it only scales the terms).  Peak-relative nodes
+// keep nu tau_j and the spacing accurate near the peak.  The cosh difference
+// is written so that no large argument enters an FP32 exponential and
+// nothing cancels, for every s >= 0 alike: with em = e^tau - 1 and
+// emn = e^{-tau} - 1 (so em emn = -(em + emn)), D = x sinh s and
+// B = x e^{-s}/2,
+//   x (cosh t - cosh s) = x e^s/2 em + B emn = em (D - B emn),
+// where D - B emn >= D/2 > 0 for t >= 0 (tau >= -s).  e^{-2 nu t_j} follows
+// a geometric recurrence; the sums are Kahan-compensated.  The order enters
+// as nu_hi + nu_lo (the FP64 order split into two floats): rounding nu itself
+// to FP32 would integrate K of a neighbouring order, off by
+// ulp(nu) d(log K)/d nu ~ ulp(nu) ln(2 nu/x), ~1e-5 at x ~ 1e-3, nu ~ 18.
+//
+// The node loop can be split over L lanes (L = 1, 2, 4, 8) for evaluations
+// whose node counts differ from lane to lane (random (x, nu) pairs).  Every
+// lane first prepares its own evaluation's job (window, node count, shift
+// point); the warp then takes the 32 jobs in L passes of 32/L jobs, each job
+// on a group of L consecutive lanes: lane r of a group evaluates nodes
+// j = r, r + L, ..., and the group adds its partial sums by a compensated
+// butterfly (__shfl_xor_sync, two-sum in FP32).  With L = 1 every lane runs
+// its own job and no lane waits for another (no shuffle).
+
+// One evaluation's quadrature job: nodes t_j = t0 + j h, j = 0..N, centred on
+// s (N < 0: no job).
+struct Job32 {
+  float t0, h, s, nu, nu_lo, B, D;
+  int N;
+};
+
+__device__ __forceinline__ Job32 no_job32() { return Job32{0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, -1}; }
+
+// The job of quad_f32 on window w; q receives the shift point (q.hS is NaN and
+// the job empty when the node bound is exceeded).
+__device__ __forceinline__ Job32 job_f32(float x, float nu, float nu_lo, const Window32& w,
+                                         Quad32& q, Tally& tl) {
   const int N = strip_node_count(x, nu, w.t1 - w.t0, kF32Log2OverTol, kF32MaxNodes);
+  q.amax = 0.0f;
   if (N > kF32MaxNodes) {
     ++tl.fail;
     q.hS = __int_as_float(0x7fc00000);
     q.ts = w.ts;
     q.cm1 = DF{0.0f, 0.0f};
-    q.amax = 0.0f;
-    return q;
+    return no_job32();
   }
-  float B, D;
-  shift_f32(x, w.ts, q.ts, q.cm1, B, D);
-  q.hS = trapezoid_f32(nu, nu_lo, w.t0, w.t1, q.ts, B, D, N, q.amax, tl);
+  Job32 jb;
+  shift_f32(x, w.ts, q.ts, q.cm1, jb.B, jb.D);
+  jb.t0 = w.t0;
+  jb.h = (w.t1 - w.t0) / (float)N;
+  jb.s = q.ts;
+  jb.nu = nu;
+  jb.nu_lo = nu_lo;
+  jb.N = N;
+  tl.nodes += N + 1;
+  return jb;
+}
+
+// Runs the 32 jobs of the warp on groups of L lanes; for L > 1 every lane of
+// the warp must call it (L = 1 runs this lane's job alone).  Each lane
+// receives h S and the largest node exponent of its own job (0 and -3e38 for
+// no job).
+template <int L>
+__device__ __forceinline__ void coop_trapezoid_f32(const Job32& my, float& hS, float& amax) {
+  static_assert(L == 1 || L == 2 || L == 4 || L == 8, "lanes per job");
+  constexpr int G = 32 / L;  // jobs per pass
+  constexpr unsigned kAll = 0xffffffffu;
+  const int lane = threadIdx.x & 31, g = lane / L, r = lane - g * L;
+  hS = 0.0f;
+  amax = -3.0e38f;
+#pragma unroll 1
+  for (int p = 0; p < L; ++p) {
+    Job32 jb = my;
+    if constexpr (L > 1) {
+      const int owner = p * G + g;
+      jb.t0 = __shfl_sync(kAll, my.t0, owner);
+      jb.h = __shfl_sync(kAll, my.h, owner);
+      jb.s = __shfl_sync(kAll, my.s, owner);
+      jb.nu = __shfl_sync(kAll, my.nu, owner);
+      jb.nu_lo = __shfl_sync(kAll, my.nu_lo, owner);
+      jb.B = __shfl_sync(kAll, my.B, owner);
+      jb.D = __shfl_sync(kAll, my.D, owner);
+      jb.N = __shfl_sync(kAll, my.N, owner);
+    }
+    const float tau0 = jb.t0 - jb.s;
+    const float l2n = -2.0f * kLog2ef * jb.nu;
+    float W = mufu_ex2(l2n * fmaf((float)r, jb.h, jb.t0));  // e^{-2 nu t_r}
+    const float rho = mufu_ex2(l2n * ((float)L * jb.h));    // e^{-2 nu L h}
+    float S = 0.0f, c = 0.0f, ends = 0.0f, am = -3.0e38f, jf = (float)r;
+    for (int j = r; j <= jb.N; j += L, jf += (float)L) {
+      const float tau = fmaf(jf, jb.h, tau0);
+      float em, emn;
+      expm1_pm_f32(tau, em, emn);
+      const float a = fmaf(jb.nu, tau, fmaf(jb.nu_lo, tau, -em * fmaf(-jb.B, emn, jb.D)));
+      am = fmaxf(am, a);
+      float f = exp_f32(a);
+      f = fmaf(f, W, f);
+      if (j == 0 || j == jb.N) ends += f;  // end weights 1/2
+      const float y = f - c;  // Kahan
+      const float s2 = S + y;
+      c = (s2 - S) - y;
+      S = s2;
+      W *= rho;
+    }
+    // this lane's part as hi + lo, then the group's butterfly
+    DF v = two_sum(S, -c);
+    v.lo = fmaf(-0.5f, ends, v.lo);
+#pragma unroll
+    for (int o = 1; o < L; o <<= 1) {
+      const float oh = __shfl_xor_sync(kAll, v.hi, o), ol = __shfl_xor_sync(kAll, v.lo, o);
+      const DF t = two_sum(v.hi, oh);
+      v = quick_two_sum(t.hi, t.lo + (v.lo + ol));
+      am = fmaxf(am, __shfl_xor_sync(kAll, am, o));
+    }
+    const float tot = jb.h * (v.hi + v.lo);
+    if constexpr (L == 1) {
+      hS = tot;
+      amax = am;
+    } else {
+      // the owner of group g' in pass p is lane p G + g'; group g' holds its sum
+      const float got = __shfl_sync(kAll, tot, (lane % G) * L);
+      const float gam = __shfl_sync(kAll, am, (lane % G) * L);
+      if (lane / G == p) {
+        hS = got;
+        amax = gam;
+      }
+    }
+  }
+}
+
+// The FP32 quadrature of one evaluation on window w, on this lane alone:
+// h S, the shift point and cosh s - 1 there (NaN h S when the node bound is
+// exceeded).
+__device__ __forceinline__ Quad32 quad_f32(float x, float nu, float nu_lo, const Window32& w,
+                                           Tally& tl) {
+  Quad32 q;
+  const Job32 jb = job_f32(x, nu, nu_lo, w, q, tl);
+  if (jb.N >= 0) coop_trapezoid_f32<1>(jb, q.hS, q.amax);
   return q;
 }
 

@@ -161,6 +161,35 @@ __global__ void __launch_bounds__(128, 6) eval_kernel(const Form form, const dou
   flush_tally(ctr, tl, evals);
 }
 
+// Bare evaluations of the FP32 forms with the quadrature split over L lanes
+// (eval_out_f32_coop), 128 pairs per block and round in input order.
+template <class Form, typename OutT, int L>
+__global__ void __launch_bounds__(128, 6) eval_coop_kernel(const Form form,
+                                                        const double* __restrict__ x,
+                                                        const double* __restrict__ nu,
+                                                        OutT* __restrict__ out,
+                                                        OutT* __restrict__ log_out, int64_t n,
+                                                        unsigned long long* __restrict__ ctr) {
+  constexpr int kB = 128;
+  __shared__ double s_tab[Form::kStageTable ? kExpTabSize : 1];
+  const Form f = bind_table(form, s_tab);
+  Tally tl{0u, 0u, 0u, 0u, 0u, 0u, 0u};
+  unsigned evals = 0;
+  const bool want_log = (log_out != nullptr);
+  for (int64_t base = (int64_t)blockIdx.x * kB; base < n; base += (int64_t)gridDim.x * kB) {
+    const int64_t i = base + threadIdx.x;
+    const bool valid = i < n;
+    OutT k, lk;
+    eval_out_f32_coop<L>(f, valid, valid ? x[i] : 1.0, valid ? nu[i] : 1.0, tl, evals, k, lk,
+                         want_log);
+    if (valid) {
+      out[i] = k;
+      if (log_out != nullptr) log_out[i] = lk;
+    }
+  }
+  flush_tally(ctr, tl, evals);
+}
+
 // K, dK/dx and dK/dnu of the plain form, 128 pairs per block and round in
 // cost order (sorted_pair).  Domain: x = 0 gives (+inf, -inf,
 // NaN), x = +inf gives (0, 0, 0), x < 0 or NaN and non-finite nu give NaN;
@@ -240,8 +269,12 @@ __device__ __forceinline__ void sym_tile(const Form& form, SymTileSmem<OutT>& sm
 #pragma unroll 1
   for (int c = warp; c < kTile; c += WARPS) {
     OutT v = (OutT)0;
-    if (r0 + lane < n && c0 + c < n)
-      v = form.template matern_out<OutT>(sm.r[lane], sm.c[c], mp, tl, evals);
+    const bool in = r0 + lane < n && c0 + c < n;
+    if constexpr (Form::kFloatEval) {
+      v = matern_out_f32_coop<Form, OutT>(form, in, sm.r[lane], sm.c[c], mp, tl, evals);
+    } else {
+      if (in) v = form.template matern_out<OutT>(sm.r[lane], sm.c[c], mp, tl, evals);
+    }
     sm.tile[lane][c] = v;
   }
   __syncthreads();
@@ -357,17 +390,40 @@ inline int tile_grid(int64_t ntiles, int per_block) {
 // Blocks for a grid-stride launch: min(work, SMs x per_sm).
 int grid_for(int64_t work_items, int per_sm);
 
+template <class Form, typename OutT>
+cudaError_t launch_eval_coop(const Form& form, int lanes, int grid, const double* x,
+                             const double* nu, OutT* out, OutT* log_out, int64_t n,
+                             unsigned long long* ctr, cudaStream_t s) {
+  switch (lanes) {
+    case 2: eval_coop_kernel<Form, OutT, 2><<<grid, 128, 0, s>>>(form, x, nu, out, log_out, n, ctr); break;
+    case 4: eval_coop_kernel<Form, OutT, 4><<<grid, 128, 0, s>>>(form, x, nu, out, log_out, n, ctr); break;
+    case 8: eval_coop_kernel<Form, OutT, 8><<<grid, 128, 0, s>>>(form, x, nu, out, log_out, n, ctr); break;
+    default: eval_coop_kernel<Form, OutT, 1><<<grid, 128, 0, s>>>(form, x, nu, out, log_out, n, ctr); break;
+  }
+  return cudaGetLastError();
+}
+
+// lanes: for the FP32 forms, the lanes per evaluation in the node loop (1, 2,
+// 4, 8; eval_coop_kernel); the FP64 forms take one lane per evaluation.
 template <class Form>
 cudaError_t launch_eval_form(const Form& form, const double* x, const double* nu, void* out, void* log_out,
-                             bk_dtype out_t, int64_t n, unsigned long long* ctr, cudaStream_t s) {
+                             bk_dtype out_t, int64_t n, unsigned long long* ctr, cudaStream_t s,
+                             int lanes = 1) {
   if (n == 0) return cudaSuccess;
   const int grid = grid_for((n + 127) / 128, 16);
-  if (out_t == BK_F64)
-    eval_kernel<Form, double><<<grid, 128, 0, s>>>(form, x, nu, (double*)out, (double*)log_out, n,
-                                                   ctr);
-  else
-    eval_kernel<Form, float><<<grid, 128, 0, s>>>(form, x, nu, (float*)out, (float*)log_out, n, ctr);
-  return cudaGetLastError();
+  if constexpr (Form::kFloatEval) {
+    if (out_t == BK_F64)
+      return launch_eval_coop(form, lanes, grid, x, nu, (double*)out, (double*)log_out, n, ctr, s);
+    return launch_eval_coop(form, lanes, grid, x, nu, (float*)out, (float*)log_out, n, ctr, s);
+  } else {
+    if (out_t == BK_F64)
+      eval_kernel<Form, double><<<grid, 128, 0, s>>>(form, x, nu, (double*)out, (double*)log_out,
+                                                     n, ctr);
+    else
+      eval_kernel<Form, float><<<grid, 128, 0, s>>>(form, x, nu, (float*)out, (float*)log_out, n,
+                                                    ctr);
+    return cudaGetLastError();
+  }
 }
 
 template <class Form>

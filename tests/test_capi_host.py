@@ -173,3 +173,20 @@ def test_matern_tile_host_checks(L):
     assert host(None, 0, 1.0, 0.1, 0.5, None, 0, 0, None, None, 0, None) == bk.BK_OK
     assert L.bk_matern_tile_host(fake, 100, 1.0, 0.1, 0.5, fake, 100, 0, None, 7, fake, need,
                                  None) == bk.BK_ERR_INVALID_ARG
+
+
+def test_lanes_option_checks(L):
+    P = ctypes.c_void_p
+    fake = P(0x1000)
+    o = bk.bk_opts()
+    L.bk_opts_default(ctypes.byref(o))
+    assert o.lanes == 0
+    o.compute = bk.BK_F32
+    for bad in (3, -1, 16):
+        o.lanes = bad
+        assert L.bk_eval_ex(fake, fake, fake, None, 1, 5, ctypes.byref(o), None) == bk.BK_ERR_INVALID_ARG
+    o.lanes = 0
+    o.compute = bk.BK_F64
+    best = ctypes.c_int(0)
+    assert L.bk_eval_autotune(fake, fake, fake, 0, 5, ctypes.byref(o), None,
+                              ctypes.byref(best)) == bk.BK_ERR_UNSUPPORTED
