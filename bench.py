@@ -55,6 +55,9 @@ LAUNCHES_PER_MATRIX = 2
 # FP64 pipe peak from the unit count and clock: 152 SMs x 2 DFMA/clk x 2.07 GHz
 # (1.26 TFLOP/s counting an FMA as two FLOPs).
 FP64_PEAK_GOPS = 152 * 2 * 2.07e9 / 1e9
+# Instruction-issue limit, which bounds the FP32 forms: 152 SMs x 4 warp
+# instructions per clock x 32 lanes x 2.07 GHz, in G thread-instructions/s.
+ISSUE_PEAK_GINST = 152 * 4 * 32 * 2.07e9 / 1e9
 
 
 def parse():
@@ -71,7 +74,8 @@ def parse():
                    help="skip the FP32, batched and learned-window measurements")
     p.add_argument("--pairs", type=int, default=100_000_000,
                    help="K_nu pairs of the learned-window evaluation workload")
-    p.add_argument("--profile-case", choices=["plain", "fp32", "learned", "learned_eval", "batched"],
+    p.add_argument("--profile-case", choices=["plain", "fp32", "learned", "learned_eval", "batched",
+                                              "fp32_forms"],
                    default=None,
                    help="run --warmup launches plus one launch of one kernel on a small case "
                         "(for profiler captures) and exit without a JSON line")
@@ -164,21 +168,38 @@ class ClockSampler:
 
 KERNEL_SOURCES = ("bk_plain.cu", "bk_math64.cuh", "bk_math32.cuh", "bk_forms.cuh", "bk_tiles.cuh",
                   "bk_matern_common.cuh", "bk_exp2_table.inc", "bk_cosh_table.inc")
+# The FP32 forms' kernels (single matrix, bare evaluations, batched, learned).
+FP32_SOURCES = ("bk_math64.cuh", "bk_math32.cuh", "bk_forms.cuh", "bk_tiles.cuh",
+                "bk_matern_common.cuh", "bk_peak_table.inc", "bk_fp32.cu", "bk_learned.cu",
+                "bk_batched.cu")
 
 
-def kernel_hash():
-    """Hash of the sources the plain FP64 tile writer is compiled from, with
-    comments removed and whitespace collapsed (so that it changes with the
-    compiled code, not with its documentation)."""
+def kernel_hash(files=KERNEL_SOURCES):
+    """Hash of the sources a kernel is compiled from (by default the plain
+    FP64 tile writer's), with comments removed and whitespace collapsed (so
+    that it changes with the compiled code, not with its documentation)."""
     import re
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in files:
         with open(os.path.join(ROOT, "paper_2502_00356_gb300", "csrc", f)) as fh:
             text = fh.read()
         text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
         text = re.sub(r"//[^\n]*", " ", text)
         h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
+
+
+def profiled_instr():
+    """Executed thread instructions per launch of the FP32 forms' bench
+    kernels from the committed ncu summary; None when the kernels changed
+    since the capture."""
+    path = os.path.join(ROOT, "profiles", "fp32_forms_instr.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    return rec if rec.get("kernel_hash") == kernel_hash(FP32_SOURCES) else None
 
 
 def profiled_traffic(n: int):
@@ -284,112 +305,173 @@ def _max_rel(got, ref, floor=1e-30):
     return float(((got.double() - ref.double()).abs() / ref.double().abs().clamp_min(floor))[big].max())
 
 
+def _counters(bk, dev):
+    import torch
+    return torch.zeros(bk.BK_NUM_COUNTERS, dtype=torch.int64, device=dev)
+
+
+def _ctr_summary(bk, c):
+    evals = max(1, int(c[bk.BK_CTR_EVALS]))
+    return {"evals": int(c[bk.BK_CTR_EVALS]), "nodes_per_eval": float(c[bk.BK_CTR_NODES]) / evals,
+            "fallback_rate": float(c[bk.BK_CTR_FALLBACK]) / evals,
+            "repairs_per_eval": float(c[bk.BK_CTR_REPAIR]) / evals,
+            "newton_iters_per_eval": float(c[bk.BK_CTR_ITERS] + c[bk.BK_CTR_PEAK_ITERS]) / evals,
+            "failed": int(c[bk.BK_CTR_FAIL])}
+
+
+def issue_roofline(key, kernel, launch_s, evals):
+    """Roofline of an FP32-form kernel, which is bound by instruction issue:
+    achieved = the kernel's executed thread instructions per launch (ncu,
+    profiles/fp32_forms_instr.json, same workload, null when the kernels
+    changed since the capture) / the live CUDA-event launch time, against the
+    issue limit 152 SMs x 4 warp instructions/clk x 32 lanes x 2.07 GHz.
+    Divergence (inactive lanes) and issue stalls both lower it."""
+    rec = profiled_instr()
+    d = (rec or {}).get("kernels", {}).get(key)
+    achieved = d["thread_inst"] / launch_s / 1e9 if d else None
+    out = {"bound": "alu", "kernel": kernel, "unit": "G thread-instr/s",
+           "peak": ISSUE_PEAK_GINST, "peak_source": "derived: 152 SMs x 4 warp-instr/clk x 32 "
+           "lanes x 2.07 GHz (of derived)", "achieved": achieved,
+           "frac": achieved / ISSUE_PEAK_GINST if achieved else None,
+           "launch_ms": 1e3 * launch_s, "evals_per_launch": evals}
+    if d:
+        out["thread_inst_per_eval"] = d["thread_inst"] / max(1, evals)
+        out["lanes_active_of_32"] = d["thread_inst"] / d["warp_inst"]
+    return out
+
+
 def measure_forms(bk, inputs, dev, stream, args, plain_rate):
-    """Throughput of the other forms (outside the headline timing).  Errors
-    are stated against the plain FP64 form, which the GPU tests hold within
-    1e-10 of the oracle."""
+    """Throughput, roofline, counters and output samples of the other forms
+    (outside the headline timing).  The samples are checked against the
+    oracle by the CPU leg (oracle_checks)."""
     import numpy as np
     import torch
 
-    res = {}
-    ckpt = os.path.join(ROOT, "paper_2502_00356_gb300", "weights", "window_mlp.bkw")
-    net = bk.LearnedWindow(path=ckpt)
+    res, samples = {}, []
+    net = bk.LearnedWindow(path=os.path.join(ROOT, "paper_2502_00356_gb300", "weights",
+                                             "window_mlp.bkw"))
 
-    def ctr():
-        return torch.zeros(bk.BK_NUM_COUNTERS, dtype=torch.int64, device=dev)
+    def sample_matrix(key, out, locs_h, sigma2, beta, nu, m, seed, near):
+        n = locs_h.shape[1]
+        I, J = inputs.entry_sample(n, m, seed=seed, near_fraction=near)
+        got = out[torch.as_tensor(J, device=dev), torch.as_tensor(I, device=dev)]  # (i, j) at out[j, i]
+        samples.append({"key": key, "kind": "matern", "locs": locs_h, "I": I, "J": J,
+                        "theta": (sigma2, beta, nu), "got": got.double().cpu().numpy()})
 
-    # -- FP32 precision form: n = 40,000 jittered grid, beta = 0.05, nu ~ U(0.3, 3.5) (seed 5)
+    # -- C3, FP32 precision form: n = 40,000 jittered grid (seed 4), beta = 0.05,
+    # nu ~ U(0.3, 3.5) (seed 5), FP32 out; error on a seeded 10^6-entry sample (seed 6,
+    # 1 % nearest-neighbour pairs)
     n3, beta3 = 40_000, 0.05
     nu3 = float(np.random.default_rng(5).uniform(0.3, 3.5))
-    L3 = torch.as_tensor(inputs.morton_sorted(inputs.jittered_grid(n3, seed=4)), device=dev)
+    L3h = inputs.morton_sorted(inputs.jittered_grid(n3, seed=4))
+    L3 = torch.as_tensor(L3h, device=dev)
     o32 = torch.empty((n3, n3), dtype=torch.float32, device=dev)
-    bk.bk_matern_tile(L3, 1.0, beta3, nu3, out=o32)
+    c = _counters(bk, dev)
+    bk.bk_matern_tile(L3, 1.0, beta3, nu3, out=o32, opts=bk.make_opts(compute=bk.BK_F32, counters=c))
+    cs = _ctr_summary(bk, c.cpu().numpy())
     t = _time(lambda: bk.bk_matern_tile(L3, 1.0, beta3, nu3, out=o32), stream, 3)
-    cols = slice(0, 2000)
-    ref = bk.bk_matern_tile2(L3, L3[:, cols].contiguous(), 1.0, beta3, nu3,
-                             opts=bk.make_opts(compute=bk.BK_F64))
     res["fp32_matern"] = {
-        "workload": f"n={n3} jittered grid, beta={beta3}, nu={nu3:.4f} (U(0.3,3.5), seed 5), FP32 out",
-        "value": n3 * n3 / t, "unit": "entries/s", "ms": 1e3 * t,
-        "max_rel_vs_fp64_form": _max_rel(o32[cols, :], ref),
-        "err_sample": "all entries of the first 2000 columns"}
-    del ref
+        "workload": f"C3: n={n3} jittered grid, beta={beta3}, nu={nu3:.4f} (U(0.3,3.5), seed 5), "
+                    "FP32 out", "value": n3 * n3 / t, "unit": "entries/s", "ms": 1e3 * t,
+        "counters": cs, "roofline": issue_roofline("fp32_matern", "matern_sym_kernel<FormF32, float>",
+                                                   t, cs["evals"])}
+    sample_matrix("fp32_matern", o32, L3h, 1.0, beta3, nu3, 1_000_000, 6, 0.01)
 
-    # -- learned vs searched window vs plain FP64 on n = 40,000, nu = 1.7, beta = 0.1 (FP32 out)
+    # -- C5 matrix: learned window vs searched window vs plain FP64, n = 40,000, beta = 0.1,
+    # nu = 1.7, FP32 out; error on a 10^5-entry sample (seed 7)
     n5, beta5, nu5 = 40_000, 0.1, 1.7
-    L5 = L3  # same 200 x 200 jittered grid (seed 4)
-    o_s = o32
-    c_s, c_l = ctr(), ctr()
-    bk.bk_matern_tile(L5, 1.0, beta5, nu5, out=o_s, opts=bk.make_opts(compute=bk.BK_F32, counters=c_s))
-    t_s = _time(lambda: bk.bk_matern_tile(L5, 1.0, beta5, nu5, out=o_s), stream, 3)
-    o_l = torch.empty_like(o_s)
-    bk.bk_matern_tile(L5, 1.0, beta5, nu5, out=o_l, opts=bk.make_opts(learned=net, counters=c_l))
+    c_l = _counters(bk, dev)
+    o_l = o32
+    bk.bk_matern_tile(L3, 1.0, beta5, nu5, out=o_l, opts=bk.make_opts(learned=net, counters=c_l))
+    cl = _ctr_summary(bk, c_l.cpu().numpy())
     lo = bk.make_opts(learned=net)
-    t_l = _time(lambda: bk.bk_matern_tile(L5, 1.0, beta5, nu5, out=o_l, opts=lo), stream, 3)
-    ref = bk.bk_matern_tile2(L5, L5[:, cols].contiguous(), 1.0, beta5, nu5,
-                             opts=bk.make_opts(compute=bk.BK_F64))
+    t_l = _time(lambda: bk.bk_matern_tile(L3, 1.0, beta5, nu5, out=o_l, opts=lo), stream, 3)
+    sample_matrix("learned_matern", o_l, L3h, 1.0, beta5, nu5, 100_000, 7, 0.01)
+    t_s = _time(lambda: bk.bk_matern_tile(L3, 1.0, beta5, nu5, out=o_l), stream, 3)
+    del o32, o_l
+    torch.cuda.empty_cache()
     o64 = torch.empty((n5, n5), dtype=torch.float64, device=dev)
-    t_p = _time(lambda: bk.bk_matern_tile(L5, 1.0, beta5, nu5, out=o64), stream, 1)
+    t_p = _time(lambda: bk.bk_matern_tile(L3, 1.0, beta5, nu5, out=o64), stream, 1)
     del o64
-    cl, cs = c_l.cpu().numpy(), c_s.cpu().numpy()
+    torch.cuda.empty_cache()
     res["learned_matern"] = {
-        "workload": f"n={n5} jittered grid, beta={beta5}, nu={nu5}, FP32 out",
-        "learned_value": n5 * n5 / t_l, "fp32_search_value": n5 * n5 / t_s,
+        "workload": f"C5: n={n5} jittered grid, beta={beta5}, nu={nu5}, FP32 out",
+        "value": n5 * n5 / t_l, "fp32_search_value": n5 * n5 / t_s,
         "plain_fp64_value": n5 * n5 / t_p, "unit": "entries/s",
         "learned_over_plain": t_p / t_l, "learned_over_fp32_search": t_s / t_l,
-        "fallback_rate": float(cl[bk.BK_CTR_FALLBACK] / max(1, cl[bk.BK_CTR_EVALS])),
-        "repairs_per_eval": float(cl[bk.BK_CTR_REPAIR] / max(1, cl[bk.BK_CTR_EVALS])),
-        "nodes_per_eval": {"learned": float(cl[bk.BK_CTR_NODES] / max(1, cl[bk.BK_CTR_EVALS])),
-                           "search": float(cs[bk.BK_CTR_NODES] / max(1, cs[bk.BK_CTR_EVALS]))},
-        "newton_iters_per_eval": {
-            "learned": float((cl[bk.BK_CTR_ITERS] + cl[bk.BK_CTR_PEAK_ITERS]) / max(1, cl[bk.BK_CTR_EVALS])),
-            "search": float((cs[bk.BK_CTR_ITERS] + cs[bk.BK_CTR_PEAK_ITERS]) / max(1, cs[bk.BK_CTR_EVALS]))},
-        "max_rel_vs_fp64_form": {"learned": _max_rel(o_l[cols, :], ref),
-                                 "search": _max_rel(o_s[cols, :], ref)}}
-    del o_s, o_l, o32, ref, L3
+        "counters": cl, "fallback_rate": cl["fallback_rate"],
+        "roofline": issue_roofline("learned_matern", "matern_sym_kernel<FormF32Learned, float>",
+                                   t_l, cl["evals"])}
+    del L3
     torch.cuda.empty_cache()
 
-    # -- learned window on 1e8 pairs: x log-uniform [1e-3, 140], nu U[0.05, 20] (seed 8)
+    # -- C5 evaluations: 10^8 pairs, x log-uniform [1e-3, 140], nu U[0.05, 20] (seed 8), FP32
+    # out; lanes per evaluation chosen by bk_eval_autotune; error on 10^6 of the pairs (seed 9)
     npairs = args.pairs
     xh, nh = inputs.kv_pairs(npairs, seed=8, nu_lo=0.05, nu_hi=20.0)
     X, V = torch.as_tensor(xh, device=dev), torch.as_tensor(nh, device=dev)
-    del xh, nh
     Y = torch.empty(npairs, dtype=torch.float32, device=dev)
-    c_e = ctr()
-    bk.bk_eval_ex(X, V, out=Y, opts=bk.make_opts(learned=net, counters=c_e))
-    t_le = _time(lambda: bk.bk_eval_ex(X, V, out=Y, opts=lo), stream, 3)
+    lanes_l = bk.bk_eval_autotune(X, V, Y, lo)
     fo = bk.make_opts(compute=bk.BK_F32)
+    lanes_f = bk.bk_eval_autotune(X, V, Y, fo)
+    c_e = _counters(bk, dev)
+    bk.bk_eval_ex(X, V, out=Y, opts=bk.make_opts(learned=net, counters=c_e))
+    ce = _ctr_summary(bk, c_e.cpu().numpy())
+    t_le = _time(lambda: bk.bk_eval_ex(X, V, out=Y, opts=lo), stream, 3)
+    per_lanes = {}
+    for L in (1, 2, 4, 8):
+        oL = bk.make_opts(learned=net, lanes=L)
+        per_lanes[str(L)] = npairs / _time(lambda: bk.bk_eval_ex(X, V, out=Y, opts=oL), stream, 2)
+    bk.bk_eval_ex(X, V, out=Y, opts=lo)
+    idx = np.sort(np.random.default_rng(9).choice(npairs, 1_000_000, replace=False))
+    got_l = Y[torch.as_tensor(idx, device=dev)].double().cpu().numpy()
+    samples.append({"key": "learned_eval", "kind": "eval", "x": xh[idx], "nu": nh[idx], "got": got_l})
+    c_f = _counters(bk, dev)
+    bk.bk_eval_ex(X, V, out=Y, opts=bk.make_opts(compute=bk.BK_F32, counters=c_f))
+    cf = _ctr_summary(bk, c_f.cpu().numpy())
     t_se = _time(lambda: bk.bk_eval_ex(X, V, out=Y, opts=fo), stream, 3)
     sub = slice(0, 2_000_000)
     Yd = torch.empty(2_000_000, dtype=torch.float64, device=dev)
     t_pe = _time(lambda: bk.bk_eval(X[sub], V[sub], out=Yd), stream, 1)
-    _, ll = bk.bk_eval_ex(X[sub], V[sub], opts=lo, want_log=True)
-    _, lp = bk.bk_eval_ex(X[sub], V[sub], want_log=True)
-    ce = c_e.cpu().numpy()
     res["learned_eval"] = {
-        "workload": f"{npairs} pairs, x log-uniform [1e-3,140], nu U[0.05,20] (seed 8), FP32 out",
-        "learned_value": npairs / t_le, "fp32_search_value": npairs / t_se,
-        "plain_fp64_value": 2_000_000 / t_pe, "unit": "K_nu evals/s",
-        "fallback_rate": float(ce[bk.BK_CTR_FALLBACK] / max(1, ce[bk.BK_CTR_EVALS])),
-        "repairs_per_eval": float(ce[bk.BK_CTR_REPAIR] / max(1, ce[bk.BK_CTR_EVALS])),
-        "max_rel_vs_fp64_form": float(torch.expm1((ll - lp).abs()).max()),
-        "err_sample": "the first 2,000,000 pairs (log K)"}
+        "workload": f"C5: {npairs} pairs, x log-uniform [1e-3,140], nu U[0.05,20] (seed 8), FP32 out",
+        "value": npairs / t_le, "unit": "K_nu evals/s", "lanes": lanes_l,
+        "value_per_lanes": per_lanes, "fp32_search_value": npairs / t_se,
+        "fp32_search_lanes": lanes_f, "plain_fp64_value": 2_000_000 / t_pe,
+        "counters": ce, "fallback_rate": ce["fallback_rate"], "fp32_search_counters": cf,
+        "roofline": issue_roofline("learned_eval" if lanes_l == 1 else f"learned_eval_L{lanes_l}",
+                                   f"eval_coop_kernel<FormF32Learned, float, {lanes_l}>",
+                                   t_le, ce["evals"]),
+        "fp32_search_roofline": issue_roofline("fp32_eval" if lanes_f == 1 else f"fp32_eval_L{lanes_f}",
+                                               f"eval_coop_kernel<FormF32, float, {lanes_f}>",
+                                               t_se, cf["evals"])}
     del X, V, Y, Yd
     torch.cuda.empty_cache()
 
-    # -- batched sweep: 256 instances, n log-uniform [500, 8000], one persistent launch in a graph
+    # -- C4 batched sweep: 256 instances, n log-uniform [500, 8000], one persistent launch
+    # replayed from a CUDA graph; the learned FP32 output sampled (400 entries per instance)
     insts = inputs.batched_instances(256)
     entries = sum(i.n * i.n for i in insts)
-    locs = [torch.as_tensor(i.locations(), device=dev) for i in insts]
-    bres = {"workload": "256 instances, n log-uniform [500, 8000], sigma2 U[0.5,2], "
+    locs_h = [i.locations() for i in insts]
+    locs = [torch.as_tensor(h, device=dev) for h in locs_h]
+    bres = {"workload": "C4: 256 instances, n log-uniform [500, 8000], sigma2 U[0.5,2], "
                         "beta U[0.02,0.3], nu U[0.3,3], one launch replayed from a CUDA graph",
             "entries": entries}
-    for name, dtype, opts in (("fp64", torch.float64, None),
-                              ("fp32", torch.float32, None),
-                              ("learned_fp32", torch.float32, bk.make_opts(learned=net))):
+    for name, dtype, form_opts in (("fp64", torch.float64, {}),
+                                   ("fp32", torch.float32, {}),
+                                   ("learned_fp32", torch.float32, {"learned": net})):
         outs = [torch.empty((i.n, i.n), dtype=dtype, device=dev) for i in insts]
         d = bk.make_descs([(L, i.sigma2, i.beta, i.nu, o) for L, i, o in zip(locs, insts, outs)])
-        plan = bk.BatchedPlan([i.n for i in insts], dtype=dtype, opts=opts)
+        cb = _counters(bk, dev)
+        cplan = bk.BatchedPlan([i.n for i in insts], dtype=dtype,
+                               opts=bk.make_opts(counters=cb, **form_opts) if form_opts else
+                               bk.make_opts(compute=bk.BK_F64 if dtype == torch.float64 else bk.BK_F32,
+                                            counters=cb))
+        bk.bk_matern_batched(d, cplan)
+        cbs = _ctr_summary(bk, cb.cpu().numpy())
+        del cplan
+        plan = bk.BatchedPlan([i.n for i in insts], dtype=dtype,
+                              opts=bk.make_opts(**form_opts) if form_opts else None)
         plan.autotune(d, sample_tiles=20_000)
         bk.bk_matern_batched(d, plan)
         g = torch.cuda.CUDAGraph()
@@ -397,7 +479,20 @@ def measure_forms(bk, inputs, dev, stream, args, plain_rate):
             bk.bk_matern_batched(d, plan)
         tb = _time(g.replay, stream, 2 if name == "fp64" else 5)
         bres[name] = {"value": entries / tb, "unit": "entries/s", "ms": 1e3 * tb,
-                      "plan": plan.info()}
+                      "plan": plan.info(), "counters": cbs}
+        if name != "fp64":
+            key = "batched_" + name
+            kern = ("matern_batched_kernel<FormF32Learned, float>" if form_opts
+                    else "matern_batched_kernel<FormF32, float>")
+            bres[name]["roofline"] = issue_roofline(key, kern, tb, cbs["evals"])
+        if name == "learned_fp32":
+            bres[name]["fallback_rate"] = cbs["fallback_rate"]
+            for k, (inst, o) in enumerate(zip(insts, outs)):
+                I, J = inputs.entry_sample(inst.n, 400, seed=1000 + k, near_fraction=0.01)
+                got = o[torch.as_tensor(J, device=dev), torch.as_tensor(I, device=dev)]
+                samples.append({"key": "batched_learned_fp32", "kind": "matern", "locs": locs_h[k],
+                                "I": I, "J": J, "theta": (inst.sigma2, inst.beta, inst.nu),
+                                "got": got.double().cpu().numpy()})
         del outs, d, g, plan
         torch.cuda.empty_cache()
     bres["learned_fp32_over_fp64"] = bres["learned_fp32"]["value"] / bres["fp64"]["value"]
@@ -452,7 +547,44 @@ def measure_forms(bk, inputs, dev, stream, args, plain_rate):
         del Ll, zl, ml, yl
         torch.cuda.empty_cache()
     res["gaussian_loglik"] = ll
-    return res
+    return res, samples
+
+
+def oracle_checks(samples, headline_samples):
+    """The CPU leg's comparison of GPU output samples with the oracle (OpenMP
+    over all host cores): the FP32 forms against the oracle's FP64 instance
+    (1e-5 tolerances), the plain FP64 headline against the long double oracle
+    (1e-10 absolute).  Returns {key: {...}} and the seconds spent."""
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    out = {}
+    groups = {}
+    for smp in samples:
+        groups.setdefault(smp["key"], []).append(smp)
+    for key, lst in groups.items():
+        worst, m = 0.0, 0
+        for smp in lst:
+            if smp["kind"] == "eval":
+                ref = oracle.besselk_f64(smp["x"], smp["nu"])
+            else:
+                ref = oracle.matern_entries_f64(smp["locs"], smp["I"], smp["J"], *smp["theta"])
+            got = smp["got"]
+            ok = (np.abs(ref) >= 1e-30) & (np.abs(ref) < 3.0e38)  # FP32-representable entries
+            rel = np.abs(got[ok] / ref[ok] - 1.0)
+            worst = max(worst, float(rel.max()) if rel.size else 0.0)
+            m += got.size
+        out[key] = {"max_rel_vs_oracle": worst, "sample": m, "oracle": "FP64 instance"}
+    for nu, (locs, I, J, got) in headline_samples.items():
+        ref = oracle.matern_entries(locs, I, J, SIGMA2, BETA, nu)
+        out.setdefault("plain_fp64", {"max_abs_vs_oracle": 0.0, "sample": 0,
+                                      "oracle": "long double"})
+        d = out["plain_fp64"]
+        d["max_abs_vs_oracle"] = max(d["max_abs_vs_oracle"], float(np.abs(got - ref).max()))
+        d["sample"] += got.size
+    return out, time.perf_counter() - t0
 
 
 def measure_e2e(bk, locs_h, n, dev, stream, args, world, device_step_ms):
@@ -525,6 +657,8 @@ def profile_case(args):
     bk.build()
     dev = torch.device("cuda")
     c = args.profile_case
+    if c == "fp32_forms":
+        return profile_fp32_forms(args, bk, inputs, dev)
     net = None
     if c in ("learned", "learned_eval", "batched"):
         net = bk.LearnedWindow(path=os.path.join(ROOT, "paper_2502_00356_gb300", "weights",
@@ -553,6 +687,50 @@ def profile_case(args):
     for _ in range(args.warmup + 1):
         run()
     torch.cuda.synchronize()
+
+
+def profile_fp32_forms(args, bk, inputs, dev):
+    """One launch of each FP32-form kernel the bench times, on the bench's own
+    workloads, in this order: the C3 FP32 matrix, the C5 learned matrix, the
+    10^8 learned and FP32 bare evaluations (1 lane per evaluation), and the
+    C4 batched FP32 and learned sweeps (for a one-pass ncu instruction count;
+    --warmup W runs each W more times first)."""
+    import numpy as np
+    import torch
+    net = bk.LearnedWindow(path=os.path.join(ROOT, "paper_2502_00356_gb300", "weights",
+                                             "window_mlp.bkw"))
+    L3 = torch.as_tensor(inputs.morton_sorted(inputs.jittered_grid(40_000, seed=4)), device=dev)
+    o = torch.empty((40_000, 40_000), dtype=torch.float32, device=dev)
+    nu3 = float(np.random.default_rng(5).uniform(0.3, 3.5))
+    lo = bk.make_opts(learned=net)
+    runs = [lambda: bk.bk_matern_tile(L3, 1.0, 0.05, nu3, out=o),
+            lambda: bk.bk_matern_tile(L3, 1.0, 0.1, 1.7, out=o, opts=lo)]
+    for r in runs:
+        for _ in range(args.warmup + 1):
+            r()
+    torch.cuda.synchronize()
+    del o, L3
+    torch.cuda.empty_cache()
+    xh, nh = inputs.kv_pairs(args.pairs, seed=8, nu_lo=0.05, nu_hi=20.0)
+    X, V = torch.as_tensor(xh, device=dev), torch.as_tensor(nh, device=dev)
+    Y = torch.empty(args.pairs, dtype=torch.float32, device=dev)
+    for opts in (bk.make_opts(learned=net, lanes=1), bk.make_opts(compute=bk.BK_F32, lanes=1)):
+        for _ in range(args.warmup + 1):
+            bk.bk_eval_ex(X, V, out=Y, opts=opts)
+    torch.cuda.synchronize()
+    del X, V, Y
+    torch.cuda.empty_cache()
+    insts = inputs.batched_instances(256)
+    locs = [torch.as_tensor(i.locations(), device=dev) for i in insts]
+    for opts in (None, lo):
+        outs = [torch.empty((i.n, i.n), dtype=torch.float32, device=dev) for i in insts]
+        d = bk.make_descs([(L, i.sigma2, i.beta, i.nu, o) for L, i, o in zip(locs, insts, outs)])
+        plan = bk.BatchedPlan([i.n for i in insts], dtype=torch.float32, opts=opts)
+        for _ in range(args.warmup + 1):
+            bk.bk_matern_batched(d, plan)
+        torch.cuda.synchronize()
+        del outs, d, plan
+        torch.cuda.empty_cache()
 
 
 def main():
@@ -640,6 +818,15 @@ def main():
     total_ms = max_over_ranks(t_start.elapsed_time(t_end), world, dev)
     value = job_rate(world, args.steps, len(NUS) * n * n, total_ms)
 
+    # -- output samples of the headline matrices for the CPU leg's oracle check
+    # (10^4 seeded entries per nu, 1 % nearest-neighbour pairs; untimed)
+    headline_samples = {}
+    for k, nu in enumerate(NUS):
+        bk.bk_matern_tile(L, SIGMA2, BETA, nu, out=out)
+        I, J = inputs.entry_sample(n, 10_000, seed=400 + k, near_fraction=0.01)
+        got = out[torch.as_tensor(J, device=dev), torch.as_tensor(I, device=dev)].cpu().numpy()
+        headline_samples[nu] = (locs_h, I, J, got)
+
     # -- roofline of the dominant kernel (the symmetric FP64 tile writer)
     mean_launch_s = statistics.mean(statistics.mean(v) for v in launch_ms) / 1e3
     flop_mean = float(np.mean(flop_per_launch))
@@ -700,18 +887,30 @@ def main():
     if not args.no_e2e:
         e2e = measure_e2e(bk, locs_h, n, dev, stream, args, world, total_ms / args.steps)
 
-    forms = None
+    forms, samples = None, []
     if not args.no_forms:
         del out
         torch.cuda.empty_cache()
-        forms = measure_forms(bk, inputs, dev, stream, args, value)
+        forms, samples = measure_forms(bk, inputs, dev, stream, args, value)
 
-    cpu = None
+    # -- the CPU leg (rank 0 at N = 1): the oracle timed on a bounded sample of the
+    # workload, and the oracle's values for the GPU output samples (errors)
+    cpu, checks = None, None
     if rank == 0 and world == 1:
         rate, sizes, cores = oracle_rate(args.cpu_seconds, n)
         cpu = {"value": rate, "unit": "entries/s", "cores": cores, "kind": "oracle",
                "sample": f"random entries of the three matrices ({'/'.join(map(str, sizes))} "
                          f"per nu), ~{args.cpu_seconds:.0f} s of CPU work, OpenMP over entries"}
+        checks, check_s = oracle_checks(samples, headline_samples)
+        cpu["error_checks_s"] = check_s
+        if forms is not None:
+            for key, d in checks.items():
+                if key == "batched_learned_fp32":
+                    forms["batched"]["learned_fp32"].update(d)
+                elif key in forms:
+                    forms[key].update(d)
+                elif key == "fp32_eval":
+                    forms["learned_eval"]["fp32_search_error"] = d
 
     if rank == 0:
         line = {
@@ -723,6 +922,7 @@ def main():
             "clocks": clk.summary(), "gpu_launches": args.steps * len(NUS) * LAUNCHES_PER_MATRIX,
             "launch_ms": {str(nu): statistics.mean(v) for nu, v in zip(NUS, launch_ms)},
             "failed_points": fails,
+            "error_vs_oracle": (checks or {}).get("plain_fp64"),
             "plain_window_fallback_rate": fallbacks / max(evals_counted, 1),
             "eval_fp64": {"value": eval_rate, "unit": "K_nu evals/s",
                           "workload": "100,000 pairs, x log-uniform [1e-3,140], nu U[0.05,10]",
