@@ -222,18 +222,23 @@ struct FormF64Fixed {
 };
 
 // The end of one FP32-form Matern entry after the quadrature (a7): the log
-// of the entry, log prefactor + nu log x + nu ts - x cosh ts - ln 2, summed as
-// a double-float (df_log_scale) and exponentiated in FP32 times h S, written
-// as OutT without FP64 instructions.  FP64 is used instead near r -> 0
-// (x < 1, where nu log x cancels against log K) and, for FP64 output, for
-// entries beyond the float range.
+// of the entry, (log prefactor - ln 2) + nu (log x + s) - x cosh s (s the
+// quadrature's shift point), summed as a double-float and exponentiated in
+// FP32 times h S, written as OutT without FP64 instructions.  Near r -> 0
+// the terms nu log x and nu s - x cosh s grow (to ~nu ln(2 nu/x)) and
+// cancel; the double-float sum (~44 bits, log x to 1e-9 absolute) keeps the
+// entry's relative error at the 1e-8 level there.  FP64 only for FP64 output
+// beyond the float range.
 template <typename OutT>
 __device__ __forceinline__ OutT matern_f32_finish(DF z, const Quad32& q,
                                                   const MaternParams& mp) {
-  if (z.hi >= 1.0f) {
+  if (!bits_pos(mp.sigma2)) return (OutT)0;  // sigma^2 = 0 (log c = -inf)
+  {
+    // (log c - ln 2) + nu (log x + s) - x cosh s
     const DF nu = DF{mp.nu_hi, mp.nu_lo};
-    DF a = df_add(DF{mp.log_pref_hi, mp.log_pref_lo}, df_mul(nu, df_log(z)));
-    a = df_add(a, df_log_scale(z, nu, q));
+    DF a = df_add(DF{mp.log_pref_m_ln2_hi, mp.log_pref_m_ln2_lo},
+                  df_mul(nu, df_add_f(df_log(z), q.ts)));
+    a = df_add(a, df_neg(df_mul(z, q.ch)));
     if constexpr (sizeof(OutT) == sizeof(float)) {
       return df_exp_times(a, q.hS);
     } else {

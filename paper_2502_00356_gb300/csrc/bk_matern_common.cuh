@@ -32,6 +32,7 @@ struct MaternParams {
   float inv_beta_f, nu_hi, nu_lo;  // nu = nu_hi + nu_lo (two floats)
   float inv_beta_lo;               // 1/beta = inv_beta_f + inv_beta_lo
   float log_pref_hi, log_pref_lo;  // a1 as two floats
+  float log_pref_m_ln2_hi, log_pref_m_ln2_lo;  // a1 - ln 2 as two floats (FP32 forms)
   float sigma2_f;                  // sigma^2 as a float (the FP32 diagonal)
 };
 
@@ -48,6 +49,9 @@ __device__ __forceinline__ MaternParams matern_params(double sigma2, double beta
   p.inv_beta_lo = (float)(p.inv_beta - (double)p.inv_beta_f);
   p.log_pref_hi = (float)p.log_pref;
   p.log_pref_lo = (float)(p.log_pref - (double)p.log_pref_hi);
+  const double lpm = p.log_pref - kLn2;
+  p.log_pref_m_ln2_hi = (float)lpm;
+  p.log_pref_m_ln2_lo = (float)(lpm - (double)p.log_pref_m_ln2_hi);
   p.sigma2_f = (float)sigma2;
   return p;
 }
@@ -68,6 +72,9 @@ inline MaternParams matern_params_host(double sigma2, double beta, double nu) {
   p.inv_beta_lo = (float)(p.inv_beta - (double)p.inv_beta_f);
   p.log_pref_hi = (float)p.log_pref;
   p.log_pref_lo = (float)(p.log_pref - (double)p.log_pref_hi);
+  const double lpm = p.log_pref - kLn2;
+  p.log_pref_m_ln2_hi = (float)lpm;
+  p.log_pref_m_ln2_lo = (float)(lpm - (double)p.log_pref_m_ln2_hi);
   p.sigma2_f = (float)sigma2;
   return p;
 }

@@ -419,13 +419,13 @@ __device__ __forceinline__ DF df_cosh_m1(float t) {
 struct Quad32 {
   float hS;
   float ts;    // the shift point s (the window's peak rounded to the grid of kPeakTab)
-  DF cm1;      // cosh s - 1 as a double-float
+  DF ch;       // cosh s as a double-float
   float amax;  // largest node exponent g(t_j) - g(s) (up to the e^{-2 nu t} factor)
 };
 
 // The shift points of the FP32 quadrature: the peak ts rounded to the grid
-// k/64 (k <= 1024), where kPeakTab holds cosh s - 1 (double-float), sinh s
-// and e^{-s} (gen_peak_table.py).  Any shift point is exact (it scales the
+// k/64 (k <= 1024), where kPeakTab holds cosh s (double-float), sinh s and
+// e^{-s} (gen_peak_table.py).  Any shift point is exact (it scales the
 // terms, and log K adds it back); one within 1/128 of the peak keeps the
 // largest scaled term at e^{|g''| / 32768} ~ 1.  The table takes the place
 // of per-evaluation FP32 exponentials of ts and of a double-float cosh ts - 1.
@@ -434,16 +434,16 @@ static __device__ const float4 kPeakTab[kPeakTabSize] = {
 #include "bk_peak_table.inc"
 };
 
-// s, cosh s - 1, D = x sinh s and B = x e^{-s}/2 for the peak ts: from the
+// s, cosh s, D = x sinh s and B = x e^{-s}/2 for the peak ts: from the
 // table on its grid, else (ts >= 16, or not a number) at ts itself from FP32
 // and double-float exponentials.
-__device__ __forceinline__ void shift_f32(float x, float ts, float& s, DF& cm1, float& B,
+__device__ __forceinline__ void shift_f32(float x, float ts, float& s, DF& ch, float& B,
                                           float& D) {
   if (ts >= 0.0f && ts < 16.0f) {
     const float r = rintf(ts * 64.0f);
     s = r * 0.015625f;
     const float4 e = __ldg(&kPeakTab[__float2int_rn(r)]);
-    cm1 = DF{e.x, e.y};
+    ch = DF{e.x, e.y};
     D = x * e.z;
     B = 0.5f * x * e.w;
   } else {
@@ -452,7 +452,7 @@ __device__ __forceinline__ void shift_f32(float x, float ts, float& s, DF& cm1, 
     exp_pm_f32(ts, ep, emx);
     B = 0.5f * x * emx;
     D = 0.5f * x * (ep - emx);  // no cancellation at ts >= 16
-    cm1 = df_cosh_m1(ts);
+    ch = df_add_f(df_cosh_m1(ts), 1.0f);
   }
 }
 
@@ -503,11 +503,11 @@ __device__ __forceinline__ Job32 job_f32(float x, float nu, float nu_lo, const W
     ++tl.fail;
     q.hS = __int_as_float(0x7fc00000);
     q.ts = w.ts;
-    q.cm1 = DF{0.0f, 0.0f};
+    q.ch = DF{1.0f, 0.0f};
     return no_job32();
   }
   Job32 jb;
-  shift_f32(x, w.ts, q.ts, q.cm1, jb.B, jb.D);
+  shift_f32(x, w.ts, q.ts, q.ch, jb.B, jb.D);
   jb.t0 = w.t0;
   jb.h = (w.t1 - w.t0) / (float)N;
   jb.s = q.ts;
@@ -604,15 +604,13 @@ __device__ __forceinline__ Quad32 quad_f32(float x, float nu, float nu_lo, const
 // log f_s = nu s - x cosh(s) - ln 2 in FP64 (nu s reaches ~200), s the
 // quadrature's shift point.
 __device__ __forceinline__ double log_scale_from(double x64, double nu64, const Quad32& q) {
-  const double xc1 = x64 * ((double)q.cm1.hi + (double)q.cm1.lo);
-  return fma(nu64, (double)q.ts, -x64) - xc1 - kLn2;
+  return fma(nu64, (double)q.ts, -x64 * ((double)q.ch.hi + (double)q.ch.lo)) - kLn2;
 }
 
 // The same log f_s = nu s - x cosh(s) - ln 2 as a double-float from the
 // double-float x and nu, without FP64 instructions.
 __device__ __forceinline__ DF df_log_scale(DF x, DF nu, const Quad32& q) {
-  DF a = df_add(df_mul_f(nu, q.ts), df_neg(x));
-  a = df_add(a, df_neg(df_mul(x, q.cm1)));
+  const DF a = df_add(df_mul_f(nu, q.ts), df_neg(df_mul(x, q.ch)));
   return df_add(a, DF{-kLn2DfHi, -kLn2DfLo});
 }
 

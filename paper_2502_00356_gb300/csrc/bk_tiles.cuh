@@ -278,6 +278,32 @@ __device__ __forceinline__ void sym_tile(const Form& form, SymTileSmem<OutT>& sm
     sm.tile[lane][c] = v;
   }
   __syncthreads();
+  if constexpr (sizeof(OutT) == sizeof(float)) {
+    // FP32 output, interior tile, 16-byte aligned columns: 16-byte stores,
+    // 256 per block half (item t: column t / 8, rows 4 (t % 8) .. 4 (t % 8)
+    // + 3; a warp writes four whole 128-byte column segments).
+    if (r0 + kTile <= n && c0 + kTile <= n && (ld & 3) == 0 &&
+        ((uintptr_t)out & 15) == 0) {
+#pragma unroll
+      for (int t = threadIdx.x; t < kTile * kTile / 4; t += WARPS * 32) {
+        const int c = t >> 3, q = (t & 7) * 4;
+        float4 v;
+        v.x = sm.tile[q][c];
+        v.y = sm.tile[q + 1][c];
+        v.z = sm.tile[q + 2][c];
+        v.w = sm.tile[q + 3][c];
+        *reinterpret_cast<float4*>(out + (r0 + q) + (c0 + c) * ld) = v;
+        if (I != J) {  // block (J, I): entry (c0 + i, r0 + c) = tile[c][i]
+          v.x = sm.tile[c][q];
+          v.y = sm.tile[c][q + 1];
+          v.z = sm.tile[c][q + 2];
+          v.w = sm.tile[c][q + 3];
+          *reinterpret_cast<float4*>(out + (c0 + q) + (r0 + c) * ld) = v;
+        }
+      }
+      return;
+    }
+  }
 #pragma unroll
   for (int c = warp; c < kTile; c += WARPS) {
     const int64_t i = r0 + lane, j = c0 + c;

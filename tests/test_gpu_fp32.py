@@ -5,6 +5,8 @@ are representable as normal FP32 numbers); the measured error is asserted
 below that.  Entries smaller than 1e-30 (far beyond the correlation range)
 are checked in absolute terms only.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -196,3 +198,37 @@ def test_default_form_follows_output_dtype(dev):
     torch.cuda.synchronize()
     assert torch.equal(d2, f32)
 
+
+
+@pytest.mark.parametrize("nu", [0.5, 1.7, 3.2])
+def test_matern_f32_small_distances(dev, nu):
+    """Entries at r << beta (x down to 1e-6), where nu log x and log K_nu(x)
+    grow and cancel in the normalisation: both FP32 forms within 1e-5 of the
+    oracle."""
+    rng = np.random.default_rng(31)
+    n = 150
+    locs = 0.5 + 1e-3 * rng.random((2, n))
+    locs[:, 1] = locs[:, 0] + 1e-7   # a pair at r ~ 1.4e-7 (x ~ 1.4e-6)
+    locs[:, 2] = locs[:, 0] + 3e-5
+    locs = np.ascontiguousarray(locs)
+    want = oracle.matern_block(locs, locs, 1.3, 0.1, nu)
+    L = to_dev(locs, dev)
+    net = bk.LearnedWindow(path=os.path.join(os.path.dirname(os.path.dirname(
+        os.path.abspath(__file__))), "paper_2502_00356_gb300", "weights", "window_mlp.bkw"))
+    for opts in (bk.make_opts(compute=bk.BK_F32), bk.make_opts(learned=net)):
+        got = bk.bk_matern_tile(L, 1.3, 0.1, nu, dtype=torch.float32, opts=opts)
+        torch.cuda.synchronize()
+        check_entries(got.cpu().numpy().astype(np.float64).T, want)
+
+
+def test_zero_sigma2_gives_zero_matrix(dev):
+    """sigma^2 = 0 (allowed by the C-ABI): every entry, the diagonal included,
+    is 0 in every form and output type."""
+    L = to_dev(inputs.morton_sorted(inputs.jittered_grid(70, seed=33)), dev)
+    net = bk.LearnedWindow(path=os.path.join(os.path.dirname(os.path.dirname(
+        os.path.abspath(__file__))), "paper_2502_00356_gb300", "weights", "window_mlp.bkw"))
+    for dtype in (torch.float64, torch.float32):
+        for opts in (None, bk.make_opts(compute=bk.BK_F32), bk.make_opts(learned=net)):
+            m = bk.bk_matern_tile(L, 0.0, 0.1, 1.7, dtype=dtype, opts=opts)
+            torch.cuda.synchronize()
+            assert bool((m == 0).all())
