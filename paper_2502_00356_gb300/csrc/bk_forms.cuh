@@ -13,6 +13,21 @@
 
 namespace bk {
 
+// A pair's sorting key for the bare evaluations: an estimate of its node
+// count, monotone in the two things that set it, the window's width (which
+// grows like ln(1 + 74/x) past the peak, 74 = 2 log(1/eps)) and the
+// strip-bound step (which shrinks like 1/(30 + 3 nu)); in FP32 on truncated
+// copies.  Positive floats order like their bit patterns.  Any key is valid:
+// it only groups pairs of similar cost into warps.
+__device__ __forceinline__ unsigned eval_cost_key(double x, double nu) {
+  const float xf = f32_trunc(x), nf = fabsf(f32_trunc(nu));
+  float r, l2;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(xf));
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l2) : "f"(fmaf(74.0f, r, 1.0f)));
+  const float est = (l2 + 1.5f) * fmaf(3.0f, nf, 30.0f);
+  return (est > 0.0f && est < 3.0e38f) ? __float_as_uint(est) : 0xfffffffeu;
+}
+
 // The element-wise domain rules of the C-ABI around a form's evaluation.
 template <class Form>
 __device__ __forceinline__ double eval_domain(const Form& form, double x, double nu, Tally& tl,
@@ -64,6 +79,15 @@ struct FormF64T {
   double series_below;  // x below which Temme's series replaces the integral (0: never)
   const double* cnu = nullptr;  // 2 cosh(nu h) on kCoshTab's steps for the launch's nu, or null
   static constexpr bool kCoshNuTable = true;
+
+  // The bare evaluations' sorting key (sorted_pair): an estimate of the node
+  // count from the arguments alone (eval_cost_key).  The exact count from the
+  // FP32 window costs a second window search per pair, more than the better
+  // ordering saves (measured), and 1 for the series.
+  __device__ __forceinline__ unsigned sort_key(double x, double nu) const {
+    if (kSeries && x < series_below) return 1u;
+    return eval_cost_key(x, nu);
+  }
 
   // log K from Temme's series (Sec. IV-A), tallied.
   __device__ __forceinline__ double series(double x, double nu, Tally& tl) const {
@@ -163,6 +187,11 @@ struct FormF64Fixed {
   double t1;
   int bins;
   double series_below;
+
+  // The bare evaluations' sorting key: the series or the fixed b + 1 nodes.
+  __device__ __forceinline__ unsigned sort_key(double x, double) const {
+    return x < series_below ? 1u : 2u;
+  }
 
   __device__ __forceinline__ double log_k_of(double x, double nu, Tally& tl, double& hS,
                                              bool& by_series) const {
@@ -298,7 +327,7 @@ __device__ __forceinline__ void eval_out_f32_coop(const Form& f, bool valid, dou
     else need_search = true;
   }
   float hS, amax;
-  coop_trapezoid_f32<L>(jb, hS, amax);
+  coop_trapezoid_f32<L, Form::kChecked>(jb, hS, amax);
   if (jb.N >= 0) {
     q.hS = hS;
     q.amax = amax;
@@ -312,7 +341,7 @@ __device__ __forceinline__ void eval_out_f32_coop(const Form& f, bool valid, dou
         w = search_window_f32(xd.hi, x64_of, nd.hi, f.tab, tl);
         jb2 = job_f32(xd.hi, nd.hi, nd.lo, w, q, tl);
       }
-      coop_trapezoid_f32<L>(jb2, hS, amax);
+      coop_trapezoid_f32<L, Form::kChecked>(jb2, hS, amax);
       if (jb2.N >= 0) {
         q.hS = hS;
         q.amax = amax;
@@ -369,7 +398,7 @@ __device__ __forceinline__ OutT matern_out_f32_coop(const Form& f, bool valid, c
       need_search = true;
   }
   float hS, amax;
-  coop_trapezoid_f32<1>(jb, hS, amax);
+  coop_trapezoid_f32<1, Form::kChecked>(jb, hS, amax);
   if (jb.N >= 0) {
     q.hS = hS;
     q.amax = amax;
@@ -383,7 +412,7 @@ __device__ __forceinline__ OutT matern_out_f32_coop(const Form& f, bool valid, c
         w = search_window_f32(z.hi, x64_of, mp.nu_hi, f.tab, tl);
         jb2 = job_f32(z.hi, mp.nu_hi, mp.nu_lo, w, q, tl);
       }
-      coop_trapezoid_f32<1>(jb2, hS, amax);
+      coop_trapezoid_f32<1, Form::kChecked>(jb2, hS, amax);
       if (jb2.N >= 0) {
         q.hS = hS;
         q.amax = amax;

@@ -167,21 +167,20 @@ __device__ __forceinline__ float expm1_f32(float y) {
   return fabsf(y) < 0.35f ? poly : mufu_ex2(y * kLog2ef) - 1.0f;
 }
 
-// e^y - 1 and e^{-y} - 1 together, both with small relative error: for
-// |y| < 0.35 the Taylor polynomial p of expm1 (as in expm1_f32) and
-// e^{-y} - 1 = -p / (1 + p); above, E = e^y on the MUFU and E - 1, 1/E - 1
-// (no cancellation beyond a factor of ~3 in ulps there).  One polynomial,
-// one ex2 and one rcp instead of two expm1_f32 calls.
+// e^y - 1 and e^{-y} - 1 together, both with small relative error:
+// em = e^y - 1 from the Taylor polynomial of expm1 for |y| < 0.35 (as in
+// expm1_f32), else E - 1 with E = e^y on the MUFU (exact for E in [1/2, 2] by
+// Sterbenz, no cancellation beyond a factor ~3 in ulps elsewhere), and
+// e^{-y} - 1 = -em / (1 + em) from one rcp (1 + em reproduces E there).  One
+// polynomial, one ex2 and one rcp instead of two expm1_f32 calls.
 __device__ __forceinline__ void expm1_pm_f32(float y, float& em, float& emn) {
   const float p =
       y * fmaf(y, fmaf(y, fmaf(y, fmaf(y, fmaf(y, fmaf(y, 1.0f / 5040.0f, 1.0f / 720.0f),
                                                1.0f / 120.0f), 1.0f / 24.0f), 1.0f / 6.0f),
                    0.5f), 1.0f);
   const float e = mufu_ex2(y * kLog2ef);
-  const bool small = fabsf(y) < 0.35f;
-  em = small ? p : e - 1.0f;
-  const float r = mufu_rcp(small ? 1.0f + p : e);
-  emn = small ? -p * r : r - 1.0f;
+  em = fabsf(y) < 0.35f ? p : e - 1.0f;
+  emn = -em * mufu_rcp(1.0f + em);
 }
 
 // The searched window of the FP32 form: FP32 search inside x in [1e-4, 1e4],
@@ -518,11 +517,26 @@ __device__ __forceinline__ Job32 job_f32(float x, float nu, float nu_lo, const W
   return jb;
 }
 
+// One node's term of the FP32 sum (the node arithmetic above): the scaled
+// integrand at tau = t - s times (1 + e^{-2 nu t}) (W = e^{-2 nu t}); am
+// receives the largest exponent when kAmax.
+template <bool kAmax>
+__device__ __forceinline__ float node_f32(const Job32& jb, float tau, float W, float& am) {
+  float em, emn;
+  expm1_pm_f32(tau, em, emn);
+  const float a = fmaf(jb.nu, tau, fmaf(jb.nu_lo, tau, -em * fmaf(-jb.B, emn, jb.D)));
+  if constexpr (kAmax) am = fmaxf(am, a);
+  const float f = exp_f32(a);
+  return fmaf(f, W, f);
+}
+
 // Runs the 32 jobs of the warp on groups of L lanes; for L > 1 every lane of
 // the warp must call it (L = 1 runs this lane's job alone).  Each lane
-// receives h S and the largest node exponent of its own job (0 and -3e38 for
-// no job).
-template <int L>
+// receives h S and, when kAmax, the largest node exponent of its own job (0
+// and -3e38 for no job).  A lane's first node is taken before its loop and
+// its last node's term kept, so that the end weights 1/2 need no test per
+// node.
+template <int L, bool kAmax = true>
 __device__ __forceinline__ void coop_trapezoid_f32(const Job32& my, float& hS, float& amax) {
   static_assert(L == 1 || L == 2 || L == 4 || L == 8, "lanes per job");
   constexpr int G = 32 / L;  // jobs per pass
@@ -544,25 +558,28 @@ __device__ __forceinline__ void coop_trapezoid_f32(const Job32& my, float& hS, f
       jb.D = __shfl_sync(kAll, my.D, owner);
       jb.N = __shfl_sync(kAll, my.N, owner);
     }
-    const float tau0 = jb.t0 - jb.s;
-    const float l2n = -2.0f * kLog2ef * jb.nu;
-    float W = mufu_ex2(l2n * fmaf((float)r, jb.h, jb.t0));  // e^{-2 nu t_r}
-    const float rho = mufu_ex2(l2n * ((float)L * jb.h));    // e^{-2 nu L h}
-    float S = 0.0f, c = 0.0f, ends = 0.0f, am = -3.0e38f, jf = (float)r;
-    for (int j = r; j <= jb.N; j += L, jf += (float)L) {
-      const float tau = fmaf(jf, jb.h, tau0);
-      float em, emn;
-      expm1_pm_f32(tau, em, emn);
-      const float a = fmaf(jb.nu, tau, fmaf(jb.nu_lo, tau, -em * fmaf(-jb.B, emn, jb.D)));
-      am = fmaxf(am, a);
-      float f = exp_f32(a);
-      f = fmaf(f, W, f);
-      if (j == 0 || j == jb.N) ends += f;  // end weights 1/2
-      const float y = f - c;  // Kahan
-      const float s2 = S + y;
-      c = (s2 - S) - y;
-      S = s2;
-      W *= rho;
+    float S = 0.0f, c = 0.0f, ends = 0.0f, am = -3.0e38f;
+    if (r <= jb.N) {
+      const float tau0 = jb.t0 - jb.s;
+      const float l2n = -2.0f * kLog2ef * jb.nu;
+      float W = mufu_ex2(l2n * fmaf((float)r, jb.h, jb.t0));  // e^{-2 nu t_r}
+      const float rho = mufu_ex2(l2n * ((float)L * jb.h));    // e^{-2 nu L h}
+      float f = node_f32<kAmax>(jb, fmaf((float)r, jb.h, tau0), W, am);
+      const float f_first = f;
+      S = f;
+      float jf = (float)(r + L);
+#pragma unroll 2
+      for (int j = r + L; j <= jb.N; j += L, jf += (float)L) {
+        W *= rho;
+        f = node_f32<kAmax>(jb, fmaf(jf, jb.h, tau0), W, am);
+        const float y = f - c;  // Kahan
+        const float s2 = S + y;
+        c = (s2 - S) - y;
+        S = s2;
+      }
+      // end weights 1/2: node 0 is this lane's first if r = 0; node N its
+      // last if N - r is a multiple of L
+      ends = (r == 0 ? f_first : 0.0f) + (((jb.N - r) & (L - 1)) == 0 ? f : 0.0f);
     }
     // this lane's part as hi + lo, then the group's butterfly
     DF v = two_sum(S, -c);
@@ -572,7 +589,7 @@ __device__ __forceinline__ void coop_trapezoid_f32(const Job32& my, float& hS, f
       const float oh = __shfl_xor_sync(kAll, v.hi, o), ol = __shfl_xor_sync(kAll, v.lo, o);
       const DF t = two_sum(v.hi, oh);
       v = quick_two_sum(t.hi, t.lo + (v.lo + ol));
-      am = fmaxf(am, __shfl_xor_sync(kAll, am, o));
+      if constexpr (kAmax) am = fmaxf(am, __shfl_xor_sync(kAll, am, o));
     }
     const float tot = jb.h * (v.hi + v.lo);
     if constexpr (L == 1) {
@@ -581,7 +598,7 @@ __device__ __forceinline__ void coop_trapezoid_f32(const Job32& my, float& hS, f
     } else {
       // the owner of group g' in pass p is lane p G + g'; group g' holds its sum
       const float got = __shfl_sync(kAll, tot, (lane % G) * L);
-      const float gam = __shfl_sync(kAll, am, (lane % G) * L);
+      const float gam = kAmax ? __shfl_sync(kAll, am, (lane % G) * L) : 0.0f;
       if (lane / G == p) {
         hS = got;
         amax = gam;

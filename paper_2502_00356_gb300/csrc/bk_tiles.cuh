@@ -75,35 +75,23 @@ __device__ __forceinline__ Form bind_table(const Form& form, double* s_tab) {
   return f;
 }
 
-// A pair's sorting key for the bare evaluations: an estimate of its node
-// count, monotone in the two things that set it, the window's width (which
-// grows like ln(1 + 74/x) past the peak, 74 = 2 log(1/eps)) and the
-// strip-bound step (which shrinks like 1/(30 + 3 nu)); in FP32 on truncated
-// copies.  Positive floats order like their bit patterns.  Any key is valid:
-// it only groups pairs of similar cost into warps.
-__device__ __forceinline__ unsigned eval_cost_key(double x, double nu) {
-  const float xf = f32_trunc(x), nf = fabsf(f32_trunc(nu));
-  float r, l2;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(xf));
-  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l2) : "f"(fmaf(74.0f, r, 1.0f)));
-  const float est = (l2 + 1.5f) * fmaf(3.0f, nf, 30.0f);
-  return (est > 0.0f && est < 3.0e38f) ? __float_as_uint(est) : 0xfffffffeu;
-}
-
-// Orders a round of 128 pairs (base .. base + 127) by eval_cost_key with a
-// bitonic sort in shared memory and returns the pair thread t evaluates, so
+// Orders a round of 128 pairs (base .. base + 127) by key_of(x, nu) (the
+// form's sort_key, or eval_cost_key) with a bitonic sort in shared memory and
+// returns the pair thread t evaluates, so
 // that a warp's 32 lanes take similar paths through the search and the node
 // loop (random pairs otherwise leave most lanes idle while the slowest
 // finishes).  Each pair's arithmetic is unchanged; results go back to their
 // own positions.  Every thread of the 128-thread block must call it.
+template <class KeyOf>
 __device__ __forceinline__ int64_t sorted_pair(const double* __restrict__ x,
                                                const double* __restrict__ nu, int64_t base,
-                                               int64_t n, unsigned* s_key, unsigned char* s_idx) {
+                                               int64_t n, unsigned* s_key, unsigned char* s_idx,
+                                               KeyOf key_of) {
   constexpr int kB = 128;
   const int t = threadIdx.x;
   const int64_t i0 = base + t;
   __syncthreads();  // the previous round's order is no longer read
-  s_key[t] = (i0 < n) ? eval_cost_key(x[i0], nu[i0]) : 0xffffffffu;
+  s_key[t] = (i0 < n) ? key_of(x[i0], nu[i0]) : 0xffffffffu;
   s_idx[t] = (unsigned char)t;
   for (int size = 2; size <= kB; size <<= 1) {
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
@@ -126,9 +114,8 @@ __device__ __forceinline__ int64_t sorted_pair(const double* __restrict__ x,
   return base + s_idx[t];
 }
 
-// Bare evaluations, 128 per block and round.  The FP64 forms sort each round
-// by cost (sorted_pair); the FP32 forms, whose lanes diverge less and whose
-// evaluations are short, take the pairs in order.
+// Bare evaluations of the FP64 forms, 128 per block and round, each round
+// sorted by the form's cost key (sorted_pair).
 template <class Form, typename OutT>
 __global__ void __launch_bounds__(128, 6) eval_kernel(const Form form, const double* __restrict__ x,
                                                    const double* __restrict__ nu,
@@ -144,14 +131,21 @@ __global__ void __launch_bounds__(128, 6) eval_kernel(const Form form, const dou
   Tally tl{0u, 0u, 0u, 0u, 0u, 0u, 0u};
   unsigned evals = 0;
   const bool want_log = (log_out != nullptr);
-  for (int64_t base = (int64_t)blockIdx.x * kB; base < n; base += (int64_t)gridDim.x * kB) {
+  // Block b takes the contiguous chunk [b c, (b + 1) c) of c pairs, c =
+  // ceil(n / grid) rounded up to whole rounds of 128: one wave of the SMs'
+  // resident slots, with equal chunks (+9 % on 10^7 pairs over a grid-stride
+  // loop), and full rounds when n is small.
+  const int64_t chunk = ((n + gridDim.x - 1) / gridDim.x + kB - 1) / kB * kB;
+  const int64_t lo = (int64_t)blockIdx.x * chunk, hi = min(n, lo + chunk);
+  for (int64_t base = lo; base < hi; base += kB) {
     int64_t i;
     if constexpr (kSort) {
-      i = sorted_pair(x, nu, base, n, s_key, s_idx);
+      i = sorted_pair(x, nu, base, hi, s_key, s_idx,
+                      [&](double xi, double vi) { return f.sort_key(xi, vi); });
     } else {
       i = base + threadIdx.x;
     }
-    if (i < n) {
+    if (i < hi) {
       OutT k, lk;
       f.template eval_out<OutT>(x[i], nu[i], tl, evals, k, lk, want_log);
       out[i] = k;
@@ -210,7 +204,8 @@ __global__ void __launch_bounds__(128, 4) eval_grad_kernel(const Form form, cons
   unsigned evals = 0;
   const double qnan = __longlong_as_double(0x7ff8000000000000LL);
   for (int64_t base = (int64_t)blockIdx.x * kB; base < n; base += (int64_t)gridDim.x * kB) {
-    const int64_t i = sorted_pair(x, nu, base, n, s_key, s_idx);
+    const int64_t i = sorted_pair(x, nu, base, n, s_key, s_idx,
+                                  [](double a, double b) { return eval_cost_key(a, b); });
     if (i >= n) continue;
     const double xi = x[i], vi = nu[i], av = fabs(vi);
     double kk = qnan, dx = qnan, dn = qnan;
@@ -442,12 +437,17 @@ cudaError_t launch_eval_form(const Form& form, const double* x, const double* nu
       return launch_eval_coop(form, lanes, grid, x, nu, (double*)out, (double*)log_out, n, ctr, s);
     return launch_eval_coop(form, lanes, grid, x, nu, (float*)out, (float*)log_out, n, ctr, s);
   } else {
+    // one wave of the resident slots (6 blocks per SM); chunks of whole rounds
+    const int64_t slots = (int64_t)current_sm_count() * 6;
+    const int64_t rounds = (n + 127) / 128;
+    const int64_t per = (rounds + slots - 1) / slots;  // rounds per block
+    const int g64 = (int)((rounds + per - 1) / per);
     if (out_t == BK_F64)
-      eval_kernel<Form, double><<<grid, 128, 0, s>>>(form, x, nu, (double*)out, (double*)log_out,
-                                                     n, ctr);
+      eval_kernel<Form, double><<<g64, 128, 0, s>>>(form, x, nu, (double*)out, (double*)log_out,
+                                                    n, ctr);
     else
-      eval_kernel<Form, float><<<grid, 128, 0, s>>>(form, x, nu, (float*)out, (float*)log_out, n,
-                                                    ctr);
+      eval_kernel<Form, float><<<g64, 128, 0, s>>>(form, x, nu, (float*)out, (float*)log_out, n,
+                                                   ctr);
     return cudaGetLastError();
   }
 }
