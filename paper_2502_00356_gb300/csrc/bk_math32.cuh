@@ -32,6 +32,10 @@ __device__ __forceinline__ float mufu_lg2(float v) {
   return r;
 }
 __device__ __forceinline__ float exp_f32(float a) { return mufu_ex2(a * kLog2ef); }
+// a / b from the MUFU reciprocal (about 2 ulp; moderate normal b), for
+// Newton steps, first guesses and low-order corrections, where a rounded
+// quotient is not needed (an IEEE division is a ~10-instruction sequence).
+__device__ __forceinline__ float fast_div(float a, float b) { return a * mufu_rcp(b); }
 
 // sinh with small relative error for all |y| <= ~80: the odd Taylor
 // polynomial to y^7 below 0.35 (truncation < 1e-9 relative), (e^y - e^-y)/2
@@ -70,7 +74,7 @@ struct Window32 {
 __device__ __forceinline__ float peak_f32(float x, float nu, Tally& tl) {
   const float nu2 = nu * nu;
   if (!(nu2 > x)) return 0.0f;
-  const float q = nu / x;
+  const float q = fast_div(nu, x);
   float hi = kLn2f * mufu_lg2(q + sqrtf(fmaf(q, q, 1.0f)));
   hi = fmaf(hi, 1.0e-4f, hi) + 1.0e-6f;
   float lo = 0.0f;
@@ -88,7 +92,7 @@ __device__ __forceinline__ float peak_f32(float x, float nu, Tally& tl) {
     if (gp > 0.0f) lo = t; else hi = t;
     float tn;
     if (gpp < 0.0f) {
-      tn = t - gp / gpp;
+      tn = t - fast_div(gp, gpp);
       if (tn > hi) tn = hi;
       if (!(tn > lo)) tn = 0.5f * (lo + hi);
     } else {
@@ -119,16 +123,16 @@ __device__ __forceinline__ Window32 window_f32(float x, float nu, float L, Tally
   const float ss = sinh_f32(ts);
   {
     const float a = x * cs, b = nu - x * ss;
-    float t = ts + (b + sqrtf(fmaf(b, b, 2.0f * a * L))) / a;
+    float t = ts + fast_div(b + sqrtf(fmaf(b, b, 2.0f * a * L)), a);
     t = fmaf(t, 1.0e-4f, t);
-    float tb = kLn2f * mufu_lg2(2.0f * (L + a + nu * t) / x);
+    float tb = kLn2f * mufu_lg2(fast_div(2.0f * (L + a + nu * t), x));
     tb = fmaf(tb, 1.0e-4f, tb);
     if (tb < t) t = tb;
     for (int it = 0; it < 40; ++it) {
       ++tl.iters;
       const float F = fmaf(nu, t - ts, -x * dcosh_f32(t, ts)) + L;
       const float Fp = fmaf(-x, sinh_f32(t), nu);
-      const float dt = F / Fp;
+      const float dt = fast_div(F, Fp);
       t -= dt;
       if (fabsf(dt) <= 1e-5f * t) break;
     }
@@ -139,12 +143,12 @@ __device__ __forceinline__ Window32 window_f32(float x, float nu, float L, Tally
     const float Lp = L + kLn2f;
     const float G0 = fmaf(-nu, ts, x * (cs - 1.0f)) + Lp;
     if (G0 < 0.0f) {
-      float t = fmaxf(0.0f, ts - Lp / nu);
+      float t = fmaxf(0.0f, ts - fast_div(Lp, nu));
       for (int it = 0; it < 40; ++it) {
         ++tl.iters;
         const float G = fmaf(nu, t - ts, -x * dcosh_f32(t, ts)) + Lp;
         const float Gp = fmaf(-x, sinh_f32(t), nu);
-        float tn = t - G / Gp;
+        float tn = t - fast_div(G, Gp);
         if (tn < 0.0f) tn = 0.0f;
         const bool done = fabsf(tn - t) <= 1e-5f * fmaxf(tn, 1e-3f);
         t = tn;
@@ -274,20 +278,26 @@ constexpr float kLn2DfLo = -1.904654323148236e-09f;   // ln 2 - kLn2DfHi
 // sqrt(2)), log m = 2 atanh(s), s = (m - 1)/(m + 1) from its series to s^13
 // (truncation < 1e-9 absolute), plus e ln 2 and the first-order lo term.
 __device__ __forceinline__ DF df_log(DF z) {
-  int e;
-  float m = frexpf(z.hi, &e);  // z.hi = m 2^e, m in [0.5, 1)
+  // z.hi = m 2^e with m in [0.5, 1), from the bits (z.hi is a positive normal float)
+  const int bits = __float_as_int(z.hi);
+  int e = ((bits >> 23) & 0xff) - 126;
+  float m = __int_as_float((bits & 0x007fffff) | 0x3f000000);
   if (m < 0.70710678f) {
     m *= 2.0f;
     e -= 1;
   }
-  const float s = (m - 1.0f) / (m + 1.0f), s2 = s * s;
+  // s = (m - 1)/(m + 1) from the MUFU reciprocal and one Newton correction
+  const float rp = mufu_rcp(m + 1.0f);
+  float s = (m - 1.0f) * rp;
+  s = fmaf(fmaf(-s, m + 1.0f, m - 1.0f), rp, s);
+  const float s2 = s * s;
   const float q = fmaf(s2, fmaf(s2, fmaf(s2, fmaf(s2, fmaf(s2, fmaf(s2, 1.0f / 13.0f, 1.0f / 11.0f),
                                                           1.0f / 9.0f), 1.0f / 7.0f), 1.0f / 5.0f),
                                 1.0f / 3.0f), 1.0f);
   const float lm = 2.0f * s * q;
   const float ef = (float)e;
   DF r = quick_two_sum(ef * kLn2HiF, fmaf(ef, kLn2LoF, lm));  // e ln2_hi exact
-  return df_add_f(r, z.lo / z.hi);
+  return df_add_f(r, fast_div(z.lo, z.hi));
 }
 
 // Distance as a double-float from the double-float coordinates: the hi-part
@@ -309,7 +319,7 @@ __device__ __forceinline__ DF df_hypot_diff(float axh, float axl, float ayh, flo
   if (r2.hi == 0.0f && dx.hi == 0.0f && dy.hi == 0.0f && dx.lo == 0.0f && dy.lo == 0.0f)
     return DF{0.0f, 0.0f};
   const float rh = sqrtf(r2.hi);
-  return DF{rh, (fmaf(-rh, rh, r2.hi) + r2.lo) * (0.5f / rh)};
+  return DF{rh, (fmaf(-rh, rh, r2.hi) + r2.lo) * fast_div(0.5f, rh)};
 }
 
 // e^a * s for a double-float a with FP32 accuracy, as a float (the FP32
@@ -508,7 +518,7 @@ __device__ __forceinline__ Job32 job_f32(float x, float nu, float nu_lo, const W
   Job32 jb;
   shift_f32(x, w.ts, q.ts, q.ch, jb.B, jb.D);
   jb.t0 = w.t0;
-  jb.h = (w.t1 - w.t0) / (float)N;
+  jb.h = fast_div(w.t1 - w.t0, (float)N);
   jb.s = q.ts;
   jb.nu = nu;
   jb.nu_lo = nu_lo;
@@ -690,7 +700,7 @@ __device__ __forceinline__ bool learned_window_f32(const LearnedView& lv, float 
   if (F1 > 0.0f) {
     const float Fp = fmaf(-x, sinh_f32(t1), nu);
     if (!(Fp < 0.0f)) return false;
-    t1 -= F1 / Fp;
+    t1 -= fast_div(F1, Fp);
     ++repairs;
   }
   // Left end (only when interior): G = F + ln 2 is concave and increasing on
@@ -700,7 +710,7 @@ __device__ __forceinline__ bool learned_window_f32(const LearnedView& lv, float 
     if (G > 0.0f) {
       const float Gp = fmaf(-x, sinh_f32(t0), nu);
       if (!(Gp > 0.0f)) return false;
-      t0 = fmaxf(0.0f, t0 - G / Gp);
+      t0 = fmaxf(0.0f, t0 - fast_div(G, Gp));
       ++repairs;
     }
   }

@@ -901,8 +901,13 @@ __device__ __forceinline__ int strip_node_count(float x, float nu, float width, 
     bn = kStripA[k];
     bd = d;
   }
-  const float h = 6.28318531f * bn / bd;
-  const float nf = ceilf(width / h);
+  // the step and ceil(width / h) need only a few digits (every strip width
+  // gives a valid bound): MUFU reciprocals instead of IEEE divisions
+  float rb, rh;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rb) : "f"(bd));
+  const float h = 6.28318531f * bn * rb;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rh) : "f"(h));
+  const float nf = ceilf(width * rh);
   if (!(nf <= (float)n_max)) return n_max + 1;
   return nf < 2.0f ? 2 : (int)nf;
 }
