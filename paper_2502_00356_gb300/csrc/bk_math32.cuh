@@ -36,6 +36,13 @@ __device__ __forceinline__ float exp_f32(float a) { return mufu_ex2(a * kLog2ef)
 // Newton steps, first guesses and low-order corrections, where a rounded
 // quotient is not needed (an IEEE division is a ~10-instruction sequence).
 __device__ __forceinline__ float fast_div(float a, float b) { return a * mufu_rcp(b); }
+// sqrt v for v > 0 from the MUFU reciprocal square root (about 2 ulp), where
+// the root is a first guess or is corrected afterwards.
+__device__ __forceinline__ float fast_sqrt_pos(float v) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+  return v * r;
+}
 
 // sinh with small relative error for all |y| <= ~80: the odd Taylor
 // polynomial to y^7 below 0.35 (truncation < 1e-9 relative), (e^y - e^-y)/2
@@ -75,11 +82,11 @@ __device__ __forceinline__ float peak_f32(float x, float nu, Tally& tl) {
   const float nu2 = nu * nu;
   if (!(nu2 > x)) return 0.0f;
   const float q = fast_div(nu, x);
-  float hi = kLn2f * mufu_lg2(q + sqrtf(fmaf(q, q, 1.0f)));
+  float hi = kLn2f * mufu_lg2(q + fast_sqrt_pos(fmaf(q, q, 1.0f)));
   hi = fmaf(hi, 1.0e-4f, hi) + 1.0e-6f;
   float lo = 0.0f;
   const float tc2 = (nu2 - x) / fmaf(nu2 * nu2, 1.0f / 3.0f, x * (1.0f / 6.0f));
-  float t = (tc2 < hi * hi) ? sqrtf(tc2) : hi;
+  float t = (tc2 < hi * hi) ? fast_sqrt_pos(tc2) : hi;
   for (int it = 0; it < 40; ++it) {
     ++tl.peak_iters;
     const float e = mufu_ex2(t * kLog2ef);
@@ -123,7 +130,7 @@ __device__ __forceinline__ Window32 window_f32(float x, float nu, float L, Tally
   const float ss = sinh_f32(ts);
   {
     const float a = x * cs, b = nu - x * ss;
-    float t = ts + fast_div(b + sqrtf(fmaf(b, b, 2.0f * a * L)), a);
+    float t = ts + fast_div(b + fast_sqrt_pos(fmaf(b, b, 2.0f * a * L)), a);
     t = fmaf(t, 1.0e-4f, t);
     float tb = kLn2f * mufu_lg2(fast_div(2.0f * (L + a + nu * t), x));
     tb = fmaf(tb, 1.0e-4f, tb);
@@ -318,7 +325,7 @@ __device__ __forceinline__ DF df_hypot_diff(float axh, float axl, float ayh, flo
   const DF r2 = df_add(px, py);
   if (r2.hi == 0.0f && dx.hi == 0.0f && dy.hi == 0.0f && dx.lo == 0.0f && dy.lo == 0.0f)
     return DF{0.0f, 0.0f};
-  const float rh = sqrtf(r2.hi);
+  const float rh = fast_sqrt_pos(r2.hi);  // its error is in the lo term below
   return DF{rh, (fmaf(-rh, rh, r2.hi) + r2.lo) * fast_div(0.5f, rh)};
 }
 
