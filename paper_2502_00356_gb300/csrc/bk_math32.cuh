@@ -55,21 +55,6 @@ __device__ __forceinline__ float sinh_f32(float y) {
   return ay < 0.35f ? poly : big;
 }
 
-// e^a in FP64 range with FP32 accuracy: a = k ln 2 + r in FP64, e^r on MUFU.
-__device__ __forceinline__ double exp_split(double a) {
-  if (a != a) return a;
-  if (a > 709.782712893384) return __longlong_as_double(0x7ff0000000000000LL);
-  if (a < -745.2) return 0.0;
-  double kd = fma(a, kLog2e, kRoundMagic);
-  const int k = __double2loint(kd);
-  kd -= kRoundMagic;
-  double r = fma(-kd, kLn2Hi, a);
-  r = fma(-kd, kLn2Lo, r);
-  const double er = (double)mufu_ex2((float)r * kLog2ef);
-  const int k1 = k >> 1;
-  return (er * pow2i(k1)) * pow2i(k - k1);
-}
-
 struct Window32 {
   float ts, t0, t1;
   float cs;  // cosh ts (window_f32 only)
@@ -167,23 +152,12 @@ __device__ __forceinline__ Window32 window_f32(float x, float nu, float L, Tally
   return w;
 }
 
-// e^y - 1 with small relative error: Taylor polynomial to y^7 for |y| < 0.35
-// (truncation < 2e-8 relative), e^y - 1 on the MUFU above (no cancellation:
-// |e^y - 1| >= 0.29 there).
-__device__ __forceinline__ float expm1_f32(float y) {
-  const float poly =
-      y * fmaf(y, fmaf(y, fmaf(y, fmaf(y, fmaf(y, fmaf(y, 1.0f / 5040.0f, 1.0f / 720.0f),
-                                                   1.0f / 120.0f), 1.0f / 24.0f), 1.0f / 6.0f),
-                       0.5f), 1.0f);
-  return fabsf(y) < 0.35f ? poly : mufu_ex2(y * kLog2ef) - 1.0f;
-}
-
 // e^y - 1 and e^{-y} - 1 together, both with small relative error:
-// em = e^y - 1 from the Taylor polynomial of expm1 for |y| < 0.35 (as in
-// expm1_f32), else E - 1 with E = e^y on the MUFU (exact for E in [1/2, 2] by
+// em = e^y - 1 from its Taylor polynomial to y^7 for |y| < 0.35 (truncation
+// < 2e-8 relative), else E - 1 with E = e^y on the MUFU (exact for E in [1/2, 2] by
 // Sterbenz, no cancellation beyond a factor ~3 in ulps elsewhere), and
 // e^{-y} - 1 = -em / (1 + em) from one rcp (1 + em reproduces E there).  One
-// polynomial, one ex2 and one rcp instead of two expm1_f32 calls.
+// polynomial, one ex2 and one rcp for both.
 __device__ __forceinline__ void expm1_pm_f32(float y, float& em, float& emn) {
   const float p =
       y * fmaf(y, fmaf(y, fmaf(y, fmaf(y, fmaf(y, fmaf(y, 1.0f / 5040.0f, 1.0f / 720.0f),
@@ -269,10 +243,6 @@ __device__ __forceinline__ DF df_mul_f(DF a, float b) {
   return quick_two_sum(p, fmaf(a.lo, b, e));
 }
 __device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
-__device__ __forceinline__ DF df_from_double(double v) {
-  const float h = (float)v;
-  return DF{h, (float)(v - (double)h)};
-}
 
 // ln 2 as a double-float, and split for range reduction (k ln2_hi exact for
 // |k| < 2^8): ln2_hi has 16 significant bits.

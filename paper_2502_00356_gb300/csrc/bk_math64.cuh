@@ -107,20 +107,6 @@ __device__ __forceinline__ double exp_taylor12(double r) {
   return p;
 }
 
-// Number of FP64 pipe operations in exp_bounded (for work accounting):
-// 1 fma + 1 add (rounding), 2 fma (reduction), 12 fma (polynomial), 1 mul.
-constexpr int kExpOps = 17;
-
-// e^a for a in [-708, 709] (callers clamp): Cody-Waite reduction
-// a = k ln2 + r, |r| <= ln2/2, then 2^k e^r.
-__device__ __forceinline__ double exp_bounded(double a) {
-  double kd = fma(a, kLog2e, kRoundMagic);
-  const int k = __double2loint(kd);
-  kd -= kRoundMagic;
-  double r = fma(-kd, kLn2Hi, a);
-  r = fma(-kd, kLn2Lo, r);
-  return exp_taylor12(r) * pow2i(k);
-}
 
 // e^a over the whole double range (NaN -> NaN, overflow -> inf, deep underflow -> 0).
 __device__ __forceinline__ double exp_full(double a) {
