@@ -60,9 +60,11 @@ __device__ __forceinline__ const Start32* plain_starts(double x, float nu, Start
   return &st;
 }
 
-// Every form carries `tab`, the 2^{j/4096} table of exp2s: the block's
-// shared-memory copy for forms whose hot loop reads it (kStageTable), else
-// the global table (read only on rare FP64 paths).  kTilesPerBlock is the
+// Every form carries `tab`, the 2^{j/4096} table of exp2s.  All forms read
+// the global table through L1, where its 32 KB stay resident: a per-block
+// shared-memory copy (kStageTable, bind_table) cost more than it saved,
+// since a block computes one tile, or one short chunk of pairs (measured:
+// +0.3 % on the FP64 tile writer, +3 % on 10^5 bare evaluations without it).  kTilesPerBlock is the
 // number of 32 x 32 tiles one block of the tile kernels computes, and
 // kMinBlocks the resident 256-thread blocks per SM the tile kernels are
 // compiled for (it caps their registers: 3 -> 85, 4 -> 64).
@@ -70,7 +72,7 @@ __device__ __forceinline__ const Start32* plain_starts(double x, float nu, Start
 // instantiation, so that the default form carries no call site for it).
 template <bool kSeries>
 struct FormF64T {
-  static constexpr bool kStageTable = true;
+  static constexpr bool kStageTable = false;
   static constexpr int kTilesPerBlock = 1;
   static constexpr int kMinBlocks = 3;
   static constexpr bool kFloatEval = false;
@@ -178,7 +180,7 @@ using FormF64Series = FormF64T<true>;   // the plain form with Temme's series be
 // series_below (0.1 in the paper), else the fixed window [0, t1] with `bins`
 // bins (9 and 40 in the paper; Sec. IV-C), no per-point search.
 struct FormF64Fixed {
-  static constexpr bool kStageTable = true;
+  static constexpr bool kStageTable = false;
   static constexpr int kTilesPerBlock = 1;
   static constexpr int kMinBlocks = 3;
   static constexpr bool kFloatEval = false;

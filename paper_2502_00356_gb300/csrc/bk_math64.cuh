@@ -167,8 +167,8 @@ __device__ __forceinline__ double log_pos(double a) {
 // the quadratic 1 + y (1 + c^2/8) + y^2/2: the Taylor quadratic with the
 // cubic term's best linear replacement on [-c, c] (y^3 ~ (3c^2/4) y, the
 // Chebyshev projection), relative error below 2.6e-14.  2^{j/4096} comes from
-// the block's shared-memory copy of kExp2Tab (exp_table_init, 32 KB); 2^k is
-// added to the entry's exponent field.  Valid for u in [-1022 * 4096,
+// kExp2Tab (32 KB, read through L1); 2^k is added to the entry's exponent
+// field.  Valid for u in [-1022 * 4096,
 // 1023 * 4096] (a in [-708, 709]); below that the result is clamped to about
 // 2^-1022, not garbage.
 static __device__ const double kExp2Tab[4096] = {
