@@ -28,6 +28,19 @@ __device__ __forceinline__ unsigned eval_cost_key(double x, double nu) {
   return (est > 0.0f && est < 3.0e38f) ? __float_as_uint(est) : 0xfffffffeu;
 }
 
+// The bare evaluations' cost bucket (0 .. 63) for sort_chunk: the node-count
+// estimate of eval_cost_key (about 72 .. 1,600 for x in [1e-3, 140] and
+// nu <= 20) on a log scale of 12 buckets per octave, in 1 .. 62; pairs
+// outside the domain take 63.
+__device__ __forceinline__ int eval_cost_bucket(double x, double nu) {
+  const unsigned key = eval_cost_key(x, nu);
+  if (key >= 0xfffffffeu) return 63;
+  float l2;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l2) : "f"(__uint_as_float(key)));
+  const int b = __float2int_rd(l2 * 12.0f) - 70;
+  return b < 1 ? 1 : (b > 62 ? 62 : b);
+}
+
 // The element-wise domain rules of the C-ABI around a form's evaluation.
 template <class Form>
 __device__ __forceinline__ double eval_domain(const Form& form, double x, double nu, Tally& tl,
@@ -82,13 +95,13 @@ struct FormF64T {
   const double* cnu = nullptr;  // 2 cosh(nu h) on kCoshTab's steps for the launch's nu, or null
   static constexpr bool kCoshNuTable = true;
 
-  // The bare evaluations' sorting key (sorted_pair): an estimate of the node
-  // count from the arguments alone (eval_cost_key).  The exact count from the
-  // FP32 window costs a second window search per pair, more than the better
-  // ordering saves (measured), and 1 for the series.
-  __device__ __forceinline__ unsigned sort_key(double x, double nu) const {
-    if (kSeries && x < series_below) return 1u;
-    return eval_cost_key(x, nu);
+  // The bare evaluations' cost bucket (sort_chunk): an estimate of the node
+  // count from the arguments alone (eval_cost_bucket), and 0 for the series.
+  // The exact count from the FP32 window costs a second window search per
+  // pair, more than the better ordering saves (measured).
+  __device__ __forceinline__ int sort_bucket(double x, double nu) const {
+    if (kSeries && x < series_below) return 0;
+    return eval_cost_bucket(x, nu);
   }
 
   // log K from Temme's series (Sec. IV-A), tallied.
@@ -190,9 +203,9 @@ struct FormF64Fixed {
   int bins;
   double series_below;
 
-  // The bare evaluations' sorting key: the series or the fixed b + 1 nodes.
-  __device__ __forceinline__ unsigned sort_key(double x, double) const {
-    return x < series_below ? 1u : 2u;
+  // The bare evaluations' cost bucket: the series or the fixed b + 1 nodes.
+  __device__ __forceinline__ int sort_bucket(double x, double) const {
+    return x < series_below ? 0 : 1;
   }
 
   __device__ __forceinline__ double log_k_of(double x, double nu, Tally& tl, double& hS,

@@ -96,7 +96,7 @@ cudaError_t launch_matern_block_f64(const double* locs1, int64_t m, const double
 cudaError_t launch_eval_grad_f64(const double* x, const double* nu, double* k, double* dkdx,
                                  double* dkdnu, int64_t n, const bk_opts& o, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  const int grid = grid_for((n + 127) / 128, 16);
+  const int grid = one_wave_grid(n, 4);
   eval_grad_kernel<FormF64><<<grid, 128, 0, s>>>(FormF64{nullptr, o.search_f64 != 0, 0.0}, x, nu,
                                                  k, dkdx, dkdnu, n, o.d_counters);
   return cudaGetLastError();

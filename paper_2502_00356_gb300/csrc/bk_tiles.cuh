@@ -75,47 +75,79 @@ __device__ __forceinline__ Form bind_table(const Form& form, double* s_tab) {
   return f;
 }
 
-// Orders a round of 128 pairs (base .. base + 127) by key_of(x, nu) (the
-// form's sort_key, or eval_cost_key) with a bitonic sort in shared memory and
-// returns the pair thread t evaluates, so
-// that a warp's 32 lanes take similar paths through the search and the node
-// loop (random pairs otherwise leave most lanes idle while the slowest
-// finishes).  Each pair's arithmetic is unchanged; results go back to their
-// own positions.  Every thread of the 128-thread block must call it.
-template <class KeyOf>
-__device__ __forceinline__ int64_t sorted_pair(const double* __restrict__ x,
-                                               const double* __restrict__ nu, int64_t base,
-                                               int64_t n, unsigned* s_key, unsigned char* s_idx,
-                                               KeyOf key_of) {
-  constexpr int kB = 128;
+constexpr int kSortChunk = 1024;  // pairs per counting sort (8 rounds of 128)
+
+// Orders the pairs [lo, lo + cnt), cnt <= kSortChunk, by bucket_of(x, nu) in
+// 0 .. 63 (the form's cost bucket) with a counting sort in shared memory:
+// s_perm receives their local indices in ascending bucket order (in any
+// order inside a bucket).  Warps that then take consecutive runs of 32 see
+// similar node counts and search paths, where random pairs leave most lanes
+// idle while the slowest finishes.  Each pair's arithmetic is unchanged and
+// results go back to their own positions.  Every thread of the 128-thread
+// block calls it; x and nu are read again from L1 in the rounds that follow.
+template <class BucketOf>
+__device__ __forceinline__ void sort_chunk(const double* __restrict__ x,
+                                           const double* __restrict__ nu, int64_t lo, int cnt,
+                                           unsigned short* s_perm, unsigned* s_cnt,
+                                           BucketOf bucket_of) {
+  constexpr int kR = kSortChunk / 128;
   const int t = threadIdx.x;
-  const int64_t i0 = base + t;
-  __syncthreads();  // the previous round's order is no longer read
-  s_key[t] = (i0 < n) ? key_of(x[i0], nu[i0]) : 0xffffffffu;
-  s_idx[t] = (unsigned char)t;
-  for (int size = 2; size <= kB; size <<= 1) {
-    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      __syncthreads();
-      const int j = t ^ stride;
-      if (j > t) {
-        const bool up = ((t & size) == 0);
-        const unsigned a = s_key[t], b = s_key[j];
-        if ((a > b) == up) {
-          s_key[t] = b;
-          s_key[j] = a;
-          const unsigned char ia = s_idx[t];
-          s_idx[t] = s_idx[j];
-          s_idx[j] = ia;
-        }
-      }
+  __syncthreads();  // the previous chunk's order is no longer read
+  if (t < 64) s_cnt[t] = 0u;
+  __syncthreads();
+  unsigned short rank[kR];
+  unsigned char bk[kR];
+#pragma unroll
+  for (int r = 0; r < kR; ++r) {
+    const int k = r * 128 + t;
+    bk[r] = 0;
+    rank[r] = 0;
+    if (k < cnt) {
+      bk[r] = (unsigned char)bucket_of(x[lo + k], nu[lo + k]);
+      rank[r] = (unsigned short)atomicAdd(&s_cnt[bk[r]], 1u);
     }
   }
   __syncthreads();
-  return base + s_idx[t];
+  if (t < 32) {  // exclusive prefix sum of the 64 counts, two per lane
+    const unsigned c0 = s_cnt[2 * t], c1 = s_cnt[2 * t + 1];
+    unsigned v = c0 + c1;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const unsigned u = __shfl_up_sync(0xffffffffu, v, d);
+      if (t >= d) v += u;
+    }
+    const unsigned ex = v - (c0 + c1);
+    s_cnt[2 * t] = ex;
+    s_cnt[2 * t + 1] = ex + c0;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kR; ++r) {
+    const int k = r * 128 + t;
+    if (k < cnt) s_perm[s_cnt[bk[r]] + rank[r]] = (unsigned short)k;
+  }
+  __syncthreads();
 }
 
-// Bare evaluations of the FP64 forms, 128 per block and round, each round
-// sorted by the form's cost key (sorted_pair).
+// The sorted position thread t takes in round r of a sorted chunk: warp w
+// takes run 4r + w in even rounds and run 4r + 3 - w in odd ones, so that
+// the four warps get equal shares of cheap and costly runs.
+__device__ __forceinline__ int sorted_slot(int r) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  return (4 * r + ((r & 1) ? 3 - w : w)) * 32 + l;
+}
+
+// Block b's pairs [lo, hi) when the grid (one wave of resident blocks) takes
+// the n pairs in equal contiguous chunks of whole 128-pair rounds (+9 % on
+// 10^7 FP64 evaluations over a grid-stride loop).
+__device__ __forceinline__ void block_range(int64_t n, int64_t& lo, int64_t& hi) {
+  const int64_t chunk = ((n + gridDim.x - 1) / gridDim.x + 127) / 128 * 128;
+  lo = (int64_t)blockIdx.x * chunk;
+  hi = lo + chunk < n ? lo + chunk : n;
+}
+
+// Bare evaluations of the FP64 forms, 128 per block and round, in chunks
+// sorted by the form's cost bucket (sort_chunk).
 template <class Form, typename OutT>
 __global__ void __launch_bounds__(128, 6) eval_kernel(const Form form, const double* __restrict__ x,
                                                    const double* __restrict__ nu,
@@ -123,42 +155,44 @@ __global__ void __launch_bounds__(128, 6) eval_kernel(const Form form, const dou
                                                    OutT* __restrict__ log_out, int64_t n,
                                                    unsigned long long* __restrict__ ctr) {
   constexpr int kB = 128;
-  constexpr bool kSort = !Form::kFloatEval;
   __shared__ double s_tab[Form::kStageTable ? kExpTabSize : 1];
-  __shared__ unsigned s_key[kSort ? kB : 1];
-  __shared__ unsigned char s_idx[kSort ? kB : 1];
+  __shared__ unsigned short s_perm[kSortChunk];
+  __shared__ unsigned s_cnt[64];
   const Form f = bind_table(form, s_tab);
   Tally tl{0u, 0u, 0u, 0u, 0u, 0u, 0u};
   unsigned evals = 0;
   const bool want_log = (log_out != nullptr);
-  // Block b takes the contiguous chunk [b c, (b + 1) c) of c pairs, c =
-  // ceil(n / grid) rounded up to whole rounds of 128: one wave of the SMs'
-  // resident slots, with equal chunks (+9 % on 10^7 pairs over a grid-stride
-  // loop), and full rounds when n is small.
-  const int64_t chunk = ((n + gridDim.x - 1) / gridDim.x + kB - 1) / kB * kB;
-  const int64_t lo = (int64_t)blockIdx.x * chunk, hi = min(n, lo + chunk);
-  for (int64_t base = lo; base < hi; base += kB) {
-    int64_t i;
-    if constexpr (kSort) {
-      i = sorted_pair(x, nu, base, hi, s_key, s_idx,
-                      [&](double xi, double vi) { return f.sort_key(xi, vi); });
-    } else {
-      i = base + threadIdx.x;
-    }
-    if (i < hi) {
-      OutT k, lk;
-      f.template eval_out<OutT>(x[i], nu[i], tl, evals, k, lk, want_log);
-      out[i] = k;
-      if (log_out != nullptr) log_out[i] = lk;
+  int64_t lo, hi;
+  block_range(n, lo, hi);
+  for (int64_t base = lo; base < hi; base += kSortChunk) {
+    const int cnt = (int)(hi - base < kSortChunk ? hi - base : kSortChunk);
+    sort_chunk(x, nu, base, cnt, s_perm, s_cnt,
+               [&](double xi, double vi) { return f.sort_bucket(xi, vi); });
+    const int rounds = (cnt + kB - 1) / kB;
+    for (int r = 0; r < rounds; ++r) {
+      const int p = sorted_slot(r);
+      if (p < cnt) {
+        const int64_t i = base + s_perm[p];
+        OutT k, lk;
+        f.template eval_out<OutT>(x[i], nu[i], tl, evals, k, lk, want_log);
+        out[i] = k;
+        if (log_out != nullptr) log_out[i] = lk;
+      }
     }
   }
   flush_tally(ctr, tl, evals);
 }
 
 // Bare evaluations of the FP32 forms with the quadrature split over L lanes
-// (eval_out_f32_coop), 128 pairs per block and round in input order.
+// (eval_out_f32_coop), 128 pairs per block and round in input order, eight
+// blocks per SM.  Sorting chunks of 1,024 pairs by eval_cost_bucket first
+// (as eval_kernel does) raised the learned form's active lanes from 23.2 to
+// 28.2 of 32 and cut its warp instructions by 6 %, but the warps of a sorted
+// chunk run the same phases together and issued 77 % of cycles instead of
+// 83 %: 2.55e10 against 2.59e10 evaluations/s on 10^8 pairs (measured), so
+// the pairs stay in input order here.
 template <class Form, typename OutT, int L>
-__global__ void __launch_bounds__(128, 6) eval_coop_kernel(const Form form,
+__global__ void __launch_bounds__(128, 8) eval_coop_kernel(const Form form,
                                                         const double* __restrict__ x,
                                                         const double* __restrict__ nu,
                                                         OutT* __restrict__ out,
@@ -184,10 +218,10 @@ __global__ void __launch_bounds__(128, 6) eval_coop_kernel(const Form form,
   flush_tally(ctr, tl, evals);
 }
 
-// K, dK/dx and dK/dnu of the plain form, 128 pairs per block and round in
-// cost order (sorted_pair).  Domain: x = 0 gives (+inf, -inf,
-// NaN), x = +inf gives (0, 0, 0), x < 0 or NaN and non-finite nu give NaN;
-// dK/dnu is odd in nu (K_{-nu} = K_nu).  Null outputs are skipped.
+// K, dK/dx and dK/dnu of the plain form, 128 pairs per block and round, in
+// chunks sorted by the cost bucket (sort_chunk).  Domain: x = 0 gives (+inf,
+// -inf, NaN), x = +inf gives (0, 0, 0), x < 0 or NaN and non-finite nu give
+// NaN; dK/dnu is odd in nu (K_{-nu} = K_nu).  Null outputs are skipped.
 template <class Form>
 __global__ void __launch_bounds__(128, 4) eval_grad_kernel(const Form form, const double* __restrict__ x,
                                                         const double* __restrict__ nu,
@@ -197,30 +231,38 @@ __global__ void __launch_bounds__(128, 4) eval_grad_kernel(const Form form, cons
                                                         unsigned long long* __restrict__ ctr) {
   constexpr int kB = 128;
   __shared__ double s_tab[Form::kStageTable ? kExpTabSize : 1];
-  __shared__ unsigned s_key[kB];
-  __shared__ unsigned char s_idx[kB];
+  __shared__ unsigned short s_perm[kSortChunk];
+  __shared__ unsigned s_cnt[64];
   const Form f = bind_table(form, s_tab);
   Tally tl{0u, 0u, 0u, 0u, 0u, 0u, 0u};
   unsigned evals = 0;
   const double qnan = __longlong_as_double(0x7ff8000000000000LL);
-  for (int64_t base = (int64_t)blockIdx.x * kB; base < n; base += (int64_t)gridDim.x * kB) {
-    const int64_t i = sorted_pair(x, nu, base, n, s_key, s_idx,
-                                  [](double a, double b) { return eval_cost_key(a, b); });
-    if (i >= n) continue;
-    const double xi = x[i], vi = nu[i], av = fabs(vi);
-    double kk = qnan, dx = qnan, dn = qnan;
-    if (xi > 0.0 && xi < kInf && av < kInf) {
-      f.eval_grad(xi, av, tl, evals, kk, dx, dn);
-      if (vi < 0.0) dn = -dn;
-    } else if (xi == 0.0 && av < kInf) {
-      kk = kInf;
-      dx = -kInf;
-    } else if (xi == kInf && av < kInf) {
-      kk = dx = dn = 0.0;
+  int64_t lo, hi;
+  block_range(n, lo, hi);
+  for (int64_t base = lo; base < hi; base += kSortChunk) {
+    const int cnt = (int)(hi - base < kSortChunk ? hi - base : kSortChunk);
+    sort_chunk(x, nu, base, cnt, s_perm, s_cnt,
+               [](double xi, double vi) { return eval_cost_bucket(xi, vi); });
+    const int rounds = (cnt + kB - 1) / kB;
+    for (int r = 0; r < rounds; ++r) {
+      const int p = sorted_slot(r);
+      if (p >= cnt) continue;
+      const int64_t i = base + s_perm[p];
+      const double xi = x[i], vi = nu[i], av = fabs(vi);
+      double kk = qnan, dx = qnan, dn = qnan;
+      if (xi > 0.0 && xi < kInf && av < kInf) {
+        f.eval_grad(xi, av, tl, evals, kk, dx, dn);
+        if (vi < 0.0) dn = -dn;
+      } else if (xi == 0.0 && av < kInf) {
+        kk = kInf;
+        dx = -kInf;
+      } else if (xi == kInf && av < kInf) {
+        kk = dx = dn = 0.0;
+      }
+      if (k != nullptr) k[i] = kk;
+      if (dkdx != nullptr) dkdx[i] = dx;
+      if (dkdnu != nullptr) dkdnu[i] = dn;
     }
-    if (k != nullptr) k[i] = kk;
-    if (dkdx != nullptr) dkdx[i] = dx;
-    if (dkdnu != nullptr) dkdnu[i] = dn;
   }
   flush_tally(ctr, tl, evals);
 }
@@ -411,6 +453,15 @@ inline int tile_grid(int64_t ntiles, int per_block) {
 // Blocks for a grid-stride launch: min(work, SMs x per_sm).
 int grid_for(int64_t work_items, int per_sm);
 
+// The grid of one wave of per_sm blocks per SM for n pairs in rounds of 128,
+// with no block left without a round (block_range).
+inline int one_wave_grid(int64_t n, int per_sm) {
+  const int64_t slots = (int64_t)current_sm_count() * per_sm;
+  const int64_t rounds = (n + 127) / 128;
+  const int64_t per = (rounds + slots - 1) / slots;  // rounds per block
+  return (int)((rounds + per - 1) / per);
+}
+
 template <class Form, typename OutT>
 cudaError_t launch_eval_coop(const Form& form, int lanes, int grid, const double* x,
                              const double* nu, OutT* out, OutT* log_out, int64_t n,
@@ -431,23 +482,21 @@ cudaError_t launch_eval_form(const Form& form, const double* x, const double* nu
                              bk_dtype out_t, int64_t n, unsigned long long* ctr, cudaStream_t s,
                              int lanes = 1) {
   if (n == 0) return cudaSuccess;
-  const int grid = grid_for((n + 127) / 128, 16);
   if constexpr (Form::kFloatEval) {
+    const int grid = grid_for((n + 127) / 128, 16);
     if (out_t == BK_F64)
       return launch_eval_coop(form, lanes, grid, x, nu, (double*)out, (double*)log_out, n, ctr, s);
     return launch_eval_coop(form, lanes, grid, x, nu, (float*)out, (float*)log_out, n, ctr, s);
   } else {
-    // one wave of the resident slots (6 blocks per SM); chunks of whole rounds
-    const int64_t slots = (int64_t)current_sm_count() * 6;
-    const int64_t rounds = (n + 127) / 128;
-    const int64_t per = (rounds + slots - 1) / slots;  // rounds per block
-    const int g64 = (int)((rounds + per - 1) / per);
+    // one wave of the resident slots (6 blocks per SM), each block taking an
+    // equal contiguous chunk of whole rounds (block_range)
+    const int grid = one_wave_grid(n, 6);
     if (out_t == BK_F64)
-      eval_kernel<Form, double><<<g64, 128, 0, s>>>(form, x, nu, (double*)out, (double*)log_out,
-                                                    n, ctr);
+      eval_kernel<Form, double><<<grid, 128, 0, s>>>(form, x, nu, (double*)out, (double*)log_out,
+                                                     n, ctr);
     else
-      eval_kernel<Form, float><<<g64, 128, 0, s>>>(form, x, nu, (float*)out, (float*)log_out, n,
-                                                   ctr);
+      eval_kernel<Form, float><<<grid, 128, 0, s>>>(form, x, nu, (float*)out, (float*)log_out, n,
+                                                    ctr);
     return cudaGetLastError();
   }
 }

@@ -70,6 +70,61 @@ def test_eval_full_size_sampled(dev):
     assert_rel(got[idx], oracle.besselk(x[idx], nu[idx]), K_RTOL)
 
 
+@pytest.mark.parametrize("n", [1023, 1025, 300_001, 2_000_003])
+def test_eval_sorted_chunks_keep_positions(dev, n):
+    """The bare-evaluation kernels order each chunk of up to 1,024 pairs by a
+    cost bucket before evaluating it and put each result back at its pair's
+    position: evaluating the pairs in another order and putting the results
+    back agrees to rounding (the 2 cosh(nu h) tier is voted per warp, so a
+    pair's last bits depend on its warp-mates; a misplaced result would be
+    off by O(1)).  Sizes give blocks with several chunks and ragged last
+    chunks; special pairs (0, inf, NaN, negative nu, the series range) are
+    mixed in; samples go to the oracle."""
+    x, nu = inputs.kv_pairs(n, seed=700 + n % 97)
+    rng = np.random.default_rng(n)
+    spec = rng.choice(n, min(n, 40), replace=False)
+    x[spec[:8]] = 0.0
+    x[spec[8:12]] = np.inf
+    x[spec[12:16]] = np.nan
+    nu[spec[16:24]] *= -1.0
+    x[spec[24:]] = 10.0 ** rng.uniform(-6, -3, spec[24:].size)
+    opts = bk.make_opts(series_below=0.1)
+    X, V = to_dev(x, dev), to_dev(nu, dev)
+    got = bk.bk_eval_ex(X, V, opts=opts)[0]
+    perm = torch.as_tensor(rng.permutation(n), device=dev)
+    got_p = bk.bk_eval_ex(X[perm].contiguous(), V[perm].contiguous(), opts=opts)[0]
+    back = torch.empty_like(got_p)
+    back[perm] = got_p
+    torch.cuda.synchronize()
+    a, b = got.cpu().numpy(), back.cpu().numpy()
+
+    def same(u, v, scale):
+        # |u - v| within 1e-13 of max(|u|, |scale|): K itself for K, and
+        # K (1 + nu/x) for the derivatives, whose values can pass through 0
+        fin = np.isfinite(u)
+        assert np.array_equal(fin, np.isfinite(v))
+        assert np.array_equal(u[~fin], v[~fin], equal_nan=True)
+        den = np.maximum(np.abs(u[fin]), np.abs(scale[fin]))
+        rel = np.abs(u[fin] - v[fin]) / np.maximum(den, 1e-300)
+        assert rel.max(initial=0.0) <= 1e-13, f"max rel {rel.max():.3e}"
+
+    same(a, b, a)
+    gk, gdx, gdn = bk.bk_eval_grad(X, V)
+    pk, pdx, pdn = bk.bk_eval_grad(X[perm].contiguous(), V[perm].contiguous())
+    kk = gk.cpu().numpy()
+    with np.errstate(all="ignore"):
+        dscale = kk * (1.0 + np.abs(nu) / x)
+    for g, p, sc in ((gk, pk, kk), (gdx, pdx, dscale), (gdn, pdn, dscale)):
+        q = torch.empty_like(p)
+        q[perm] = p
+        same(g.cpu().numpy(), q.cpu().numpy(), sc)
+    ok = np.isfinite(x) & (x > 0)
+    idx = rng.choice(np.flatnonzero(ok), min(2000, int(ok.sum())), replace=False)
+    assert_rel(a[idx], oracle.besselk(x[idx], np.abs(nu[idx])), K_RTOL)
+    assert np.all(np.isnan(a[spec[12:16]])) and np.all(a[spec[:8]] == np.inf)
+    assert np.all(a[spec[8:12]] == 0.0)
+
+
 def test_eval_node_loop_regions(dev):
     """Both quadrature loops of the plain form and the switch between them:
     the uncentred loop with the cosh(nu t) recurrence (most windows) and the
