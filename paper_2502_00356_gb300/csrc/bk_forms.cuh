@@ -124,9 +124,11 @@ struct FormF64T {
     const Start32* sp = search_f64 ? nullptr : plain_starts(x, f32_trunc(nu), st);
     double hS;
     const double sc = scale_f64(x, nu, kPlainLog2OverTol, kPlainMaxNodes, tab, hS, tl, sp);
-    const double lh = (want_log || sc > 700.0) ? log_tab(hS, tab) : 0.0;
+    if (!want_log && __double_as_longlong(sc) == 0) return hS;  // windows from t = 0
+    const bool big = !bits_le(sc, 700.0);
+    const double lh = (want_log || big) ? log_tab(hS, tab) : 0.0;
     if (want_log) log_k = sc + lh;
-    return (sc > 700.0) ? exp_tab_full(sc + lh, tab) : exp_tab_full(sc, tab) * hS;
+    return big ? exp_tab_full(sc + lh, tab) : exp_tab_full(sc, tab) * hS;
   }
 
   // K, dK/dx and dK/dnu for finite x > 0, nu >= 0 on one set of nodes
@@ -168,7 +170,12 @@ struct FormF64T {
     const Start32* sp = search_f64 ? nullptr : plain_starts(z, mp.nu_hi, st);
     double hS;
     const double sc = scale_f64(z, mp.nu, kPlainLog2OverTol, kPlainMaxNodes, tab, hS, tl, sp, cnu);
-    return exp_tab_full(fma(mp.nu, log_tab(z, tab), mp.log_pref) + sc, tab) * hS;
+    // exp(a1 + nu log z + sc) hS with the exponent formed in the table's
+    // units (K = 4096/ln 2 folded into nu_k and log_pref_k): one FMA, and a
+    // second only for windows that do not start at t = 0 (sc != 0)
+    double u = fma(mp.nu_k, log_tab(z, tab), mp.log_pref_k);
+    if (__double_as_longlong(sc) != 0) u = fma(sc, kExpScale, u);
+    return exp_units_full(u, tab) * hS;
   }
 
   template <typename OutT>

@@ -29,6 +29,7 @@ __device__ __forceinline__ double matern_log_prefactor(double sigma2, double nu)
 // Per-matrix constants of one Matern launch (a1 and the order split).
 struct MaternParams {
   double sigma2, beta, nu, log_pref, inv_beta;
+  double nu_k, log_pref_k;         // nu and a1 times 4096/ln 2 (exp_units_full's units)
   float inv_beta_f, nu_hi, nu_lo;  // nu = nu_hi + nu_lo (two floats)
   float inv_beta_lo;               // 1/beta = inv_beta_f + inv_beta_lo
   float log_pref_hi, log_pref_lo;  // a1 as two floats
@@ -42,6 +43,8 @@ __device__ __forceinline__ MaternParams matern_params(double sigma2, double beta
   p.beta = beta;
   p.nu = nu;
   p.log_pref = matern_log_prefactor(sigma2, nu);
+  p.nu_k = nu * kExpScale;
+  p.log_pref_k = p.log_pref * kExpScale;
   p.inv_beta = 1.0 / beta;
   p.inv_beta_f = (float)p.inv_beta;
   p.nu_hi = (float)nu;
@@ -65,6 +68,8 @@ inline MaternParams matern_params_host(double sigma2, double beta, double nu) {
   p.beta = beta;
   p.nu = nu;
   p.log_pref = (sigma2 > 0.0 ? std::log(sigma2) : -kInf) - (nu - 1.0) * kLn2 - std::lgamma(nu);
+  p.nu_k = nu * kExpScale;
+  p.log_pref_k = p.log_pref * kExpScale;
   p.inv_beta = 1.0 / beta;
   p.inv_beta_f = (float)p.inv_beta;
   p.nu_hi = (float)nu;

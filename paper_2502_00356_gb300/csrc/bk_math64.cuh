@@ -273,6 +273,10 @@ __device__ __forceinline__ double exp2s_node(double u, const double* __restrict_
 // exponent is clamped at -1022 (a result near 2^-1022, not garbage), and a
 // finite D >= 2^22 gives some value below 2^-990 (m is clamped to 2^22).
 // NaN gives NaN.
+// kHalve: T times 1/2 (its exponent lowered by one, on the integer pipe) for
+// the trapezoid's end weights; the node loops keep D below 4.08e6, where the
+// exponent k of T is at least -997, so the result stays normal.
+template <bool kHalve = false>
 __device__ __forceinline__ void exp2s_neg_parts(double D, const double* __restrict__ tab,
                                                 double& p, double& T) {
   const long long b = __double_as_longlong(D);
@@ -299,7 +303,7 @@ __device__ __forceinline__ void exp2s_neg_parts(double D, const double* __restri
   p = fma(fma(kExpK2, rho, -kExpK1), rho, 1.0);
   const int n = -m;
   const double tj = tab[n & (kExpTabSize - 1)];
-  const int k = max(n >> kExpTabBits, -1022);
+  const int k = max(n >> kExpTabBits, -1022) - (kHalve ? 1 : 0);
   T = __hiloint2double(__double2hiint(tj) + (k << 20), __double2loint(tj));
 }
 
@@ -357,6 +361,16 @@ __device__ __forceinline__ double exp_tab_full(double a, const double* __restric
   if (!((__double_as_longlong(a) & 0x7fffffffffffffffLL) < 0x4086200000000000LL))  // |a| < 708
     return exp_full(a);
   return exp2s_cubic(a * kExpScale, tab);
+}
+
+// e^{u / K}, K = 4096 / ln 2, for an exponent the caller formed directly in
+// the table's units (u = a K with the scaling folded into its constants):
+// exp2s_cubic for |u| < 4.18e6 (|a| < 707.4), exp_full of u ln2/4096 beyond
+// (overflow, deep underflow, NaN).  4 FP64 operations on the common path.
+__device__ __forceinline__ double exp_units_full(double u, const double* __restrict__ tab) {
+  if (!((__double_as_longlong(u) & 0x7fffffffffffffffLL) < 0x414fe41000000000LL))  // |u| < 4.18e6
+    return exp_full(u * kExpC1);
+  return exp2s_cubic(u, tab);
 }
 
 // log a for finite a > 0 with the same table: a = 2^e m, m in [1, 2); j =
@@ -756,10 +770,10 @@ __device__ __forceinline__ NodeSumC node_sum_cosh(double t_start, double H, int 
                                                   double nu, const double* __restrict__ tab,
                                                   int cosh_idx, const double* __restrict__ cnu) {
   const double xh = (0.5 * kExpScale) * x;
-  const double th = nu * H;
   const bool start_pos = bits_pos(t_start);
   double c, D0, D1, cn, C0, C1, C0h = 1.0;
   if (start_pos) {
+    const double th = nu * H;
     const double e0 = exp_acc(t_start, tab), r0 = rcp_nr2(e0);
     const double eh = exp_acc(H, tab), rh = rcp_nr2(eh);
     c = bits_le(H, 0.35) ? two_cosh_small(H) : eh + rh;
@@ -773,9 +787,11 @@ __device__ __forceinline__ NodeSumC node_sum_cosh(double t_start, double H, int 
     C1 = fma(W, rn, en);  // e^{nu H} + e^{-2 nu t_start} e^{-nu H}
   } else {
     c = (cosh_idx >= 0) ? kCoshTab[cosh_idx] : two_cosh_warp(H, tab);
-    D0 = 2.0 * xh;
+    // D0 = 2 xh by its exponent (xh is normal: the callers' x lies in the
+    // FP32 search's range and x cosh t1 <= 690)
+    D0 = __hiloint2double(__double2hiint(xh) + (1 << 20), __double2loint(xh));
     D1 = xh * c;
-    cn = (cosh_idx >= 0 && cnu != nullptr) ? cnu[cosh_idx] : two_cosh_warp(th, tab);
+    cn = (cosh_idx >= 0 && cnu != nullptr) ? cnu[cosh_idx] : two_cosh_warp(nu * H, tab);
     C0 = 2.0;
     C1 = cn;
   }
@@ -803,9 +819,9 @@ __device__ __forceinline__ NodeSumC node_sum_cosh(double t_start, double H, int 
     exp2s_neg_parts(D0, tab, p, T);
     s = fma(p, T * C0, s);
   }
-  {  // the last node (D_N, C_N after the loop), weight 1/2; count >= 3
-    exp2s_neg_parts(D1, tab, p, T);
-    const double qh = T * (0.5 * C1);
+  {  // the last node (D_N, C_N after the loop), weight 1/2 folded into T; count >= 3
+    exp2s_neg_parts<true>(D1, tab, p, T);
+    const double qh = T * C1;
     s = fma(p, qh, s);
     float l2p;
     asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l2p) : "f"(f32_trunc(p)));
@@ -968,8 +984,9 @@ __device__ __forceinline__ double take_search(const Scaled64& r, double& hS, Tal
   return r.scale;
 }
 
-// The plain form's K_nu in scaled form: returns the scale and sets h S
-// (K = e^{scale} h S).  With FP32 start values (st) the window is taken from
+// The plain form's K_nu in scaled form: returns the scale and sets hS
+// (K = e^{scale} hS; on the checked windows hS holds the step halved, and
+// the scale is 0 for windows that start at t = 0).  With FP32 start values (st) the window is taken from
 // them (the ends widened as in window_from_start) and checked on the
 // computed end nodes against the rule of window_f64, whose F bounds these
 // from above: e(t1) <= eps and, for t0 > 0, 2 e(t0) <= eps, where e(t) =
@@ -1024,8 +1041,10 @@ __device__ __forceinline__ double scale_f64(double x, double nu, float log2_over
         ok = ok && ns.l2_first - lw0 - G <= -53.0f;
       }
       if (ok) {
-        hS = h * ns.S;
-        return bits_pos(t0) ? fma(nu, t0, -kLn2) : -kLn2;
+        // the 1/2 of the sum's scale e^{nu t0}/2 goes into the step (exact
+        // in FP32), so that the common window (t0 = 0) returns scale 0
+        hS = widen_f(0.5f * hq) * ns.S;
+        return bits_pos(t0) ? nu * t0 : 0.0;
       }
     } else {
       Window64 w;
@@ -1041,8 +1060,8 @@ __device__ __forceinline__ double scale_f64(double x, double nu, float log2_over
       // e_last <= eps, (t0 == 0 or 2 e_first <= eps), 0 < S < 1e300, as integer tests
       if (bits_le(ns.e_last, kEps64) && (!bits_pos(t0) || bits_le(ns.e_first, 0.5 * kEps64)) &&
           bits_pos(ns.S) && bits_le(ns.S, 1e300)) {
-        hS = h * (ns.S - 0.5 * (ns.first + ns.last));
-        return fma(nu, w.ts, -x * w.cs) - kLn2;
+        hS = widen_f(0.5f * hq) * (ns.S - 0.5 * (ns.first + ns.last));
+        return fma(nu, w.ts, -x * w.cs);
       }
     }
   }
