@@ -342,6 +342,18 @@ bk_status bk_learned_destroy(bk_learned* model);
 bk_status bk_learned_train(bk_learned* model, const double* d_x, const double* d_nu,
                            const double* d_labels, int64_t n, int32_t steps, int32_t batch,
                            float lr, uint64_t seed, float* d_loss, bk_stream_t stream);
+/* The kernel of each training step (bk_learned_train, bk_learned_grad).
+   BK_TRAIN_TENSOR (the default): the products of the two 64 x 64 hidden
+   layers in the forward and backward passes and their weight gradients run
+   as tcgen05 MMAs on the tensor cores, TF32 operands (10 significand bits)
+   with FP32 accumulation, from shared memory into tensor memory; the other
+   layers, tanh and the bias gradients on the FP32 pipes.  A step whose wait
+   for its MMAs gives up (a bounded wait) leaves its gradient incomplete and
+   sets an error that the next bk_learned_params(get) returns as BK_ERR_CUDA.
+   BK_TRAIN_SIMT: the whole step in FP32 on the FP32 pipes.  Errors:
+   BK_ERR_INVALID_ARG for another value or a NULL model. */
+enum { BK_TRAIN_TENSOR = 0, BK_TRAIN_SIMT = 1 };
+bk_status bk_learned_set_train_path(bk_learned* model, int path);
 /* Full-batch gradient of the training loss over samples 0 .. n-1 (n a
    multiple of 128) into d_grad[8772] (device), and the loss into *d_loss. */
 bk_status bk_learned_grad(bk_learned* model, const double* d_x, const double* d_nu,

@@ -29,6 +29,7 @@ BK_CTR_FALLBACK, BK_CTR_FAIL, BK_CTR_NODES, BK_CTR_ITERS, BK_CTR_EVALS, BK_CTR_P
 BK_CTR_REPAIR, BK_CTR_SERIES = 6, 7
 BK_NUM_COUNTERS = 8
 BK_HOST_AUTO, BK_HOST_STAGED = 0, 1
+BK_TRAIN_TENSOR, BK_TRAIN_SIMT = 0, 1
 
 #: every symbol include/bk.h declares (checked by the CPU tests)
 EXPORTS = (
@@ -39,7 +40,7 @@ EXPORTS = (
     "bk_batched_plan_info", "bk_batched_autotune", "bk_matern_batched",
     "bk_matern_batched_static", "bk_learned_create", "bk_learned_destroy", "bk_learned_train",
     "bk_learned_grad", "bk_learned_infer", "bk_learned_params", "bk_learned_stats",
-    "bk_learned_set_margins", "bk_learned_save", "bk_learned_load",
+    "bk_learned_set_margins", "bk_learned_set_train_path", "bk_learned_save", "bk_learned_load",
 )
 
 
@@ -116,6 +117,7 @@ def lib() -> ctypes.CDLL:
             "bk_learned_params": (I, [P, P, P]),
             "bk_learned_stats": (I, [P, P, P]),
             "bk_learned_set_margins": (I, [P, ctypes.c_float, ctypes.c_float]),
+            "bk_learned_set_train_path": (I, [P, ctypes.c_int]),
             "bk_learned_save": (I, [P, ctypes.c_char_p]),
             "bk_learned_load": (I, [P, ctypes.c_char_p]),
         }
@@ -669,6 +671,10 @@ class LearnedWindow:
 
     def set_margins(self, rel: float, abs_margin: float):
         _check(lib().bk_learned_set_margins(self.handle, float(rel), float(abs_margin)))
+
+    def set_train_path(self, path: int):
+        """BK_TRAIN_TENSOR (tcgen05 MMAs, the default) or BK_TRAIN_SIMT."""
+        _check(lib().bk_learned_set_train_path(self.handle, int(path)))
 
     def save(self, path: str):
         _check(lib().bk_learned_save(self.handle, path.encode()))

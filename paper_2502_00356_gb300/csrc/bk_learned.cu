@@ -20,6 +20,7 @@
 
 #include "bk_forms.cuh"
 #include "bk_internal.h"
+#include "bk_tc.cuh"
 #include "bk_tiles.cuh"
 
 namespace bk {
@@ -192,6 +193,24 @@ __device__ __forceinline__ void back_tanh(const float* __restrict__ Wt, const fl
   }
 }
 
+// Training sample `pos` of a step: index hash(seed, step, pos) mod n (step ==
+// ~0 selects pos itself: the full-batch gradient), its network inputs
+// u = ((ln x - c) / s, (nu - c) / s) and standardised targets.
+__device__ __forceinline__ void draw_sample(int pos, const double* __restrict__ x,
+                                            const double* __restrict__ nu,
+                                            const double* __restrict__ labels, int64_t n,
+                                            const float* __restrict__ stats, uint64_t seed,
+                                            uint64_t step, float u[2], float tt[4]) {
+  const uint64_t h = mix64(seed ^ mix64(step * 0x9E3779B97F4A7C15ull + (uint64_t)pos));
+  const int64_t i = (step == ~0ull) ? (int64_t)pos : (int64_t)(h % (uint64_t)n);
+  u[0] = ((float)log(x[i]) - kUxC) / kUxS;
+  u[1] = ((float)nu[i] - kUnC) / kUnS;
+  float t[4];
+  label_targets(labels + 6 * i, t);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) tt[k] = (t[k] - stats[k]) / stats[4 + k];
+}
+
 __global__ void __launch_bounds__(kTrainThreads) mlp_train_kernel(
     const float* __restrict__ params, float* __restrict__ grad, const double* __restrict__ x,
     const double* __restrict__ nu, const double* __restrict__ labels, int64_t n,
@@ -201,18 +220,9 @@ __global__ void __launch_bounds__(kTrainThreads) mlp_train_kernel(
   TrainSmem& s = *reinterpret_cast<TrainSmem*>(smem_raw);
   load_params(s, params);
   // samples drawn with replacement: index = hash(seed, step, position) mod n
-  if (threadIdx.x < kChunk) {
-    const int pos = blockIdx.x * kChunk + threadIdx.x;
-    // step == ~0 selects the samples 0 .. batch-1 in order (full-batch gradient)
-    const uint64_t h = mix64(seed ^ mix64(step * 0x9E3779B97F4A7C15ull + (uint64_t)pos));
-    const int64_t i = (step == ~0ull) ? (int64_t)pos : (int64_t)(h % (uint64_t)n);
-    s.U[threadIdx.x][0] = ((float)log(x[i]) - kUxC) / kUxS;
-    s.U[threadIdx.x][1] = ((float)nu[i] - kUnC) / kUnS;
-    float t[4];
-    label_targets(labels + 6 * i, t);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) s.T[threadIdx.x][k] = (t[k] - stats[k]) / stats[4 + k];
-  }
+  if (threadIdx.x < kChunk)
+    draw_sample(blockIdx.x * kChunk + threadIdx.x, x, nu, labels, n, stats, seed, step,
+                s.U[threadIdx.x], s.T[threadIdx.x]);
   __syncthreads();
   // layer 1 (2 inputs)
   {
@@ -284,6 +294,283 @@ __global__ void __launch_bounds__(kTrainThreads) mlp_train_kernel(
     atomicAdd(grad + kOffW1 + e, a);
   }
   grad_b(grad + kOffB1, s.H1);
+}
+
+// ---- the same training step on the tensor cores (tcgen05, kind::tf32).  The
+// four 128 x 64 x 64 products of the hidden layers (H1 W2^T, H2 W3^T, D3 W3,
+// D2 W2) and the two weight gradients D3^T H2 and D2^T H1 (64 x 64 x 128,
+// issued as M = 128 with the upper 64 rows unused) run as MMAs from shared
+// memory into TMEM (256 columns); the 2-input and 4-output layers, tanh and
+// the bias gradients stay on the FP32 pipes.  Operands are FP32 in shared
+// memory, read by the MMA as TF32 (10 significand bits); accumulation is FP32.
+// Thread (w, l) of the 8 warps owns sample r = 32 (w mod 4) + l and features
+// c0 .. c0 + 31, c0 = 32 (w / 4), of every 128 x 64 activation: the TMEM
+// lanes and columns its warp may load.
+constexpr int kTcThreads = 256;
+constexpr int kTcTile = 32768;         // one 128 x 64 or 64 x 128 FP32 operand
+constexpr int kTcMaxTries = 1 << 21;   // bound of each MMA completion wait
+struct TcMisc {
+  float W1[2 * kH], b1[kH], b2[kH], b3[kH], W4[4 * kH], b4[4];
+  float U[kChunk][2], T[kChunk][4], Yp[2][kChunk][4];
+  uint64_t mbar;
+  uint32_t tmem;
+};
+// Shared memory: W (two 64 x 64 B operands) | R0 | R2 | R3 | R4 | R5 | misc.
+// The padded weight-gradient MMAs read up to 1,023 bytes past R5, in misc.
+constexpr size_t kTcSmem = 6 * (size_t)kTcTile + sizeof(TcMisc);
+static_assert(sizeof(TcMisc) >= 1024, "the M = 128 MMAs over R5 read into misc");
+
+// Byte offsets of element (row, k) in the K-major core-matrix layouts (8 rows
+// x 16 bytes per core matrix, rows 16 bytes apart): 128 rows x 64 K (chunks
+// of 4 along K 2,048 bytes apart), and 64 rows x any K (1,024 bytes apart).
+__device__ __forceinline__ int off128(int r, int k) { return (k >> 2) * 2048 + r * 16 + (k & 3) * 4; }
+__device__ __forceinline__ int off64(int r, int k) { return (k >> 2) * 1024 + r * 16 + (k & 3) * 4; }
+
+// This thread's 32 values (sample r, features c0 ..) into a 128 x 64 operand
+// (eight 16-byte stores), into the transposed 64 x 128 operand (rows are
+// features, K the samples), and back from a 128 x 64 operand.
+__device__ __forceinline__ void put128(unsigned char* tile, int r, int c0, const float (&v)[32]) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    *reinterpret_cast<float4*>(tile + off128(r, c0 + 4 * q)) =
+        make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+}
+__device__ __forceinline__ void put64t(unsigned char* tile, int r, int c0, const float (&v)[32]) {
+#pragma unroll
+  for (int j = 0; j < 32; ++j) *reinterpret_cast<float*>(tile + off64(c0 + j, r)) = v[j];
+}
+__device__ __forceinline__ void get128(const unsigned char* tile, int r, int c0, float (&v)[32]) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const float4 a = *reinterpret_cast<const float4*>(tile + off128(r, c0 + 4 * q));
+    v[4 * q] = a.x;
+    v[4 * q + 1] = a.y;
+    v[4 * q + 2] = a.z;
+    v[4 * q + 3] = a.w;
+  }
+}
+
+// The sum over the warp's lanes of each of v[0 .. 31]; lane l returns that of
+// v[l] (recursive halving, 31 shuffles).  Overwrites v.
+__device__ __forceinline__ float warp_colsum(float (&v)[32]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < o; ++i) {
+      const float send = up ? v[i] : v[i + o];
+      const float keep = up ? v[i + o] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return v[0];
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) mlp_train_tc_kernel(
+    const float* __restrict__ params, float* __restrict__ grad, const double* __restrict__ x,
+    const double* __restrict__ nu, const double* __restrict__ labels, int64_t n,
+    const float* __restrict__ stats, int batch, uint64_t seed, uint64_t step,
+    float* __restrict__ loss, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* const W = smem_raw;       // W2 | W3, then W3^T | W2^T (B operands)
+  unsigned char* const R0 = W + kTcTile;   // H1 (128 x 64)
+  unsigned char* const R2 = R0 + kTcTile;  // H2 (128 x 64)
+  unsigned char* const R3 = R2 + kTcTile;  // H2^T, then H1^T (64 x 128)
+  unsigned char* const R4 = R3 + kTcTile;  // D3, then D2 (128 x 64)
+  unsigned char* const R5 = R4 + kTcTile;  // D3^T, then D2^T (64 x 128)
+  TcMisc& s = *reinterpret_cast<TcMisc*>(R5 + kTcTile);
+  const int t = threadIdx.x, w = t >> 5, l = t & 31;
+  const int r = 32 * (w & 3) + l, c0 = 32 * (w >> 2);
+  const uint32_t lanes = (uint32_t)(32 * (w & 3)) << 16;  // this warp's TMEM lanes
+  constexpr uint32_t kIdesc = tc::idesc_tf32(kChunk, kH);
+
+  // W2 and W3 as B operands: row j (output), K = k (input)
+  for (int i = t; i < kH * kH; i += kTcThreads) {
+    const int j = i / kH, k = i % kH;
+    *reinterpret_cast<float*>(W + off64(j, k)) = params[kOffW2 + i];
+    *reinterpret_cast<float*>(W + kTcTile / 2 + off64(j, k)) = params[kOffW3 + i];
+  }
+  for (int i = t; i < 2 * kH; i += kTcThreads) s.W1[i] = params[kOffW1 + i];  // W1[f][i] at 2 f + i
+  for (int i = t; i < 4 * kH; i += kTcThreads) s.W4[i] = params[kOffW4 + i];  // W4[o][f] at 64 o + f
+  if (t < kH) {
+    s.b1[t] = params[kOffB1 + t];
+    s.b2[t] = params[kOffB2 + t];
+    s.b3[t] = params[kOffB3 + t];
+  }
+  if (t < 4) s.b4[t] = params[kOffB4 + t];
+  if (t < kChunk)
+    draw_sample(blockIdx.x * kChunk + t, x, nu, labels, n, stats, seed, step, s.U[t], s.T[t]);
+  if (t == 0) tc::mbar_init(&s.mbar, 1);
+  if (w == 0) tc::tmem_alloc(&s.tmem, 256);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tm = s.tmem;
+
+  // D(TMEM columns dcol ..) = A B^T over `slices` K slices of 8: A of 128
+  // rows (lbo 2,048) or 64 rows read as 128 (lbo 1,024), B of 64 rows.
+  auto gemm = [&](uint32_t dcol, const unsigned char* a, uint32_t a_lbo, const unsigned char* b,
+                  int slices) {
+    const uint32_t a0 = tc::smem_addr(a), b0 = tc::smem_addr(b);
+    for (int q = 0; q < slices; ++q)
+      tc::mma_tf32(tm + dcol, tc::desc_kmajor(a0 + 2u * q * a_lbo, a_lbo, 128),
+                   tc::desc_kmajor(b0 + 2048u * q, 1024, 128), kIdesc, q > 0);
+  };
+  // Publishes the shared-memory operands, has thread 0 issue the MMAs and
+  // commit them, and waits for them (bounded); false, for the whole CTA,
+  // when some thread's wait gave up.
+  uint32_t phase = 0;
+  auto run = [&](auto issue) {
+    tc::fence_proxy_async();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (t == 0) {
+      issue();
+      tc::commit(&s.mbar);
+    }
+    const bool done = tc::mbar_wait(&s.mbar, phase, kTcMaxTries);
+    phase ^= 1u;
+    tc::fence_after();
+    return __syncthreads_or(!done) == 0;
+  };
+
+  float v[32], q[32];
+  // layer 1 (2 inputs) on the FP32 pipes: H1
+  {
+    const float u0 = s.U[r][0], u1 = s.U[r][1];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int f = c0 + j;
+      v[j] = tanhf(fmaf(s.W1[2 * f], u0, fmaf(s.W1[2 * f + 1], u1, s.b1[f])));
+    }
+    put128(R0, r, c0, v);
+  }
+  bool ok = run([&] { gemm(0, R0, 2048, W, 8); });  // H1 W2^T
+  if (ok) {
+    tc::ld32(tm + lanes + c0, v);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = tanhf(v[j] + s.b2[c0 + j]);
+    put128(R2, r, c0, v);
+    put64t(R3, r, c0, v);
+    ok = run([&] { gemm(64, R2, 2048, W + kTcTile / 2, 8); });  // H2 W3^T
+  }
+  if (ok) {
+    tc::ld32(tm + lanes + 64 + c0, v);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = tanhf(v[j] + s.b3[c0 + j]);  // H3, kept in registers
+    // the W tiles become W3^T | W2^T (row k, K = j) for the backward products
+    for (int i = t; i < kH * kH; i += kTcThreads) {
+      const int j = i / kH, k = i % kH;
+      *reinterpret_cast<float*>(W + off64(k, j)) = params[kOffW3 + i];
+      *reinterpret_cast<float*>(W + kTcTile / 2 + off64(k, j)) = params[kOffW2 + i];
+    }
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {  // this thread's half of the output layer
+      float a = 0.0f;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) a = fmaf(s.W4[kH * o + c0 + j], v[j], a);
+      s.Yp[w >> 2][r][o] = a;
+    }
+  }
+  __syncthreads();
+  if (ok) {
+    // dL/dy for L = mean over the batch and the 4 outputs of (y - t)^2
+    float dy[4], lsum = 0.0f;
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+      const float e = s.b4[o] + s.Yp[0][r][o] + s.Yp[1][r][o] - s.T[r][o];
+      dy[o] = 2.0f * e / (float)(batch * 4);
+      lsum += e * e;
+    }
+    if (c0 == 0) {  // one of the two warps of each sample range: loss and db4
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+      if (l == 0 && loss != nullptr) atomicAdd(loss, lsum / (float)(batch * 4));
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        float a = dy[o];
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) a += __shfl_xor_sync(0xffffffffu, a, d);
+        if (l == 0) atomicAdd(grad + kOffB4 + o, a);
+      }
+    }
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {  // dW4[o][f] = sum_s dy[s][o] H3[s][f]
+#pragma unroll
+      for (int j = 0; j < 32; ++j) q[j] = dy[o] * v[j];
+      atomicAdd(grad + kOffW4 + kH * o + c0 + l, warp_colsum(q));
+    }
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {  // D3 = (dy W4) (1 - H3^2)
+      const int f = c0 + j;
+      float a = 0.0f;
+#pragma unroll
+      for (int o = 0; o < 4; ++o) a = fmaf(dy[o], s.W4[kH * o + f], a);
+      v[j] = a * (1.0f - v[j] * v[j]);
+    }
+    put128(R4, r, c0, v);
+    put64t(R5, r, c0, v);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) q[j] = v[j];
+    atomicAdd(grad + kOffB3 + c0 + l, warp_colsum(q));
+    ok = run([&] {
+      gemm(128, R4, 2048, W, 8);   // D3 W3 (B = W3^T)
+      gemm(192, R5, 1024, R3, 16); // D3^T H2: dW3 in TMEM lanes 0 .. 63
+    });
+  }
+  if (ok) {
+    if ((w & 3) < 2) {  // dW3[j][k], j = r < 64
+      tc::ld32(tm + lanes + 192 + c0, v);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) atomicAdd(grad + kOffW3 + kH * r + c0 + j, v[j]);
+    }
+    tc::ld32(tm + lanes + 128 + c0, v);
+    get128(R2, r, c0, q);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] *= 1.0f - q[j] * q[j];  // D2 = (D3 W3)(1 - H2^2)
+    get128(R0, r, c0, q);
+    put64t(R3, r, c0, q);  // H1^T (the MMAs have read H2^T and D3)
+    put128(R4, r, c0, v);
+    put64t(R5, r, c0, v);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) q[j] = v[j];
+    atomicAdd(grad + kOffB2 + c0 + l, warp_colsum(q));
+    ok = run([&] {
+      gemm(64, R4, 2048, W + kTcTile / 2, 8);  // D2 W2 (B = W2^T)
+      gemm(0, R5, 1024, R3, 16);               // D2^T H1: dW2 in TMEM lanes 0 .. 63
+    });
+  }
+  if (ok) {
+    if ((w & 3) < 2) {  // dW2[j][k]
+      tc::ld32(tm + lanes + c0, v);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) atomicAdd(grad + kOffW2 + kH * r + c0 + j, v[j]);
+    }
+    tc::ld32(tm + lanes + 64 + c0, v);
+    get128(R0, r, c0, q);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] *= 1.0f - q[j] * q[j];  // D1 = (D2 W2)(1 - H1^2)
+#pragma unroll
+    for (int j = 0; j < 32; ++j) q[j] = v[j];
+    atomicAdd(grad + kOffB1 + c0 + l, warp_colsum(q));
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {  // dW1[f][i] = sum_s D1[s][f] u[s][i]
+      const float ui = s.U[r][i];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) q[j] = v[j] * ui;
+      atomicAdd(grad + kOffW1 + 2 * (c0 + l) + i, warp_colsum(q));
+    }
+  } else {
+    // a completion wait gave up: wait once more (bounded) for MMAs still in
+    // flight, then report it; the gradient of this step is incomplete
+    tc::mbar_wait(&s.mbar, phase ^ 1u, kTcMaxTries);
+    if (t == 0 && err != nullptr) atomicExch(err, 1);
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (w == 0) tc::tmem_dealloc(tm, 256);
 }
 
 // Adam (Kingma & Ba 2015) with bias correction; zeroes the gradient.
@@ -369,6 +656,9 @@ cudaError_t set_train_smem() {
   if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
   e = cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)sizeof(TrainSmem));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(mlp_train_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kTcSmem);
   if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
   return e;
 }
@@ -378,6 +668,8 @@ cudaError_t set_train_smem() {
 // ---------------------------------------------------------------------------
 struct bk_learned {
   int device;
+  int train_path;   // BK_TRAIN_TENSOR or BK_TRAIN_SIMT
+  int* d_err;       // set by a tensor-core step whose MMA wait gave up
   float* d_params;
   float* d_grad;
   float* d_m;
@@ -403,6 +695,22 @@ uint64_t fnv1a(const unsigned char* d, size_t n, uint64_t h = 146959810393466560
   }
   return h;
 }
+
+}  // namespace
+
+// One training step's gradient kernel on the model's path (batch / 128 CTAs).
+void launch_train_step(const bk_learned* m, float* grad, const double* x, const double* nu,
+                       const double* labels, int64_t n, int batch, uint64_t seed, uint64_t step,
+                       float* loss, cudaStream_t s) {
+  if (m->train_path == BK_TRAIN_SIMT)
+    mlp_train_kernel<<<batch / kChunk, kTrainThreads, sizeof(TrainSmem), s>>>(
+        m->d_params, grad, x, nu, labels, n, m->d_stats, batch, seed, step, loss);
+  else
+    mlp_train_tc_kernel<<<batch / kChunk, kTcThreads, kTcSmem, s>>>(
+        m->d_params, grad, x, nu, labels, n, m->d_stats, batch, seed, step, loss, m->d_err);
+}
+
+namespace {
 
 cudaError_t build_table(bk_learned* m, cudaStream_t s) {
   const int n = kTabX * kTabNu;
@@ -468,6 +776,8 @@ bk_status bk_learned_create(bk_learned** model, uint64_t seed) {
   if (e == cudaSuccess) e = cudaMalloc((void**)&m->d_stats, 8 * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc((void**)&m->d_acc, 8 * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc((void**)&m->d_table, (size_t)kTabX * kTabNu * sizeof(float4));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&m->d_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(m->d_err, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(m->d_grad, 0, pb);
   if (e == cudaSuccess) e = cudaMemset(m->d_m, 0, pb);
   if (e == cudaSuccess) e = cudaMemset(m->d_v, 0, pb);
@@ -493,6 +803,7 @@ bk_status bk_learned_destroy(bk_learned* m) {
   cudaFree(m->d_stats);
   cudaFree(m->d_acc);
   cudaFree(m->d_table);
+  cudaFree(m->d_err);
   delete m;
   return BK_OK;
 }
@@ -521,9 +832,8 @@ bk_status bk_learned_train(bk_learned* m, const double* d_x, const double* d_nu,
   for (int32_t k = 0; k < steps; ++k) {
     // cosine decay from lr to 0.05 lr over this call's steps
     const float lrk = lr * (0.05f + 0.95f * 0.5f * (1.0f + cosf(3.14159265f * k / fmaxf(1.0f, (float)steps))));
-    mlp_train_kernel<<<batch / kChunk, kTrainThreads, sizeof(TrainSmem), s>>>(
-        m->d_params, m->d_grad, d_x, d_nu, d_labels, n, m->d_stats, batch, seed, (uint64_t)m->step,
-        d_loss != nullptr ? d_loss + k : nullptr);
+    launch_train_step(m, m->d_grad, d_x, d_nu, d_labels, n, batch, seed, (uint64_t)m->step,
+                      d_loss != nullptr ? d_loss + k : nullptr, s);
     m->step += 1;
     const float c1 = 1.0f - powf(b1, (float)m->step), c2 = 1.0f - powf(b2, (float)m->step);
     adam_kernel<<<(kNParams + 255) / 256, 256, 0, s>>>(m->d_params, m->d_grad, m->d_m, m->d_v, lrk,
@@ -546,8 +856,7 @@ bk_status bk_learned_grad(bk_learned* m, const double* d_x, const double* d_nu,
   cudaError_t e = set_train_smem();
   if (e != cudaSuccess) return check_cuda(e, "bk_learned_grad");
   cudaMemsetAsync(d_grad_out, 0, kNParams * sizeof(float), s);
-  mlp_train_kernel<<<(int)(n / kChunk), kTrainThreads, sizeof(TrainSmem), s>>>(
-      m->d_params, d_grad_out, d_x, d_nu, d_labels, n, m->d_stats, (int)n, 0, ~0ull, d_loss);
+  launch_train_step(m, d_grad_out, d_x, d_nu, d_labels, n, (int)n, 0, ~0ull, d_loss, s);
   return check_cuda(cudaGetLastError(), "bk_learned_grad");
 }
 
@@ -564,10 +873,29 @@ bk_status bk_learned_infer(const bk_learned* m, const double* d_x, const double*
   return check_cuda(cudaGetLastError(), "bk_learned_infer");
 }
 
+bk_status bk_learned_set_train_path(bk_learned* m, int path) {
+  if (m == nullptr || (path != BK_TRAIN_TENSOR && path != BK_TRAIN_SIMT))
+    return set_error(BK_ERR_INVALID_ARG,
+                     "bk_learned_set_train_path: need a model and BK_TRAIN_TENSOR or BK_TRAIN_SIMT");
+  m->train_path = path;
+  return BK_OK;
+}
+
 bk_status bk_learned_params(bk_learned* m, float* h_get, const float* h_set) {
   if (m == nullptr) return set_error(BK_ERR_INVALID_ARG, "model is NULL");
   cudaError_t e = cudaSuccess;
-  if (h_get != nullptr) e = cudaMemcpy(h_get, m->d_params, kNParams * sizeof(float), cudaMemcpyDeviceToHost);
+  if (h_get != nullptr) {
+    int failed = 0;
+    e = cudaMemcpy(&failed, m->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && failed) {
+      cudaMemset(m->d_err, 0, sizeof(int));
+      return set_error(BK_ERR_CUDA,
+                       "bk_learned_params: a tensor-core training step gave up waiting for its "
+                       "MMAs; its gradient was incomplete");
+    }
+  }
+  if (e == cudaSuccess && h_get != nullptr)
+    e = cudaMemcpy(h_get, m->d_params, kNParams * sizeof(float), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && h_set != nullptr) {
     e = cudaMemcpy(m->d_params, h_set, kNParams * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && m->has_stats) e = build_table(m, nullptr);

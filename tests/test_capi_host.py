@@ -61,6 +61,9 @@ def test_host_side_argument_checks(L):
     assert L.bk_matern_tile(None, 4, 1.0, 0.1, 0.5, fake, 4, 0, None) == bk.BK_ERR_INVALID_ARG
     assert L.bk_matern_tile2(fake, 4, fake, 3, 1.0, 0.1, 0.5, fake, 2, 0, None, None) == bk.BK_ERR_INVALID_ARG
     assert L.bk_matern_tile(None, 0, 1.0, 0.1, 0.5, None, 0, 0, None) == bk.BK_OK
+    # training path of a window network: a model is required (none is created here)
+    assert L.bk_learned_set_train_path(None, bk.BK_TRAIN_TENSOR) == bk.BK_ERR_INVALID_ARG
+    assert L.bk_learned_set_train_path(None, bk.BK_TRAIN_SIMT) == bk.BK_ERR_INVALID_ARG
     assert b"ld" in L.bk_last_error() or len(L.bk_last_error()) > 0
 
 

@@ -52,9 +52,18 @@ def trained(dev):
     return m
 
 
-def test_gradient_matches_fp64_reference(dev, small_labels):
+# Tolerances of the two training kernels: the FP32 SIMT step (relative loss
+# 1e-5, gradient 2e-4 of its largest component) and the tensor-core step,
+# whose hidden-layer products read TF32 operands (10 significand bits,
+# relative rounding up to 2^-10 per operand): 5e-3 and 1e-2.
+TRAIN_TOL = {bk.BK_TRAIN_SIMT: (1e-5, 2e-4), bk.BK_TRAIN_TENSOR: (5e-3, 1e-2)}
+
+
+@pytest.mark.parametrize("path", [bk.BK_TRAIN_SIMT, bk.BK_TRAIN_TENSOR])
+def test_gradient_matches_fp64_reference(dev, small_labels, path):
     x, nu, lab = small_labels
     m = bk.LearnedWindow(seed=3)
+    m.set_train_path(path)
     X, V, Lb = to_dev(x, dev), to_dev(nu, dev), to_dev(lab, dev)
     m.train(X, V, Lb, steps=0)  # computes the target statistics only
     stats = m.stats()
@@ -66,21 +75,47 @@ def test_gradient_matches_fp64_reference(dev, small_labels):
     T = (mlp.targets_from_labels(lab[:n]) - stats[:4]) / stats[4:]
     ref_loss, ref_g = mlp.loss_and_grad(p, U, T)
     got = g.cpu().numpy().astype(np.float64)
-    assert abs(float(loss) - ref_loss) <= 1e-5 * ref_loss + 1e-7
+    ltol, gtol = TRAIN_TOL[path]
+    assert abs(float(loss) - ref_loss) <= ltol * ref_loss + 1e-7
     scale = np.abs(ref_g).max()
-    assert np.abs(got - ref_g).max() <= 2e-4 * scale
+    assert np.abs(got - ref_g).max() <= gtol * scale
+    # every parameter block (W1, b1, ..., b4) carries its gradient
+    for a, b in ((0, 128), (128, 192), (192, 4288), (4288, 4352), (4352, 8448), (8448, 8512),
+                 (8512, 8768), (8768, 8772)):
+        blk = np.abs(ref_g[a:b]).max()
+        assert np.abs(got[a:b] - ref_g[a:b]).max() <= 5 * gtol * blk + gtol * scale, (a, b)
     # and against central finite differences of the FP64 forward pass
     rng = np.random.default_rng(5)
     for i in rng.choice(mlp.N_PARAMS, 25, replace=False):
         e = np.zeros_like(p)
         e[i] = 1e-6
         fd = (mlp.loss_only(p + e, U, T) - mlp.loss_only(p - e, U, T)) / 2e-6
-        assert abs(fd - got[i]) <= 2e-4 * scale
+        assert abs(fd - got[i]) <= gtol * scale
+    assert m.params() is not None  # no tensor-core step gave up (BK_ERR_CUDA otherwise)
 
 
-def test_training_reduces_loss(dev, small_labels):
+def test_tensor_core_and_simt_steps_agree(dev, small_labels):
+    """The two training kernels on the same 1,024 samples: gradients within
+    the TF32 tolerance of each other, and one Adam step apart by little."""
+    x, nu, lab = small_labels
+    X, V, Lb = to_dev(x, dev), to_dev(nu, dev), to_dev(lab, dev)
+    grads = {}
+    for path in (bk.BK_TRAIN_SIMT, bk.BK_TRAIN_TENSOR):
+        m = bk.LearnedWindow(seed=6)
+        m.set_train_path(path)
+        m.train(X, V, Lb, steps=0)
+        grads[path] = m.grad(X[:1024], V[:1024], Lb[:1024])[0].cpu().numpy().astype(np.float64)
+    a, b = grads[bk.BK_TRAIN_SIMT], grads[bk.BK_TRAIN_TENSOR]
+    assert np.abs(a - b).max() <= 1e-2 * np.abs(a).max()
+    with pytest.raises(bk.BkError):
+        bk.LearnedWindow(seed=1).set_train_path(7)
+
+
+@pytest.mark.parametrize("path", [bk.BK_TRAIN_SIMT, bk.BK_TRAIN_TENSOR])
+def test_training_reduces_loss(dev, small_labels, path):
     x, nu, lab = small_labels
     m = bk.LearnedWindow(seed=4)
+    m.set_train_path(path)
     loss = torch.zeros(400, dtype=torch.float32, device=dev)
     m.train(to_dev(x, dev), to_dev(nu, dev), to_dev(lab, dev), steps=400, batch=1024, lr=3e-3,
             loss=loss)
