@@ -44,11 +44,12 @@ WORKLOAD = "matern_jittered_grid_n20000_beta0.1_nu{0.5,1.5,2.3}_fp64"
 # or outside the FP32 search region), and a fixed part per Matern entry
 # (distance, square root, set-ups, end terms, log x and the final
 # exponential).  The fixed part is ncu's executed DFMA + DADD + DMUL per
-# entry minus 6 x nodes per entry on the n = 6000 case of the same kernel
-# (28.5, 28.6, 28.6 for nu = 0.5, 1.5, 2.3; the mean).  The FP32 Newton iterations
+# evaluation minus 6 x nodes per evaluation on the n = 6000 case of the same
+# kernel (--profile-case plain_nus: 24.89 for each of nu = 0.5, 1.5, 2.3).
+# The FP32 Newton iterations
 # that place the window and the FP32 window check run on the FP32/MUFU pipes
 # and are not counted.
-OPS_NODE, OPS_PEAK_IT, OPS_WIN_IT, OPS_ENTRY_FIXED = 6, 54, 31, 28.6
+OPS_NODE, OPS_PEAK_IT, OPS_WIN_IT, OPS_ENTRY_FIXED = 6, 54, 31, 24.9
 # Kernels per bk_matern_tile call of the plain form: the per-launch table of
 # 2 cosh(nu h) on the quantised steps, then the symmetric tile writer.
 LAUNCHES_PER_MATRIX = 2
@@ -74,8 +75,8 @@ def parse():
                    help="skip the FP32, batched and learned-window measurements")
     p.add_argument("--pairs", type=int, default=100_000_000,
                    help="K_nu pairs of the learned-window evaluation workload")
-    p.add_argument("--profile-case", choices=["plain", "fp32", "learned", "learned_eval", "batched",
-                                              "fp32_forms"],
+    p.add_argument("--profile-case", choices=["plain", "plain_nus", "fp32", "learned", "learned_eval",
+                                              "batched", "fp32_forms", "train"],
                    default=None,
                    help="run --warmup launches plus one launch of one kernel on a small case "
                         "(for profiler captures) and exit without a JSON line")
@@ -664,6 +665,10 @@ def profile_case(args):
     c = args.profile_case
     if c == "fp32_forms":
         return profile_fp32_forms(args, bk, inputs, dev)
+    if c == "plain_nus":
+        return profile_plain_nus(bk, inputs, dev)
+    if c == "train":
+        return profile_train(args, bk, dev)
     net = None
     if c in ("learned", "learned_eval", "batched"):
         net = bk.LearnedWindow(path=os.path.join(ROOT, "paper_2502_00356_gb300", "weights",
@@ -692,6 +697,56 @@ def profile_case(args):
     for _ in range(args.warmup + 1):
         run()
     torch.cuda.synchronize()
+
+
+def profile_plain_nus(bk, inputs, dev):
+    """The plain FP64 tile writer on the n = 6,000 case for nu = 0.5, 1.5 and
+    2.3: one launch each with the counters (nodes per entry, printed as one
+    JSON line), then one launch each without them, the three launches an FP64
+    instruction-count capture takes (-k regex:matern_sym -s 3 -c 3)."""
+    import torch
+    n = 6000
+    L = torch.as_tensor(inputs.morton_sorted(inputs.jittered_grid(n, seed=4)), device=dev)
+    out = torch.empty((n, n), dtype=torch.float64, device=dev)
+    res = {}
+    for nu in NUS:
+        c = torch.zeros(bk.BK_NUM_COUNTERS, dtype=torch.int64, device=dev)
+        bk.bk_matern_tile(L, 1.0, BETA, nu, out=out, opts=bk.make_opts(counters=c))
+        c = c.cpu().numpy()
+        res[str(nu)] = {"entries": n * n, "evals": int(c[bk.BK_CTR_EVALS]),
+                        "nodes_per_eval": float(c[bk.BK_CTR_NODES]) / max(1, int(c[bk.BK_CTR_EVALS])),
+                        "fallback": int(c[bk.BK_CTR_FALLBACK])}
+    for nu in NUS:
+        bk.bk_matern_tile(L, 1.0, BETA, nu, out=out)
+    torch.cuda.synchronize()
+    print(json.dumps(res))
+
+
+def profile_train(args, bk, dev):
+    """Window-network training steps of batch 8,192 on synthetic labelled
+    points (2^20): --warmup + 1 steps of the tensor-core step kernel
+    (mlp_train_tc_kernel), then as many of the FP32 SIMT one; the mean time
+    per step of each over 200 more is printed as one JSON line."""
+    import numpy as np
+    import torch
+    rng = np.random.default_rng(1)
+    n = 1 << 20
+    x = np.exp(rng.uniform(math.log(1e-3), math.log(140.0), n))
+    nu = rng.uniform(0.05, 20.0, n)
+    ts = rng.uniform(0.0, 8.0, n)
+    lab = np.stack([ts, np.maximum(ts - rng.uniform(0.5, 4.0, n), 0.0), ts + rng.uniform(0.5, 4.0, n),
+                    -x, rng.uniform(5.0, 40.0, n), np.zeros(n)], axis=1)
+    X, V, Lb = (torch.as_tensor(np.ascontiguousarray(a), device=dev) for a in (x, nu, lab))
+    res = {}
+    for path, name in ((bk.BK_TRAIN_TENSOR, "tensor"), (bk.BK_TRAIN_SIMT, "simt")):
+        net = bk.LearnedWindow(seed=1)
+        net.set_train_path(path)
+        net.train(X, V, Lb, steps=args.warmup + 1, batch=8192)
+        torch.cuda.synchronize()
+        res[name + "_us_per_step"] = round(1e6 * _time(
+            lambda: net.train(X, V, Lb, steps=200, batch=8192), torch.cuda.current_stream()) / 200, 2)
+        net.params()  # raises if a tensor-core step gave up waiting
+    print(json.dumps(res))
 
 
 def profile_fp32_forms(args, bk, inputs, dev):
