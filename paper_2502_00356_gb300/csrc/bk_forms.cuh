@@ -124,7 +124,7 @@ struct FormF64T {
     const Start32* sp = search_f64 ? nullptr : plain_starts(x, f32_trunc(nu), st);
     double hS;
     const double sc = scale_f64(x, nu, kPlainLog2OverTol, kPlainMaxNodes, tab, hS, tl, sp);
-    if (!want_log && __double_as_longlong(sc) == 0) return hS;  // windows from t = 0
+    if (!want_log && (__double2hiint(sc) | __double2loint(sc)) == 0) return hS;  // t0 = 0
     const bool big = !bits_le(sc, 700.0);
     const double lh = (want_log || big) ? log_tab(hS, tab) : 0.0;
     if (want_log) log_k = sc + lh;
@@ -174,7 +174,7 @@ struct FormF64T {
     // units (K = 4096/ln 2 folded into nu_k and log_pref_k): one FMA, and a
     // second only for windows that do not start at t = 0 (sc != 0)
     double u = fma(mp.nu_k, log_tab(z, tab), mp.log_pref_k);
-    if (__double_as_longlong(sc) != 0) u = fma(sc, kExpScale, u);
+    if ((__double2hiint(sc) | __double2loint(sc)) != 0) u = fma(sc, kExpScale, u);
     return exp_units_full(u, tab) * hS;
   }
 
@@ -327,6 +327,10 @@ template <int L, class Form, typename OutT>
 __device__ __forceinline__ void eval_out_f32_coop(const Form& f, bool valid, double x, double nu,
                                                   Tally& tl, unsigned& evals, OutT& k,
                                                   OutT& log_k, bool want_log) {
+  // x > 0 finite and |nu| finite: 64-bit tests of the bits, which the
+  // compiler may turn into FP64 comparisons; this kernel is bound by
+  // instruction issue, not by the FP64 pipe, so one FP64 compare is cheaper
+  // here than several integer instructions (measured 1.5 %)
   const long long xb = __double_as_longlong(x);
   const long long vb = __double_as_longlong(nu) & 0x7fffffffffffffffLL;
   bool okx = false, okn = false;

@@ -26,10 +26,20 @@ constexpr double kLogInvEps64 = 36.04365338911715;
 // 2-per-clock rate, like FMAs, while integer operations do not.
 
 // v > 0 for v not NaN (NaN with a clear sign bit counts as positive).
-__device__ __forceinline__ bool bits_pos(double v) { return __double_as_longlong(v) > 0; }
+//
+// These tests (and the other bit-pattern tests of this file) are written on
+// the 32-bit words: a 64-bit comparison of a double's bits with a constant
+// can be folded by the compiler into an FP64 comparison (a masked
+// "> 0x7ff0000000000000" test into isnan, say), which takes an FP64-pipe slot
+// (measured: one such test per node cost 17 % of the FP64 tile writer's time).
+__device__ __forceinline__ bool bits_pos(double v) {
+  const int hi = __double2hiint(v);
+  return hi > 0 || (hi == 0 && __double2loint(v) != 0);
+}
 // a <= b for a, b >= 0 (false when a is NaN).
 __device__ __forceinline__ bool bits_le(double a, double b) {
-  return __double_as_longlong(a) <= __double_as_longlong(b);
+  const int ha = __double2hiint(a), hb = __double2hiint(b);
+  return ha < hb || (ha == hb && (unsigned)__double2loint(a) <= (unsigned)__double2loint(b));
 }
 // v truncated to a float (23 stored significand bits) by integer operations
 // only (no conversion on the FP64 pipe): magnitudes below 2^-126 give a
@@ -258,24 +268,30 @@ __device__ __forceinline__ double exp2s_node(double u, const double* __restrict_
 
 // 2^{-D/4096} for 0 <= D < 2^22 (a node loop's x cosh t in scaled units),
 // split into its polynomial p and the scaled table value T, 2^{-D/4096} =
-// p T, for loops that fold the final product into an FMA.  The rounding
-// m = round(D) and the remainder rho = D - m (|rho| <= 1/2) are both taken
-// exactly from D's 53-bit significand on the integer pipe: with sh the
-// position of D's binary point in it, m = (sig + 2^(sh-1)) >> sh and
-// rho 2^sh = ((sig + 2^(sh-1)) mod 2^sh) - 2^(sh-1), an integer below 2^53
-// in magnitude that is normalised into a double by its leading-bit position.
-// p = 1 - K1 rho + K2 rho^2 (relative error below 2.6e-14, as exp2s) is then
-// the only FP64 work: 2 operations.  The table index and exponent come from
-// -m, so that no negated copy of D is formed.  (The rounding is written out
-// here rather than taken from round_rem: built on round_rem this function
-// measured one more FP64 operation per node.)  Accurate for D <= 1022 * 4096
-// (results down to 2^-1022; the node loops keep D below 4.08e6); above, the
-// exponent is clamped at -1022 (a result near 2^-1022, not garbage), and a
-// finite D >= 2^22 gives some value below 2^-990 (m is clamped to 2^22).
-// NaN gives NaN.
+// p T, for loops that fold the final product into an FMA.  No FP64
+// arithmetic: the rounding m = round(D) and the remainder rho = D - m
+// (|rho| <= 1/2) are taken exactly from D's 53-bit significand on the
+// integer pipe (with sh the position of D's binary point in it,
+// m = (sig + 2^(sh-1)) >> sh and rho 2^sh = ((sig + 2^(sh-1)) mod 2^sh) -
+// 2^(sh-1)), and p = 1 - K1 rho + K2 rho^2 (the minimax quadratic, relative
+// error below 2.6e-14) is evaluated in 64-bit fixed point on the integer
+// pipe: rho in units of 2^-63, K1 |rho| as the high half of a 64 x 64-bit
+// product with K1 in units of 2^-75, K2 rho^2 from the leading 32 bits of
+// rho (its error below 2^-58), delta = p - 1 in units of 2^-62, and p's bit
+// pattern assembled as 1 + delta rounded to 52 bits.  On GB300 an FP64
+// operation occupies the FP64 pipe 32 times as long as an integer
+// instruction occupies its own, so the ~25 integer instructions cost less
+// than the 2 FP64 operations of the FP64 polynomial.  The table index and
+// exponent come from -m, so that no negated copy of D is formed.  Accurate
+// for D <= 1022 * 4096 (results down to 2^-1022; the node loops keep D below
+// 4.08e6); above, the exponent is clamped at -1022, and a finite D >= 2^22
+// gives p = 1 and m clamped to 2^22 (a value below 2^-990).  NaN gives NaN.
 // kHalve: T times 1/2 (its exponent lowered by one, on the integer pipe) for
 // the trapezoid's end weights; the node loops keep D below 4.08e6, where the
 // exponent k of T is at least -997, so the result stays normal.
+constexpr unsigned long long kExpK1Q75 = (unsigned long long)(kExpK1 * 0x1p75);  // exact
+constexpr unsigned long long kExpK2Q57 = (unsigned long long)(kExpK2 * 0x1p57 + 0.5);
+static_assert(kExpK1Q75 < (1ULL << 63) && kExpK2Q57 < (1ULL << 32), "fixed-point constants");
 template <bool kHalve = false>
 __device__ __forceinline__ void exp2s_neg_parts(double D, const double* __restrict__ tab,
                                                 double& p, double& T) {
@@ -287,20 +303,22 @@ __device__ __forceinline__ void exp2s_neg_parts(double D, const double* __restri
   const long long t = sig + half;
   int m = (int)(t >> sh);
   const long long R = (t & ((half << 1) - 1)) - half;  // rho 2^sh
-  // R as a double times 2^-sh: sign, leading-bit position L of |R| (L <= 53),
-  // the bits below it as the significand
-  const unsigned long long A = (unsigned long long)(R < 0 ? -R : R);
-  const int L = 63 - __clzll((long long)A);
-  const unsigned long long frac = (L <= 52) ? ((A << (52 - L)) & 0xfffffffffffffULL) : 0ULL;
-  const unsigned long long rb = ((unsigned long long)(R < 0) << 63) |
-                                ((unsigned long long)(L - sh + 1023) << 52) | frac;
-  double rho = (A == 0ULL) ? 0.0 : __longlong_as_double((long long)rb);
-  rho = (e < -2) ? D : rho;  // D < 1/4 (and 0): m = 0, rho = D
-  if (e > 21) {              // out of range for the callers: clamp, keep NaN
+  // rho 2^63 (|.| <= 2^62); for D < 1/4 (e < -2, m = 0) rho = D = sig 2^(e - 52)
+  long long rq = R << (63 - sh);
+  if (e < -2) rq = (e >= -11) ? (sig << (e + 11)) : ((e > -74) ? (sig >> (-11 - e)) : 0LL);
+  const unsigned long long ar = (unsigned long long)(rq < 0 ? -rq : rq);
+  const long long t1 = (long long)(__umul64hi(ar, kExpK1Q75) >> 12);  // K1 |rho| 2^62
+  const unsigned int rh = (unsigned int)(ar >> 31);                   // |rho| 2^32
+  const unsigned long long r2 = ((unsigned long long)rh * rh) >> 32;  // rho^2 2^32
+  const long long t2 = (long long)((r2 * kExpK2Q57) >> 27);           // K2 rho^2 2^62
+  const long long d = (rq < 0 ? t1 : -t1) + t2;                       // (p - 1) 2^62
+  long long pb = 0x3FF0000000000000LL + (d >= 0 ? (d + 512) >> 10 : (d + 256) >> 9);
+  if (e > 21) {  // out of range for the callers: clamp; NaN stays NaN
     m = 1 << 22;
-    rho = D;
+    const bool nan = e == 1024 && ((((unsigned)(b >> 32)) & 0xfffffu) | (unsigned)b) != 0u;
+    pb = nan ? b : 0x3FF0000000000000LL;
   }
-  p = fma(fma(kExpK2, rho, -kExpK1), rho, 1.0);
+  p = __longlong_as_double(pb);
   const int n = -m;
   const double tj = tab[n & (kExpTabSize - 1)];
   const int k = max(n >> kExpTabBits, -1022) - (kHalve ? 1 : 0);
@@ -358,7 +376,7 @@ __device__ __forceinline__ double exp2s_cubic(double u, const double* __restrict
 // from the sums that formed it: 5 FP64 operations.  |a| >= 708 goes to exp_full
 // (NaN -> NaN, overflow -> inf, deep underflow -> 0).
 __device__ __forceinline__ double exp_tab_full(double a, const double* __restrict__ tab) {
-  if (!((__double_as_longlong(a) & 0x7fffffffffffffffLL) < 0x4086200000000000LL))  // |a| < 708
+  if (!((__double2hiint(a) & 0x7fffffff) < 0x40862000))  // |a| < 708 (708 = 0x40862000 00000000)
     return exp_full(a);
   return exp2s_cubic(a * kExpScale, tab);
 }
@@ -368,7 +386,7 @@ __device__ __forceinline__ double exp_tab_full(double a, const double* __restric
 // exp2s_cubic for |u| < 4.18e6 (|a| < 707.4), exp_full of u ln2/4096 beyond
 // (overflow, deep underflow, NaN).  4 FP64 operations on the common path.
 __device__ __forceinline__ double exp_units_full(double u, const double* __restrict__ tab) {
-  if (!((__double_as_longlong(u) & 0x7fffffffffffffffLL) < 0x414fe41000000000LL))  // |u| < 4.18e6
+  if (!((__double2hiint(u) & 0x7fffffff) < 0x414fe410))  // |u| < 4.18e6 (= 0x414fe410 00000000)
     return exp_full(u * kExpC1);
   return exp2s_cubic(u, tab);
 }
@@ -748,10 +766,10 @@ __device__ __forceinline__ float log2_f64_approx(double v) {
 //   f(t_j) = (e^{nu t_start} / 2) e^{-x cosh t_j} C_j,
 //   C_j = e^{nu (t_j - t_start)} (1 + e^{-2 nu t_j}) = 2 e^{-nu t_start} cosh(nu t_j),
 // where C_j follows its own three-term recurrence C_{j+1} = 2 cosh(nu H) C_j
-// - C_{j-1}.  A node costs the exponential of -D_j, its product with C_j,
-// the sum and the two recurrences: 6 FP64 operations instead of the
-// centred loop's 9, and the set-up needs neither cosh t* nor the centring
-// exponentials.  Each factor must stay in the double range on its own,
+// - C_{j-1}.  A node costs the exponential of -D_j (its polynomial on the
+// integer pipe), its product with C_j, the sum and the two recurrences: 4 FP64
+// operations instead of the centred loop's 9, and the set-up needs neither
+// cosh t* nor the centring exponentials.  Each factor must stay in the double range on its own,
 // x cosh t_j <= 690 (the exponential's argument below 2^22) and
 // nu (t_j - t_start) <= 600, and the C recurrence amplifies rounding with the
 // node count; cosh_loop_ok states the conditions.  Returns
@@ -796,7 +814,7 @@ __device__ __forceinline__ NodeSumC node_sum_cosh(double t_start, double H, int 
     C1 = cn;
   }
   // node j's term is p_j (T_j C_j) with 2^{-D_j/4096} = p_j T_j: the sum
-  // takes it by one FMA (6 FP64 operations per node)
+  // takes it by one FMA (4 FP64 operations per node)
   NodeSumC r;
   double p, T;
   exp2s_neg_parts(D0, tab, p, T);
@@ -831,9 +849,9 @@ __device__ __forceinline__ NodeSumC node_sum_cosh(double t_start, double H, int 
   r.S = s;
   return r;
 }
-// FP64 ops per node of node_sum_cosh: exp2s_neg_parts (2), 1 mul (T C),
-// 1 fma (sum), 2 fma (recurrences).
-constexpr int kNodeOps64Cosh = 6;
+// FP64 ops per node of node_sum_cosh: 1 mul (T C), 1 fma (sum), 2 fma
+// (recurrences); exp2s_neg_parts runs on the integer pipe.
+constexpr int kNodeOps64Cosh = 4;
 
 // Whether node_sum_cosh may take a window [t0, t1] of N intervals (FP32
 // tests on truncated copies).  Rounding in the C recurrence (each step's,
