@@ -267,34 +267,32 @@ __device__ __forceinline__ double exp2s_node(double u, const double* __restrict_
 }
 
 // 2^{-D/4096} for 0 <= D < 2^22 (a node loop's x cosh t in scaled units),
-// split into its polynomial p and the scaled table value T, 2^{-D/4096} =
-// p T, for loops that fold the final product into an FMA.  No FP64
-// arithmetic: the rounding m = round(D) and the remainder rho = D - m
-// (|rho| <= 1/2) are taken exactly from D's 53-bit significand on the
-// integer pipe (with sh the position of D's binary point in it,
-// m = (sig + 2^(sh-1)) >> sh and rho 2^sh = ((sig + 2^(sh-1)) mod 2^sh) -
-// 2^(sh-1)), and p = 1 - K1 rho + K2 rho^2 (the minimax quadratic, relative
-// error below 2.6e-14) is evaluated in 64-bit fixed point on the integer
-// pipe: rho in units of 2^-63, K1 |rho| as the high half of a 64 x 64-bit
-// product with K1 in units of 2^-75, K2 rho^2 from the leading 32 bits of
-// rho (its error below 2^-58), delta = p - 1 in units of 2^-62, and p's bit
-// pattern assembled as 1 + delta rounded to 52 bits.  On GB300 an FP64
-// operation occupies the FP64 pipe 32 times as long as an integer
-// instruction occupies its own, so the ~25 integer instructions cost less
-// than the 2 FP64 operations of the FP64 polynomial.  The table index and
-// exponent come from -m, so that no negated copy of D is formed.  Accurate
-// for D <= 1022 * 4096 (results down to 2^-1022; the node loops keep D below
-// 4.08e6); above, the exponent is clamped at -1022, and a finite D >= 2^22
-// gives p = 1 and m clamped to 2^22 (a value below 2^-990).  NaN gives NaN.
-// kHalve: T times 1/2 (its exponent lowered by one, on the integer pipe) for
-// the trapezoid's end weights; the node loops keep D below 4.08e6, where the
-// exponent k of T is at least -997, so the result stays normal.
+// times 2^kAdj, computed on the integer pipe without FP64 arithmetic.  The
+// rounding m = round(D) and the remainder rho = D - m (|rho| <= 1/2) are
+// taken exactly from D's 53-bit significand (with sh the position of D's
+// binary point in it, m = (sig + 2^(sh-1)) >> sh and rho 2^sh = ((sig +
+// 2^(sh-1)) mod 2^sh) - 2^(sh-1)); p = 2^{-rho/4096} = 1 - K1 rho + K2 rho^2
+// (the minimax quadratic, relative error below 2.6e-14) is evaluated in 64-bit
+// fixed point: rho in units of 2^-63, K1 |rho| as the high half of a 64 x
+// 64-bit product with K1 in units of 2^-75, K2 rho^2 from the leading 32 bits
+// of rho (its error below 2^-58), delta = p - 1 in units of 2^-62.  The
+// result p T, T = 2^{-m/4096} = 2^k t_j with t_j = 2^{j/4096} from the table,
+// is t_j's 53-bit significand M plus delta M (the high half of a 64 x 64-bit
+// product, truncated: below 2^-52 relative), renormalised into [2^52, 2^53)
+// and given the exponent k.  On GB300 an FP64 operation occupies the FP64
+// pipe 32 times as long as an integer instruction occupies its own, so these
+// ~40 integer instructions cost less than the 3 FP64 operations of the FP64
+// polynomial and product they replace.  The table index and exponent come
+// from -m, so that no negated copy of D is formed.  Accurate for D <= 1022 *
+// 4096 (results down to 2^-1022; the node loops keep D below 4.08e6, where k
+// is at least -997); a finite D >= 2^22 gives p = 1 and m clamped to 2^22 (a
+// value below 2^-990); NaN gives NaN.  kAdj = -1 halves the result (the
+// trapezoid's end weights).
 constexpr unsigned long long kExpK1Q75 = (unsigned long long)(kExpK1 * 0x1p75);  // exact
 constexpr unsigned long long kExpK2Q57 = (unsigned long long)(kExpK2 * 0x1p57 + 0.5);
 static_assert(kExpK1Q75 < (1ULL << 63) && kExpK2Q57 < (1ULL << 32), "fixed-point constants");
-template <bool kHalve = false>
-__device__ __forceinline__ void exp2s_neg_parts(double D, const double* __restrict__ tab,
-                                                double& p, double& T) {
+template <int kAdj = 0>
+__device__ __forceinline__ double exp2s_neg_int(double D, const double* __restrict__ tab) {
   const long long b = __double_as_longlong(D);
   const int e = (int)((b >> 52) & 0x7ff) - 1023;
   const long long sig = (b & 0xfffffffffffffLL) | 0x10000000000000LL;
@@ -311,18 +309,29 @@ __device__ __forceinline__ void exp2s_neg_parts(double D, const double* __restri
   const unsigned int rh = (unsigned int)(ar >> 31);                   // |rho| 2^32
   const unsigned long long r2 = ((unsigned long long)rh * rh) >> 32;  // rho^2 2^32
   const long long t2 = (long long)((r2 * kExpK2Q57) >> 27);           // K2 rho^2 2^62
-  const long long d = (rq < 0 ? t1 : -t1) + t2;                       // (p - 1) 2^62
-  long long pb = 0x3FF0000000000000LL + (d >= 0 ? (d + 512) >> 10 : (d + 256) >> 9);
-  if (e > 21) {  // out of range for the callers: clamp; NaN stays NaN
+  long long d = (rq < 0 ? t1 : -t1) + t2;                             // (p - 1) 2^62
+  const bool out = e > 21;  // out of range for the callers: clamp; NaN stays NaN
+  if (out) {
     m = 1 << 22;
-    const bool nan = e == 1024 && ((((unsigned)(b >> 32)) & 0xfffffu) | (unsigned)b) != 0u;
-    pb = nan ? b : 0x3FF0000000000000LL;
+    d = 0;
   }
-  p = __longlong_as_double(pb);
   const int n = -m;
-  const double tj = tab[n & (kExpTabSize - 1)];
-  const int k = max(n >> kExpTabBits, -1022) - (kHalve ? 1 : 0);
-  T = __hiloint2double(__double2hiint(tj) + (k << 20), __double2loint(tj));
+  const long long tb = __double_as_longlong(tab[n & (kExpTabSize - 1)]);  // t_j in [1, 2)
+  const long long M = (tb & 0xfffffffffffffLL) | 0x10000000000000LL;      // t_j 2^52
+  const unsigned long long ad = (unsigned long long)(d < 0 ? -d : d);      // < 2^49
+  const long long X = (long long)__umul64hi(ad << 2, (unsigned long long)M);  // |delta| M
+  long long Mp = M + (d < 0 ? -X : X);  // p t_j 2^52, within 2^40 of [2^52, 2^53)
+  int k = max(n >> kExpTabBits, -1022) + kAdj;
+  if (Mp >= 0x20000000000000LL) {  // p t_j >= 2: halve (rounded), exponent up
+    Mp = (Mp + 1) >> 1;
+    ++k;
+  } else if (Mp < 0x10000000000000LL) {  // p t_j < 1: double, exponent down
+    Mp <<= 1;
+    --k;
+  }
+  const double r = __longlong_as_double(((long long)(k + 1023) << 52) | (Mp & 0xfffffffffffffLL));
+  const bool nan = out && e == 1024 && ((((unsigned)(b >> 32)) & 0xfffffu) | (unsigned)b) != 0u;
+  return nan ? D : r;
 }
 
 // e^a for a in [-708, 709] (callers clamp); one scaling multiply on top of exp2s.
@@ -766,10 +775,10 @@ __device__ __forceinline__ float log2_f64_approx(double v) {
 //   f(t_j) = (e^{nu t_start} / 2) e^{-x cosh t_j} C_j,
 //   C_j = e^{nu (t_j - t_start)} (1 + e^{-2 nu t_j}) = 2 e^{-nu t_start} cosh(nu t_j),
 // where C_j follows its own three-term recurrence C_{j+1} = 2 cosh(nu H) C_j
-// - C_{j-1}.  A node costs the exponential of -D_j (its polynomial on the
-// integer pipe), its product with C_j, the sum and the two recurrences: 4 FP64
-// operations instead of the centred loop's 9, and the set-up needs neither
-// cosh t* nor the centring exponentials.  Each factor must stay in the double range on its own,
+// - C_{j-1}.  A node costs the exponential of -D_j (on the integer pipe),
+// the sum of its product with C_j and the two recurrences: 3 FP64 operations
+// instead of the centred loop's 9, and the set-up needs neither cosh t* nor
+// the centring exponentials.  Each factor must stay in the double range on its own,
 // x cosh t_j <= 690 (the exponential's argument below 2^22) and
 // nu (t_j - t_start) <= 600, and the C recurrence amplifies rounding with the
 // node count; cosh_loop_ok states the conditions.  Returns
@@ -813,18 +822,14 @@ __device__ __forceinline__ NodeSumC node_sum_cosh(double t_start, double H, int 
     C0 = 2.0;
     C1 = cn;
   }
-  // node j's term is p_j (T_j C_j) with 2^{-D_j/4096} = p_j T_j: the sum
-  // takes it by one FMA (4 FP64 operations per node)
+  // node j's term is E_j C_j with E_j = 2^{-D_j/4096} from the integer pipe:
+  // the sum takes it by one FMA (3 FP64 operations per node)
   NodeSumC r;
-  double p, T;
-  exp2s_neg_parts(D0, tab, p, T);
-  double s = p * T;  // the first term times 1/2 (C_0 / 2 = 1 at t_start = 0)
+  double s = exp2s_neg_int(D0, tab);  // the first term times 1/2 (C_0 / 2 = 1 at t_start = 0)
   r.l2_first = 0.0f;
   if (start_pos) {
+    r.l2_first = log2_f64_approx(s) + log2_f64_approx(C0h) + 1.0f;
     s *= C0h;
-    float l2p;
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l2p) : "f"(f32_trunc(p)));
-    r.l2_first = l2p + log2_f64_approx(T) + log2_f64_approx(C0h) + 1.0f;
   }
 #pragma unroll 2
   for (int j = 1; j < count - 1; ++j) {
@@ -834,24 +839,20 @@ __device__ __forceinline__ NodeSumC node_sum_cosh(double t_start, double H, int 
     const double C2 = fma(cn, C1, -C0);
     C0 = C1;
     C1 = C2;
-    exp2s_neg_parts(D0, tab, p, T);
-    s = fma(p, T * C0, s);
+    s = fma(exp2s_neg_int(D0, tab), C0, s);
   }
-  {  // the last node (D_N, C_N after the loop), weight 1/2 folded into T; count >= 3
-    exp2s_neg_parts<true>(D1, tab, p, T);
-    const double qh = T * C1;
-    s = fma(p, qh, s);
-    float l2p;
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l2p) : "f"(f32_trunc(p)));
-    r.l2_last = l2p + log2_f64_approx(qh) + 1.0f;
-    r.pos = bits_pos(qh) && bits_pos(p);
+  {  // the last node (D_N, C_N after the loop), weight 1/2 folded into E; count >= 3
+    const double Eh = exp2s_neg_int<-1>(D1, tab);
+    s = fma(Eh, C1, s);
+    r.l2_last = log2_f64_approx(Eh) + log2_f64_approx(C1) + 1.0f;
+    r.pos = bits_pos(Eh) && bits_pos(C1);
   }
   r.S = s;
   return r;
 }
-// FP64 ops per node of node_sum_cosh: 1 mul (T C), 1 fma (sum), 2 fma
-// (recurrences); exp2s_neg_parts runs on the integer pipe.
-constexpr int kNodeOps64Cosh = 4;
+// FP64 ops per node of node_sum_cosh: 1 fma (sum), 2 fma (recurrences);
+// exp2s_neg_int runs on the integer pipe.
+constexpr int kNodeOps64Cosh = 3;
 
 // Whether node_sum_cosh may take a window [t0, t1] of N intervals (FP32
 // tests on truncated copies).  Rounding in the C recurrence (each step's,

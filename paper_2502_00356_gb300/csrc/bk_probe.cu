@@ -114,12 +114,7 @@ __global__ void math_probe_kernel(int fn, const double* __restrict__ in, double*
       case 0: out[i] = exp_tab_full(v, tab); break;
       case 1: out[i] = log_tab(v, tab); break;
       case 2: out[i] = exp2s_node(v, tab); break;
-      case 3: {
-        double p, T;
-        exp2s_neg_parts(v, tab, p, T);
-        out[i] = p * T;
-        break;
-      }
+      case 3: out[i] = exp2s_neg_int(v, tab); break;
       case 4: {
         int M;
         double r;
