@@ -446,6 +446,11 @@ bk_status bk_probe_pipe(int kind, int64_t iters, int grid, int block, double* si
  *   5  2 cosh v for v >= 0 (the series tiers and the exponential path)
  *   6  sqrt a for a > 0
  *   7  e^a by the accurate set-up exponential, |a| < 708
+ *   8  e^a by the Matern entries' final exponential on the integer pipe,
+ *      exp_units_full(a 4096/ln 2) (any a; |a| >= 707.4 takes the
+ *      range-checked path)
+ *   9  log a from the Matern entries' log parts (nd and log1p(d) on the
+ *      integer pipe), assembled as nd ln2/4096 + log1p(d), finite a > 0
  * in: device, n doubles; out: device, n doubles (2n for fn 4).  Inputs
  * outside a function's stated domain give unspecified values (no fault).
  * Errors: BK_ERR_INVALID_ARG for an unknown fn, n < 0 or null pointers with

@@ -171,9 +171,13 @@ struct FormF64T {
     double hS;
     const double sc = scale_f64(z, mp.nu, kPlainLog2OverTol, kPlainMaxNodes, tab, hS, tl, sp, cnu);
     // exp(a1 + nu log z + sc) hS with the exponent formed in the table's
-    // units (K = 4096/ln 2 folded into nu_k and log_pref_k): one FMA, and a
-    // second only for windows that do not start at t = 0 (sc != 0)
-    double u = fma(mp.nu_k, log_tab(z, tab), mp.log_pref_k);
+    // units, u = (a1 + sc) K + nu (nd + K log1p(d)) for log z = nd ln2/4096 +
+    // log1p(d) (K = 4096/ln 2 folded into nu_k and log_pref_k; the log's
+    // parts from the integer pipe): two FMAs, and a third only for windows
+    // that do not start at t = 0 (sc != 0)
+    double nd;
+    const double l1p = log_tab_parts(z, tab, nd);
+    double u = fma(mp.nu, nd, fma(mp.nu_k, l1p, mp.log_pref_k));
     if ((__double2hiint(sc) | __double2loint(sc)) != 0) u = fma(sc, kExpScale, u);
     return exp_units_full(u, tab) * hS;
   }

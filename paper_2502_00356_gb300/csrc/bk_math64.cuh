@@ -379,6 +379,56 @@ __device__ __forceinline__ double exp2s_cubic(double u, const double* __restrict
   return p * __hiloint2double(__double2hiint(tj) + (k << 20), __double2loint(tj));
 }
 
+// 2^{u/4096} for |u| < 4.18e6 on the integer pipe, to the accuracy of
+// exp2s_cubic: the nearest integer n of u and the remainder rho = u - n
+// (|rho| <= 1/2) taken exactly from u's significand as in exp2s_neg_int (on
+// |u|, the signs restored by integer operations), p = 2^{rho/4096} = 1 +
+// C1 rho + K2 rho^2 + C3 rho^3 (the Taylor cubic, truncation below 3e-18
+// relative) in 64-bit fixed point (C1 rho from a 64 x 64-bit high product,
+// the square and cube from the leading 32 bits of rho, their errors below
+// 2^-58), and p t_j 2^k, t_j = 2^{j/4096}, from t_j's significand as in
+// exp2s_neg_int (truncation below 2^-52 relative).  No FP64 arithmetic.
+constexpr unsigned long long kExpC1Q75 = (unsigned long long)(kExpC1 * 0x1p75);  // exact
+constexpr unsigned long long kExpC3Q72 = (unsigned long long)(kExpC3 * 0x1p72 + 0.5);
+static_assert(kExpC1Q75 < (1ULL << 63) && kExpC3Q72 < (1ULL << 32), "fixed-point constants");
+__device__ __forceinline__ double exp2s_int(double u, const double* __restrict__ tab) {
+  const long long b = __double_as_longlong(u);
+  const bool neg = (int)(b >> 32) < 0;
+  const int e = (int)((b >> 52) & 0x7ff) - 1023;
+  const long long sig = (b & 0xfffffffffffffLL) | 0x10000000000000LL;
+  const int sh = 52 - min(max(e, -2), 21);  // 31 .. 54
+  const long long half = 1LL << (sh - 1);
+  const long long t = sig + half;
+  const int m = (int)(t >> sh);                        // round(|u|)
+  const long long R = (t & ((half << 1) - 1)) - half;  // (|u| - m) 2^sh
+  long long rq = R << (63 - sh);                       // (|u| - m) 2^63
+  if (e < -2) rq = (e >= -11) ? (sig << (e + 11)) : ((e > -74) ? (sig >> (-11 - e)) : 0LL);
+  const bool negr = neg != (rq < 0);  // the sign of rho = u - n
+  const unsigned long long ar = (unsigned long long)(rq < 0 ? -rq : rq);
+  const long long c1 = (long long)(__umul64hi(ar, kExpC1Q75) >> 12);  // C1 |rho| 2^62
+  const unsigned long long rh = ar >> 31;                             // |rho| 2^32
+  const unsigned long long r2 = (rh * rh) >> 32;                      // rho^2 2^32
+  const unsigned long long r3 = (r2 * rh) >> 32;                      // |rho|^3 2^32
+  const long long c2 = (long long)((r2 * kExpK2Q57) >> 27);           // K2 rho^2 2^62
+  const long long c3 = (long long)((r3 * kExpC3Q72) >> 42);           // C3 |rho|^3 2^62
+  const long long d = (negr ? -(c1 + c3) : (c1 + c3)) + c2;           // (p - 1) 2^62
+  const int n = neg ? -m : m;
+  const long long tb = __double_as_longlong(tab[n & (kExpTabSize - 1)]);  // t_j in [1, 2)
+  const long long M = (tb & 0xfffffffffffffLL) | 0x10000000000000LL;
+  const unsigned long long ad = (unsigned long long)(d < 0 ? -d : d);      // < 2^49
+  const long long X = (long long)__umul64hi(ad << 2, (unsigned long long)M);
+  long long Mp = M + (d < 0 ? -X : X);
+  int k = n >> kExpTabBits;
+  if (Mp >= 0x20000000000000LL) {
+    Mp = (Mp + 1) >> 1;
+    ++k;
+  } else if (Mp < 0x10000000000000LL) {
+    Mp <<= 1;
+    --k;
+  }
+  return __longlong_as_double(((long long)(k + 1023) << 52) | (Mp & 0xfffffffffffffLL));
+}
+
 // e^a over the whole double range for the final normalisations: u = a K
 // rounded to a double, then exp2s_cubic.  The roundings of u and of K cost
 // at most 1.3e-16 |a| relative, the order of the rounding a itself carries
@@ -392,12 +442,12 @@ __device__ __forceinline__ double exp_tab_full(double a, const double* __restric
 
 // e^{u / K}, K = 4096 / ln 2, for an exponent the caller formed directly in
 // the table's units (u = a K with the scaling folded into its constants):
-// exp2s_cubic for |u| < 4.18e6 (|a| < 707.4), exp_full of u ln2/4096 beyond
-// (overflow, deep underflow, NaN).  4 FP64 operations on the common path.
+// exp2s_int for |u| < 4.18e6 (|a| < 707.4; no FP64 operation), exp_full of
+// u ln2/4096 beyond (overflow, deep underflow, NaN).
 __device__ __forceinline__ double exp_units_full(double u, const double* __restrict__ tab) {
   if (!((__double2hiint(u) & 0x7fffffff) < 0x414fe410))  // |u| < 4.18e6 (= 0x414fe410 00000000)
     return exp_full(u * kExpC1);
-  return exp2s_cubic(u, tab);
+  return exp2s_int(u, tab);
 }
 
 // log a for finite a > 0 with the same table: a = 2^e m, m in [1, 2); j =
@@ -433,6 +483,57 @@ __device__ __forceinline__ double log_tab(double a, const double* __restrict__ t
   // 2^-53, the order of the result's own rounding)
   const double nd = widen_f(__int2float_rn(e * kExpTabSize + j));
   return fma(nd, kExpC1, l1p);
+}
+
+// log a for finite a > 0 split as log a = nd ln2/4096 + l1p, with nd =
+// 4096 e + j an integer (exact as a double) and l1p = log1p(d), d = m
+// 2^{-j/4096} - 1 (|d| <= 8.5e-5), for callers that scale the two parts
+// themselves (log_tab's reduction, a = 2^e m, j = round(4096 log2 m)).  No
+// FP64 arithmetic: d = M_m M_t 2^-105 - 1 from the 53-bit significands of m
+// and of 2^{(4096-j)/4096} by a 64 x 64-bit high product (exact to 2^-62), the
+// series d - d^2/2 + d^3/3 (truncation below 2e-17 absolute) in 64-bit fixed
+// point, and l1p rounded to a double from its leading bit.  Subnormal a is
+// scaled as in log_tab.
+__device__ __forceinline__ double log_tab_parts(double a, const double* __restrict__ tab,
+                                                double& nd) {
+  int hi = __double2hiint(a);
+  int lo = __double2loint(a);
+  int e = 0;
+  if (hi < 0x00100000) {  // subnormal: scale into the normal range
+    a *= 0x1p54;
+    e = -54;
+    hi = __double2hiint(a);
+    lo = __double2loint(a);
+  }
+  e += (hi >> 20) - 1023;
+  const int mh = hi & 0x000fffff;
+  const float mf = __int_as_float(0x3f800000 | (mh << 3) | ((unsigned)lo >> 29));
+  float l2;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l2) : "f"(mf));
+  const int j = __float2int_rn(l2 * (float)kExpTabSize);  // 0..4096
+  nd = widen_f(__int2float_rn(e * kExpTabSize + j));
+  const unsigned long long Mm = ((unsigned long long)(unsigned)(mh | 0x00100000) << 32) | (unsigned)lo;
+  long long dq;  // d 2^62
+  if (j > 0) {
+    const long long tb = __double_as_longlong(tab[(kExpTabSize - j) & (kExpTabSize - 1)]);
+    const unsigned long long Mt = (unsigned long long)((tb & 0xfffffffffffffLL) | 0x10000000000000LL);
+    dq = (long long)__umul64hi(Mm << 11, Mt << 10) - (1LL << 62);  // M_m M_t 2^-43 - 2^62
+  } else {
+    dq = (long long)(Mm << 10) - (1LL << 62);
+  }
+  const bool neg = dq < 0;
+  const unsigned long long ad = (unsigned long long)(neg ? -dq : dq);      // < 2^49
+  const unsigned long long d2 = __umul64hi(ad << 14, ad << 14) >> 26;      // d^2 2^62
+  const unsigned long long d3 = __umul64hi(d2 << 20, ad << 14) >> 32;      // |d|^3 2^62
+  const unsigned long long d33 = __umul64hi(d3, 0x5555555555555556ULL);    // |d|^3 / 3 2^62
+  const long long q = (neg ? -(long long)(ad + d33) : (long long)(ad + d33)) - (long long)(d2 >> 1);
+  // q 2^-62 as a double, rounded to nearest from its leading bit
+  if (q == 0) return 0.0;
+  const unsigned long long aq = (unsigned long long)(q < 0 ? -q : q);
+  const int L = 63 - __clzll((long long)aq);  // <= 49
+  const unsigned long long mant = (L > 52) ? ((aq + (1ULL << (L - 53))) >> (L - 52)) : (aq << (52 - L));
+  const long long bits = ((long long)(L - 62 + 1023) << 52) + (long long)(mant - (1ULL << 52));
+  return __longlong_as_double(q < 0 ? (bits | (long long)0x8000000000000000ULL) : bits);
 }
 
 // 1/a from the hardware approximation refined by Newton-Raphson steps

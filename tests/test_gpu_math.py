@@ -55,6 +55,28 @@ def test_final_exponential(dev):
     assert 0.0 < edge[2] < 1e-320 and np.isposinf(edge[5]) and edge[6] == 0.0
 
 
+def test_final_exponential_integer_pipe(dev):
+    """The Matern entries' final exponential, e^a = 2^{u/4096} with u = a
+    4096/ln 2 formed in table units and evaluated on the integer pipe (the
+    cubic in fixed point, the table product as a 64-bit significand)."""
+    rng = np.random.default_rng(66)
+    a = np.concatenate([rng.uniform(-707.3, 707.3, 1500), rng.uniform(-20, 20, 500),
+                        rng.uniform(-1e-3, 1e-3, 200),
+                        [0.0, 1e-300, -1e-300, 0.5 * math.log(2) / 4096, -0.5 * math.log(2) / 4096,
+                         707.3, -707.3, 1.0, -1.0]])
+    got = probe("exp_units", a, dev)
+    for ai, gi in zip(a, got):
+        ref = Decimal(float(ai)).exp()
+        # the rounding of u = a 4096/ln2 (1.3e-16 |a|), the cubic's truncation
+        # (3e-18), the fixed-point terms (below 2^-58) and the truncated
+        # significand product and renormalisation (below 2^-52)
+        assert rel_err(gi, ref) <= Decimal(abs(float(ai)) * 1.5e-16 + 4e-16), (ai, gi)
+    edge = probe("exp_units", np.array([709.0, 709.9, -740.0, -746.0, np.nan, np.inf, -np.inf]), dev)
+    assert rel_err(edge[0], Decimal(709).exp()) < Decimal(1e-15)
+    assert np.isposinf(edge[1]) and edge[3] == 0.0 and np.isnan(edge[4])
+    assert 0.0 < edge[2] < 1e-320 and np.isposinf(edge[5]) and edge[6] == 0.0
+
+
 def test_table_log(dev):
     rng = np.random.default_rng(62)
     a = np.concatenate([np.exp(rng.uniform(-690, 690, 1500)), 1.0 + rng.uniform(-1e-6, 1e-6, 200),
@@ -66,6 +88,28 @@ def test_table_log(dev):
         # the series and two roundings
         assert abs(Decimal(float(gi)) - ref) <= abs(ref) * Decimal(1.2e-16) + Decimal(3e-19) + \
             abs(ref) * Decimal(2.3e-16), (ai, gi)
+
+
+def test_table_log_parts(dev):
+    """log a as the Matern entries form it: nd = 4096 e + j and log1p(d)
+    from the integer pipe (d from a 64-bit significand product, the series in
+    fixed point), assembled here by one FMA with ln2/4096."""
+    rng = np.random.default_rng(67)
+    a = np.concatenate([np.exp(rng.uniform(-690, 690, 1500)), 1.0 + rng.uniform(-1e-6, 1e-6, 200),
+                        np.exp(rng.uniform(-12, 5, 500)),
+                        [1.0, 2.0, 0.5, 5e-324, 1e-310, 1.7976931348623157e308, 1 + 2**-52,
+                         2 - 2**-52, 1.5, 0.1, 14.1]])
+    got = probe("log_parts", a, dev)
+    for ai, gi in zip(a, got):
+        ref = Decimal(float(ai)).ln()
+        # ln2/4096 rounded once times |nd| (below |log a| 2^-53) and two
+        # roundings, relative; absolute: the table value's own rounding (2^-53
+        # in d, as for the FP64 table log), the series' truncation (2e-17) and
+        # its fixed-point terms (2^-62)
+        assert abs(Decimal(float(gi)) - ref) <= abs(ref) * Decimal(3.5e-16) + Decimal(1.3e-16), (ai, gi)
+    # the same values as the FP64 table log to within its rounding
+    old = probe("log", a, dev)
+    assert np.all(np.abs(got - old) <= 2.3e-16 * np.abs(old) + 2e-17)
 
 
 def test_node_exponentials(dev):
