@@ -287,30 +287,32 @@ __device__ __forceinline__ double exp2s_node(double u, const double* __restrict_
 // 4096 (results down to 2^-1022; the node loops keep D below 4.08e6, where k
 // is at least -997); a finite D >= 2^22 gives p = 1 and m clamped to 2^22 (a
 // value below 2^-990); NaN gives NaN.  kAdj = -1 halves the result (the
-// trapezoid's end weights).
+// trapezoid's end weights).  kNode: the node loops' variant, for 0.25 <= D <
+// 2^22 only (x >= 1e-4 and x cosh t <= 690 there), without the tests and
+// selects of the other ranges (the same arithmetic inside its range).
 constexpr unsigned long long kExpK1Q75 = (unsigned long long)(kExpK1 * 0x1p75);  // exact
 constexpr unsigned long long kExpK2Q57 = (unsigned long long)(kExpK2 * 0x1p57 + 0.5);
 static_assert(kExpK1Q75 < (1ULL << 63) && kExpK2Q57 < (1ULL << 32), "fixed-point constants");
-template <int kAdj = 0>
+template <int kAdj = 0, bool kNode = false>
 __device__ __forceinline__ double exp2s_neg_int(double D, const double* __restrict__ tab) {
   const long long b = __double_as_longlong(D);
   const int e = (int)((b >> 52) & 0x7ff) - 1023;
   const long long sig = (b & 0xfffffffffffffLL) | 0x10000000000000LL;
-  const int sh = 52 - min(max(e, -2), 21);  // 31 .. 54 (D < 1/2 gives m = 0)
+  const int sh = kNode ? 52 - e : 52 - min(max(e, -2), 21);  // 31 .. 54 (D < 1/2: m = 0)
   const long long half = 1LL << (sh - 1);
   const long long t = sig + half;
   int m = (int)(t >> sh);
   const long long R = (t & ((half << 1) - 1)) - half;  // rho 2^sh
   // rho 2^63 (|.| <= 2^62); for D < 1/4 (e < -2, m = 0) rho = D = sig 2^(e - 52)
   long long rq = R << (63 - sh);
-  if (e < -2) rq = (e >= -11) ? (sig << (e + 11)) : ((e > -74) ? (sig >> (-11 - e)) : 0LL);
+  if (!kNode && e < -2) rq = (e >= -11) ? (sig << (e + 11)) : ((e > -74) ? (sig >> (-11 - e)) : 0LL);
   const unsigned long long ar = (unsigned long long)(rq < 0 ? -rq : rq);
   const long long t1 = (long long)(__umul64hi(ar, kExpK1Q75) >> 12);  // K1 |rho| 2^62
   const unsigned int rh = (unsigned int)(ar >> 31);                   // |rho| 2^32
   const unsigned long long r2 = ((unsigned long long)rh * rh) >> 32;  // rho^2 2^32
   const long long t2 = (long long)((r2 * kExpK2Q57) >> 27);           // K2 rho^2 2^62
   long long d = (rq < 0 ? t1 : -t1) + t2;                             // (p - 1) 2^62
-  const bool out = e > 21;  // out of range for the callers: clamp; NaN stays NaN
+  const bool out = !kNode && e > 21;  // out of range: clamp; NaN stays NaN
   if (out) {
     m = 1 << 22;
     d = 0;
@@ -321,7 +323,7 @@ __device__ __forceinline__ double exp2s_neg_int(double D, const double* __restri
   const unsigned long long ad = (unsigned long long)(d < 0 ? -d : d);      // < 2^49
   const long long X = (long long)__umul64hi(ad << 2, (unsigned long long)M);  // |delta| M
   long long Mp = M + (d < 0 ? -X : X);  // p t_j 2^52, within 2^40 of [2^52, 2^53)
-  int k = max(n >> kExpTabBits, -1022) + kAdj;
+  int k = (kNode ? (n >> kExpTabBits) : max(n >> kExpTabBits, -1022)) + kAdj;
   if (Mp >= 0x20000000000000LL) {  // p t_j >= 2: halve (rounded), exponent up
     Mp = (Mp + 1) >> 1;
     ++k;
@@ -330,6 +332,7 @@ __device__ __forceinline__ double exp2s_neg_int(double D, const double* __restri
     --k;
   }
   const double r = __longlong_as_double(((long long)(k + 1023) << 52) | (Mp & 0xfffffffffffffLL));
+  if constexpr (kNode) return r;
   const bool nan = out && e == 1024 && ((((unsigned)(b >> 32)) & 0xfffffu) | (unsigned)b) != 0u;
   return nan ? D : r;
 }
@@ -926,7 +929,7 @@ __device__ __forceinline__ NodeSumC node_sum_cosh(double t_start, double H, int 
   // node j's term is E_j C_j with E_j = 2^{-D_j/4096} from the integer pipe:
   // the sum takes it by one FMA (3 FP64 operations per node)
   NodeSumC r;
-  double s = exp2s_neg_int(D0, tab);  // the first term times 1/2 (C_0 / 2 = 1 at t_start = 0)
+  double s = exp2s_neg_int<0, true>(D0, tab);  // the first term times 1/2 (C_0 / 2 = 1 at t0 = 0)
   r.l2_first = 0.0f;
   if (start_pos) {
     r.l2_first = log2_f64_approx(s) + log2_f64_approx(C0h) + 1.0f;
@@ -940,10 +943,10 @@ __device__ __forceinline__ NodeSumC node_sum_cosh(double t_start, double H, int 
     const double C2 = fma(cn, C1, -C0);
     C0 = C1;
     C1 = C2;
-    s = fma(exp2s_neg_int(D0, tab), C0, s);
+    s = fma(exp2s_neg_int<0, true>(D0, tab), C0, s);
   }
   {  // the last node (D_N, C_N after the loop), weight 1/2 folded into E; count >= 3
-    const double Eh = exp2s_neg_int<-1>(D1, tab);
+    const double Eh = exp2s_neg_int<-1, true>(D1, tab);
     s = fma(Eh, C1, s);
     r.l2_last = log2_f64_approx(Eh) + log2_f64_approx(C1) + 1.0f;
     r.pos = bits_pos(Eh) && bits_pos(C1);
