@@ -35,21 +35,20 @@ N_LOC, BETA, SIGMA2, NUS, SEED = 20_000, 0.1, 1.0, (0.5, 1.5, 2.3), 2
 WORKLOAD = "matern_jittered_grid_n20000_beta0.1_nu{0.5,1.5,2.3}_fp64"
 
 # FP64 work model of the plain form in FP64 arithmetic operations (one per
-# thread and DFMA/DADD/DMUL): 6 per quadrature node of the common loop (the
-# table exponential's polynomial, 2, with its rounding and remainder on the
-# integer pipe; its product with the cosh(nu t) factor; the summing FMA; the
-# two three-term recurrences; windows outside that loop's conditions take 9
-# and are counted at 6), per FP64 peak Newton iteration and per FP64
-# window-end Newton iteration (these run only for windows the check rejects,
-# or outside the FP32 search region), and a fixed part per Matern entry
-# (distance, square root, set-ups, end terms, log x and the final
-# exponential).  The fixed part is ncu's executed DFMA + DADD + DMUL per
-# evaluation minus 6 x nodes per evaluation on the n = 6000 case of the same
-# kernel (--profile-case plain_nus: 24.89 for each of nu = 0.5, 1.5, 2.3).
-# The FP32 Newton iterations
-# that place the window and the FP32 window check run on the FP32/MUFU pipes
-# and are not counted.
-OPS_NODE, OPS_PEAK_IT, OPS_WIN_IT, OPS_ENTRY_FIXED = 6, 54, 31, 24.9
+# thread and DFMA/DADD/DMUL): 3 per quadrature node of the common loop (the
+# summing FMA and the two three-term recurrences; the node's exponential,
+# polynomial and table product included, runs on the integer pipe; windows
+# outside that loop's conditions take 9 and are counted at 3), per FP64 peak
+# Newton iteration and per FP64 window-end Newton iteration (these run only
+# for windows the check rejects, or outside the FP32 search region), and a
+# fixed part per Matern entry (distance, square root, set-ups, the end
+# terms' scaling, the exponent's FMAs; log z and the final exponential run on
+# the integer pipe).  The fixed part is ncu's executed DFMA + DADD + DMUL per
+# evaluation minus 3 x nodes per evaluation on the n = 6000 case of the same
+# kernel (--profile-case plain_nus: 15.89 for each of nu = 0.5, 1.5, 2.3).
+# The FP32 Newton iterations that place the window and the FP32 window check
+# run on the FP32/MUFU pipes and are not counted.
+OPS_NODE, OPS_PEAK_IT, OPS_WIN_IT, OPS_ENTRY_FIXED = 3, 54, 31, 15.9
 # Kernels per bk_matern_tile call of the plain form: the per-launch table of
 # 2 cosh(nu h) on the quantised steps, then the symmetric tile writer.
 LAUNCHES_PER_MATRIX = 2
