@@ -220,7 +220,7 @@ __device__ __forceinline__ double exp2s(double u, const double* __restrict__ tab
 // rho 2^sh = ((sig + 2^(sh-1)) mod 2^sh) - 2^(sh-1), an integer below 2^53 in
 // magnitude, normalised into a double by its leading-bit position.  v < 1/4
 // (and 0) gives M = 0, rho = v.  Out of range (v >= 2^22) gives
-// M = 4,000,000 and rho = v, so that exp2s_node stays finite for finite
+// M = 4,000,000 and rho = v, so that exp2s_cubic stays finite for finite
 // arguments; NaN gives rho = NaN.
 __device__ __forceinline__ void round_rem(double v, int& M, double& rho) {
   const long long b = __double_as_longlong(v);
@@ -242,28 +242,6 @@ __device__ __forceinline__ void round_rem(double v, int& M, double& rho) {
     M = 4000000;
     rho = v;
   }
-}
-
-// exp2s for the node loops (every node exponent of an eps-window has
-// |u| < 3e5): the nearest integer n of u and rho = u - n come from round_rem
-// of |u| on the integer pipe (signs restored by integer operations), so that
-// only the polynomial and the final product use the FP64 pipe: 3 FP64
-// operations instead of 6.  Accurate for u in [-1022 * 4096, 1023 * 4096];
-// below, the exponent is clamped at -1022 (a result near 2^-1022), and
-// |u| >= 2^22 gives some finite value (about 2^{+-976}); NaN stays NaN.
-constexpr int kExp2sNodeOps = 3;
-__device__ __forceinline__ double exp2s_node(double u, const double* __restrict__ tab) {
-  const long long ub = __double_as_longlong(u);
-  int M;
-  double r;
-  round_rem(__longlong_as_double(ub & 0x7fffffffffffffffLL), M, r);
-  const bool neg = ub < 0;
-  const int n = neg ? -M : M;
-  const double rho = __longlong_as_double(__double_as_longlong(r) ^ (ub & (long long)0x8000000000000000ULL));
-  const double p = fma(fma(kExpK2, rho, kExpK1), rho, 1.0);
-  const double tj = tab[n & (kExpTabSize - 1)];
-  const int k = max(n >> kExpTabBits, -1022);
-  return p * __hiloint2double(__double2hiint(tj) + (k << 20), __double2loint(tj));
 }
 
 // 2^{-D/4096} for 0 <= D < 2^22 (a node loop's x cosh t in scaled units),
@@ -382,18 +360,23 @@ __device__ __forceinline__ double exp2s_cubic(double u, const double* __restrict
   return p * __hiloint2double(__double2hiint(tj) + (k << 20), __double2loint(tj));
 }
 
-// 2^{u/4096} for |u| < 4.18e6 on the integer pipe, to the accuracy of
-// exp2s_cubic: the nearest integer n of u and the remainder rho = u - n
-// (|rho| <= 1/2) taken exactly from u's significand as in exp2s_neg_int (on
-// |u|, the signs restored by integer operations), p = 2^{rho/4096} = 1 +
-// C1 rho + K2 rho^2 + C3 rho^3 (the Taylor cubic, truncation below 3e-18
-// relative) in 64-bit fixed point (C1 rho from a 64 x 64-bit high product,
-// the square and cube from the leading 32 bits of rho, their errors below
-// 2^-58), and p t_j 2^k, t_j = 2^{j/4096}, from t_j's significand as in
-// exp2s_neg_int (truncation below 2^-52 relative).  No FP64 arithmetic.
+// 2^{u/4096} on the integer pipe.  The nearest integer n of u and the
+// remainder rho = u - n (|rho| <= 1/2) are taken exactly from u's
+// significand as in exp2s_neg_int (on |u|, the signs restored by integer
+// operations); p = 2^{rho/4096} in 64-bit fixed point (C1 rho from a 64 x
+// 64-bit high product, the square and cube from the leading 32 bits of rho,
+// their errors below 2^-58); and p t_j 2^k, t_j = 2^{j/4096}, from t_j's
+// significand as in exp2s_neg_int (truncation below 2^-52 relative).  No
+// FP64 arithmetic.  kCubic: the Taylor cubic (truncation below 3e-18
+// relative; the final exponential, |u| < 4.18e6); else the minimax quadratic
+// (2.6e-14; the FP64 node loops, whose node exponents satisfy |u| < 3e5)
+// with these ranges: accurate for u in [-1022 * 4096, 1023 * 4096], the
+// exponent clamped at -1022 below, |u| >= 2^22 giving a finite value near
+// 2^{+-976}, NaN NaN.
 constexpr unsigned long long kExpC1Q75 = (unsigned long long)(kExpC1 * 0x1p75);  // exact
 constexpr unsigned long long kExpC3Q72 = (unsigned long long)(kExpC3 * 0x1p72 + 0.5);
 static_assert(kExpC1Q75 < (1ULL << 63) && kExpC3Q72 < (1ULL << 32), "fixed-point constants");
+template <bool kCubic = true>
 __device__ __forceinline__ double exp2s_int(double u, const double* __restrict__ tab) {
   const long long b = __double_as_longlong(u);
   const bool neg = (int)(b >> 32) < 0;
@@ -402,34 +385,44 @@ __device__ __forceinline__ double exp2s_int(double u, const double* __restrict__
   const int sh = 52 - min(max(e, -2), 21);  // 31 .. 54
   const long long half = 1LL << (sh - 1);
   const long long t = sig + half;
-  const int m = (int)(t >> sh);                        // round(|u|)
+  int m = (int)(t >> sh);                              // round(|u|)
   const long long R = (t & ((half << 1) - 1)) - half;  // (|u| - m) 2^sh
   long long rq = R << (63 - sh);                       // (|u| - m) 2^63
   if (e < -2) rq = (e >= -11) ? (sig << (e + 11)) : ((e > -74) ? (sig >> (-11 - e)) : 0LL);
   const bool negr = neg != (rq < 0);  // the sign of rho = u - n
   const unsigned long long ar = (unsigned long long)(rq < 0 ? -rq : rq);
-  const long long c1 = (long long)(__umul64hi(ar, kExpC1Q75) >> 12);  // C1 |rho| 2^62
-  const unsigned long long rh = ar >> 31;                             // |rho| 2^32
-  const unsigned long long r2 = (rh * rh) >> 32;                      // rho^2 2^32
-  const unsigned long long r3 = (r2 * rh) >> 32;                      // |rho|^3 2^32
-  const long long c2 = (long long)((r2 * kExpK2Q57) >> 27);           // K2 rho^2 2^62
-  const long long c3 = (long long)((r3 * kExpC3Q72) >> 42);           // C3 |rho|^3 2^62
-  const long long d = (negr ? -(c1 + c3) : (c1 + c3)) + c2;           // (p - 1) 2^62
+  const long long c1 = (long long)(__umul64hi(ar, kCubic ? kExpC1Q75 : kExpK1Q75) >> 12);
+  const unsigned long long rh = ar >> 31;         // |rho| 2^32
+  const unsigned long long r2 = (rh * rh) >> 32;  // rho^2 2^32
+  const long long c2 = (long long)((r2 * kExpK2Q57) >> 27);  // K2 rho^2 2^62
+  long long c3 = 0;
+  if constexpr (kCubic) c3 = (long long)((((r2 * rh) >> 32) * kExpC3Q72) >> 42);  // C3 |rho|^3
+  long long d = (negr ? -(c1 + c3) : (c1 + c3)) + c2;  // (p - 1) 2^62
+  const bool out = !kCubic && e > 21;  // |u| >= 2^22 (and NaN): clamp
+  if (out) {
+    m = 4000000;
+    d = 0;
+  }
   const int n = neg ? -m : m;
   const long long tb = __double_as_longlong(tab[n & (kExpTabSize - 1)]);  // t_j in [1, 2)
   const long long M = (tb & 0xfffffffffffffLL) | 0x10000000000000LL;
   const unsigned long long ad = (unsigned long long)(d < 0 ? -d : d);      // < 2^49
   const long long X = (long long)__umul64hi(ad << 2, (unsigned long long)M);
   long long Mp = M + (d < 0 ? -X : X);
-  int k = n >> kExpTabBits;
+  int k = kCubic ? (n >> kExpTabBits) : max(n >> kExpTabBits, -1022);
   if (Mp >= 0x20000000000000LL) {
     Mp = (Mp + 1) >> 1;
     ++k;
-  } else if (Mp < 0x10000000000000LL) {
+  } else if (Mp < 0x10000000000000LL && k > -1022) {
     Mp <<= 1;
     --k;
   }
-  return __longlong_as_double(((long long)(k + 1023) << 52) | (Mp & 0xfffffffffffffLL));
+  const double r = __longlong_as_double(((long long)(k + 1023) << 52) | (Mp & 0xfffffffffffffLL));
+  if constexpr (!kCubic) {
+    const bool nan = out && e == 1024 && ((((unsigned)(b >> 32)) & 0xfffffu) | (unsigned)b) != 0u;
+    return nan ? u : r;
+  }
+  return r;
 }
 
 // e^a over the whole double range for the final normalisations: u = a K
@@ -783,7 +776,7 @@ __device__ __forceinline__ NodeSum node_sum_f64(double t_start, double H, int co
   double s = 0.0, f = 0.0, ev = 0.0;
 #pragma unroll 2  // two nodes' exponentials in flight per warp (measured +0.4 % over 1 and 4)
   for (int j = 0; j < count; ++j) {
-    ev = exp2s_node(A - D0, tab);
+    ev = exp2s_int<false>(A - D0, tab);
     f = fma(ev, W, ev);
     if (j == 0) {
       r.first = f;
@@ -802,8 +795,9 @@ __device__ __forceinline__ NodeSum node_sum_f64(double t_start, double H, int co
   return r;
 }
 // FP64 ops per node in node_sum_f64 (work accounting): 1 sub (exponent),
-// exp2s_node, 1 fma + 1 add (f, s), 1 fma (recurrence), 1 add + 1 mul.
-constexpr int kNodeOps64 = 6 + kExp2sNodeOps;  // 9
+// 1 fma + 1 add (f, s), 1 fma (recurrence), 1 add + 1 mul; the exponential
+// (exp2s_int) on the integer pipe.
+constexpr int kNodeOps64 = 6;
 
 // 2 cosh v for 0 <= v <= 0.75 from its Taylor series in y = v^2 to y^9
 // (truncation < 2e-18); the terms from y^6 on (below 1.3e-10) in FP32: 7 FP64
@@ -1230,7 +1224,7 @@ __device__ __forceinline__ NodeSum3 node_sum3_f64(double t_start, double H, int 
   NodeSum3 r;
   double s = 0.0, sx = 0.0, sn = 0.0, t = t_start, ev = 0.0, f = 0.0, fx = 0.0, fn = 0.0;
   for (int j = 0; j < count; ++j) {
-    ev = exp2s_node(A - D0, tab);
+    ev = exp2s_int<false>(A - D0, tab);
     f = fma(ev, W, ev);
     fx = D0 * f;
     fn = fma(-ev, W, ev) * t;

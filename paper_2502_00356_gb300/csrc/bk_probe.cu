@@ -113,7 +113,7 @@ __global__ void math_probe_kernel(int fn, const double* __restrict__ in, double*
     switch (fn) {
       case 0: out[i] = exp_tab_full(v, tab); break;
       case 1: out[i] = log_tab(v, tab); break;
-      case 2: out[i] = exp2s_node(v, tab); break;
+      case 2: out[i] = exp2s_int<false>(v, tab); break;
       case 3: out[i] = exp2s_neg_int(v, tab); break;
       case 4: {
         int M;
