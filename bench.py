@@ -202,18 +202,31 @@ def profiled_instr():
     return rec if rec.get("kernel_hash") == kernel_hash(FP32_SOURCES) else None
 
 
-def profiled_traffic(n: int):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu
-    summary, scaled to n^2 output entries; None when the kernel changed since."""
+def _traffic_record():
+    """The committed ncu record of the dominant kernel, or None when the
+    kernel changed since it was taken."""
     path = os.path.join(ROOT, "profiles", "matern_sym_f64_traffic.json")
     try:
         with open(path) as fh:
             rec = json.load(fh)
     except (OSError, ValueError):
         return None
-    if rec.get("kernel_hash") != kernel_hash():
-        return None
-    return rec["dram_bytes_per_entry"] * n * n
+    return rec if rec.get("kernel_hash") == kernel_hash() else None
+
+
+def profiled_traffic(n: int):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, scaled to n^2 output entries; None when the kernel changed since."""
+    rec = _traffic_record()
+    return None if rec is None else rec["dram_bytes_per_entry"] * n * n
+
+
+def profiled_pipes():
+    """Pipe utilisation of the dominant kernel from the committed ncu record
+    (--set full on the n = 6000 case): the FP64 pipe, the integer ALU and
+    instruction issue, fractions of their peaks; None when the kernel changed."""
+    rec = _traffic_record()
+    return None if rec is None else rec.get("pipe_utilisation")
 
 
 # ---------------------------------------------------------------------------
@@ -895,6 +908,7 @@ def main():
                 "frac": achieved / FP64_PEAK_GOPS,
                 "peak_source": "derived: 152 SMs x 2 FP64 ops/clk x 2.07 GHz (of derived)",
                 "traffic": profiled_traffic(n),
+                "pipes_ncu": profiled_pipes(),
                 "algorithmic_fp64_ops_per_launch": flop_mean,
                 "algorithmic_bytes_per_launch": n * n * 8 + 16 * n,
                 "work": work}
