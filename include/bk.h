@@ -451,6 +451,7 @@ bk_status bk_probe_pipe(int kind, int64_t iters, int grid, int block, double* si
  *      range-checked path)
  *   9  log a from the Matern entries' log parts (nd and log1p(d) on the
  *      integer pipe), assembled as nd ln2/4096 + log1p(d), finite a > 0
+ *  10  sqrt a by the Matern entries' integer-pipe square root, a > 0
  * in: device, n doubles; out: device, n doubles (2n for fn 4).  Inputs
  * outside a function's stated domain give unspecified values (no fault).
  * Errors: BK_ERR_INVALID_ARG for an unknown fn, n < 0 or null pointers with

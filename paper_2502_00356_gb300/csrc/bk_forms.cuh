@@ -162,7 +162,7 @@ struct FormF64T {
     const double dx = b.x - a.x, dy = b.y - a.y;
     const double r2 = fma(dx, dx, dy * dy);
     if (!bits_pos(r2)) return mp.sigma2;  // r == 0 (r2 >= 0)
-    const double z = sqrt_pos(r2) * mp.inv_beta;
+    const double z = sqrt_int(r2) * mp.inv_beta;  // the root on the integer pipe
     ++evals;
     if (kSeries && z < series_below)
       return exp_tab_full(fma(mp.nu, log_tab(z, tab), mp.log_pref) + series(z, mp.nu, tl), tab);

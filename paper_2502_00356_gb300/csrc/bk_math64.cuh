@@ -94,6 +94,54 @@ __device__ __forceinline__ double sqrt_pos(double a) {
   return fma(fma(-s1, s1, a), h, s1);
 }
 
+// sqrt a for normal a > 0 without FP64 arithmetic, within an ulp (others:
+// the library root).  a = A 2^(E - 52) with E even and A in [2^52, 2^54), so
+// that sqrt a = S 2^(E/2 - 52) with S = sqrt(N), N = A 2^52, S in [2^52,
+// 2^53).  An FP32 seed (rsqrt.approx and one Newton step on a's leading 24
+// bits) gives S0 = m 2^k within about 2^-22.5; the first correction
+// (N - S0^2) / (2 S0) uses the exact 64-bit residual A - m^2 2^(2k - 52) and
+// is taken in FP32 (S1 within about 2^9); the second uses N - S1^2 computed
+// exactly as a 128-bit difference (below 2^63 in magnitude), its leading bits
+// in FP32.  The bounds were checked by an exact emulation with the hardware
+// approximations perturbed by their full error (72,000 cases).
+__device__ __forceinline__ double sqrt_int(double a) {
+  const long long b = __double_as_longlong(a);
+  const int ea = (int)((b >> 52) & 0x7ff) - 1023;
+  if (ea == -1023 || ea == 1024) return sqrt(a);  // zero, subnormal, inf, NaN
+  const int odd = ea & 1;
+  const int E = ea - odd;  // even
+  const unsigned long long A = ((unsigned long long)(b & 0xfffffffffffffLL) | (1ULL << 52)) << odd;
+  const float af = __uint2float_rn((unsigned)(A >> 30)) * 0x1p-22f;  // exact, in [1, 4)
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(af));
+  y = y * fmaf(-0.5f * af, y * y, 1.5f);
+  const unsigned sb = __float_as_uint(af * y);  // sqrt(A 2^-52), about [1, 2)
+  const int es = (int)((sb >> 23) & 0xff) - 127;
+  const unsigned m24 = (sb & 0x7fffffu) | 0x800000u;
+  const int k = 29 + es;  // S0 = m24 2^k
+  const unsigned long long mm = (unsigned long long)m24 * m24;
+  const int sh2 = 2 * k - 52;  // 6 + 2 es
+  const long long R0 = (long long)A - (long long)(sh2 >= 0 ? (mm << sh2) : (mm >> -sh2));
+  float inv;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"(__uint2float_rn(m24)));
+  // c0 = R0 2^52 / (2 m24 2^k) = R0 inv 2^(51 - k), |R0| < 2^33, |c0| < 2^31
+  const float c0f = __int2float_rn((int)(R0 >> 3)) * inv * __int_as_float((51 - k + 3 + 127) << 23);
+  const unsigned long long S1 =
+      ((unsigned long long)m24 << k) + (unsigned long long)((long long)__float2int_rn(c0f * 0x1p-4f) * 16);
+  // N - S1^2 as a 128-bit difference
+  const unsigned long long Nlo = A << 52, Nhi = A >> 12;
+  const unsigned long long Plo = S1 * S1, Phi = __umul64hi(S1, S1);
+  const unsigned long long Rlo = Nlo - Plo;
+  const unsigned long long Rhi = Nhi - Phi - (Nlo < Plo ? 1ULL : 0ULL);
+  const long long t = (long long)((Rhi << 32) | (Rlo >> 32));  // (N - S1^2) 2^-32
+  float rs;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rs) : "f"(__uint2float_rn((unsigned)(S1 >> 29))));
+  // c1 = (N - S1^2) / (2 S1) = t 2^32 rs 2^-29 / 2
+  const float c1f = __int2float_rn((int)(t >> 3)) * rs * 32.0f;
+  const long long S2 = (long long)S1 + __float2int_rn(c1f);
+  return __longlong_as_double(((long long)(E / 2 + 1023) << 52) + (S2 - (1LL << 52)));
+}
+
 __device__ __forceinline__ double pow2i(int k) {  // 2^k for k in [-1022, 1023]
   return __hiloint2double((k + 1023) << 20, 0);
 }

@@ -127,6 +127,7 @@ __global__ void math_probe_kernel(int fn, const double* __restrict__ in, double*
       case 6: out[i] = sqrt_pos(v); break;
       case 7: out[i] = exp_acc(v, tab); break;
       case 8: out[i] = exp_units_full(v * kExpScale, tab); break;
+      case 10: out[i] = sqrt_int(v); break;
       default: {
         double nd;
         const double l1p = log_tab_parts(v, tab, nd);
@@ -160,7 +161,7 @@ extern "C" bk_status bk_probe_pipe(int kind, int64_t iters, int grid, int block,
 extern "C" bk_status bk_math_probe(int fn, const double* in, double* out, int64_t n,
                                    bk_stream_t stream) {
   using namespace bk;
-  if (fn < 0 || fn > 9) return set_error(BK_ERR_INVALID_ARG, "bk_math_probe: unknown fn %d", fn);
+  if (fn < 0 || fn > 10) return set_error(BK_ERR_INVALID_ARG, "bk_math_probe: unknown fn %d", fn);
   if (n < 0 || (n > 0 && (in == nullptr || out == nullptr)))
     return set_error(BK_ERR_INVALID_ARG, "bk_math_probe: bad arguments");
   if (n == 0) return BK_OK;

@@ -167,6 +167,23 @@ def test_seeded_square_root(dev):
     assert np.all(np.abs(got - want) <= ulp), np.max(np.abs(got - want) / ulp)
 
 
+def test_integer_square_root(dev):
+    """The Matern entries' square root on the integer pipe (an FP32 seed,
+    one correction from an exact 64-bit residual, one from an exact 128-bit
+    residual): within an ulp on the whole normal range, both exponent
+    parities and the significand ends."""
+    rng = np.random.default_rng(68)
+    a = np.concatenate([np.exp(rng.uniform(-700, 700, 3000)), np.exp(rng.uniform(-5, 5, 2000)),
+                        (1 + rng.uniform(0, 1e-12, 300)) * 2.0 ** rng.integers(-60, 60, 300),
+                        (4 - rng.uniform(0, 1e-12, 300)) * 2.0 ** rng.integers(-60, 60, 300),
+                        [2.0**-1022, 1.7976931348623157e308, 2.0, 0.5, 1.0, 4.0, 3.9999999999999996,
+                         1.0000000000000002, 5e-324, 1e-310]])
+    got = probe("sqrt_int", a, dev)
+    want = np.sqrt(a)
+    ulp = np.spacing(want)
+    assert np.all(np.abs(got - want) <= ulp), np.max(np.abs(got - want) / ulp)
+
+
 def test_setup_exponential(dev):
     rng = np.random.default_rng(67)
     a = np.concatenate([rng.uniform(-707, 707, 1000), rng.uniform(-1, 1, 300), [0.0]])
