@@ -64,13 +64,15 @@ __device__ __forceinline__ double eval_domain(const Form& form, double x, double
 // and cosh stay accurate; none outside (the FP64 search then starts from
 // its own bounds).  Its iterations are FP32 work and are not tallied: the
 // plain form's counters count FP64 Newton iterations.
-__device__ __forceinline__ const Start32* plain_starts(double x, float nu, Start32& st) {
-  const float xf = f32_trunc(x);
+__device__ __forceinline__ const Start32* plain_starts_f(float xf, float nu, Start32& st) {
   if (!(xf >= 1e-4f && xf <= 1e4f && nu <= 40.0f)) return nullptr;
   Tally fp32_work{0u, 0u, 0u, 0u, 0u, 0u, 0u};
   const Window32 w = window_f32(xf, nu, (float)kLogInvEps64, fp32_work);
   st = Start32{w.ts, w.t0, w.t1, w.cs};
   return &st;
+}
+__device__ __forceinline__ const Start32* plain_starts(double x, float nu, Start32& st) {
+  return plain_starts_f(f32_trunc(x), nu, st);
 }
 
 // Every form carries `tab`, the 2^{j/4096} table of exp2s.  All forms read
@@ -123,7 +125,8 @@ struct FormF64T {
     Start32 st;
     const Start32* sp = search_f64 ? nullptr : plain_starts(x, f32_trunc(nu), st);
     double hS;
-    const double sc = scale_f64(x, nu, kPlainLog2OverTol, kPlainMaxNodes, tab, hS, tl, sp);
+    const double sc =
+        scale_f64((0.5 * kExpScale) * x, nu, kPlainLog2OverTol, kPlainMaxNodes, tab, hS, tl, sp);
     if (!want_log && (__double2hiint(sc) | __double2loint(sc)) == 0) return hS;  // t0 = 0
     const bool big = !bits_le(sc, 700.0);
     const double lh = (want_log || big) ? log_tab(hS, tab) : 0.0;
@@ -156,28 +159,35 @@ struct FormF64T {
 
   // a2 + a3..a7 for one entry: distance, x = r / beta, log K_nu(x),
   // M = exp(log prefactor + nu log x + log K).  sigma^2 where r == 0
-  // (Algorithm 3 tests the computed distance for exact zero).
+  // (Algorithm 3 tests the computed distance for exact zero).  x is carried
+  // as xh = x K/2 (K = 4096/ln 2), the node loop's half-scaled argument, from
+  // one product and the integer-pipe root: xh = sqrt(r^2 xh_c2) with the
+  // matrix's constant xh_c2 = (K/2 / beta)^2.
   __device__ __forceinline__ double matern(const Loc& a, const Loc& b, const MaternParams& mp,
                                            Tally& tl, unsigned& evals) const {
     const double dx = b.x - a.x, dy = b.y - a.y;
     const double r2 = fma(dx, dx, dy * dy);
     if (!bits_pos(r2)) return mp.sigma2;  // r == 0 (r2 >= 0)
-    const double z = sqrt_int(r2) * mp.inv_beta;  // the root on the integer pipe
+    const double xh = sqrt_int(r2 * mp.xh_c2);
     ++evals;
-    if (kSeries && z < series_below)
-      return exp_tab_full(fma(mp.nu, log_tab(z, tab), mp.log_pref) + series(z, mp.nu, tl), tab);
+    if constexpr (kSeries) {
+      const double z = xh * kTwoOverK;
+      if (z < series_below)
+        return exp_tab_full(fma(mp.nu, log_tab(z, tab), mp.log_pref) + series(z, mp.nu, tl), tab);
+    }
     Start32 st;
-    const Start32* sp = search_f64 ? nullptr : plain_starts(z, mp.nu_hi, st);
+    const Start32* sp =
+        search_f64 ? nullptr : plain_starts_f(f32_trunc(xh) * (float)kTwoOverK, mp.nu_hi, st);
     double hS;
-    const double sc = scale_f64(z, mp.nu, kPlainLog2OverTol, kPlainMaxNodes, tab, hS, tl, sp, cnu);
-    // exp(a1 + nu log z + sc) hS with the exponent formed in the table's
-    // units, u = (a1 + sc) K + nu (nd + K log1p(d)) for log z = nd ln2/4096 +
-    // log1p(d) (K = 4096/ln 2 folded into nu_k and log_pref_k; the log's
-    // parts from the integer pipe): two FMAs, and a third only for windows
-    // that do not start at t = 0 (sc != 0)
+    const double sc = scale_f64(xh, mp.nu, kPlainLog2OverTol, kPlainMaxNodes, tab, hS, tl, sp, cnu);
+    // exp(a1 + nu log x + sc) hS with the exponent formed in the table's
+    // units: log x = log(xh 2^-12) + ln(2 ln 2), log(xh 2^-12) = nd ln2/4096 +
+    // log1p(d) from the integer pipe, so u = K (a1 + nu ln(2 ln 2)) + nu nd +
+    // nu K log1p(d) + K sc (the constant per matrix): two FMAs, and a third
+    // only for windows that do not start at t = 0 (sc != 0)
     double nd;
-    const double l1p = log_tab_parts(z, tab, nd);
-    double u = fma(mp.nu, nd, fma(mp.nu_k, l1p, mp.log_pref_k));
+    const double l1p = log_tab_parts(xh, tab, nd, -12);
+    double u = fma(mp.nu_k, l1p, fma(mp.nu, nd, mp.log_pref_kh));
     if ((__double2hiint(sc) | __double2loint(sc)) != 0) u = fma(sc, kExpScale, u);
     return exp_units_full(u, tab) * hS;
   }

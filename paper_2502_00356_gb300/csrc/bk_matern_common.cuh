@@ -29,7 +29,9 @@ __device__ __forceinline__ double matern_log_prefactor(double sigma2, double nu)
 // Per-matrix constants of one Matern launch (a1 and the order split).
 struct MaternParams {
   double sigma2, beta, nu, log_pref, inv_beta;
-  double nu_k, log_pref_k;         // nu and a1 times 4096/ln 2 (exp_units_full's units)
+  double nu_k;                     // nu times K = 4096/ln 2 (exp_units_full's units)
+  double log_pref_kh;              // K (a1 + nu ln(2 ln 2)): the exponent's constant for log(xh 2^-12)
+  double xh_c2;                    // (K/2 / beta)^2: xh = x K/2 = sqrt(r^2 xh_c2)
   float inv_beta_f, nu_hi, nu_lo;  // nu = nu_hi + nu_lo (two floats)
   float inv_beta_lo;               // 1/beta = inv_beta_f + inv_beta_lo
   float log_pref_hi, log_pref_lo;  // a1 as two floats
@@ -44,8 +46,10 @@ __device__ __forceinline__ MaternParams matern_params(double sigma2, double beta
   p.nu = nu;
   p.log_pref = matern_log_prefactor(sigma2, nu);
   p.nu_k = nu * kExpScale;
-  p.log_pref_k = p.log_pref * kExpScale;
+  p.log_pref_kh = fma(nu, 0.32663425997828094, p.log_pref) * kExpScale;  // ln(2 ln 2)
   p.inv_beta = 1.0 / beta;
+  const double hb = (0.5 * kExpScale) * p.inv_beta;
+  p.xh_c2 = hb * hb;
   p.inv_beta_f = (float)p.inv_beta;
   p.nu_hi = (float)nu;
   p.nu_lo = (float)(nu - (double)p.nu_hi);
@@ -69,8 +73,10 @@ inline MaternParams matern_params_host(double sigma2, double beta, double nu) {
   p.nu = nu;
   p.log_pref = (sigma2 > 0.0 ? std::log(sigma2) : -kInf) - (nu - 1.0) * kLn2 - std::lgamma(nu);
   p.nu_k = nu * kExpScale;
-  p.log_pref_k = p.log_pref * kExpScale;
+  p.log_pref_kh = std::fma(nu, std::log(2.0 * kLn2), p.log_pref) * kExpScale;
   p.inv_beta = 1.0 / beta;
+  const double hb = (0.5 * kExpScale) * p.inv_beta;
+  p.xh_c2 = hb * hb;
   p.inv_beta_f = (float)p.inv_beta;
   p.nu_hi = (float)nu;
   p.nu_lo = (float)(nu - (double)p.nu_hi);

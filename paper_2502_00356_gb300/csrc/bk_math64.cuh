@@ -537,9 +537,10 @@ __device__ __forceinline__ double log_tab(double a, const double* __restrict__ t
 // and of 2^{(4096-j)/4096} by a 64 x 64-bit high product (exact to 2^-62), the
 // series d - d^2/2 + d^3/3 (truncation below 2e-17 absolute) in 64-bit fixed
 // point, and l1p rounded to a double from its leading bit.  Subnormal a is
-// scaled as in log_tab.
+// scaled as in log_tab.  eoff: the parts of log(a 2^eoff) (nd shifted by
+// 4096 eoff, exactly).
 __device__ __forceinline__ double log_tab_parts(double a, const double* __restrict__ tab,
-                                                double& nd) {
+                                                double& nd, int eoff = 0) {
   int hi = __double2hiint(a);
   int lo = __double2loint(a);
   int e = 0;
@@ -555,7 +556,7 @@ __device__ __forceinline__ double log_tab_parts(double a, const double* __restri
   float l2;
   asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l2) : "f"(mf));
   const int j = __float2int_rn(l2 * (float)kExpTabSize);  // 0..4096
-  nd = widen_f(__int2float_rn(e * kExpTabSize + j));
+  nd = widen_f(__int2float_rn((e + eoff) * kExpTabSize + j));  // of a 2^eoff
   const unsigned long long Mm = ((unsigned long long)(unsigned)(mh | 0x00100000) << 32) | (unsigned)lo;
   long long dq;  // d 2^62
   if (j > 0) {
@@ -939,10 +940,9 @@ struct NodeSumC {
 // the end nodes are folded into their terms (at t_start = 0, C_0/2 = 1), and
 // the end terms' logs for the window check come from the factors on the
 // FP32/integer pipes, so the ends cost no extra FP64 products.
-__device__ __forceinline__ NodeSumC node_sum_cosh(double t_start, double H, int count, double x,
+__device__ __forceinline__ NodeSumC node_sum_cosh(double t_start, double H, int count, double xh,
                                                   double nu, const double* __restrict__ tab,
                                                   int cosh_idx, const double* __restrict__ cnu) {
-  const double xh = (0.5 * kExpScale) * x;
   const bool start_pos = bits_pos(t_start);
   double c, D0, D1, cn, C0, C1, C0h = 1.0;
   if (start_pos) {
@@ -1149,9 +1149,11 @@ __device__ __forceinline__ double take_search(const Scaled64& r, double& hS, Tal
   return r.scale;
 }
 
-// The plain form's K_nu in scaled form: returns the scale and sets hS
-// (K = e^{scale} hS; on the checked windows hS holds the step halved, and
-// the scale is 0 for windows that start at t = 0).  With FP32 start values (st) the window is taken from
+// The plain form's K_nu in scaled form for x = xh 2/K (xh = x 2048/ln 2,
+// the node loop's half-scaled argument, which the callers form directly):
+// returns the scale and sets hS (K = e^{scale} hS; on the checked windows hS
+// holds the step halved, and the scale is 0 for windows that start at
+// t = 0).  With FP32 start values (st) the window is taken from
 // them (the ends widened as in window_from_start) and checked on the
 // computed end nodes against the rule of window_f64, whose F bounds these
 // from above: e(t1) <= eps and, for t0 > 0, 2 e(t0) <= eps, where e(t) =
@@ -1166,12 +1168,14 @@ __device__ __forceinline__ double take_search(const Scaled64& r, double& hS, Tal
 //    2^{3e-4}.
 //  - node_sum_f64 elsewhere (centred at t*, cosh t* in FP64): scale
 //    nu t* - x cosh t* - ln 2, the check on its FP64 end values.
-__device__ __forceinline__ double scale_f64(double x, double nu, float log2_over_tol, int n_max,
+constexpr double kTwoOverK = 2.0 / kExpScale;  // x = xh 2/K (ln2 / 2048)
+__device__ __forceinline__ double scale_f64(double xh, double nu, float log2_over_tol, int n_max,
                                             const double* __restrict__ tab, double& hS,
                                             Tally& tl, const Start32* st = nullptr,
                                             const double* __restrict__ cnu = nullptr) {
   constexpr double kEps64 = 0x1p-52;
-  if (st == nullptr) return take_search(scaled_search_f64(x, nu, log2_over_tol, n_max, tab), hS, tl);
+  if (st == nullptr)
+    return take_search(scaled_search_f64(xh * kTwoOverK, nu, log2_over_tol, n_max, tab), hS, tl);
   // The window's geometry in FP32, taken exactly to FP64: the ends widened by
   // 2e-5 relative and 1e-5 absolute (as window_from_start), h = (t1 - t0)/N
   // rounded up to 8 significand bits (quantise_step, so that 2 cosh h comes
@@ -1181,7 +1185,7 @@ __device__ __forceinline__ double scale_f64(double x, double nu, float log2_over
   const float t1f = fmaf(st->t1, 2e-5f, st->t1) + 1e-5f;
   const float t0f = (st->t0 > 0.0f && st->ts > 0.0f) ? fmaxf(0.0f, fmaf(st->t0, -2e-5f, st->t0) - 1e-5f)
                                                      : 0.0f;
-  const float xf = f32_trunc(x), nuf = f32_trunc(nu), wf = t1f - t0f;
+  const float xf = f32_trunc(xh) * (float)kTwoOverK, nuf = f32_trunc(nu), wf = t1f - t0f;
   const int N = strip_node_count(xf, nuf, wf, log2_over_tol, n_max);
   if (N <= n_max) {
     int cosh_idx;
@@ -1190,7 +1194,7 @@ __device__ __forceinline__ double scale_f64(double x, double nu, float log2_over
     const double t0 = widen_f(t0f), h = widen_f(hq);
     tl.nodes += N + 1;
     if (cosh_loop_ok(xf, nuf, t0f, tnf, N)) {
-      const NodeSumC ns = node_sum_cosh(t0, h, N + 1, x, nu, tab, cosh_idx, cnu);
+      const NodeSumC ns = node_sum_cosh(t0, h, N + 1, xh, nu, tab, cosh_idx, cnu);
       constexpr float kL2e = 1.44269504f;
       const float G = fmaf(nuf, st->ts - t0f, -xf * st->cs) * kL2e;  // log2 of the peak term
       float w1;
@@ -1212,6 +1216,7 @@ __device__ __forceinline__ double scale_f64(double x, double nu, float log2_over
         return bits_pos(t0) ? nu * t0 : 0.0;
       }
     } else {
+      const double x = xh * kTwoOverK;
       Window64 w;
       w.ts = widen_f(st->ts);  // 0 when the FP32 search found nu^2 <= x
       if (st->ts > 0.0f) {
@@ -1231,7 +1236,7 @@ __device__ __forceinline__ double scale_f64(double x, double nu, float log2_over
     }
   }
   ++tl.fallback;
-  return take_search(scaled_search_f64(x, nu, log2_over_tol, n_max, tab), hS, tl);
+  return take_search(scaled_search_f64(xh * kTwoOverK, nu, log2_over_tol, n_max, tab), hS, tl);
 }
 
 // ---------------------------------------------------------------------------
