@@ -35,21 +35,22 @@ N_LOC, BETA, SIGMA2, NUS, SEED = 20_000, 0.1, 1.0, (0.5, 1.5, 2.3), 2
 WORKLOAD = "matern_jittered_grid_n20000_beta0.1_nu{0.5,1.5,2.3}_fp64"
 
 # FP64 work model of the plain form in FP64 arithmetic operations (one per
-# thread and DFMA/DADD/DMUL): 3 per quadrature node of the common loop (the
-# summing FMA and the two three-term recurrences; the node's exponential,
-# polynomial and table product included, runs on the integer pipe; windows
-# outside that loop's conditions take 9 and are counted at 3), per FP64 peak
-# Newton iteration and per FP64 window-end Newton iteration (these run only
-# for windows the check rejects, or outside the FP32 search region), and a
-# fixed part per Matern entry (the distance, r^2 times the matrix's
-# constant, set-ups, the end terms' scaling, the exponent's FMAs; the square
-# root, log x and the final exponential run on the integer pipe).  The fixed
-# part is ncu's executed DFMA + DADD + DMUL per evaluation minus 3 x nodes
-# per evaluation on the n = 6000 case of the same kernel (--profile-case
-# plain_nus: 10.89 for each of nu = 0.5, 1.5, 2.3).
+# thread and DFMA/DADD/DMUL): 2 per quadrature node of the common loop (the
+# summing FMA and the three-term recurrence of x cosh t; the node's
+# exponential, the factor e^{nu t} in its exponent and the geometric factor
+# 1 + e^{-2 nu t} run on the integer pipe; windows outside that loop's
+# conditions take 9 and are counted at 2), per FP64 peak Newton iteration and
+# per FP64 window-end Newton iteration (these run only for windows the check
+# rejects, or outside the FP32 search region), and a fixed part per Matern
+# entry (the distance, r^2 times the matrix's constant, set-ups, the
+# exponent step K nu h, the end terms' scaling, the exponent's FMAs; the
+# square root, log x and the final exponential run on the integer pipe).  The
+# fixed part is ncu's executed DFMA + DADD + DMUL per evaluation minus 2 x
+# nodes per evaluation on the n = 6000 case of the same kernel
+# (--profile-case plain_nus: 14.89 for each of nu = 0.5, 1.5, 2.3).
 # The FP32 Newton iterations that place the window and the FP32 window check
 # run on the FP32/MUFU pipes and are not counted.
-OPS_NODE, OPS_PEAK_IT, OPS_WIN_IT, OPS_ENTRY_FIXED = 3, 54, 31, 10.9
+OPS_NODE, OPS_PEAK_IT, OPS_WIN_IT, OPS_ENTRY_FIXED = 2, 54, 31, 14.9
 # Kernels per bk_matern_tile call of the plain form: the per-launch table of
 # 2 cosh(nu h) on the quantised steps, then the symmetric tile writer.
 LAUNCHES_PER_MATRIX = 2

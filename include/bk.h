@@ -107,8 +107,9 @@ typedef struct {
   /* Optional device scratch of BK_COSH_TABLE_LEN doubles for the plain
      form's Matern writers (bk_matern_tile_ex, bk_matern_tile2 with compute
      BK_F64 and the searched window): each call first fills it, on its
-     stream, with 2 cosh(nu h) over the quantised quadrature steps of the
-     node loop, a per-call table that saves about 6 FP64 operations per
+     stream, with e^{-2 nu h} over the quantised quadrature steps of the
+     node loop (the ratio of its geometric factor e^{-2 nu t_j}), a per-call
+     table that saves an accurate exponential (about 9 FP64 operations) per
      entry.  Caller-owned; one buffer must not serve two calls that can
      overlap on the GPU.  NULL (default): the kernels compute the values.
      No call allocates either way. */
@@ -440,7 +441,8 @@ bk_status bk_probe_pipe(int kind, int64_t iters, int grid, int block, double* si
  *      the range-checked path)
  *   1  log a for finite a > 0 (subnormals included)
  *   2  2^{u/4096} by the centred node loop's exponential, |u| < 2^22
- *   3  2^{-D/4096} by the uncentred node loop's exponential, 0 <= D < 2^22
+ *   3  2^{-D/4096} by the uncentred node loop's exponential of a node
+ *      exponent in fixed point (fix40_node, exp2s_fix), 0.25 <= D < 2^22
  *   4  round(v) and v - round(v) for 0 <= v < 2^22 (halves round up), taken
  *      on the integer pipe: out[2i] = round(v), out[2i + 1] = the remainder
  *   5  2 cosh v for v >= 0 (the series tiers and the exponential path)
@@ -452,6 +454,12 @@ bk_status bk_probe_pipe(int kind, int64_t iters, int grid, int block, double* si
  *   9  log a from the Matern entries' log parts (nd and log1p(d) on the
  *      integer pipe), assembled as nd ln2/4096 + log1p(d), finite a > 0
  *  10  sqrt a by the Matern entries' integer-pipe square root, a > 0
+ *  11  2^{-U/4096} by the same exponential for U = round(a 2^40) 2^-40,
+ *      -4.09e6 < a < 4.09e6 (signed: the node loop's D_j - G_j)
+ *  12  1 + w by the node loop's fixed-point geometric factor (w in units of
+ *      2^-63, truncated, then rounded to a double), 0 <= w <= 1
+ *  13  r truncated to units of 2^-64 (clamped below 2^64), as a double,
+ *      0 <= r <= 1
  * in: device, n doubles; out: device, n doubles (2n for fn 4).  Inputs
  * outside a function's stated domain give unspecified values (no fault).
  * Errors: BK_ERR_INVALID_ARG for an unknown fn, n < 0 or null pointers with

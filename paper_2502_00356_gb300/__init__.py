@@ -484,7 +484,8 @@ def bk_probe_pipe(kind: int, iters: int, grid: int, block: int, sink, stream=Non
 
 MATH_PROBE_FNS = {"exp": 0, "log": 1, "exp2s_node": 2, "exp2s_neg": 3, "round_rem": 4,
                   "two_cosh": 5, "sqrt": 6, "exp_acc": 7, "exp_units": 8,
-                  "log_parts": 9, "sqrt_int": 10}
+                  "log_parts": 9, "sqrt_int": 10, "exp2s_fix": 11, "one_plus_w": 12,
+                  "fix64": 13}
 
 
 def bk_math_probe(fn, x, stream=None):

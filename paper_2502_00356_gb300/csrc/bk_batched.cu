@@ -43,7 +43,7 @@ struct BatchSmem {
   OutT* out;
   int64_t n, ld, item;
   MaternParams mp;
-  const double* cnu;  // the instance's 2 cosh(nu h) table, or null
+  const double* wnu;  // the instance's table of e^{-2 nu h}, or null
 };
 
 // Persistent kernel: each CTA repeatedly takes `chunk` consecutive tiles from
@@ -52,7 +52,7 @@ template <class Form, typename OutT, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, Form::kMinBlocks * 8 / WARPS) matern_batched_kernel(
     const Form form, const bk_matern_desc* __restrict__ descs, int count, const int64_t* __restrict__ prefix,
     const int64_t* __restrict__ sizes, int64_t limit, unsigned long long* __restrict__ next,
-    int chunk, unsigned long long* __restrict__ ctr, const double* __restrict__ cnu_tabs) {
+    int chunk, unsigned long long* __restrict__ ctr, const double* __restrict__ wnu_tabs) {
   __shared__ BatchSmem<OutT> sm;
   __shared__ double s_tab[Form::kStageTable ? kExpTabSize : 1];
   const Form f = bind_table(form, s_tab);
@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(WARPS * 32, Form::kMinBlocks * 8 / WARPS) mate
           sm.n = d.n;
           sm.ld = d.ld;
           sm.mp = matern_params(d.sigma2, d.beta, d.nu);  // a1, once per instance run
-          sm.cnu = (cnu_tabs != nullptr) ? cnu_tabs + (int64_t)k * kCoshTabSize : nullptr;
+          sm.wnu = (wnu_tabs != nullptr) ? wnu_tabs + (int64_t)k * kCoshTabSize : nullptr;
         }
         __syncthreads();
         cur = k;
@@ -92,9 +92,9 @@ __global__ void __launch_bounds__(WARPS * 32, Form::kMinBlocks * 8 / WARPS) mate
       int64_t I, J;
       tri_tile(w - __ldg(prefix + k), I, J);
       __syncthreads();
-      if constexpr (Form::kCoshNuTable) {
+      if constexpr (Form::kDecayTable) {
         Form fk = f;
-        fk.cnu = sm.cnu;
+        fk.wnu = sm.wnu;
         sym_tile<Form, OutT, WARPS>(fk, sm.tile, sm.locs, sm.n, I, J, sm.mp, sm.out, sm.ld, tl,
                                     evals);
       } else {
@@ -106,16 +106,16 @@ __global__ void __launch_bounds__(WARPS * 32, Form::kMinBlocks * 8 / WARPS) mate
   flush_tally(ctr, tl, evals);
 }
 
-// Fills each instance's table of 2 cosh(nu h) on kCoshTab's steps from its
+// Fills each instance's table of e^{-2 nu h} on kCoshTab's steps from its
 // descriptor's nu (instances with a bad descriptor are skipped by the tile
 // kernel whatever their table holds).
-__global__ void __launch_bounds__(256) batched_cosh_nu_kernel(const bk_matern_desc* __restrict__ descs,
+__global__ void __launch_bounds__(256) batched_decay_kernel(const bk_matern_desc* __restrict__ descs,
                                                               int count, double* __restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (int64_t)count * kCoshTabSize) return;
   const int k = (int)(i / kCoshTabSize), j = (int)(i % kCoshTabSize);
   const double nu = descs[k].nu;
-  out[i] = cosh_nu_entry(nu > 0.0 ? nu : 0.0, j, kExp2Tab);
+  out[i] = decay_entry(nu > 0.0 ? nu : 0.0, j, kExp2Tab);
 }
 
 }  // namespace bk
@@ -132,7 +132,7 @@ struct bk_plan {
   int64_t* d_prefix;               // count + 1 tile offsets (device)
   int64_t* d_sizes;                // count instance sizes (device)
   unsigned long long* d_next;      // tile counter (device scratch)
-  double* d_cnu;                   // count x kCoshTabSize: 2 cosh(nu h) per instance, or null
+  double* d_wnu;                   // count x kCoshTabSize: e^{-2 nu h} per instance, or null
   int warps, ctas_per_sm, chunk;   // launch shape
   int tuned;                       // 1 when the shape came from the autotuner or its cache
   double tuned_ms;
@@ -167,7 +167,7 @@ cudaError_t launch_batched_t(const bk_plan* p, const bk_matern_desc* d, int64_t 
   const int grid = current_sm_count() * ctas_per_sm;
   matern_batched_kernel<Form, OutT, WARPS><<<grid, WARPS * 32, 0, s>>>(
       make_form<Form>(p), d, p->count, p->d_prefix, p->d_sizes, limit, p->d_next, chunk, p->opts.d_counters,
-      Form::kCoshNuTable ? p->d_cnu : nullptr);
+      Form::kDecayTable ? p->d_wnu : nullptr);
   return cudaGetLastError();
 }
 
@@ -182,9 +182,9 @@ cudaError_t launch_batched(const bk_plan* p, const bk_matern_desc* d, int64_t li
                            int ctas_per_sm, int chunk, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(p->d_next, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  if (p->d_cnu != nullptr) {
+  if (p->d_wnu != nullptr) {
     const int64_t cells = (int64_t)p->count * kCoshTabSize;
-    batched_cosh_nu_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, s>>>(d, p->count, p->d_cnu);
+    batched_decay_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, s>>>(d, p->count, p->d_wnu);
   }
   const bool f64 = (p->opts.compute == BK_F64);
   const bool learned = (p->opts.window == BK_WIN_LEARNED);
@@ -351,7 +351,7 @@ bk_status bk_batched_plan_create(bk_plan** plan, const int64_t* sizes, int32_t c
   p->d_prefix = nullptr;
   p->d_sizes = nullptr;
   p->d_next = nullptr;
-  p->d_cnu = nullptr;
+  p->d_wnu = nullptr;
   p->warps = 8;
   p->chunk = 1;
   p->tuned = 0;
@@ -365,14 +365,14 @@ bk_status bk_batched_plan_create(bk_plan** plan, const int64_t* sizes, int32_t c
                    cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(p->d_sizes, sizes, (size_t)count * sizeof(int64_t), cudaMemcpyHostToDevice);
-  // per-instance tables of 2 cosh(nu h) for the searched-window FP64 forms
+  // per-instance tables of e^{-2 nu h} for the searched-window FP64 forms
   // (without them, or for more than 4,096 instances, the kernel computes the
   // values itself)
   if (e == cudaSuccess && o.compute == BK_F64 && o.window != BK_WIN_FIXED &&
       o.window != BK_WIN_LEARNED && count <= 4096) {
-    if (cudaMalloc((void**)&p->d_cnu, (size_t)count * kCoshTabSize * sizeof(double)) != cudaSuccess) {
+    if (cudaMalloc((void**)&p->d_wnu, (size_t)count * kCoshTabSize * sizeof(double)) != cudaSuccess) {
       (void)cudaGetLastError();
-      p->d_cnu = nullptr;
+      p->d_wnu = nullptr;
     }
   }
   if (e != cudaSuccess) {
@@ -404,7 +404,7 @@ bk_status bk_batched_plan_destroy(bk_plan* plan) {
   cudaFree(plan->d_prefix);
   cudaFree(plan->d_sizes);
   cudaFree(plan->d_next);
-  cudaFree(plan->d_cnu);
+  cudaFree(plan->d_wnu);
   delete plan;
   return BK_OK;
 }

@@ -94,8 +94,8 @@ struct FormF64T {
   const double* tab;
   bool search_f64;      // FP64 Newton search for every point (no FP32 roots)
   double series_below;  // x below which Temme's series replaces the integral (0: never)
-  const double* cnu = nullptr;  // 2 cosh(nu h) on kCoshTab's steps for the launch's nu, or null
-  static constexpr bool kCoshNuTable = true;
+  const double* wnu = nullptr;  // e^{-2 nu h} on kCoshTab's steps for the launch's nu, or null
+  static constexpr bool kDecayTable = true;
 
   // The bare evaluations' cost bucket (sort_chunk): an estimate of the node
   // count from the arguments alone (eval_cost_bucket), and 0 for the series.
@@ -179,7 +179,7 @@ struct FormF64T {
     const Start32* sp =
         search_f64 ? nullptr : plain_starts_f(f32_trunc(xh) * (float)kTwoOverK, mp.nu_hi, st);
     double hS;
-    const double sc = scale_f64(xh, mp.nu, kPlainLog2OverTol, kPlainMaxNodes, tab, hS, tl, sp, cnu);
+    const double sc = scale_f64(xh, mp.nu, kPlainLog2OverTol, kPlainMaxNodes, tab, hS, tl, sp, wnu);
     // exp(a1 + nu log x + sc) hS with the exponent formed in the table's
     // units: log x = log(xh 2^-12) + ln(2 ln 2), log(xh 2^-12) = nd ln2/4096 +
     // log1p(d) from the integer pipe, so u = K (a1 + nu ln(2 ln 2)) + nu nd +
@@ -218,7 +218,7 @@ struct FormF64Fixed {
   static constexpr int kTilesPerBlock = 1;
   static constexpr int kMinBlocks = 3;
   static constexpr bool kFloatEval = false;
-  static constexpr bool kCoshNuTable = false;
+  static constexpr bool kDecayTable = false;
   const double* tab;
   double t1;
   int bins;
@@ -472,7 +472,7 @@ struct FormF32 {
   static constexpr int kTilesPerBlock = 4;
   static constexpr int kMinBlocks = 4;
   static constexpr bool kFloatEval = true;
-  static constexpr bool kCoshNuTable = false;
+  static constexpr bool kDecayTable = false;
   static constexpr bool kChecked = false;  // the searched window needs no check
   const double* tab;
 
@@ -531,7 +531,7 @@ struct FormF32Learned {
   static constexpr int kTilesPerBlock = 4;
   static constexpr int kMinBlocks = 4;
   static constexpr bool kFloatEval = true;
-  static constexpr bool kCoshNuTable = false;
+  static constexpr bool kDecayTable = false;
   static constexpr bool kChecked = true;  // quadratures of predicted windows are checked
   LearnedView lv;
   const double* tab;

@@ -292,75 +292,103 @@ __device__ __forceinline__ void round_rem(double v, int& M, double& rho) {
   }
 }
 
-// 2^{-D/4096} for 0 <= D < 2^22 (a node loop's x cosh t in scaled units),
-// times 2^kAdj, computed on the integer pipe without FP64 arithmetic.  The
-// rounding m = round(D) and the remainder rho = D - m (|rho| <= 1/2) are
-// taken exactly from D's 53-bit significand (with sh the position of D's
-// binary point in it, m = (sig + 2^(sh-1)) >> sh and rho 2^sh = ((sig +
-// 2^(sh-1)) mod 2^sh) - 2^(sh-1)); p = 2^{-rho/4096} = 1 - K1 rho + K2 rho^2
-// (the minimax quadratic, relative error below 2.6e-14) is evaluated in 64-bit
-// fixed point: rho in units of 2^-63, K1 |rho| as the high half of a 64 x
-// 64-bit product with K1 in units of 2^-75, K2 rho^2 from the leading 32 bits
-// of rho (its error below 2^-58), delta = p - 1 in units of 2^-62.  The
+// Constants of the node loop's exponential (exp2s_fix): K1 = (ln2/4096)(1 +
+// c^2/8) in units of 2^-75 and K2 = (ln2/4096)^2/2 in units of 2^-57.
+constexpr unsigned long long kExpK1Q75 = (unsigned long long)(kExpK1 * 0x1p75);  // exact
+constexpr unsigned long long kExpK2Q57 = (unsigned long long)(kExpK2 * 0x1p57 + 0.5);
+static_assert(kExpK1Q75 < (1ULL << 63) && kExpK2Q57 < (1ULL << 32), "fixed-point constants");
+// ---------------------------------------------------------------------------
+// 64-bit fixed point for the uncentred node loop (node_sum_cosh), whose node
+// exponent U_j = D_j - G_j (D_j = K x cosh t_j from the FP64 recurrence, G_j
+// = K nu (t_j - t_start) a multiple of a fixed step) is formed on the integer
+// pipe in units of 2^-40: |U| < 2^23 fits 64 bits with 40 fractional bits.
+
+// D in [0.25, 2^22) (a node loop's K x cosh t_j) in units of 2^-40: the
+// significand shifted by the exponent, truncated (below 2^-40 absolute, the
+// error of a relative 1.7e-16 in 2^{-D/4096}; exact for D >= 2^12).
+__device__ __forceinline__ long long fix40_node(double D) {
+  const int e = (int)((unsigned)__double2hiint(D) >> 20) - 1023;  // -2 .. 21
+  const unsigned long long sig =
+      (((unsigned long long)__double_as_longlong(D) & 0xfffffffffffffULL) | 0x10000000000000ULL)
+      << 11;                                                     // D 2^{63 - e}
+  return (long long)(sig >> (23 - e));
+}
+
+// w in [0, 1] in units of 2^-63 (w = 1 gives 2^63), truncated; values above 1
+// are clamped to 1.
+__device__ __forceinline__ unsigned long long fix63_unit(double w) {
+  const int e = (int)((unsigned)__double2hiint(w) >> 20) - 1023;
+  const unsigned long long sig =
+      (((unsigned long long)__double_as_longlong(w) & 0xfffffffffffffULL) | 0x10000000000000ULL)
+      << 11;  // w 2^{63 - e}
+  if (e >= 0) return 1ULL << 63;
+  return (e < -63) ? 0ULL : sig >> (-e);
+}
+
+// r in [0, 1] in units of 2^-64, truncated and clamped below 2^64 (r = 1
+// gives 2^64 - 1).
+__device__ __forceinline__ unsigned long long fix64_unit(double r) {
+  const int e = (int)((unsigned)__double2hiint(r) >> 20) - 1023;
+  const unsigned long long sig =
+      (((unsigned long long)__double_as_longlong(r) & 0xfffffffffffffULL) | 0x10000000000000ULL)
+      << 11;  // r 2^{63 - e}
+  if (e >= 0) return ~0ULL;
+  return (e < -64) ? 0ULL : sig >> (-1 - e);
+}
+
+// 1 + w for w = Wq 2^-63 in [0, 1], rounded to nearest (ties up) by adding
+// the 52-bit fraction to the bits of 1.0 (w = 1 carries into the exponent
+// field and gives 2.0): integer operations only.
+__device__ __forceinline__ double one_plus_w(unsigned long long Wq) {
+  return __longlong_as_double(0x3ff0000000000000LL + (long long)((Wq + 1024ULL) >> 11));
+}
+
+// 2^{-U/4096} times 2^kAdj for U = U40 2^-40 in (-2^23, 2^23) with the
+// result in [2^-1000, 2^1000] (the node loop's range), computed on the
+// integer pipe without FP64 arithmetic.  m = round(U) (ties up) is U40 + 2^39
+// shifted right by 40 (arithmetically); the remainder rho = U - m in [-1/2,
+// 1/2) comes from the low 40 bits of U40 + 2^39, moved to the top of a 64-bit
+// word, the top bit flipped (subtracting 1/2) and shifted back by one (rho
+// 2^63).  p = 2^{-rho/4096} = 1 - K1 rho + K2 rho^2 (the minimax quadratic,
+// relative error below 2.6e-14) is evaluated in 64-bit fixed point: K1 |rho|
+// as the high half of a 64 x 64-bit product, K2 rho^2 from the leading 32
+// bits of rho (its error below 2^-58), delta = p - 1 in units of 2^-62.  The
 // result p T, T = 2^{-m/4096} = 2^k t_j with t_j = 2^{j/4096} from the table,
 // is t_j's 53-bit significand M plus delta M (the high half of a 64 x 64-bit
 // product, truncated: below 2^-52 relative), renormalised into [2^52, 2^53)
 // and given the exponent k.  On GB300 an FP64 operation occupies the FP64
 // pipe 32 times as long as an integer instruction occupies its own, so these
-// ~40 integer instructions cost less than the 3 FP64 operations of the FP64
-// polynomial and product they replace.  The table index and exponent come
-// from -m, so that no negated copy of D is formed.  Accurate for D <= 1022 *
-// 4096 (results down to 2^-1022; the node loops keep D below 4.08e6, where k
-// is at least -997); a finite D >= 2^22 gives p = 1 and m clamped to 2^22 (a
-// value below 2^-990); NaN gives NaN.  kAdj = -1 halves the result (the
-// trapezoid's end weights).  kNode: the node loops' variant, for 0.25 <= D <
-// 2^22 only (x >= 1e-4 and x cosh t <= 690 there), without the tests and
-// selects of the other ranges (the same arithmetic inside its range).
-constexpr unsigned long long kExpK1Q75 = (unsigned long long)(kExpK1 * 0x1p75);  // exact
-constexpr unsigned long long kExpK2Q57 = (unsigned long long)(kExpK2 * 0x1p57 + 0.5);
-static_assert(kExpK1Q75 < (1ULL << 63) && kExpK2Q57 < (1ULL << 32), "fixed-point constants");
-template <int kAdj = 0, bool kNode = false>
-__device__ __forceinline__ double exp2s_neg_int(double D, const double* __restrict__ tab) {
-  const long long b = __double_as_longlong(D);
-  const int e = (int)((b >> 52) & 0x7ff) - 1023;
-  const long long sig = (b & 0xfffffffffffffLL) | 0x10000000000000LL;
-  const int sh = kNode ? 52 - e : 52 - min(max(e, -2), 21);  // 31 .. 54 (D < 1/2: m = 0)
-  const long long half = 1LL << (sh - 1);
-  const long long t = sig + half;
-  int m = (int)(t >> sh);
-  const long long R = (t & ((half << 1) - 1)) - half;  // rho 2^sh
-  // rho 2^63 (|.| <= 2^62); for D < 1/4 (e < -2, m = 0) rho = D = sig 2^(e - 52)
-  long long rq = R << (63 - sh);
-  if (!kNode && e < -2) rq = (e >= -11) ? (sig << (e + 11)) : ((e > -74) ? (sig >> (-11 - e)) : 0LL);
-  const unsigned long long ar = (unsigned long long)(rq < 0 ? -rq : rq);
+// ~30 integer instructions cost less than the 3 FP64 operations of an FP64
+// polynomial and product.  The table index and exponent come from -m.  No
+// range tests: the callers keep U inside the range.  kAdj = -1 halves the
+// result (the trapezoid's end weights).
+template <int kAdj = 0>
+__device__ __forceinline__ double exp2s_fix(long long U40, const double* __restrict__ tab) {
+  const long long t = U40 + (1LL << 39);
+  const int m = (int)(t >> 40);  // round(U)
+  const long long rq =
+      (long long)(((unsigned long long)t << 24) ^ 0x8000000000000000ULL) >> 1;  // rho 2^63
+  const unsigned long long ar = (unsigned long long)(rq < 0 ? -rq : rq);         // <= 2^62
   const long long t1 = (long long)(__umul64hi(ar, kExpK1Q75) >> 12);  // K1 |rho| 2^62
   const unsigned int rh = (unsigned int)(ar >> 31);                   // |rho| 2^32
   const unsigned long long r2 = ((unsigned long long)rh * rh) >> 32;  // rho^2 2^32
   const long long t2 = (long long)((r2 * kExpK2Q57) >> 27);           // K2 rho^2 2^62
-  long long d = (rq < 0 ? t1 : -t1) + t2;                             // (p - 1) 2^62
-  const bool out = !kNode && e > 21;  // out of range: clamp; NaN stays NaN
-  if (out) {
-    m = 1 << 22;
-    d = 0;
-  }
+  const long long d = (rq < 0 ? t1 : -t1) + t2;                       // (p - 1) 2^62
   const int n = -m;
   const long long tb = __double_as_longlong(tab[n & (kExpTabSize - 1)]);  // t_j in [1, 2)
   const long long M = (tb & 0xfffffffffffffLL) | 0x10000000000000LL;      // t_j 2^52
   const unsigned long long ad = (unsigned long long)(d < 0 ? -d : d);      // < 2^49
   const long long X = (long long)__umul64hi(ad << 2, (unsigned long long)M);  // |delta| M
   long long Mp = M + (d < 0 ? -X : X);  // p t_j 2^52, within 2^40 of [2^52, 2^53)
-  int k = (kNode ? (n >> kExpTabBits) : max(n >> kExpTabBits, -1022)) + kAdj;
-  if (Mp >= 0x20000000000000LL) {  // p t_j >= 2: halve (rounded), exponent up
+  int k = (n >> kExpTabBits) + kAdj;
+  if (Mp >= 0x20000000000000LL) {
     Mp = (Mp + 1) >> 1;
     ++k;
-  } else if (Mp < 0x10000000000000LL) {  // p t_j < 1: double, exponent down
+  } else if (Mp < 0x10000000000000LL) {
     Mp <<= 1;
     --k;
   }
-  const double r = __longlong_as_double(((long long)(k + 1023) << 52) | (Mp & 0xfffffffffffffLL));
-  if constexpr (kNode) return r;
-  const bool nan = out && e == 1024 && ((((unsigned)(b >> 32)) & 0xfffffu) | (unsigned)b) != 0u;
-  return nan ? D : r;
+  return __longlong_as_double(((long long)(k + 1023) << 52) | (Mp & 0xfffffffffffffLL));
 }
 
 // e^a for a in [-708, 709] (callers clamp); one scaling multiply on top of exp2s.
@@ -410,11 +438,11 @@ __device__ __forceinline__ double exp2s_cubic(double u, const double* __restrict
 
 // 2^{u/4096} on the integer pipe.  The nearest integer n of u and the
 // remainder rho = u - n (|rho| <= 1/2) are taken exactly from u's
-// significand as in exp2s_neg_int (on |u|, the signs restored by integer
+// significand (on |u|, the signs restored by integer
 // operations); p = 2^{rho/4096} in 64-bit fixed point (C1 rho from a 64 x
 // 64-bit high product, the square and cube from the leading 32 bits of rho,
 // their errors below 2^-58); and p t_j 2^k, t_j = 2^{j/4096}, from t_j's
-// significand as in exp2s_neg_int (truncation below 2^-52 relative).  No
+// significand as in exp2s_fix (truncation below 2^-52 relative).  No
 // FP64 arithmetic.  kCubic: the Taylor cubic (truncation below 3e-18
 // relative; the final exponential, |u| < 4.18e6); else the minimax quadratic
 // (2.6e-14; the FP64 node loops, whose node exponents satisfy |u| < 3e5)
@@ -897,12 +925,18 @@ __device__ __forceinline__ float quantise_step(float h, int& idx) {
   return __int_as_float(up);
 }
 
-// 2 cosh(nu h_k) for the steps of kCoshTab (h_k = 2^e (1 + j/256), k =
-// (e + 12) 256 + j), as node_sum_cosh would compute it: the per-launch table
-// of the Matern tile writers, whose nu is fixed.
-__device__ __forceinline__ double cosh_nu_entry(double nu, int k, const double* __restrict__ tab) {
+// e^{-2 nu h} for a step h and nu >= 0, by the accurate set-up exponential:
+// the ratio of the node loop's geometric factor e^{-2 nu t_j}.
+__device__ __forceinline__ double decay_step(double nu, double h, const double* __restrict__ tab) {
+  return exp_acc(fmax(-2.0 * nu * h, -708.0), tab);
+}
+
+// decay_step for the steps of kCoshTab (h_k = 2^e (1 + j/256), k = (e + 12)
+// 256 + j), as node_sum_cosh would compute it: the per-launch table of the
+// Matern tile writers, whose nu is fixed.
+__device__ __forceinline__ double decay_entry(double nu, int k, const double* __restrict__ tab) {
   const double h = __hiloint2double(((k >> 8) - 12 + 1023) << 20 | ((k & 255) << 12), 0);
-  return two_cosh_warp(nu * h, tab);
+  return decay_step(nu, h, tab);
 }
 
 // log2 v of a positive finite double to about 1e-6, on the integer, FP32 and
@@ -920,58 +954,62 @@ __device__ __forceinline__ float log2_f64_approx(double v) {
 
 // The same sum without centring, for the checked windows of scale_f64:
 //   f(t_j) = (e^{nu t_start} / 2) e^{-x cosh t_j} C_j,
-//   C_j = e^{nu (t_j - t_start)} (1 + e^{-2 nu t_j}) = 2 e^{-nu t_start} cosh(nu t_j),
-// where C_j follows its own three-term recurrence C_{j+1} = 2 cosh(nu H) C_j
-// - C_{j-1}.  A node costs the exponential of -D_j (on the integer pipe),
-// the sum of its product with C_j and the two recurrences: 3 FP64 operations
-// instead of the centred loop's 9, and the set-up needs neither cosh t* nor
-// the centring exponentials.  Each factor must stay in the double range on its own,
-// x cosh t_j <= 690 (the exponential's argument below 2^22) and
-// nu (t_j - t_start) <= 600, and the C recurrence amplifies rounding with the
-// node count; cosh_loop_ok states the conditions.  Returns
-// S = sum_j e^{-x cosh t_j} C_j and the end terms.
+//   C_j = 2 e^{-nu t_start} cosh(nu t_j) = e^{nu (t_j - t_start)} (1 + W_j),
+//   W_j = e^{-2 nu t_j} = e^{-2 nu t_start} r^j, r = e^{-2 nu H}.
+// D_j = K x cosh t_j follows the three-term recurrence D_{j+1} = 2 cosh(H)
+// D_j - D_{j-1} (one FP64 FMA); the factor e^{nu (t_j - t_start)} joins the
+// exponent as G_j = j K nu H, a running sum in 64-bit fixed point (units of
+// 2^-40, exact steps: no rounding growth), so that node j's term is
+// 2^{-(D_j - G_j)/4096} (1 + W_j) with the exponential from D_j - G_j on the
+// integer pipe (exp2s_fix) and W_j a geometric sequence in fixed point (units
+// of 2^-63, one 64 x 64-bit high product per node, its truncation below 2^-63
+// a step), 1 + W_j rounded to a double by integer operations.  A node costs
+// the D recurrence and the summing FMA: 2 FP64 operations, and the set-up
+// needs neither cosh t* nor the centring exponentials.  Each factor must stay
+// in the double range, x cosh t_j <= 690 (D_j below 2^22) and nu (t_j -
+// t_start) <= 600 (G_j below 2^22, the terms below 2^880); cosh_loop_ok
+// states the conditions.  Returns S = sum_j e^{-x cosh t_j} C_j and the end
+// terms.
 struct NodeSumC {
   double S;                   // the trapezoid sum, end weights 1/2 included
   float l2_first, l2_last;    // log2 of the unweighted end terms (window check)
-  bool pos;                   // the last term's factors are positive
+  bool pos;                   // the last term is positive
 };
-// cosh_idx: the step's index in kCoshTab (or -1); cnu: a table of
-// 2 cosh(nu h) on the same steps for this nu (or null).  The weights 1/2 of
-// the end nodes are folded into their terms (at t_start = 0, C_0/2 = 1), and
-// the end terms' logs for the window check come from the factors on the
-// FP32/integer pipes, so the ends cost no extra FP64 products.
+// step_idx: the step's index in kCoshTab (or -1); wnu: a table of
+// decay_step(nu, h) on the same steps for this nu (or null).  The weights 1/2
+// of the end nodes are folded into their terms (at t_start = 0, (1 + W_0)/2 =
+// 1), and the end terms' logs for the window check come from the factors on
+// the FP32/integer pipes, so the ends cost no extra FP64 products.
+constexpr double kExpScale40 = kExpScale * 0x1p40;  // K in units of 2^-40 (exact scaling)
 __device__ __forceinline__ NodeSumC node_sum_cosh(double t_start, double H, int count, double xh,
                                                   double nu, const double* __restrict__ tab,
-                                                  int cosh_idx, const double* __restrict__ cnu) {
+                                                  int step_idx, const double* __restrict__ wnu) {
   const bool start_pos = bits_pos(t_start);
-  double c, D0, D1, cn, C0, C1, C0h = 1.0;
+  double c, D0, D1, C0h = 1.0;
+  unsigned long long Wq = 1ULL << 63;  // W_0 2^63 (W_0 = 1 at t_start = 0)
   if (start_pos) {
-    const double th = nu * H;
     const double e0 = exp_acc(t_start, tab), r0 = rcp_nr2(e0);
     const double eh = exp_acc(H, tab), rh = rcp_nr2(eh);
     c = bits_le(H, 0.35) ? two_cosh_small(H) : eh + rh;
     D0 = xh * (e0 + r0);
     D1 = xh * fma(e0, eh, r0 * rh);
     const double W = exp_acc(fmax(-2.0 * nu * t_start, -708.0), tab);
-    const double en = exp_acc(th, tab), rn = rcp_nr2(en);
-    cn = bits_le(th, 0.35) ? two_cosh_small(th) : en + rn;
-    C0 = 1.0 + W;
     C0h = fma(W, 0.5, 0.5);
-    C1 = fma(W, rn, en);  // e^{nu H} + e^{-2 nu t_start} e^{-nu H}
+    Wq = fix63_unit(W);
   } else {
-    c = (cosh_idx >= 0) ? kCoshTab[cosh_idx] : two_cosh_warp(H, tab);
+    c = (step_idx >= 0) ? kCoshTab[step_idx] : two_cosh_warp(H, tab);
     // D0 = 2 xh by its exponent (xh is normal: the callers' x lies in the
     // FP32 search's range and x cosh t1 <= 690)
     D0 = __hiloint2double(__double2hiint(xh) + (1 << 20), __double2loint(xh));
     D1 = xh * c;
-    cn = (cosh_idx >= 0 && cnu != nullptr) ? cnu[cosh_idx] : two_cosh_warp(nu * H, tab);
-    C0 = 2.0;
-    C1 = cn;
   }
-  // node j's term is E_j C_j with E_j = 2^{-D_j/4096} from the integer pipe:
-  // the sum takes it by one FMA (3 FP64 operations per node)
+  const unsigned long long Rq =  // r 2^64
+      fix64_unit((step_idx >= 0 && wnu != nullptr) ? wnu[step_idx] : decay_step(nu, H, tab));
+  const long long Gs = __double2ll_rn(nu * H * kExpScale40);  // K nu H 2^40
+  long long G = 0;                                            // G_j 2^40
   NodeSumC r;
-  double s = exp2s_neg_int<0, true>(D0, tab);  // the first term times 1/2 (C_0 / 2 = 1 at t0 = 0)
+  // the first term times 1/2: D_0 with G_0 = 0, (1 + W_0)/2 = C0h
+  double s = exp2s_fix<0>(fix40_node(D0), tab);
   r.l2_first = 0.0f;
   if (start_pos) {
     r.l2_first = log2_f64_approx(s) + log2_f64_approx(C0h) + 1.0f;
@@ -982,31 +1020,31 @@ __device__ __forceinline__ NodeSumC node_sum_cosh(double t_start, double H, int 
     const double D2 = fma(c, D1, -D0);
     D0 = D1;
     D1 = D2;
-    const double C2 = fma(cn, C1, -C0);
-    C0 = C1;
-    C1 = C2;
-    s = fma(exp2s_neg_int<0, true>(D0, tab), C0, s);
+    G += Gs;
+    Wq = __umul64hi(Wq, Rq);
+    s = fma(exp2s_fix<0>(fix40_node(D0) - G, tab), one_plus_w(Wq), s);
   }
-  {  // the last node (D_N, C_N after the loop), weight 1/2 folded into E; count >= 3
-    const double Eh = exp2s_neg_int<-1, true>(D1, tab);
-    s = fma(Eh, C1, s);
-    r.l2_last = log2_f64_approx(Eh) + log2_f64_approx(C1) + 1.0f;
-    r.pos = bits_pos(Eh) && bits_pos(C1);
+  {  // the last node (D_N after the loop), weight 1/2 folded into E; count >= 3
+    G += Gs;
+    Wq = __umul64hi(Wq, Rq);
+    const double Eh = exp2s_fix<-1>(fix40_node(D1) - G, tab);
+    const double w = one_plus_w(Wq);
+    s = fma(Eh, w, s);
+    r.l2_last = log2_f64_approx(Eh) + log2_f64_approx(w) + 1.0f;
+    r.pos = bits_pos(Eh);
   }
   r.S = s;
   return r;
 }
-// FP64 ops per node of node_sum_cosh: 1 fma (sum), 2 fma (recurrences);
-// exp2s_neg_int runs on the integer pipe.
-constexpr int kNodeOps64Cosh = 3;
+// FP64 ops per node of node_sum_cosh: 1 fma (sum), 1 fma (the D recurrence);
+// the exponential, G and W run on the integer pipe.
+constexpr int kNodeOps64Cosh = 2;
 
 // Whether node_sum_cosh may take a window [t0, t1] of N intervals (FP32
-// tests on truncated copies).  Rounding in the C recurrence (each step's,
-// and that of 2 cosh(nu h)) reaches node j amplified by about
-// sum_k (1 - e^{-2 nu h k}) / (2 sinh(nu h)) <= min(j^2 / 2, j / (2 nu h)),
-// so its relative error stays below about u N^2 min(1, 1 / (nu (t1 - t0))),
-// u = 2^-53; the test keeps that under 2^16 u ~ 7e-12 (every window of up to
-// 256 intervals passes).  Range: x cosh t1 <= 690 (cosh t <= (e^t + 1)/2)
+// tests on truncated copies).  Rounding in the D recurrence reaches node j
+// amplified by about j / (2 sinh h) relative to D_j; the test bounds N^2 by
+// 2^16 max(nu (t1 - t0), 1) (every window of up to 256 intervals passes).
+// Range: x cosh t1 <= 690 (cosh t <= (e^t + 1)/2)
 // and nu (t1 - t0) <= 600.  NaN fails.
 __device__ __forceinline__ bool cosh_loop_ok(float x, float nu, float t0, float t1, int N) {
   const float nw = nu * (t1 - t0), nf = (float)N;
@@ -1172,7 +1210,7 @@ constexpr double kTwoOverK = 2.0 / kExpScale;  // x = xh 2/K (ln2 / 2048)
 __device__ __forceinline__ double scale_f64(double xh, double nu, float log2_over_tol, int n_max,
                                             const double* __restrict__ tab, double& hS,
                                             Tally& tl, const Start32* st = nullptr,
-                                            const double* __restrict__ cnu = nullptr) {
+                                            const double* __restrict__ wnu = nullptr) {
   constexpr double kEps64 = 0x1p-52;
   if (st == nullptr)
     return take_search(scaled_search_f64(xh * kTwoOverK, nu, log2_over_tol, n_max, tab), hS, tl);
@@ -1188,13 +1226,13 @@ __device__ __forceinline__ double scale_f64(double xh, double nu, float log2_ove
   const float xf = f32_trunc(xh) * (float)kTwoOverK, nuf = f32_trunc(nu), wf = t1f - t0f;
   const int N = strip_node_count(xf, nuf, wf, log2_over_tol, n_max);
   if (N <= n_max) {
-    int cosh_idx;
-    const float hq = quantise_step(__fdividef(wf, (float)N), cosh_idx);
+    int step_idx;
+    const float hq = quantise_step(__fdividef(wf, (float)N), step_idx);
     const float tnf = fmaf((float)N, hq, t0f);  // the last node
     const double t0 = widen_f(t0f), h = widen_f(hq);
     tl.nodes += N + 1;
     if (cosh_loop_ok(xf, nuf, t0f, tnf, N)) {
-      const NodeSumC ns = node_sum_cosh(t0, h, N + 1, xh, nu, tab, cosh_idx, cnu);
+      const NodeSumC ns = node_sum_cosh(t0, h, N + 1, xh, nu, tab, step_idx, wnu);
       constexpr float kL2e = 1.44269504f;
       const float G = fmaf(nuf, st->ts - t0f, -xf * st->cs) * kL2e;  // log2 of the peak term
       float w1;

@@ -15,27 +15,27 @@ namespace bk {
 
 namespace {
 
-// Fills the per-launch table of 2 cosh(nu h) on kCoshTab's steps.
-__global__ void __launch_bounds__(256) cosh_nu_table_kernel(double nu, double* __restrict__ out) {
+// Fills the per-launch table of e^{-2 nu h} on kCoshTab's steps.
+__global__ void __launch_bounds__(256) decay_table_kernel(double nu, double* __restrict__ out) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < kCoshTabSize) out[k] = cosh_nu_entry(nu, k, kExp2Tab);
+  if (k < kCoshTabSize) out[k] = decay_entry(nu, k, kExp2Tab);
 }
 
 // Runs launch(form) for a Matern tile writer of the searched-window form with
-// form.cnu pointing at the caller's table (bk_opts.d_cosh_table), first
-// filled on s with 2 cosh(nu h) for this launch's nu.  Without a table the
+// form.wnu pointing at the caller's table (bk_opts.d_cosh_table), first
+// filled on s with e^{-2 nu h} for this launch's nu.  Without a table the
 // kernels compute the values themselves; forms without the table run as
 // they are.  Allocates nothing.
 // fill = false: the table already holds this nu's values (an earlier launch
 // for the same matrix filled it on s).
 template <class Form, class Launch>
-cudaError_t with_cosh_nu_table(Form form, double nu, double* table, cudaStream_t s,
+cudaError_t with_decay_table(Form form, double nu, double* table, cudaStream_t s,
                                Launch&& launch, bool fill = true) {
-  if constexpr (Form::kCoshNuTable) {
+  if constexpr (Form::kDecayTable) {
     if (table != nullptr) {
       static_assert(kCoshTabSize == BK_COSH_TABLE_LEN, "table length");
-      if (fill) cosh_nu_table_kernel<<<(kCoshTabSize + 255) / 256, 256, 0, s>>>(nu, table);
-      form.cnu = table;
+      if (fill) decay_table_kernel<<<(kCoshTabSize + 255) / 256, 256, 0, s>>>(nu, table);
+      form.wnu = table;
     }
   }
   return launch(form);
@@ -71,7 +71,7 @@ cudaError_t launch_matern_sym_f64(const double* locs, int64_t n, double sigma2, 
                                   const bk_opts& o, cudaStream_t s, const SymRange& range) {
   if (n == 0) return cudaSuccess;
   return with_plain_form(o, [&](const auto& form) {
-    return with_cosh_nu_table(
+    return with_decay_table(
         form, nu, o.d_cosh_table, s,
         [&](const auto& f) {
           return launch_matern_sym_form(f, locs, n, sigma2, beta, nu, out, ld, out_t,
@@ -86,7 +86,7 @@ cudaError_t launch_matern_block_f64(const double* locs1, int64_t m, const double
                                     int64_t ld, bk_dtype out_t, const bk_opts& o, cudaStream_t s) {
   if (m == 0 || n == 0) return cudaSuccess;
   return with_plain_form(o, [&](const auto& form) {
-    return with_cosh_nu_table(form, nu, o.d_cosh_table, s, [&](const auto& f) {
+    return with_decay_table(form, nu, o.d_cosh_table, s, [&](const auto& f) {
       return launch_matern_block_form(f, locs1, m, locs2, n, sigma2, beta, nu, out, ld, out_t,
                                       o.d_counters, s);
     });

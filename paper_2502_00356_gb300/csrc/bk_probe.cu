@@ -114,7 +114,7 @@ __global__ void math_probe_kernel(int fn, const double* __restrict__ in, double*
       case 0: out[i] = exp_tab_full(v, tab); break;
       case 1: out[i] = log_tab(v, tab); break;
       case 2: out[i] = exp2s_int<false>(v, tab); break;
-      case 3: out[i] = exp2s_neg_int(v, tab); break;
+      case 3: out[i] = exp2s_fix(fix40_node(v), tab); break;
       case 4: {
         int M;
         double r;
@@ -128,6 +128,9 @@ __global__ void math_probe_kernel(int fn, const double* __restrict__ in, double*
       case 7: out[i] = exp_acc(v, tab); break;
       case 8: out[i] = exp_units_full(v * kExpScale, tab); break;
       case 10: out[i] = sqrt_int(v); break;
+      case 11: out[i] = exp2s_fix(__double2ll_rn(v * 0x1p40), tab); break;
+      case 12: out[i] = one_plus_w(fix63_unit(v)); break;
+      case 13: out[i] = (double)fix64_unit(v) * 0x1p-64; break;
       default: {
         double nd;
         const double l1p = log_tab_parts(v, tab, nd);
@@ -161,7 +164,7 @@ extern "C" bk_status bk_probe_pipe(int kind, int64_t iters, int grid, int block,
 extern "C" bk_status bk_math_probe(int fn, const double* in, double* out, int64_t n,
                                    bk_stream_t stream) {
   using namespace bk;
-  if (fn < 0 || fn > 10) return set_error(BK_ERR_INVALID_ARG, "bk_math_probe: unknown fn %d", fn);
+  if (fn < 0 || fn > 13) return set_error(BK_ERR_INVALID_ARG, "bk_math_probe: unknown fn %d", fn);
   if (n < 0 || (n > 0 && (in == nullptr || out == nullptr)))
     return set_error(BK_ERR_INVALID_ARG, "bk_math_probe: bad arguments");
   if (n == 0) return BK_OK;

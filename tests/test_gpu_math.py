@@ -121,12 +121,47 @@ def test_node_exponentials(dev):
     for ui, gi in zip(u, got):
         ref = (Decimal(float(ui)) * LN2 / 4096).exp()
         assert rel_err(gi, ref) <= Decimal(3e-14), (ui, gi)  # the quadratic: 2.6e-14
-    D = np.concatenate([rng.uniform(0, 4.18e6, 1500), rng.uniform(0, 8, 300),
-                        np.arange(0, 12) * 0.5, [0.0, 5e-324, 0.25, 0.2499999999999999]])
+    # the uncentred loop's node exponent D = K x cosh t (x >= 1e-4: D >= 0.59,
+    # x cosh t <= 690: D < 4.08e6) truncated to units of 2^-40 (1.7e-16
+    # relative in the result) and the fixed-point exponential
+    D = np.concatenate([rng.uniform(0.25, 4.08e6, 1500), rng.uniform(0.25, 8, 300),
+                        np.arange(1, 12) * 0.5, [0.25, 4096.0, 4096.5, 2**21 + 0.5, 4.08e6]])
     got = probe("exp2s_neg", D, dev)
     for di, gi in zip(D, got):
         ref = (-Decimal(float(di)) * LN2 / 4096).exp()
         assert rel_err(gi, ref) <= Decimal(3e-14), (di, gi)
+
+
+def test_fixed_point_node_exponential(dev):
+    """The node loop's exponential of a signed fixed-point exponent U = D -
+    G (units of 2^-40), over the loop's range: results in [2^-1000, 2^1000],
+    halves rounding up, the renormalisation at both ends of the table."""
+    rng = np.random.default_rng(68)
+    a = np.concatenate([rng.uniform(-4.09e6, 4.09e6, 1500), rng.uniform(-8, 8, 500),
+                        np.arange(-9, 10) * 0.5, np.arange(-3, 4) * 4096.0,
+                        [2.0**-41, -2.0**-41, 3 * 2.0**-41, 1e-20, 4095.5, -4095.5]])
+    got = probe("exp2s_fix", a, dev)
+    for ai, gi in zip(a, got):
+        u40 = round(Fraction(float(ai)) * 2**40)  # the probe's rounding: to nearest, ties to even
+        ref = (-Decimal(u40) / Decimal(2**40) * LN2 / 4096).exp()
+        assert rel_err(gi, ref) <= Decimal(3e-14), (ai, gi)  # the quadratic: 2.6e-14
+
+
+def test_fixed_point_geometric_factor(dev):
+    """1 + W_j from W_j in units of 2^-63 (truncated) rounded to a double, and
+    the ratio r in units of 2^-64 (truncated, clamped below 2^64)."""
+    rng = np.random.default_rng(69)
+    w = np.concatenate([rng.uniform(0, 1, 2000), rng.uniform(0, 1e-10, 200),
+                        [0.0, 1.0, 0.5, 0.25, 1 - 2**-53, 2**-60, 2**-64, 1e-300]])
+    got = probe("one_plus_w", w, dev)
+    for wi, gi in zip(w, got):
+        assert abs(Fraction(float(gi)) - 1 - Fraction(float(wi))) <= Fraction(1, 2**53) + Fraction(1, 2**63), (wi, gi)
+    assert got[-8] == 1.0 and got[-7] == 2.0 and got[-6] == 1.5 and got[-5] == 1.25
+    r = np.concatenate([rng.uniform(0, 1, 2000), [0.0, 1.0, 0.5, 1 - 2**-53, 2**-64, 2**-70, 1e-300]])
+    got = probe("fix64", r, dev)
+    for ri, gi in zip(r, got):
+        q = min(math.floor(Fraction(float(ri)) * 2**64), 2**64 - 1)
+        assert gi == float(q) * 2.0**-64, (ri, gi)
 
 
 def test_integer_rounding_is_exact(dev):
