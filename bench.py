@@ -52,7 +52,7 @@ WORKLOAD = "matern_jittered_grid_n20000_beta0.1_nu{0.5,1.5,2.3}_fp64"
 # run on the FP32/MUFU pipes and are not counted.
 OPS_NODE, OPS_PEAK_IT, OPS_WIN_IT, OPS_ENTRY_FIXED = 2, 54, 31, 14.9
 # Kernels per bk_matern_tile call of the plain form: the per-launch table of
-# 2 cosh(nu h) on the quantised steps, then the symmetric tile writer.
+# e^{-2 nu h} on the quantised steps, then the symmetric tile writer.
 LAUNCHES_PER_MATRIX = 2
 # FP64 pipe peak from the unit count and clock: 152 SMs x 2 DFMA/clk x 2.07 GHz
 # (1.26 TFLOP/s counting an FMA as two FLOPs).

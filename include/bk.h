@@ -235,7 +235,7 @@ bk_status bk_matern_tile2(const double* locs1, int64_t m, const double* locs2, i
  * ATS, pageable memory as well), the tile writer stores the matrix straight
  * into h_out over the GPU-CPU link (NVLink-C2C) and d_work needs only
  * bk_matern_tile_host_workspace(n, dtype, 0) bytes (locations and the plain
- * form's 2 cosh(nu h) table).  Otherwise, and always with BK_HOST_STAGED,
+ * form's e^{-2 nu h} table).  Otherwise, and always with BK_HOST_STAGED,
  * the matrix is staged in d_work, which then needs
  * bk_matern_tile_host_workspace(n, dtype, 1) bytes: it is generated in up to
  * 16 panels of block-columns, and each finished panel's columns are copied to
@@ -394,8 +394,8 @@ bk_status bk_learned_load(bk_learned* model, const char* path);
  * the output type and the form (compute = dtype).  There are no counters on
  * this path: an invalid descriptor (n < 0, ld < n, NULL pointers, beta or
  * nu <= 0, sigma2 < 0) is skipped without a report and its output is left
- * untouched.  The FP64 form here computes 2 cosh(nu h) inside the node loop
- * (a plan keeps per-instance tables of it), so it is somewhat slower than
+ * untouched.  The FP64 form here computes e^{-2 nu h} once per entry (a plan
+ * keeps per-instance tables of it), so it is somewhat slower than
  * bk_matern_batched with a plan.  Launch shape fixed (8 warps, 2 CTAs per
  * SM).  Enqueues two kernels on `stream` and does not synchronise.
  */

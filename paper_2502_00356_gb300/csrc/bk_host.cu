@@ -35,7 +35,7 @@ constexpr size_t kAlign = 256;
 
 size_t round_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
-// Workspace layout: locations (16 n bytes), the 2 cosh(nu h) table of the
+// Workspace layout: locations (16 n bytes), the e^{-2 nu h} table of the
 // plain form, then the n x n matrix with leading dimension n.
 struct Layout {
   size_t locs, table, matrix, total;

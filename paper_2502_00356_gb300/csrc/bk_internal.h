@@ -21,7 +21,7 @@ bk_status check_cuda(cudaError_t e, const char* what);
 
 // A range of block-columns [j0, j1) of a symmetric matrix (32-wide blocks),
 // written in block-column order; j1 < 0 means the whole matrix.  fill_table:
-// whether a launch of the plain form refills the caller's 2 cosh(nu h) table
+// whether a launch of the plain form refills the caller's e^{-2 nu h} table
 // (a caller writing several ranges of one matrix fills it with the first).
 struct SymRange {
   int64_t j0 = 0, j1 = -1;

@@ -91,7 +91,7 @@ def test_batched_graph_capture_and_replay(dev):
 
 
 def test_batched_fp64_replay_follows_new_parameters(dev):
-    """The FP64 plan's per-instance tables of 2 cosh(nu h) are filled from
+    """The FP64 plan's per-instance tables of e^{-2 nu h} are filled from
     the descriptors at every launch: a captured graph replayed after the
     descriptors' nu (and beta, sigma2) changed in place gives the single-call
     results for the new parameters."""

@@ -75,9 +75,9 @@ def test_eval_sorted_chunks_keep_positions(dev, n):
     """The bare-evaluation kernels order each chunk of up to 1,024 pairs by a
     cost bucket before evaluating it and put each result back at its pair's
     position: evaluating the pairs in another order and putting the results
-    back agrees to rounding (the 2 cosh(nu h) tier is voted per warp, so a
-    pair's last bits depend on its warp-mates; a misplaced result would be
-    off by O(1)).  Sizes give blocks with several chunks and ragged last
+    back agrees to rounding (the 2 cosh h tier of steps off the table's grid
+    is voted per warp, so a pair's last bits can depend on its warp-mates; a
+    misplaced result would be off by O(1)).  Sizes give blocks with several chunks and ragged last
     chunks; special pairs (0, inf, NaN, negative nu, the series range) are
     mixed in; samples go to the oracle."""
     x, nu = inputs.kv_pairs(n, seed=700 + n % 97)
@@ -267,7 +267,7 @@ def test_matern_fp64_search_option(dev, nu):
 
 def test_matern_graph_capture(dev):
     """bk_matern_tile captured in a CUDA graph (its per-call table of
-    2 cosh(nu h) lives in stream-ordered memory, which capture turns into
+    e^{-2 nu h} lives in stream-ordered memory, which capture turns into
     graph allocations) replays to the eager result, twice."""
     n = 700
     L = to_dev(inputs.morton_sorted(inputs.jittered_grid(n, seed=240)), dev)
@@ -292,10 +292,9 @@ def test_matern_graph_capture(dev):
 
 
 def test_matern_with_and_without_cosh_table(dev):
-    """The C entry point without bk_opts.d_cosh_table computes 2 cosh(nu h)
-    in the kernel; the Python binding passes a scratch table: the two agree
-    to the last bits (the table holds the same values, up to the series tier
-    a warp picks)."""
+    """The C entry point without bk_opts.d_cosh_table computes e^{-2 nu h}
+    in the kernel; the Python binding passes a scratch table that a small
+    kernel fills by the same arithmetic: the two agree to the last bits."""
     import ctypes
     n = 600
     L = to_dev(inputs.morton_sorted(inputs.jittered_grid(n, seed=241)), dev)
