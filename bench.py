@@ -76,8 +76,8 @@ def parse():
                    help="skip the FP32, batched and learned-window measurements")
     p.add_argument("--pairs", type=int, default=100_000_000,
                    help="K_nu pairs of the learned-window evaluation workload")
-    p.add_argument("--profile-case", choices=["plain", "plain_nus", "fp32", "learned", "learned_eval",
-                                              "batched", "fp32_forms", "train"],
+    p.add_argument("--profile-case", choices=["plain", "plain_nus", "plain_eval", "fp32", "learned",
+                                              "learned_eval", "batched", "fp32_forms", "train"],
                    default=None,
                    help="run --warmup launches plus one launch of one kernel on a small case "
                         "(for profiler captures) and exit without a JSON line")
@@ -695,6 +695,14 @@ def profile_case(args):
         beta, nu = (0.1, 0.5) if c == "plain" else ((0.05, 2.876) if c == "fp32" else (0.1, 1.7))
         opts = bk.make_opts(learned=net) if c == "learned" else None
         run = lambda: bk.bk_matern_tile(L, 1.0, beta, nu, out=out, opts=opts)
+    elif c == "plain_eval":
+        # the plain FP64 bare evaluation on 10^7 pairs of the 100,000-pair
+        # workload's distribution (x log-uniform in [1e-3, 140], nu in [0.05,
+        # 10]): 240 MB of inputs and output, above the L2
+        xh, nh = inputs.kv_pairs(10_000_000, seed=1)
+        X, V = torch.as_tensor(xh, device=dev), torch.as_tensor(nh, device=dev)
+        Y = torch.empty(X.numel(), dtype=torch.float64, device=dev)
+        run = lambda: bk.bk_eval(X, V, out=Y)
     elif c == "learned_eval":
         xh, nh = inputs.kv_pairs(20_000_000, seed=8, nu_lo=0.05, nu_hi=20.0)
         X, V = torch.as_tensor(xh, device=dev), torch.as_tensor(nh, device=dev)
