@@ -127,12 +127,13 @@ def test_eval_sorted_chunks_keep_positions(dev, n):
 
 def test_eval_node_loop_regions(dev):
     """Both quadrature loops of the plain form and the switch between them:
-    the uncentred loop with the cosh(nu t) recurrence (most windows) and the
-    centred loop (x cosh t1 > 690, many nodes at nu (t1 - t0) small, nu
-    (t1 - t0) > 600, the FP64 search).  Beyond the 1e-10 requirement, log K
-    must agree with the oracle to 1e-12 + 2e-15 |log K| (the rounding of a
-    log assembled from terms as large as |log K|), so that an error growing
-    in either recurrence would show."""
+    the uncentred loop (most windows: the x cosh t recurrence, e^{nu t} as a
+    fixed-point running exponent, 1 + e^{-2 nu t} as a fixed-point geometric
+    factor) and the centred loop (x cosh t1 > 690, many nodes at nu (t1 -
+    t0) small, nu (t1 - t0) > 600, the FP64 search).  Beyond the 1e-10
+    requirement, log K must agree with the oracle to 1e-12 + 2e-15 |log K|
+    (the rounding of a log assembled from terms as large as |log K|), so that
+    an error growing along either loop would show."""
     rng = np.random.default_rng(41)
     m = 4000
     sets = {
